@@ -1,0 +1,264 @@
+/*
+ * fe.h -- C ABI of the GB300 nonlinear-elasticity solver library (libfe.so).
+ *
+ * The library solves the quasi-static hyperelastic problem of the paper
+ * (arxiv 2203.05610, Section "The hyperelasticity problem"): find the
+ * displacement d with R(d) = f - div P(F) = 0, F = I + grad d, P = dPsi/dF,
+ * with Dirichlet data d = d_D and Neumann data P n = t, on P1 or P2
+ * tetrahedra (and a P1 pressure for the Taylor-Hood u-p form).  It provides
+ * the four nonlinear solvers the paper compares (Section "Numerical solvers"
+ * and Appendix A): Newton-Krylov (NK), inexact Newton-Krylov with
+ * Eisenstat-Walker forcing (iNK), BFGS-preonly (B) and inexact BFGS (iB).
+ *
+ * Conventions for every call:
+ *  - All functions return int: 0 = FE_OK, < 0 = API error (FE_ERR_*),
+ *    > 0 = solver outcome (NL_*, only from nl_solve).  A message for the
+ *    last error of the calling thread is returned by fe_last_error().
+ *  - "device" pointers are CUDA device addresses on the mesh's device;
+ *    "host" pointers are ordinary host memory.  The caller owns every
+ *    buffer it passes; the library never keeps a caller pointer after the
+ *    call returns.  The library owns everything reachable from an fe_mesh
+ *    (mesh, pattern, tangent, solver workspace) and frees it in
+ *    fe_mesh_destroy.
+ *  - Vectors of unknowns have length ndof = 3*nn (+ np for the u-p form),
+ *    laid out node-major: u[3*a + c] for node a, component c, followed by
+ *    the np pressure values.  Nodes 0..nv-1 are the vertices; for P2 the
+ *    edge nodes follow, numbered by the ascending (min, max) vertex pair of
+ *    their edge.  Local node order in an element is v0..v3 then the edges
+ *    01, 02, 03, 12, 13, 23.
+ *  - Calls are stream-ordered on the stream given at fe_mesh_create and are
+ *    synchronous with respect to the host unless stated otherwise.
+ *  - Kernels never trap.  A device-side check that fails (bounds, a bounded
+ *    wait that ran out) sets an error word that the host reads after the
+ *    launch, and the call returns FE_ERR_DEVICE_FLAG or FE_ERR_TIMEOUT.
+ */
+#ifndef FE_H
+#define FE_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ------------------------------------------------------ */
+#define FE_OK 0
+#define FE_ERR_ARG (-1)          /* invalid argument (message says which) */
+#define FE_ERR_OOM (-2)          /* device or host allocation failed */
+#define FE_ERR_CUDA (-3)         /* a CUDA runtime call failed */
+#define FE_ERR_TIMEOUT (-4)      /* a bounded device wait ran out */
+#define FE_ERR_DEVICE_FLAG (-5)  /* a device-side check failed */
+#define FE_ERR_STATE (-6)        /* call out of order (e.g. no tangent yet) */
+#define NL_DIVERGED 1            /* ||R|| > dtol*||R0|| */
+#define NL_MAX_IT 2              /* max_it nonlinear iterations without convergence */
+#define NL_NONFINITE 3           /* a residual norm became NaN or Inf */
+#define KSP_BREAKDOWN 4          /* the Krylov solver broke down (non-finite) */
+
+/* ---- enums ------------------------------------------------------------- */
+typedef enum { NL_NK = 0, NL_INK = 1, NL_B = 2, NL_IB = 3 } nl_method;
+typedef enum {
+  FE_PREC_FP64 = 0,       /* tangent, SpMV, preconditioner in FP64 */
+  FE_PREC_MIXED_FP32 = 1, /* tangent assembled and stored in FP32; SpMV and
+                             preconditioner in FP32; Arnoldi, residual,
+                             update and BFGS products stay FP64 */
+  FE_PREC_MIXED_BF16 = 2  /* as MIXED_FP32 with BF16 tangent storage */
+} fe_precision;
+typedef enum {
+  FE_MAT_COOK_NH = 0,  /* Psi = mu/2 (tr(Fbar^T Fbar) - 3) + c_vol (J^2 - 1 - 2 ln J),
+                          Fbar = J^{-1/3} F, mu = E/(2(1+nu)), lambda = 2 mu nu/(1-2nu),
+                          kappa = lambda + 2mu/3; c_vol = kappa/4 (vol_literal = 0,
+                          small-strain consistent reading) or kappa (vol_literal = 1,
+                          as printed).  Paper: Cook test, Psi_Cook. */
+  FE_MAT_TH_NH = 1,    /* Psi = mu/2 (tr(F^T F) - 3) - mu ln J - p (J - 1); with
+                          pressure_order = 1 this is the Taylor-Hood u-p form
+                          (twist test stand-in).  Without pressure, p = 0. */
+  FE_MAT_GUCCIONE = 2  /* Psi = C/2 (e^Q - 1) + kappa/2 (J - 1) ln J, Q in the fibre
+                          frame with b_ff = bf, b_ss = b_nn = b_sn = bt,
+                          b_fs = b_fn = bfs; plus active stress
+                          P_act = gamma(t) (F f) x f / |F f|,
+                          gamma(t) = Ta_peak max(sin(2 pi t / period), 0).
+                          Paper: Heartbeat test. */
+} fe_material_kind;
+typedef enum {
+  FE_FACE_TRACTION = 0, /* dead traction t = load * data[0..2] per unit reference area */
+  FE_FACE_PRESSURE = 1, /* dead pressure: t = -load * data[0] * N (reference outward normal) */
+  FE_FACE_ROBIN = 2     /* springs: t = -(kperp N x N + kpar (I - N x N)) d,
+                           data = {kperp, kpar, 0}; not scaled by load */
+} fe_face_kind;
+
+/* ---- mesh description (host data, copied by fe_mesh_create) ------------ */
+typedef struct {
+  int32_t kind;        /* fe_material_kind */
+  int32_t vol_literal; /* COOK_NH only, see above */
+  double E, nu;        /* COOK_NH */
+  double mu;           /* TH_NH */
+  double C, bf, bt, bfs, kappa, Ta_peak, period; /* GUCCIONE */
+} fe_material;
+
+typedef struct {
+  uint32_t comp_mask;    /* bit c set: component c of d is prescribed */
+  double center[3];      /* a point on the rotation axis (axis parallel to z) */
+  double angle;          /* rotation angle in radians at load factor 1 */
+  double translation[3]; /* translation at load factor 1 */
+} fe_dirichlet_group;    /* prescribed d(X) = load-scaled rigid motion of X minus X */
+
+typedef struct {
+  int32_t order;          /* displacement order: 1 (P1) or 2 (P2) */
+  int32_t pressure_order; /* 0: displacement only; 1: P1 pressure (needs order 2 and TH_NH) */
+  int32_t nv;             /* number of vertices */
+  int32_t ne;             /* number of tetrahedra */
+  const double* coords;   /* host [nv][3] vertex coordinates */
+  const int32_t* tets;    /* host [ne][4] vertex ids, positively oriented */
+  const uint8_t* dir_group; /* host [nv]: 0 = free, g = member of groups[g-1];
+                             a P2 edge node belongs to group g when both of its
+                             end vertices do */
+  int32_t ngroups;
+  const fe_dirichlet_group* groups; /* host [ngroups] */
+  int32_t nf;                /* boundary faces carrying loads or springs */
+  const int32_t* faces;      /* host [nf][3] vertex ids, (x1-x0)x(x2-x0) outward */
+  const int32_t* face_kind;  /* host [nf] fe_face_kind */
+  const double* face_data;   /* host [nf][3] */
+  fe_material material;
+  const double* fibers;      /* host [ne][9] rows f, s, n (GUCCIONE), else NULL */
+  int32_t device;            /* CUDA device ordinal */
+  void* stream;              /* cudaStream_t; NULL = legacy default stream */
+} fe_mesh_desc;
+
+typedef struct fe_mesh_s* fe_mesh; /* opaque, library-owned */
+
+typedef struct {
+  int32_t order, pressure_order;
+  int32_t nv, ne, nn;  /* vertices, elements, displacement nodes */
+  int32_t np;          /* pressure unknowns (nv for P1 pressure, else 0) */
+  int64_t ndof;        /* 3*nn + np */
+  int32_t nen;         /* nodes per element: 4 or 10 */
+  int64_t nnzb;        /* 3x3 blocks in the displacement BCSR pattern */
+  int64_t nnz_up;      /* 3x1 blocks of the u-p coupling (0 without pressure) */
+  int32_t ncolors;     /* colours of the element colouring */
+  int64_t device_bytes;/* device memory held by the mesh and its workspace */
+} fe_mesh_info;
+
+/* Create a mesh: copies the description to the device, builds the P2 edge
+ * nodes, the element colouring (first-fit greedy in descending
+ * splitmix64(element id) priority, ties by id) and the block-CSR pattern
+ * (one 3x3 block per pair of nodes that share an element, columns
+ * ascending).  Paper: FE discretisation of the quasi-static problem
+ * (Sections "The hyperelasticity problem" and "Test problems").
+ * Returns FE_ERR_ARG on inconsistent sizes or ids out of range. */
+int fe_mesh_create(const fe_mesh_desc* desc, fe_mesh* out);
+int fe_mesh_destroy(fe_mesh m);
+int fe_mesh_get_info(fe_mesh m, fe_mesh_info* out);
+
+/* Copy the mesh topology to host buffers (each may be NULL):
+ * conn [ne][nen], colors [ne], row_ptr [nn+1], col [nnzb],
+ * node_coords [nn][3]. */
+int fe_mesh_get_topology(fe_mesh m, int32_t* conn, int32_t* colors,
+                         int32_t* row_ptr, int32_t* col, double* node_coords);
+
+/* Set the load factor (scales tractions, pressures and prescribed motions)
+ * and the time (activation gamma(t) of the GUCCIONE material).  Paper:
+ * quasi-static problem with time-dependent data; load stepping of the
+ * tests. */
+int fe_set_load(fe_mesh m, double load, double time);
+
+/* Write the prescribed Dirichlet values of the current load into d
+ * (device, [ndof]); other entries are left unchanged. */
+int fe_apply_dirichlet(fe_mesh m, double* d);
+
+/* Residual R(d) = internal - external forces (the gradient of Pi), with
+ * R = 0 at prescribed components.  d, r: device [ndof] FP64.  norm_out
+ * (host, nullable) receives ||R||_2 (paper, the l2 norm of the EW
+ * definition).  Paper: residual form R(d) = f - div P (sign: gradient of
+ * the energy, Eq. "minimization"). */
+int fe_assemble_residual(fe_mesh m, const double* d, double* r, double* norm_out);
+
+/* Energy Pi(d) = int Psi(F) - external work + spring energy (host out).
+ * Paper: Eq. "minimization". */
+int fe_energy(fe_mesh m, const double* d, double* pi_out);
+
+/* Assemble the consistent tangent dR/dd at d (device [ndof]) into the
+ * library-owned block-CSR matrix in the given fe_precision, and set up the
+ * preconditioner (nodal block-Jacobi: inverse 3x3 diagonal blocks; for the
+ * u-p form the lower Schur preconditioner of Appendix B with the SIMPLE
+ * approximation S = -B2 diag(A)^{-1} B1 and point Jacobi on S).
+ * Prescribed components get zero rows and columns and a unit diagonal.
+ * Paper: Eq. "newton" (tangent problem). */
+int fe_assemble_tangent(fe_mesh m, const double* d, int precision);
+
+/* Copy the assembled tangent to host as FP64 (any of the pointers may be
+ * NULL): val [nnzb][9] row-major 3x3 blocks, bup [nnz_up][3] (u-p
+ * coupling, u rows), dinv [nn][9] (inverse diagonal blocks). */
+int fe_tangent_copy(fe_mesh m, double* val, double* bup, double* dinv);
+
+/* y = K x with the assembled tangent (device [ndof] FP64 in and out). */
+int fe_spmv(fe_mesh m, const double* x, double* y);
+
+/* y = M^{-1} x with the preconditioner of the assembled tangent. */
+int fe_pc_apply(fe_mesh m, const double* x, double* y);
+
+/* ---- solvers ----------------------------------------------------------- */
+typedef struct {
+  int32_t precision;   /* fe_precision (default FE_PREC_FP64) */
+  double ksp_rtol;     /* NK 1e-6, iB 1e-2 (Appendix A); < 0 = default */
+  double ksp_atol;     /* NK 1e-10, iNK/iB 1e-14; < 0 = default */
+  double ew_rtol0;     /* iNK first forcing term, default 0.1 */
+  double ew_rtolmax;   /* iNK forcing cap, default 0.1 */
+  int32_t ksp_restart; /* GMRES restart length, default 500 */
+  int32_t ksp_max_it;  /* GMRES iteration cap per solve, default 10000 */
+  int32_t lbfgs_m;     /* stored secant pairs, default 50 */
+  double dtol;         /* divergence: ||R|| > dtol*||R0||, default 1e4 */
+  int32_t apply_dirichlet; /* 1 (default): write prescribed values into d first */
+} nl_opts;
+
+#define NL_HIST 1024
+typedef struct {
+  int32_t status;      /* same as the return value of nl_solve */
+  int32_t nit;         /* nonlinear iterations */
+  int64_t lit_total;   /* Krylov iterations summed over the solve */
+  int32_t assemblies;  /* tangent assemblies */
+  double r0, rfinal;   /* ||R(d_0)||, ||R(d_final)|| */
+  double time_s;       /* wall time of the solve */
+  int32_t hist_len;
+  double res_hist[NL_HIST]; /* ||R_k||, k = 0..nit */
+  int32_t lit_hist[NL_HIST];/* Krylov iterations of iteration k */
+  double eta_hist[NL_HIST]; /* relative Krylov tolerance used at iteration k */
+} nl_stats;
+
+/* Fill opts with the defaults of the given method (Appendix A options). */
+int nl_opts_default(nl_method method, nl_opts* opts);
+
+/* Solve R(d) = 0 from the initial guess in d (device [ndof], overwritten
+ * with the last iterate) with the given method, until
+ * ||R_k|| <= tol*||R_0|| or max_it iterations.  Line search "basic" (full
+ * step).  NK/iNK: Eq. "newton" with GMRES (right block-Jacobi / Schur
+ * preconditioning, MGS Arnoldi, restarted every ksp_restart), iNK forcing
+ * by Eisenstat-Walker choice 1 with the safeguard; B/iB: limited-memory
+ * BFGS two-loop (Nocedal 1980) with H0 = preconditioner (B) or GMRES at
+ * ksp_rtol (iB) on the tangent assembled once at d_0.  opts may be NULL
+ * (method defaults); stats may be NULL.  Returns 0 on convergence or an
+ * NL_* outcome (> 0) or an FE_ERR_* (< 0). */
+int nl_solve(fe_mesh m, int method, double tol, int max_it, double* d,
+             const nl_opts* opts, nl_stats* stats);
+
+/* Solve K x = b with GMRES on the assembled tangent (device [ndof] FP64;
+ * x holds the initial guess and is overwritten).  iters/res_out (host,
+ * nullable) receive the iteration count and the final residual estimate. */
+int fe_gmres(fe_mesh m, const double* b, double* x, double rtol, double atol,
+             int restart, int max_it, int* iters, double* res_out);
+
+/* One L-BFGS two-loop application z = H q over k stored pairs (device
+ * pointers: S, Y [k][ndof] row-major oldest first, rho [k], q, z [ndof]),
+ * with H0 = the preconditioner of the assembled tangent (h0 = 0) or
+ * identity (h0 = 1).  Paper: BFGS update formula and its two-loop
+ * recursion (Section "Numerical solvers", BFGS method). */
+int fe_lbfgs_apply(fe_mesh m, const double* S, const double* Y, const double* rho,
+                   int k, const double* q, double* z, int h0);
+
+/* Thread-local message describing the last error. */
+const char* fe_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* FE_H */

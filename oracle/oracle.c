@@ -1,0 +1,1184 @@
+/*
+ * oracle.c -- plain FP64 CPU oracle (TEST INFRASTRUCTURE ONLY).
+ *
+ * Follows arxiv 2203.05610 step by step:
+ *   - problem: quasi-static R(d) = f - div P(F), F = I + grad d, P = dPsi/dF
+ *     (Section "The hyperelasticity problem"), energy Pi (Eq. "minimization");
+ *   - materials: Cook neo-Hookean Psi_Cook, Taylor-Hood neo-Hookean u-p form
+ *     (twist stand-in), Guccione + active stress + epicardial springs
+ *     (Section "Test problems and solvers details");
+ *   - solvers: NK (Eq. "newton"), iNK with Eisenstat-Walker forcing, BFGS
+ *     update and its two-loop recursion, BFGS-preonly and inexact BFGS
+ *     (Section "Numerical solvers"), options of Appendix A, lower Schur
+ *     preconditioner of Appendix B with the SIMPLE approximation;
+ *   - GMRES with modified Gram-Schmidt, no restart in the paper (restart
+ *     cap here), right preconditioning.
+ * Readings where the paper is silent or garbled are listed in the
+ * project's design notes and restated beside the code that takes them.
+ */
+#include "oracle.h"
+
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+/* ======================================================================
+ * small helpers
+ * ====================================================================== */
+static void* xcalloc(size_t n, size_t sz) {
+  void* p = calloc(n ? n : 1, sz);
+  if (!p) abort();
+  return p;
+}
+
+static double dot(const double* a, const double* b, long n) {
+  double s = 0.0;
+  for (long i = 0; i < n; i++) s += a[i] * b[i];
+  return s;
+}
+
+static double nrm2(const double* a, long n) { return sqrt(dot(a, a, n)); }
+
+static double det3(const double M[3][3]) {
+  return M[0][0] * (M[1][1] * M[2][2] - M[1][2] * M[2][1]) -
+         M[0][1] * (M[1][0] * M[2][2] - M[1][2] * M[2][0]) +
+         M[0][2] * (M[1][0] * M[2][1] - M[1][1] * M[2][0]);
+}
+
+/* inverse by the adjugate: Minv = adj(M) / det(M) */
+static double inv3(const double M[3][3], double Minv[3][3]) {
+  double d = det3(M);
+  Minv[0][0] = (M[1][1] * M[2][2] - M[1][2] * M[2][1]) / d;
+  Minv[0][1] = (M[0][2] * M[2][1] - M[0][1] * M[2][2]) / d;
+  Minv[0][2] = (M[0][1] * M[1][2] - M[0][2] * M[1][1]) / d;
+  Minv[1][0] = (M[1][2] * M[2][0] - M[1][0] * M[2][2]) / d;
+  Minv[1][1] = (M[0][0] * M[2][2] - M[0][2] * M[2][0]) / d;
+  Minv[1][2] = (M[0][2] * M[1][0] - M[0][0] * M[1][2]) / d;
+  Minv[2][0] = (M[1][0] * M[2][1] - M[1][1] * M[2][0]) / d;
+  Minv[2][1] = (M[0][1] * M[2][0] - M[0][0] * M[2][1]) / d;
+  Minv[2][2] = (M[0][0] * M[1][1] - M[0][1] * M[1][0]) / d;
+  return d;
+}
+
+unsigned long long om_splitmix64(unsigned long long x) {
+  /* splitmix64 output function (S. Vigna), applied to state x */
+  unsigned long long z = x + 0x9E3779B97F4A7C15ULL;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+  return z ^ (z >> 31);
+}
+
+/* ======================================================================
+ * quadrature (paper silent; readings: P1 one point, P2 the 4-point
+ * degree-2 symmetric rule, triangles the 6-point degree-4 rule)
+ * ====================================================================== */
+int om_tet_rule(int order, double* lam, double* w) {
+  if (order == 1) {
+    for (int a = 0; a < 4; a++) lam[a] = 0.25;
+    w[0] = 1.0;
+    return 1;
+  }
+  const double a = 0.5854101966249685, b = 0.1381966011250105;
+  for (int q = 0; q < 4; q++) {
+    for (int c = 0; c < 4; c++) lam[4 * q + c] = (c == q) ? a : b;
+    w[q] = 0.25;
+  }
+  return 4;
+}
+
+int om_tri_rule(double* lam, double* w) {
+  const double a1 = 0.445948490915965, b1 = 0.108103018168070, w1 = 0.223381589678011;
+  const double a2 = 0.091576213509771, b2 = 0.816847572980459, w2 = 0.109951743655322;
+  int q = 0;
+  for (int k = 0; k < 3; k++, q++) {
+    for (int c = 0; c < 3; c++) lam[3 * q + c] = (c == k) ? b1 : a1;
+    w[q] = w1;
+  }
+  for (int k = 0; k < 3; k++, q++) {
+    for (int c = 0; c < 3; c++) lam[3 * q + c] = (c == k) ? b2 : a2;
+    w[q] = w2;
+  }
+  return 6;
+}
+
+/* local edges of a tet and of a triangle */
+static const int TET_EDGE[6][2] = {{0, 1}, {0, 2}, {0, 3}, {1, 2}, {1, 3}, {2, 3}};
+static const int TRI_EDGE[3][2] = {{0, 1}, {1, 2}, {0, 2}};
+
+/* values of the nen shape functions at barycentric lam (tet) */
+static void tet_shape(int order, const double* lam, double* N) {
+  if (order == 1) {
+    for (int a = 0; a < 4; a++) N[a] = lam[a];
+    return;
+  }
+  for (int a = 0; a < 4; a++) N[a] = lam[a] * (2.0 * lam[a] - 1.0);
+  for (int e = 0; e < 6; e++) N[4 + e] = 4.0 * lam[TET_EDGE[e][0]] * lam[TET_EDGE[e][1]];
+}
+
+/* physical gradients of the shape functions given the gradients G[4][3] of
+ * the barycentric coordinates */
+static void tet_grad(int order, const double* lam, const double G[4][3], double dN[][3]) {
+  if (order == 1) {
+    for (int a = 0; a < 4; a++)
+      for (int i = 0; i < 3; i++) dN[a][i] = G[a][i];
+    return;
+  }
+  for (int a = 0; a < 4; a++)
+    for (int i = 0; i < 3; i++) dN[a][i] = (4.0 * lam[a] - 1.0) * G[a][i];
+  for (int e = 0; e < 6; e++) {
+    int p = TET_EDGE[e][0], q = TET_EDGE[e][1];
+    for (int i = 0; i < 3; i++) dN[4 + e][i] = 4.0 * (lam[p] * G[q][i] + lam[q] * G[p][i]);
+  }
+}
+
+static void tri_shape(int order, const double* lam, double* N) {
+  if (order == 1) {
+    for (int a = 0; a < 3; a++) N[a] = lam[a];
+    return;
+  }
+  for (int a = 0; a < 3; a++) N[a] = lam[a] * (2.0 * lam[a] - 1.0);
+  for (int e = 0; e < 3; e++) N[3 + e] = 4.0 * lam[TRI_EDGE[e][0]] * lam[TRI_EDGE[e][1]];
+}
+
+/* ======================================================================
+ * materials: Psi, P = dPsi/dF, A = dP/dF (A[9*(3i+J) + 3k+L]) and dP/dp
+ * ====================================================================== */
+#define IDX(i, J) (3 * (i) + (J))
+
+static void cofactor_H(const double F[9], double* J, double H[9]) {
+  /* H = F^{-T} */
+  double M[3][3], Mi[3][3];
+  for (int i = 0; i < 3; i++)
+    for (int j = 0; j < 3; j++) M[i][j] = F[IDX(i, j)];
+  *J = inv3(M, Mi);
+  for (int i = 0; i < 3; i++)
+    for (int j = 0; j < 3; j++) H[IDX(i, j)] = Mi[j][i];
+}
+
+void om_material(const double* matp, const double* F, const double* fib, double gamma,
+                 double p, double* psi, double* P, double* A, double* dPdp) {
+  int kind = (int)matp[0];
+  double J, H[9];
+  cofactor_H(F, &J, H);
+  double I1 = 0.0;
+  for (int k = 0; k < 9; k++) I1 += F[k] * F[k];
+  if (dPdp)
+    for (int k = 0; k < 9; k++) dPdp[k] = 0.0;
+
+  if (kind == 0) {
+    /* Cook: Psi = C1 (tr(Fbar^T Fbar) - 3) + c_vol (J^2 - 1 - 2 ln J),
+     * C1 = mu/2, tr(Fbar^T Fbar) = J^{-2/3} I1, mu = E/(2(1+nu)),
+     * lambda = 2 mu nu/(1-2 nu), kappa = lambda + 2 mu/3.
+     * Reading: c_vol = kappa/4 (consistent with linear elasticity at small
+     * strain); vol_literal = 1 takes the printed coefficient kappa. */
+    double E = matp[2], nu = matp[3];
+    double mu = E / (2.0 * (1.0 + nu));
+    double lam = 2.0 * mu * nu / (1.0 - 2.0 * nu);
+    double kap = lam + 2.0 * mu / 3.0;
+    double cv = ((int)matp[1]) ? kap : 0.25 * kap;
+    double Jm23 = pow(J, -2.0 / 3.0);
+    if (psi) *psi = 0.5 * mu * (Jm23 * I1 - 3.0) + cv * (J * J - 1.0 - 2.0 * log(J));
+    /* P = mu J^{-2/3} (F - I1/3 H) + 2 c_vol (J^2 - 1) H */
+    for (int k = 0; k < 9; k++)
+      P[k] = mu * Jm23 * (F[k] - I1 / 3.0 * H[k]) + 2.0 * cv * (J * J - 1.0) * H[k];
+    if (A) {
+      for (int i = 0; i < 3; i++)
+        for (int Jj = 0; Jj < 3; Jj++)
+          for (int k = 0; k < 3; k++)
+            for (int L = 0; L < 3; L++) {
+              double dik = (i == k), dJL = (Jj == L);
+              double iso = dik * dJL -
+                           2.0 / 3.0 * (H[IDX(k, L)] * F[IDX(i, Jj)] + F[IDX(k, L)] * H[IDX(i, Jj)]) +
+                           2.0 / 9.0 * I1 * H[IDX(i, Jj)] * H[IDX(k, L)] +
+                           I1 / 3.0 * H[IDX(i, L)] * H[IDX(k, Jj)];
+              double vol = 4.0 * cv * J * J * H[IDX(i, Jj)] * H[IDX(k, L)] -
+                           2.0 * cv * (J * J - 1.0) * H[IDX(i, L)] * H[IDX(k, Jj)];
+              A[9 * IDX(i, Jj) + IDX(k, L)] = mu * Jm23 * iso + vol;
+            }
+    }
+    return;
+  }
+
+  if (kind == 1) {
+    /* Taylor-Hood neo-Hookean (reading of the twist stand-in):
+     * Psi = mu/2 (I1 - 3) - mu ln J - p (J - 1); P = mu (F - H) - p J H */
+    double mu = matp[4];
+    if (psi) *psi = 0.5 * mu * (I1 - 3.0) - mu * log(J) - p * (J - 1.0);
+    for (int k = 0; k < 9; k++) P[k] = mu * (F[k] - H[k]) - p * J * H[k];
+    if (dPdp)
+      for (int k = 0; k < 9; k++) dPdp[k] = -J * H[k];
+    if (A) {
+      for (int i = 0; i < 3; i++)
+        for (int Jj = 0; Jj < 3; Jj++)
+          for (int k = 0; k < 3; k++)
+            for (int L = 0; L < 3; L++) {
+              double dik = (i == k), dJL = (Jj == L);
+              double hh = H[IDX(i, L)] * H[IDX(k, Jj)];
+              A[9 * IDX(i, Jj) + IDX(k, L)] =
+                  mu * (dik * dJL + hh) - p * J * (H[IDX(i, Jj)] * H[IDX(k, L)] - hh);
+            }
+    }
+    return;
+  }
+
+  /* kind 2: Guccione, Psi = C/2 (e^Q - 1) + kappa/2 (J - 1) ln J + gamma |F f|,
+   * Q = sum_ab b_ab E_ab^2 in the fibre frame {f, s, n}, E = (F^T F - I)/2.
+   * The active stress gamma (Ff) x f / |Ff| is the derivative of gamma |Ff|. */
+  double C = matp[5], bf = matp[6], bt = matp[7], bfs = matp[8], kap = matp[9];
+  double Bm[3][3] = {{bf, bfs, bfs}, {bfs, bt, bt}, {bfs, bt, bt}};
+  double E[3][3];
+  for (int M = 0; M < 3; M++)
+    for (int N = 0; N < 3; N++) {
+      double s = 0.0;
+      for (int a = 0; a < 3; a++) s += F[IDX(a, M)] * F[IDX(a, N)];
+      E[M][N] = 0.5 * (s - (M == N));
+    }
+  /* E in the fibre frame: Ef[a][b] = f_a . E f_b, fib rows are f, s, n */
+  double Ef[3][3], Q = 0.0;
+  for (int a = 0; a < 3; a++)
+    for (int b = 0; b < 3; b++) {
+      double s = 0.0;
+      for (int M = 0; M < 3; M++)
+        for (int N = 0; N < 3; N++) s += fib[3 * a + M] * E[M][N] * fib[3 * b + N];
+      Ef[a][b] = s;
+      Q += Bm[a][b] * s * s;
+    }
+  double eQ = exp(Q);
+  /* D = R (B o Ef) R^T in the global frame; dQ/dE = 2 D; S = C e^Q D */
+  double D[3][3];
+  for (int M = 0; M < 3; M++)
+    for (int N = 0; N < 3; N++) {
+      double s = 0.0;
+      for (int a = 0; a < 3; a++)
+        for (int b = 0; b < 3; b++) s += fib[3 * a + M] * Bm[a][b] * Ef[a][b] * fib[3 * b + N];
+      D[M][N] = s;
+    }
+  double S[3][3];
+  for (int M = 0; M < 3; M++)
+    for (int N = 0; N < 3; N++) S[M][N] = C * eQ * D[M][N];
+  double phi = 0.5 * kap * (J * log(J) + J - 1.0); /* dPsi_vol/dJ * J */
+  double dphi = 0.5 * kap * (log(J) + 2.0);        /* d phi / dJ */
+  double a_[3], an = 0.0;
+  for (int i = 0; i < 3; i++) {
+    a_[i] = 0.0;
+    for (int Jj = 0; Jj < 3; Jj++) a_[i] += F[IDX(i, Jj)] * fib[Jj];
+    an += a_[i] * a_[i];
+  }
+  an = sqrt(an);
+  if (psi) *psi = 0.5 * C * (eQ - 1.0) + 0.5 * kap * (J - 1.0) * log(J) + gamma * an;
+  for (int i = 0; i < 3; i++)
+    for (int Jj = 0; Jj < 3; Jj++) {
+      double s = 0.0;
+      for (int M = 0; M < 3; M++) s += F[IDX(i, M)] * S[M][Jj];
+      P[IDX(i, Jj)] = s + phi * H[IDX(i, Jj)] + gamma * a_[i] * fib[Jj] / an;
+    }
+  if (!A) return;
+  /* A by directional derivatives dP[dF] with dF = e_k x e_L:
+   * dE = (dF^T F + F^T dF)/2, dS = C e^Q (2 (D:dE) D + R (B o (R^T dE R)) R^T),
+   * dP = dF S + F dS + vol + active parts. */
+  for (int k = 0; k < 3; k++)
+    for (int L = 0; L < 3; L++) {
+      double dE[3][3];
+      for (int M = 0; M < 3; M++)
+        for (int N = 0; N < 3; N++)
+          dE[M][N] = 0.5 * ((L == M) * F[IDX(k, N)] + F[IDX(k, M)] * (L == N));
+      double DdE = 0.0;
+      for (int M = 0; M < 3; M++)
+        for (int N = 0; N < 3; N++) DdE += D[M][N] * dE[M][N];
+      double dEf[3][3];
+      for (int a = 0; a < 3; a++)
+        for (int b = 0; b < 3; b++) {
+          double s = 0.0;
+          for (int M = 0; M < 3; M++)
+            for (int N = 0; N < 3; N++) s += fib[3 * a + M] * dE[M][N] * fib[3 * b + N];
+          dEf[a][b] = s;
+        }
+      double dS[3][3];
+      for (int M = 0; M < 3; M++)
+        for (int N = 0; N < 3; N++) {
+          double s = 0.0;
+          for (int a = 0; a < 3; a++)
+            for (int b = 0; b < 3; b++) s += fib[3 * a + M] * Bm[a][b] * dEf[a][b] * fib[3 * b + N];
+          dS[M][N] = C * eQ * (2.0 * DdE * D[M][N] + s);
+        }
+      for (int i = 0; i < 3; i++)
+        for (int Jj = 0; Jj < 3; Jj++) {
+          double v = (i == k) ? S[L][Jj] : 0.0;
+          for (int M = 0; M < 3; M++) v += F[IDX(i, M)] * dS[M][Jj];
+          v += dphi * J * H[IDX(i, Jj)] * H[IDX(k, L)] - phi * H[IDX(i, L)] * H[IDX(k, Jj)];
+          v += gamma / an * ((i == k) - a_[i] * a_[k] / (an * an)) * fib[L] * fib[Jj];
+          A[9 * IDX(i, Jj) + IDX(k, L)] = v;
+        }
+    }
+}
+
+/* ======================================================================
+ * mesh
+ * ====================================================================== */
+struct om_mesh {
+  int order, pres, nv, ne, nn, nen, np;
+  long ndof;
+  double* X;   /* [nn][3] */
+  int* conn;   /* [ne][nen] */
+  int* colors; /* [ne] */
+  int ncolors;
+  int* row_ptr; /* [nn+1] */
+  int* col;     /* [nnzb] */
+  long nnzb;
+  int* up_ptr; /* [nn+1] u-p coupling rows (u nodes), columns = vertices */
+  int* up_col;
+  long nnz_up;
+  unsigned char* dgroup; /* [nn] */
+  int ngroups;
+  double* groups; /* [ngroups][8] */
+  int nf;
+  int* fnodes; /* [nf][6] face nodes (3 vertices, then 3 edge nodes for P2) */
+  int* fkind;
+  double* fdata;
+  double matp[12];
+  double* fib; /* [ne][9] or NULL */
+  double load, time;
+  /* tangent */
+  double* K;    /* [nnzb][9] */
+  double* B1;   /* [nnz_up][3] */
+  double* Dinv; /* [nn][9] */
+  double* Sd;   /* [np] Schur diagonal */
+  int have_K;
+  long long lit; /* Krylov iterations, accumulated by om_gmres */
+};
+
+static int cmp_ll(const void* a, const void* b) {
+  long long x = *(const long long*)a, y = *(const long long*)b;
+  return (x > y) - (x < y);
+}
+
+/* id of the edge node between vertices a and b: binary search in the sorted
+ * unique edge list */
+static int edge_node(const long long* edges, long nedge, int nv, int a, int b) {
+  long long key = (long long)(a < b ? a : b) * nv + (a < b ? b : a);
+  long lo = 0, hi = nedge - 1;
+  while (lo <= hi) {
+    long mid = (lo + hi) / 2;
+    if (edges[mid] == key) return nv + (int)mid;
+    if (edges[mid] < key) lo = mid + 1;
+    else hi = mid - 1;
+  }
+  return -1;
+}
+
+typedef struct {
+  unsigned long long pri;
+  int id;
+} pri_t;
+static int cmp_pri(const void* a, const void* b) {
+  const pri_t* x = (const pri_t*)a;
+  const pri_t* y = (const pri_t*)b;
+  if (x->pri != y->pri) return x->pri > y->pri ? -1 : 1; /* descending */
+  return (x->id > y->id) - (x->id < y->id);
+}
+
+static void build_pattern(long nrow, long ncolk, const int* conn, int ne, int nen, int nenc,
+                          const int* conn_c, int stride_c, int** ptr_out, int** col_out,
+                          long* nnz_out) {
+  /* all (row, col) pairs of nodes sharing an element, sorted and made unique */
+  long npair = (long)ne * nen * nenc;
+  long long* keys = (long long*)xcalloc(npair, sizeof(long long));
+  long t = 0;
+  for (int e = 0; e < ne; e++)
+    for (int a = 0; a < nen; a++)
+      for (int b = 0; b < nenc; b++)
+        keys[t++] = (long long)conn[(long)e * nen + a] * ncolk + conn_c[(long)e * stride_c + b];
+  qsort(keys, npair, sizeof(long long), cmp_ll);
+  long nu = 0;
+  for (long i = 0; i < npair; i++)
+    if (i == 0 || keys[i] != keys[i - 1]) keys[nu++] = keys[i];
+  int* ptr = (int*)xcalloc(nrow + 1, sizeof(int));
+  int* col = (int*)xcalloc(nu, sizeof(int));
+  for (long i = 0; i < nu; i++) {
+    long r = keys[i] / ncolk;
+    ptr[r + 1]++;
+    col[i] = (int)(keys[i] % ncolk);
+  }
+  for (long r = 0; r < nrow; r++) ptr[r + 1] += ptr[r];
+  free(keys);
+  *ptr_out = ptr;
+  *col_out = col;
+  *nnz_out = nu;
+}
+
+om_mesh* om_create(int order, int pressure_order, int nv, int ne, const double* coords,
+                   const int* tets, const unsigned char* dir_group, int ngroups,
+                   const double* groups, int nf, const int* faces, const int* face_kind,
+                   const double* face_data, const double* matp, const double* fibers) {
+  om_mesh* m = (om_mesh*)xcalloc(1, sizeof(om_mesh));
+  m->order = order;
+  m->pres = pressure_order;
+  m->nv = nv;
+  m->ne = ne;
+  m->nen = order == 1 ? 4 : 10;
+  memcpy(m->matp, matp, 12 * sizeof(double));
+  /* P2: unique edges sorted by (min, max) vertex id, numbered after vertices */
+  long long* edges = NULL;
+  long nedge = 0;
+  if (order == 2) {
+    edges = (long long*)xcalloc((long)ne * 6, sizeof(long long));
+    for (int e = 0; e < ne; e++)
+      for (int k = 0; k < 6; k++) {
+        int a = tets[4 * e + TET_EDGE[k][0]], b = tets[4 * e + TET_EDGE[k][1]];
+        edges[6L * e + k] = (long long)(a < b ? a : b) * nv + (a < b ? b : a);
+      }
+    qsort(edges, (long)ne * 6, sizeof(long long), cmp_ll);
+    for (long i = 0; i < (long)ne * 6; i++)
+      if (i == 0 || edges[i] != edges[i - 1]) edges[nedge++] = edges[i];
+  }
+  m->nn = nv + (int)nedge;
+  m->np = pressure_order ? nv : 0;
+  m->ndof = 3L * m->nn + m->np;
+  m->X = (double*)xcalloc(3L * m->nn, sizeof(double));
+  memcpy(m->X, coords, 3L * nv * sizeof(double));
+  for (long k = 0; k < nedge; k++) {
+    int a = (int)(edges[k] / nv), b = (int)(edges[k] % nv);
+    for (int i = 0; i < 3; i++) m->X[3L * (nv + k) + i] = 0.5 * (coords[3L * a + i] + coords[3L * b + i]);
+  }
+  m->conn = (int*)xcalloc((long)ne * m->nen, sizeof(int));
+  for (int e = 0; e < ne; e++) {
+    for (int a = 0; a < 4; a++) m->conn[(long)e * m->nen + a] = tets[4 * e + a];
+    if (order == 2)
+      for (int k = 0; k < 6; k++)
+        m->conn[(long)e * m->nen + 4 + k] =
+            edge_node(edges, nedge, nv, tets[4 * e + TET_EDGE[k][0]], tets[4 * e + TET_EDGE[k][1]]);
+  }
+  /* Dirichlet groups per node: an edge node inherits its vertices' common group */
+  m->dgroup = (unsigned char*)xcalloc(m->nn, 1);
+  for (int a = 0; a < nv; a++) m->dgroup[a] = dir_group ? dir_group[a] : 0;
+  for (long k = 0; k < nedge; k++) {
+    int a = (int)(edges[k] / nv), b = (int)(edges[k] % nv);
+    if (m->dgroup[a] && m->dgroup[a] == m->dgroup[b]) m->dgroup[nv + k] = m->dgroup[a];
+  }
+  m->ngroups = ngroups;
+  m->groups = (double*)xcalloc(8L * (ngroups > 0 ? ngroups : 1), sizeof(double));
+  if (ngroups) memcpy(m->groups, groups, 8L * ngroups * sizeof(double));
+  /* faces */
+  m->nf = nf;
+  m->fnodes = (int*)xcalloc(6L * (nf > 0 ? nf : 1), sizeof(int));
+  m->fkind = (int*)xcalloc(nf > 0 ? nf : 1, sizeof(int));
+  m->fdata = (double*)xcalloc(3L * (nf > 0 ? nf : 1), sizeof(double));
+  for (int f = 0; f < nf; f++) {
+    for (int a = 0; a < 3; a++) m->fnodes[6 * f + a] = faces[3 * f + a];
+    if (order == 2)
+      for (int k = 0; k < 3; k++)
+        m->fnodes[6 * f + 3 + k] =
+            edge_node(edges, nedge, nv, faces[3 * f + TRI_EDGE[k][0]], faces[3 * f + TRI_EDGE[k][1]]);
+    m->fkind[f] = face_kind[f];
+    for (int i = 0; i < 3; i++) m->fdata[3 * f + i] = face_data[3 * f + i];
+  }
+  if (fibers) {
+    m->fib = (double*)xcalloc(9L * ne, sizeof(double));
+    memcpy(m->fib, fibers, 9L * ne * sizeof(double));
+  }
+  free(edges);
+
+  /* colouring: first-fit greedy, elements visited by descending
+   * splitmix64(id), ties by ascending id; two elements conflict when they
+   * share a vertex (equivalently, any node) */
+  pri_t* pr = (pri_t*)xcalloc(ne, sizeof(pri_t));
+  for (int e = 0; e < ne; e++) {
+    pr[e].pri = om_splitmix64((unsigned long long)e);
+    pr[e].id = e;
+  }
+  qsort(pr, ne, sizeof(pri_t), cmp_pri);
+  int* vptr = (int*)xcalloc(nv + 1, sizeof(int));
+  for (int e = 0; e < ne; e++)
+    for (int a = 0; a < 4; a++) vptr[tets[4 * e + a] + 1]++;
+  for (int v = 0; v < nv; v++) vptr[v + 1] += vptr[v];
+  int* vel = (int*)xcalloc((long)ne * 4, sizeof(int));
+  int* fill = (int*)xcalloc(nv, sizeof(int));
+  for (int e = 0; e < ne; e++)
+    for (int a = 0; a < 4; a++) {
+      int v = tets[4 * e + a];
+      vel[vptr[v] + fill[v]++] = e;
+    }
+  m->colors = (int*)xcalloc(ne, sizeof(int));
+  for (int e = 0; e < ne; e++) m->colors[e] = -1;
+  int maxc = 0;
+  unsigned char* used = (unsigned char*)xcalloc(4096, 1);
+  for (int t = 0; t < ne; t++) {
+    int e = pr[t].id;
+    memset(used, 0, 4096);
+    for (int a = 0; a < 4; a++) {
+      int v = tets[4 * e + a];
+      for (int k = vptr[v]; k < vptr[v + 1]; k++) {
+        int c = m->colors[vel[k]];
+        if (c >= 0) used[c] = 1;
+      }
+    }
+    int c = 0;
+    while (used[c]) c++;
+    m->colors[e] = c;
+    if (c + 1 > maxc) maxc = c + 1;
+  }
+  m->ncolors = maxc;
+  free(used);
+  free(fill);
+  free(vel);
+  free(vptr);
+  free(pr);
+
+  /* block pattern */
+  build_pattern(m->nn, m->nn, m->conn, ne, m->nen, m->nen, m->conn, m->nen, &m->row_ptr, &m->col,
+                &m->nnzb);
+  if (m->pres)
+    build_pattern(m->nn, nv, m->conn, ne, m->nen, 4, tets, 4, &m->up_ptr, &m->up_col, &m->nnz_up);
+  m->K = (double*)xcalloc(9 * m->nnzb, sizeof(double));
+  m->B1 = (double*)xcalloc(3 * (m->nnz_up > 0 ? m->nnz_up : 1), sizeof(double));
+  m->Dinv = (double*)xcalloc(9L * m->nn, sizeof(double));
+  m->Sd = (double*)xcalloc(m->np > 0 ? m->np : 1, sizeof(double));
+  return m;
+}
+
+void om_destroy(om_mesh* m) {
+  if (!m) return;
+  free(m->X); free(m->conn); free(m->colors); free(m->row_ptr); free(m->col);
+  free(m->up_ptr); free(m->up_col); free(m->dgroup); free(m->groups); free(m->fnodes);
+  free(m->fkind); free(m->fdata); free(m->fib); free(m->K); free(m->B1); free(m->Dinv);
+  free(m->Sd); free(m);
+}
+
+void om_info(const om_mesh* m, long long* out) {
+  out[0] = m->nn; out[1] = m->np; out[2] = m->ndof; out[3] = m->nnzb;
+  out[4] = m->nnz_up; out[5] = m->ncolors; out[6] = m->nen;
+}
+
+void om_topology(const om_mesh* m, int* conn, int* colors, int* row_ptr, int* col, double* X) {
+  if (conn) memcpy(conn, m->conn, sizeof(int) * (size_t)m->ne * m->nen);
+  if (colors) memcpy(colors, m->colors, sizeof(int) * (size_t)m->ne);
+  if (row_ptr) memcpy(row_ptr, m->row_ptr, sizeof(int) * (size_t)(m->nn + 1));
+  if (col) memcpy(col, m->col, sizeof(int) * (size_t)m->nnzb);
+  if (X) memcpy(X, m->X, sizeof(double) * 3 * (size_t)m->nn);
+}
+
+void om_set_load(om_mesh* m, double load, double time) {
+  m->load = load;
+  m->time = time;
+}
+
+static int is_fixed(const om_mesh* m, int node, int c) {
+  int g = m->dgroup[node];
+  if (!g) return 0;
+  unsigned mask = (unsigned)m->groups[8 * (g - 1)];
+  return (mask >> c) & 1u;
+}
+
+void om_apply_dirichlet(const om_mesh* m, double* d) {
+  /* prescribed d(X) = T(X) - X, T = rotation by load*angle about the axis
+   * parallel to z through center, followed by load*translation */
+  for (int a = 0; a < m->nn; a++) {
+    int g = m->dgroup[a];
+    if (!g) continue;
+    const double* G = m->groups + 8 * (g - 1);
+    double th = m->load * G[4];
+    double x = m->X[3 * a] - G[1], y = m->X[3 * a + 1] - G[2];
+    double T[3] = {G[1] + cos(th) * x - sin(th) * y + m->load * G[5],
+                   G[2] + sin(th) * x + cos(th) * y + m->load * G[6],
+                   m->X[3 * a + 2] + m->load * G[7]};
+    for (int c = 0; c < 3; c++)
+      if (is_fixed(m, a, c)) d[3L * a + c] = T[c] - m->X[3 * a + c];
+  }
+}
+
+/* activation gamma(t) = Ta_peak max(sin(2 pi t / period), 0) */
+static double om_gamma(const om_mesh* m) {
+  if ((int)m->matp[0] != 2) return 0.0;
+  double s = sin(2.0 * M_PI * m->time / m->matp[11]);
+  return m->matp[10] * (s > 0.0 ? s : 0.0);
+}
+
+/* element geometry: barycentric gradients G[4][3] and volume */
+static double elem_geom(const om_mesh* m, int e, double G[4][3]) {
+  const int* c = m->conn + (long)e * m->nen;
+  double Jm[3][3], Ji[3][3];
+  for (int i = 0; i < 3; i++)
+    for (int j = 0; j < 3; j++) Jm[i][j] = m->X[3 * c[j + 1] + i] - m->X[3 * c[0] + i];
+  double det = inv3(Jm, Ji);
+  /* grad lambda_{j+1} = row j of J^{-1}; grad lambda_0 = -sum */
+  for (int i = 0; i < 3; i++) {
+    G[0][i] = 0.0;
+    for (int j = 0; j < 3; j++) {
+      G[j + 1][i] = Ji[j][i];
+      G[0][i] -= Ji[j][i];
+    }
+  }
+  return det / 6.0;
+}
+
+/* face geometry: area and unit outward normal */
+static double face_geom(const om_mesh* m, int f, double N[3]) {
+  const int* v = m->fnodes + 6 * f;
+  double a[3], b[3];
+  for (int i = 0; i < 3; i++) {
+    a[i] = m->X[3 * v[1] + i] - m->X[3 * v[0] + i];
+    b[i] = m->X[3 * v[2] + i] - m->X[3 * v[0] + i];
+  }
+  double n[3] = {a[1] * b[2] - a[2] * b[1], a[2] * b[0] - a[0] * b[2], a[0] * b[1] - a[1] * b[0]};
+  double ln = sqrt(n[0] * n[0] + n[1] * n[1] + n[2] * n[2]);
+  for (int i = 0; i < 3; i++) N[i] = n[i] / ln;
+  return 0.5 * ln;
+}
+
+/* per-face: consistent load vector (dead traction / pressure) and spring
+ * mass-type matrix M_ab = int phi_a phi_b dA */
+static int face_terms(const om_mesh* m, int f, double fvec[6][3], double M[6][6], double Ks[3][3]) {
+  int nfn = m->order == 1 ? 3 : 6;
+  double N[3];
+  double area = face_geom(m, f, N);
+  double lam[18], w[6], phi[6];
+  int nq = om_tri_rule(lam, w);
+  double intphi[6] = {0}, mm[6][6];
+  memset(mm, 0, sizeof(mm));
+  for (int q = 0; q < nq; q++) {
+    tri_shape(m->order, lam + 3 * q, phi);
+    for (int a = 0; a < nfn; a++) {
+      intphi[a] += w[q] * area * phi[a];
+      for (int b = 0; b < nfn; b++) mm[a][b] += w[q] * area * phi[a] * phi[b];
+    }
+  }
+  int kind = m->fkind[f];
+  const double* fd = m->fdata + 3 * f;
+  double t[3] = {0, 0, 0};
+  if (kind == 0)
+    for (int i = 0; i < 3; i++) t[i] = m->load * fd[i];
+  else if (kind == 1)
+    for (int i = 0; i < 3; i++) t[i] = -m->load * fd[0] * N[i];
+  for (int a = 0; a < nfn; a++)
+    for (int i = 0; i < 3; i++) fvec[a][i] = t[i] * intphi[a];
+  memcpy(M, mm, sizeof(mm));
+  memset(Ks, 0, 9 * sizeof(double));
+  if (kind == 2)
+    for (int i = 0; i < 3; i++)
+      for (int k = 0; k < 3; k++)
+        Ks[i][k] = fd[0] * N[i] * N[k] + fd[1] * ((i == k) - N[i] * N[k]);
+  return nfn;
+}
+
+double om_residual(om_mesh* m, const double* d, double* r) {
+  memset(r, 0, sizeof(double) * m->ndof);
+  int nen = m->nen;
+  double gam = om_gamma(m);
+  double lam[16], w[4], N[10], dN[10][3], G[4][3];
+  int nq = om_tet_rule(m->order, lam, w);
+  for (int e = 0; e < m->ne; e++) {
+    const int* c = m->conn + (long)e * nen;
+    double vol = elem_geom(m, e, G);
+    for (int q = 0; q < nq; q++) {
+      tet_shape(m->order, lam + 4 * q, N);
+      tet_grad(m->order, lam + 4 * q, G, dN);
+      double F[9];
+      for (int i = 0; i < 3; i++)
+        for (int J = 0; J < 3; J++) {
+          double s = (i == J);
+          for (int a = 0; a < nen; a++) s += d[3L * c[a] + i] * dN[a][J];
+          F[IDX(i, J)] = s;
+        }
+      double p = 0.0;
+      if (m->pres)
+        for (int a = 0; a < 4; a++) p += d[3L * m->nn + c[a]] * lam[4 * q + a];
+      double P[9];
+      om_material(m->matp, F, m->fib ? m->fib + 9L * e : NULL, gam, p, NULL, P, NULL, NULL);
+      double wq = w[q] * vol;
+      for (int a = 0; a < nen; a++)
+        for (int i = 0; i < 3; i++) {
+          double s = 0.0;
+          for (int J = 0; J < 3; J++) s += P[IDX(i, J)] * dN[a][J];
+          r[3L * c[a] + i] += wq * s;
+        }
+      if (m->pres) {
+        double det, H[9];
+        cofactor_H(F, &det, H);
+        /* R_p = -int (J - 1) q_h */
+        for (int a = 0; a < 4; a++) r[3L * m->nn + c[a]] -= wq * (det - 1.0) * lam[4 * q + a];
+      }
+    }
+  }
+  /* surface terms: R -= external load; R += springs K_s d */
+  for (int f = 0; f < m->nf; f++) {
+    double fv[6][3], M[6][6], Ks[3][3];
+    int nfn = face_terms(m, f, fv, M, Ks);
+    const int* v = m->fnodes + 6 * f;
+    for (int a = 0; a < nfn; a++)
+      for (int i = 0; i < 3; i++) {
+        double s = -fv[a][i];
+        for (int b = 0; b < nfn; b++)
+          for (int k = 0; k < 3; k++) s += M[a][b] * Ks[i][k] * d[3L * v[b] + k];
+        r[3L * v[a] + i] += s;
+      }
+  }
+  for (int a = 0; a < m->nn; a++)
+    for (int c = 0; c < 3; c++)
+      if (is_fixed(m, a, c)) r[3L * a + c] = 0.0;
+  return nrm2(r, m->ndof);
+}
+
+double om_energy(om_mesh* m, const double* d) {
+  int nen = m->nen;
+  double gam = om_gamma(m);
+  double lam[16], w[4], N[10], dN[10][3], G[4][3];
+  int nq = om_tet_rule(m->order, lam, w);
+  double Pi = 0.0;
+  for (int e = 0; e < m->ne; e++) {
+    const int* c = m->conn + (long)e * nen;
+    double vol = elem_geom(m, e, G);
+    for (int q = 0; q < nq; q++) {
+      tet_shape(m->order, lam + 4 * q, N);
+      tet_grad(m->order, lam + 4 * q, G, dN);
+      double F[9];
+      for (int i = 0; i < 3; i++)
+        for (int J = 0; J < 3; J++) {
+          double s = (i == J);
+          for (int a = 0; a < nen; a++) s += d[3L * c[a] + i] * dN[a][J];
+          F[IDX(i, J)] = s;
+        }
+      double p = 0.0;
+      if (m->pres)
+        for (int a = 0; a < 4; a++) p += d[3L * m->nn + c[a]] * lam[4 * q + a];
+      double psi, P[9];
+      om_material(m->matp, F, m->fib ? m->fib + 9L * e : NULL, gam, p, &psi, P, NULL, NULL);
+      Pi += w[q] * vol * psi;
+    }
+  }
+  for (int f = 0; f < m->nf; f++) {
+    double fv[6][3], M[6][6], Ks[3][3];
+    int nfn = face_terms(m, f, fv, M, Ks);
+    const int* v = m->fnodes + 6 * f;
+    for (int a = 0; a < nfn; a++)
+      for (int i = 0; i < 3; i++) {
+        Pi -= fv[a][i] * d[3L * v[a] + i];
+        for (int b = 0; b < nfn; b++)
+          for (int k = 0; k < 3; k++)
+            Pi += 0.5 * M[a][b] * d[3L * v[a] + i] * Ks[i][k] * d[3L * v[b] + k];
+      }
+  }
+  return Pi;
+}
+
+static long find_block(const int* ptr, const int* col, int row, int c) {
+  for (int k = ptr[row]; k < ptr[row + 1]; k++)
+    if (col[k] == c) return k;
+  abort();
+}
+
+void om_tangent(om_mesh* m, const double* d) {
+  memset(m->K, 0, sizeof(double) * 9 * m->nnzb);
+  if (m->pres) memset(m->B1, 0, sizeof(double) * 3 * m->nnz_up);
+  int nen = m->nen;
+  double gam = om_gamma(m);
+  double lam[16], w[4], N[10], dN[10][3], G[4][3];
+  int nq = om_tet_rule(m->order, lam, w);
+  double Ke[10][10][3][3], Be[10][4][3], A[81], dPdp[9];
+  for (int e = 0; e < m->ne; e++) {
+    const int* c = m->conn + (long)e * nen;
+    double vol = elem_geom(m, e, G);
+    memset(Ke, 0, sizeof(Ke));
+    memset(Be, 0, sizeof(Be));
+    for (int q = 0; q < nq; q++) {
+      tet_shape(m->order, lam + 4 * q, N);
+      tet_grad(m->order, lam + 4 * q, G, dN);
+      double F[9];
+      for (int i = 0; i < 3; i++)
+        for (int J = 0; J < 3; J++) {
+          double s = (i == J);
+          for (int a = 0; a < nen; a++) s += d[3L * c[a] + i] * dN[a][J];
+          F[IDX(i, J)] = s;
+        }
+      double p = 0.0;
+      if (m->pres)
+        for (int a = 0; a < 4; a++) p += d[3L * m->nn + c[a]] * lam[4 * q + a];
+      double P[9];
+      om_material(m->matp, F, m->fib ? m->fib + 9L * e : NULL, gam, p, NULL, P, A, dPdp);
+      double wq = w[q] * vol;
+      /* K_ab[i][k] += w sum_JL dN_a[J] A[iJ][kL] dN_b[L] */
+      for (int a = 0; a < nen; a++)
+        for (int b = 0; b < nen; b++)
+          for (int i = 0; i < 3; i++)
+            for (int k = 0; k < 3; k++) {
+              double s = 0.0;
+              for (int J = 0; J < 3; J++)
+                for (int L = 0; L < 3; L++) s += dN[a][J] * A[9 * IDX(i, J) + IDX(k, L)] * dN[b][L];
+              Ke[a][b][i][k] += wq * s;
+            }
+      /* coupling dR_u(a,i)/dp_v = w sum_J dPdp[iJ] dN_a[J] lambda_v */
+      if (m->pres)
+        for (int a = 0; a < nen; a++)
+          for (int v = 0; v < 4; v++)
+            for (int i = 0; i < 3; i++) {
+              double s = 0.0;
+              for (int J = 0; J < 3; J++) s += dPdp[IDX(i, J)] * dN[a][J];
+              Be[a][v][i] += wq * s * lam[4 * q + v];
+            }
+    }
+    for (int a = 0; a < nen; a++)
+      for (int b = 0; b < nen; b++) {
+        long k = find_block(m->row_ptr, m->col, c[a], c[b]);
+        for (int i = 0; i < 3; i++)
+          for (int kk = 0; kk < 3; kk++) m->K[9 * k + 3 * i + kk] += Ke[a][b][i][kk];
+      }
+    if (m->pres)
+      for (int a = 0; a < nen; a++)
+        for (int v = 0; v < 4; v++) {
+          long k = find_block(m->up_ptr, m->up_col, c[a], c[v]);
+          for (int i = 0; i < 3; i++) m->B1[3 * k + i] += Be[a][v][i];
+        }
+  }
+  /* springs */
+  for (int f = 0; f < m->nf; f++) {
+    double fv[6][3], M[6][6], Ks[3][3];
+    int nfn = face_terms(m, f, fv, M, Ks);
+    if (m->fkind[f] != 2) continue;
+    const int* v = m->fnodes + 6 * f;
+    for (int a = 0; a < nfn; a++)
+      for (int b = 0; b < nfn; b++) {
+        long k = find_block(m->row_ptr, m->col, v[a], v[b]);
+        for (int i = 0; i < 3; i++)
+          for (int kk = 0; kk < 3; kk++) m->K[9 * k + 3 * i + kk] += M[a][b] * Ks[i][kk];
+      }
+  }
+  /* Dirichlet: zero rows and columns of prescribed components, unit diagonal */
+  for (int a = 0; a < m->nn; a++)
+    for (int k = m->row_ptr[a]; k < m->row_ptr[a + 1]; k++) {
+      int b = m->col[k];
+      for (int i = 0; i < 3; i++)
+        for (int kk = 0; kk < 3; kk++)
+          if (is_fixed(m, a, i) || is_fixed(m, b, kk))
+            m->K[9 * k + 3 * i + kk] = (a == b && i == kk) ? 1.0 : 0.0;
+    }
+  if (m->pres)
+    for (int a = 0; a < m->nn; a++)
+      for (int k = m->up_ptr[a]; k < m->up_ptr[a + 1]; k++)
+        for (int i = 0; i < 3; i++)
+          if (is_fixed(m, a, i)) m->B1[3 * k + i] = 0.0;
+  /* nodal block-Jacobi: inverse of each 3x3 diagonal block */
+  for (int a = 0; a < m->nn; a++) {
+    long k = find_block(m->row_ptr, m->col, a, a);
+    double Db[3][3], Di[3][3];
+    for (int i = 0; i < 3; i++)
+      for (int kk = 0; kk < 3; kk++) Db[i][kk] = m->K[9 * k + 3 * i + kk];
+    inv3(Db, Di);
+    for (int i = 0; i < 3; i++)
+      for (int kk = 0; kk < 3; kk++) m->Dinv[9L * a + 3 * i + kk] = Di[i][kk];
+  }
+  /* SIMPLE Schur diagonal: S_vv = -sum_{a,i} B1[a,v]_i^2 / A_(ai,ai) */
+  if (m->pres) {
+    memset(m->Sd, 0, sizeof(double) * m->np);
+    for (int a = 0; a < m->nn; a++) {
+      long kd = find_block(m->row_ptr, m->col, a, a);
+      for (int k = m->up_ptr[a]; k < m->up_ptr[a + 1]; k++)
+        for (int i = 0; i < 3; i++) {
+          double b = m->B1[3 * k + i];
+          m->Sd[m->up_col[k]] -= b * b / m->K[9 * kd + 4 * i];
+        }
+    }
+  }
+  m->have_K = 1;
+}
+
+void om_tangent_copy(const om_mesh* m, double* val, double* bup, double* dinv) {
+  if (val) memcpy(val, m->K, sizeof(double) * 9 * m->nnzb);
+  if (bup && m->pres) memcpy(bup, m->B1, sizeof(double) * 3 * m->nnz_up);
+  if (dinv) memcpy(dinv, m->Dinv, sizeof(double) * 9 * (size_t)m->nn);
+}
+
+void om_spmv(const om_mesh* m, const double* x, double* y) {
+  /* y_u = A x_u + B1 x_p; y_p = B2 x_u with B2 = B1^T */
+  for (long i = 0; i < m->ndof; i++) y[i] = 0.0;
+  for (int a = 0; a < m->nn; a++)
+    for (int k = m->row_ptr[a]; k < m->row_ptr[a + 1]; k++) {
+      int b = m->col[k];
+      for (int i = 0; i < 3; i++)
+        for (int kk = 0; kk < 3; kk++) y[3L * a + i] += m->K[9L * k + 3 * i + kk] * x[3L * b + kk];
+    }
+  if (m->pres) {
+    const double* xp = x + 3L * m->nn;
+    double* yp = y + 3L * m->nn;
+    for (int a = 0; a < m->nn; a++)
+      for (int k = m->up_ptr[a]; k < m->up_ptr[a + 1]; k++) {
+        int v = m->up_col[k];
+        for (int i = 0; i < 3; i++) {
+          y[3L * a + i] += m->B1[3L * k + i] * xp[v];
+          yp[v] += m->B1[3L * k + i] * x[3L * a + i];
+        }
+      }
+  }
+}
+
+void om_pc(const om_mesh* m, const double* x, double* y) {
+  /* displacement: nodal block-Jacobi; u-p: lower Schur (Appendix B),
+   * z_u = D^{-1} x_u, z_p = S^{-1} (x_p - B2 z_u), S = point diagonal */
+  for (int a = 0; a < m->nn; a++)
+    for (int i = 0; i < 3; i++) {
+      double s = 0.0;
+      for (int k = 0; k < 3; k++) s += m->Dinv[9L * a + 3 * i + k] * x[3L * a + k];
+      y[3L * a + i] = s;
+    }
+  if (m->pres) {
+    double* t = (double*)xcalloc(m->np, sizeof(double));
+    for (int v = 0; v < m->np; v++) t[v] = x[3L * m->nn + v];
+    for (int a = 0; a < m->nn; a++)
+      for (int k = m->up_ptr[a]; k < m->up_ptr[a + 1]; k++)
+        for (int i = 0; i < 3; i++) t[m->up_col[k]] -= m->B1[3L * k + i] * y[3L * a + i];
+    for (int v = 0; v < m->np; v++) y[3L * m->nn + v] = m->Sd[v] != 0.0 ? t[v] / m->Sd[v] : t[v];
+    free(t);
+  }
+}
+
+/* ======================================================================
+ * GMRES: right preconditioned, modified Gram-Schmidt Arnoldi, Givens
+ * rotations, restart every `restart` steps (the paper uses none; the cap
+ * is a reading).  Stops when the residual estimate <= max(rtol ||b||, atol)
+ * or after max_it iterations.  Returns the iteration count.
+ * ====================================================================== */
+int om_gmres(om_mesh* m, const double* b, double* x, double rtol, double atol, int restart,
+             int max_it, double* res_out) {
+  long n = m->ndof;
+  int kmax = restart;
+  double* V = (double*)xcalloc((size_t)(kmax + 1) * n, sizeof(double));
+  double* H = (double*)xcalloc((size_t)(kmax + 1) * kmax, sizeof(double));
+  double* cs = (double*)xcalloc(kmax, sizeof(double));
+  double* sn = (double*)xcalloc(kmax, sizeof(double));
+  double* g = (double*)xcalloc(kmax + 1, sizeof(double));
+  double* yv = (double*)xcalloc(kmax, sizeof(double));
+  double* w = (double*)xcalloc(n, sizeof(double));
+  double* z = (double*)xcalloc(n, sizeof(double));
+  double bnorm = nrm2(b, n);
+  double target = fmax(rtol * bnorm, atol);
+  int it = 0;
+  double res = 0.0;
+  for (;;) {
+    /* r = b - K x */
+    om_spmv(m, x, w);
+    for (long i = 0; i < n; i++) V[i] = b[i] - w[i];
+    double beta = nrm2(V, n);
+    res = beta;
+    if (beta <= target || it >= max_it || !isfinite(beta)) break;
+    for (long i = 0; i < n; i++) V[i] /= beta;
+    memset(g, 0, sizeof(double) * (kmax + 1));
+    g[0] = beta;
+    int j = 0, done = 0;
+    for (j = 0; j < kmax; j++) {
+      om_pc(m, V + (size_t)j * n, z);
+      om_spmv(m, z, w);
+      for (int i = 0; i <= j; i++) { /* modified Gram-Schmidt */
+        double h = dot(w, V + (size_t)i * n, n);
+        H[(size_t)i * kmax + j] = h;
+        for (long l = 0; l < n; l++) w[l] -= h * V[(size_t)i * n + l];
+      }
+      double hn = nrm2(w, n);
+      H[(size_t)(j + 1) * kmax + j] = hn;
+      for (int i = 0; i < j; i++) { /* previous rotations */
+        double a = H[(size_t)i * kmax + j], c = H[(size_t)(i + 1) * kmax + j];
+        H[(size_t)i * kmax + j] = cs[i] * a + sn[i] * c;
+        H[(size_t)(i + 1) * kmax + j] = -sn[i] * a + cs[i] * c;
+      }
+      double a = H[(size_t)j * kmax + j], c = H[(size_t)(j + 1) * kmax + j];
+      double r = hypot(a, c);
+      cs[j] = a / r;
+      sn[j] = c / r;
+      H[(size_t)j * kmax + j] = r;
+      H[(size_t)(j + 1) * kmax + j] = 0.0;
+      g[j + 1] = -sn[j] * g[j];
+      g[j] = cs[j] * g[j];
+      it++;
+      res = fabs(g[j + 1]);
+      if (res <= target || it >= max_it || hn == 0.0 || !isfinite(res)) {
+        done = 1;
+        j++;
+        break;
+      }
+      for (long l = 0; l < n; l++) V[(size_t)(j + 1) * n + l] = w[l] / hn;
+    }
+    if (!done) j = kmax;
+    /* y = H^{-1} g (upper triangular j x j), x += M^{-1} V y */
+    for (int i = j - 1; i >= 0; i--) {
+      double s = g[i];
+      for (int k = i + 1; k < j; k++) s -= H[(size_t)i * kmax + k] * yv[k];
+      yv[i] = s / H[(size_t)i * kmax + i];
+    }
+    memset(w, 0, sizeof(double) * n);
+    for (int i = 0; i < j; i++)
+      for (long l = 0; l < n; l++) w[l] += yv[i] * V[(size_t)i * n + l];
+    om_pc(m, w, z);
+    for (long l = 0; l < n; l++) x[l] += z[l];
+    if (done) break;
+  }
+  m->lit += it;
+  if (res_out) *res_out = res;
+  free(V); free(H); free(cs); free(sn); free(g); free(yv); free(w); free(z);
+  return it;
+}
+
+/* L-BFGS two-loop recursion over k pairs stored oldest first:
+ * q = input; for i newest..oldest: alpha_i = rho_i s_i.q, q -= alpha_i y_i;
+ * z = H0 q; for i oldest..newest: beta = rho_i y_i.z, z += (alpha_i - beta) s_i.
+ * This is the product with the BFGS inverse update of the paper applied k
+ * times to H0 (Nocedal 1980). */
+static void twoloop(om_mesh* m, const double* S, const double* Y, const double* rho, int k,
+                    const double* qin, double* z, int h0, double ksp_rtol, double ksp_atol,
+                    int restart, int kmaxit) {
+  long n = m->ndof;
+  double* q = (double*)xcalloc(n, sizeof(double));
+  double* alpha = (double*)xcalloc(k > 0 ? k : 1, sizeof(double));
+  memcpy(q, qin, sizeof(double) * n);
+  for (int i = k - 1; i >= 0; i--) {
+    alpha[i] = rho[i] * dot(S + (size_t)i * n, q, n);
+    for (long l = 0; l < n; l++) q[l] -= alpha[i] * Y[(size_t)i * n + l];
+  }
+  if (h0 == 0) {
+    om_pc(m, q, z);
+  } else if (h0 == 1) {
+    memcpy(z, q, sizeof(double) * n);
+  } else {
+    memset(z, 0, sizeof(double) * n);
+    om_gmres(m, q, z, ksp_rtol, ksp_atol, restart, kmaxit, NULL);
+  }
+  for (int i = 0; i < k; i++) {
+    double beta = rho[i] * dot(Y + (size_t)i * n, z, n);
+    for (long l = 0; l < n; l++) z[l] += (alpha[i] - beta) * S[(size_t)i * n + l];
+  }
+  free(q);
+  free(alpha);
+}
+
+void om_lbfgs_apply(om_mesh* m, const double* S, const double* Y, const double* rho, int k,
+                    const double* q, double* z, int h0) {
+  twoloop(m, S, Y, rho, k, q, z, h0, 0, 0, 1, 1);
+}
+
+/* ======================================================================
+ * nonlinear solvers (Section "Numerical solvers", Appendix A)
+ * ====================================================================== */
+int om_solve(om_mesh* m, int method, double tol, int max_it, double* d, const double* opts,
+             double* stats) {
+  long n = m->ndof;
+  double ksp_rtol = opts[1], ksp_atol = opts[2], ew0 = opts[3], ewmax = opts[4];
+  int restart = (int)opts[5], kmaxit = (int)opts[6], mm = (int)opts[7];
+  double dtol = opts[8];
+  double* res_hist = stats + 6;
+  double* lit_hist = stats + 6 + OM_HIST;
+  double* eta_hist = stats + 6 + 2 * OM_HIST;
+  for (int i = 0; i < 6 + 3 * OM_HIST; i++) stats[i] = 0.0;
+  if ((int)opts[9]) om_apply_dirichlet(m, d);
+  double* R = (double*)xcalloc(n, sizeof(double));
+  double* Rn = (double*)xcalloc(n, sizeof(double));
+  double* dl = (double*)xcalloc(n, sizeof(double));
+  double* t = (double*)xcalloc(n, sizeof(double));
+  m->lit = 0;
+  int assemblies = 0, status = 2, nit = 0;
+  double r0 = om_residual(m, d, R), rk = r0;
+  res_hist[0] = r0;
+  if (!isfinite(r0)) {
+    status = 3;
+    goto out;
+  }
+  if (r0 == 0.0) {
+    status = 0;
+    goto out;
+  }
+  if (method == 0 || method == 1) {
+    double eta = method == 0 ? ksp_rtol : ew0, eta_prev = eta;
+    const double alpha2 = 0.5 * (1.0 + sqrt(5.0));
+    for (int k = 1; k <= max_it; k++) {
+      om_tangent(m, d);
+      assemblies++;
+      /* K delta = -R */
+      for (long i = 0; i < n; i++) t[i] = -R[i];
+      memset(dl, 0, sizeof(double) * n);
+      long long lit0 = m->lit;
+      om_gmres(m, t, dl, eta, ksp_atol, restart, kmaxit, NULL);
+      if (k < OM_HIST) {
+        lit_hist[k] = (double)(m->lit - lit0);
+        eta_hist[k] = eta;
+      }
+      /* linear residual ||R_{k-1} + K delta|| (used by Eisenstat-Walker) */
+      om_spmv(m, dl, Rn);
+      for (long i = 0; i < n; i++) Rn[i] += R[i];
+      double lnorm = nrm2(Rn, n);
+      for (long i = 0; i < n; i++) d[i] += dl[i]; /* basic line search: full step */
+      double rprev = rk;
+      rk = om_residual(m, d, R);
+      nit = k;
+      if (k < OM_HIST) res_hist[k] = rk;
+      if (!isfinite(rk)) { status = 3; goto out; }
+      if (rk <= tol * r0) { status = 0; goto out; }
+      if (rk > dtol * r0) { status = 1; goto out; }
+      if (method == 1) {
+        /* Eisenstat-Walker choice 1: eta = | ||R_k|| - ||R_{k-1} + K delta|| | / ||R_{k-1}||,
+         * safeguard eta >= eta_prev^((1+sqrt5)/2) when that exceeds 0.1, cap ew_rtolmax.
+         * (Reading of the garbled formula of the paper.) */
+        eta_prev = eta;
+        eta = fabs(rk - lnorm) / rprev;
+        double st = pow(eta_prev, alpha2);
+        if (st > 0.1) eta = fmax(eta, st);
+        eta = fmin(eta, ewmax);
+      }
+    }
+    status = 2;
+    goto out;
+  } else {
+    /* B / iB: K assembled once at d_0; H0 = preconditioner (B) or GMRES (iB) */
+    om_tangent(m, d);
+    assemblies = 1;
+    double* S = (double*)xcalloc((size_t)mm * n, sizeof(double));
+    double* Y = (double*)xcalloc((size_t)mm * n, sizeof(double));
+    double* rho = (double*)xcalloc(mm, sizeof(double));
+    int np = 0;
+    for (int k = 1; k <= max_it; k++) {
+      long long lit0 = m->lit;
+      twoloop(m, S, Y, rho, np, R, t, method == 2 ? 0 : 2, ksp_rtol, ksp_atol, restart, kmaxit);
+      if (k < OM_HIST) {
+        lit_hist[k] = (double)(m->lit - lit0);
+        eta_hist[k] = method == 2 ? 0.0 : ksp_rtol;
+      }
+      for (long i = 0; i < n; i++) {
+        dl[i] = -t[i];
+        d[i] += dl[i];
+      }
+      rk = om_residual(m, d, Rn);
+      nit = k;
+      if (k < OM_HIST) res_hist[k] = rk;
+      /* secant pair s = delta, y = R_{k+1} - R_k, rho = 1/(y.s), skipped when y.s <= 0 */
+      for (long i = 0; i < n; i++) t[i] = Rn[i] - R[i];
+      double ys = dot(t, dl, n);
+      if (ys > 0.0) {
+        if (np == mm) {
+          memmove(S, S + n, sizeof(double) * (size_t)(mm - 1) * n);
+          memmove(Y, Y + n, sizeof(double) * (size_t)(mm - 1) * n);
+          memmove(rho, rho + 1, sizeof(double) * (mm - 1));
+          np--;
+        }
+        memcpy(S + (size_t)np * n, dl, sizeof(double) * n);
+        memcpy(Y + (size_t)np * n, t, sizeof(double) * n);
+        rho[np] = 1.0 / ys;
+        np++;
+      }
+      memcpy(R, Rn, sizeof(double) * n);
+      if (!isfinite(rk)) { status = 3; break; }
+      if (rk <= tol * r0) { status = 0; break; }
+      if (rk > dtol * r0) { status = 1; break; }
+      status = 2;
+    }
+    free(S);
+    free(Y);
+    free(rho);
+  }
+out:
+  stats[0] = status;
+  stats[1] = nit;
+  stats[2] = (double)m->lit;
+  stats[3] = assemblies;
+  stats[4] = r0;
+  stats[5] = rk;
+  free(R);
+  free(Rn);
+  free(dl);
+  free(t);
+  return status;
+}

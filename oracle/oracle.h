@@ -1,0 +1,67 @@
+/*
+ * oracle.h -- plain, slow, single-threaded FP64 CPU oracle of the
+ * paper's nonlinear-elasticity solver hot path (arxiv 2203.05610).
+ *
+ * TEST INFRASTRUCTURE ONLY.  Only the tests, the smoke check and the CPU
+ * baseline leg of the benchmark may call this code.  It shares no code,
+ * header or table with the CUDA library; both consume the same synthetic
+ * inputs.  Every function follows the paper's definitions step by step
+ * with plain loops, in the paper's order, so that it can be checked by eye.
+ *
+ * Material parameter array matp[12]:
+ *   [0] kind (0 Cook neo-Hookean, 1 Taylor-Hood neo-Hookean, 2 Guccione)
+ *   [1] vol_literal  [2] E  [3] nu  [4] mu  [5] C  [6] bf  [7] bt  [8] bfs
+ *   [9] kappa  [10] Ta_peak  [11] period
+ * Dirichlet group array groups[ngroups][8]:
+ *   mask, center x, y, z, angle, translation x, y, z
+ * Solver option array opts[10]:
+ *   precision(ignored: FP64), ksp_rtol, ksp_atol, ew_rtol0, ew_rtolmax,
+ *   ksp_restart, ksp_max_it, lbfgs_m, dtol, apply_dirichlet
+ * Stats array (6 + 3*OM_HIST doubles):
+ *   status, nit, lit_total, assemblies, r0, rfinal,
+ *   res_hist[OM_HIST], lit_hist[OM_HIST], eta_hist[OM_HIST]
+ */
+#ifndef ORACLE_H
+#define ORACLE_H
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define OM_HIST 1024
+
+typedef struct om_mesh om_mesh;
+
+om_mesh* om_create(int order, int pressure_order, int nv, int ne, const double* coords,
+                   const int* tets, const unsigned char* dir_group, int ngroups,
+                   const double* groups, int nf, const int* faces, const int* face_kind,
+                   const double* face_data, const double* matp, const double* fibers);
+void om_destroy(om_mesh* m);
+/* out: nn, np, ndof, nnzb, nnz_up, ncolors, nen */
+void om_info(const om_mesh* m, long long* out);
+void om_topology(const om_mesh* m, int* conn, int* colors, int* row_ptr, int* col, double* X);
+void om_set_load(om_mesh* m, double load, double time);
+void om_apply_dirichlet(const om_mesh* m, double* d);
+double om_residual(om_mesh* m, const double* d, double* r);
+double om_energy(om_mesh* m, const double* d);
+void om_tangent(om_mesh* m, const double* d);
+void om_tangent_copy(const om_mesh* m, double* val, double* bup, double* dinv);
+void om_spmv(const om_mesh* m, const double* x, double* y);
+void om_pc(const om_mesh* m, const double* x, double* y);
+int om_gmres(om_mesh* m, const double* b, double* x, double rtol, double atol, int restart,
+             int max_it, double* res_out);
+int om_solve(om_mesh* m, int method, double tol, int max_it, double* d, const double* opts,
+             double* stats);
+void om_lbfgs_apply(om_mesh* m, const double* S, const double* Y, const double* rho, int k,
+                    const double* q, double* z, int h0);
+
+/* pointwise pieces, exposed for the pins */
+void om_material(const double* matp, const double* F, const double* fib, double gamma, double p,
+                 double* psi, double* P, double* A, double* dPdp);
+int om_tet_rule(int order, double* lam, double* w);   /* barycentric points, weights (sum 1) */
+int om_tri_rule(double* lam, double* w);              /* degree-4 triangle rule, weights sum 1 */
+unsigned long long om_splitmix64(unsigned long long x);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

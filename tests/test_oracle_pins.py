@@ -1,0 +1,557 @@
+"""Pins of the CPU oracle against what the paper and the mathematics fix.
+
+Each test checks the oracle against something other than itself: closed
+forms, invariants, brute force on tiny inputs, finite differences, dense
+library solves, or a published value (tests/golden).  Citations name the
+section or equation of arxiv 2203.05610 the property follows from.
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+
+import oracle as O
+import workloads as W
+from oracle_helpers import oracle_dense_K, rotation, small_cases, strip_bc
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+# ---------------------------------------------------------------- hashing
+def test_splitmix64_published_value():
+    # priority hash of the colouring (reading; Vigna's splitmix64)
+    with open(os.path.join(GOLDEN, "splitmix64.txt")) as f:
+        rows = [l.split() for l in f if l.strip() and not l.startswith("#")]
+    for x, v in rows:
+        assert O.splitmix64(int(x)) == int(v, 16)
+
+
+# ---------------------------------------------------------------- quadrature
+def _bary_moment(alpha, dim):
+    # int over the reference simplex of prod lambda_i^alpha_i / |simplex|
+    num = np.prod([math.factorial(a) for a in alpha]) * math.factorial(dim)
+    return num / math.factorial(sum(alpha) + dim)
+
+
+def test_tet_rules_exact():
+    for order, deg in ((1, 1), (2, 2)):
+        lam, w = O.tet_rule(order)
+        assert abs(w.sum() - 1.0) < 1e-15
+        for alpha in np.ndindex(deg + 1, deg + 1, deg + 1, deg + 1):
+            if sum(alpha) > deg:
+                continue
+            q = (w * np.prod(lam ** np.array(alpha), axis=1)).sum()
+            assert abs(q - _bary_moment(alpha, 3)) < 1e-14
+
+
+def test_tri_rule_degree4():
+    lam, w = O.tri_rule()
+    for alpha in np.ndindex(5, 5, 5):
+        if sum(alpha) > 4:
+            continue
+        q = (w * np.prod(lam ** np.array(alpha), axis=1)).sum()
+        assert abs(q - _bary_moment(alpha, 2)) < 1e-13
+
+
+# ---------------------------------------------------------------- mesh
+def test_cook_config1_counts():
+    w = W.cook(8, 8, 2)
+    m = O.Mesh(w)
+    assert (m.ne, m.nn, m.ndof, m.nnzb) == (768, 243, 729, 2647)
+    v = W.signed_volumes(w["coords"], w["tets"])
+    assert (v > 0).all() and abs(v.sum() - 14400.0) < 1e-9
+
+
+def _brute_pattern(conn, nn):
+    rows = [set() for _ in range(nn)]
+    for e in conn:
+        for a in e:
+            rows[a].update(int(b) for b in e)
+    return rows
+
+
+@pytest.mark.parametrize("order", [1, 2])
+def test_topology_bruteforce(order):
+    w = W.cook(3, 2, 2, order=order)
+    m = O.Mesh(w)
+    t = m.topology()
+    conn = t["conn"]
+    tets = w["tets"]
+    nv = w["coords"].shape[0]
+    assert (conn[:, :4] == tets).all()
+    if order == 2:
+        edges = sorted({(min(a, b), max(a, b)) for e in tets
+                        for a, b in ((e[0], e[1]), (e[0], e[2]), (e[0], e[3]),
+                                     (e[1], e[2]), (e[1], e[3]), (e[2], e[3]))})
+        assert m.nn == nv + len(edges)
+        eid = {e: nv + k for k, e in enumerate(edges)}
+        loc = [(0, 1), (0, 2), (0, 3), (1, 2), (1, 3), (2, 3)]
+        for e in range(m.ne):
+            for k, (a, b) in enumerate(loc):
+                va, vb = tets[e, a], tets[e, b]
+                node = eid[(min(va, vb), max(va, vb))]
+                assert conn[e, 4 + k] == node
+                assert np.allclose(t["X"][node], 0.5 * (w["coords"][va] + w["coords"][vb]))
+    rows = _brute_pattern(conn, m.nn)
+    assert m.nnzb == sum(len(r) for r in rows)
+    for a in range(m.nn):
+        cols = t["col"][t["row_ptr"][a]:t["row_ptr"][a + 1]]
+        assert list(cols) == sorted(rows[a])
+        for b in cols:  # symmetric pattern
+            assert a in rows[b]
+
+
+def test_colouring_is_first_fit_greedy():
+    w = W.cook(4, 4, 3)
+    m = O.Mesh(w)
+    col = m.topology()["colors"]
+    tets = w["tets"]
+    nv = w["coords"].shape[0]
+    vel = [[] for _ in range(nv)]
+    for e, t in enumerate(tets):
+        for v in t:
+            vel[v].append(e)
+    pri = [(O.splitmix64(e), e) for e in range(m.ne)]
+    rank = {e: r for r, (_, e) in enumerate(sorted(pri, key=lambda p: (-p[0], p[1])))}
+    maxval = max(len(v) for v in vel)
+    assert m.ncolors >= maxval
+    for e, t in enumerate(tets):
+        nb = {f for v in t for f in vel[v] if f != e}
+        assert all(col[f] != col[e] for f in nb)  # proper colouring
+        earlier = {col[f] for f in nb if rank[f] < rank[e]}
+        # first fit: every smaller colour is taken by an earlier neighbour
+        assert all(c in earlier for c in range(col[e]))
+
+
+# ---------------------------------------------------------------- materials
+MATS = {
+    "cook": dict(kind=W.MAT_COOK_NH, E=1.0, nu=0.49),
+    "cook_literal": dict(kind=W.MAT_COOK_NH, E=3.0, nu=0.3, vol_literal=1),
+    "th": dict(kind=W.MAT_TH_NH, mu=1.0),
+    "gucc": dict(kind=W.MAT_GUCCIONE, C=0.88, bf=18.5, bt=3.58, bfs=1.63, kappa=1e3,
+                 Ta_peak=60.0, period=0.8),
+}
+
+
+def _rand_F(rng, scale=0.15):
+    return np.eye(3) + scale * rng.standard_normal((3, 3))
+
+
+def _fib(rng):
+    q, _ = np.linalg.qr(rng.standard_normal((3, 3)))
+    return q.T  # rows f, s, n orthonormal
+
+
+@pytest.mark.parametrize("name", list(MATS))
+def test_material_derivatives(name):
+    # P = dPsi/dF (Section "The hyperelasticity problem"), A = dP/dF
+    rng = np.random.default_rng(1)
+    mat = MATS[name]
+    for trial in range(4):
+        F = _rand_F(rng)
+        fib = _fib(rng)
+        gam, p = (7.0 if name == "gucc" else 0.0), (0.3 if name == "th" else 0.0)
+        psi, P, A, dPdp = O.material_point(mat, F, fib, gam, p)
+        h = 1e-6
+        Pfd = np.zeros((3, 3))
+        Afd = np.zeros((9, 9))
+        for k in range(3):
+            for L in range(3):
+                E = np.zeros((3, 3)); E[k, L] = h
+                pp, Pp, _, _ = O.material_point(mat, F + E, fib, gam, p)
+                pm, Pm, _, _ = O.material_point(mat, F - E, fib, gam, p)
+                Pfd[k, L] = (pp - pm) / (2 * h)
+                Afd[:, 3 * k + L] = ((Pp - Pm) / (2 * h)).reshape(9)
+        assert np.abs(P - Pfd).max() <= 1e-6 * max(1.0, np.abs(P).max())
+        assert np.abs(A - Afd).max() <= 1e-6 * max(1.0, np.abs(A).max())
+        assert np.abs(A - A.T).max() <= 1e-9 * max(1.0, np.abs(A).max())  # major symmetry
+        if name == "th":
+            _, Pp, _, _ = O.material_point(mat, F, fib, gam, p + h)
+            _, Pm, _, _ = O.material_point(mat, F, fib, gam, p - h)
+            assert np.abs((Pp - Pm) / (2 * h) - dPdp).max() < 1e-8
+
+
+@pytest.mark.parametrize("name", list(MATS))
+def test_material_frame_indifference(name):
+    rng = np.random.default_rng(2)
+    mat = MATS[name]
+    F = _rand_F(rng)
+    fib = _fib(rng)
+    Q = rotation([1, 2, 3], 0.7)
+    psi, P, _, _ = O.material_point(mat, F, fib, 5.0, 0.2)
+    psiq, Pq, _, _ = O.material_point(mat, Q @ F, fib, 5.0, 0.2)
+    assert abs(psi - psiq) < 1e-10 * max(1, abs(psi))
+    assert np.abs(Q @ P - Pq).max() < 1e-10 * max(1, np.abs(P).max())
+
+
+def test_cook_tangent_at_identity_is_linear_elastic():
+    # with the kappa/4 reading the Cook potential linearises to (lambda, mu)
+    E, nu = 2.0, 0.3
+    mu = E / (2 * (1 + nu)); lam = 2 * mu * nu / (1 - 2 * nu)
+    _, P, A, _ = O.material_point(dict(kind=0, E=E, nu=nu), np.eye(3))
+    d = np.eye(3)
+    C = (mu * (np.einsum("ik,JL->iJkL", d, d) + np.einsum("iL,kJ->iJkL", d, d))
+         + lam * np.einsum("iJ,kL->iJkL", d, d))
+    assert np.abs(P).max() < 1e-14
+    assert np.abs(A - C.reshape(9, 9)).max() < 1e-12
+
+
+# ---------------------------------------------------------------- assembly
+@pytest.mark.parametrize("case", list(small_cases()))
+def test_residual_zero_at_rest(case):
+    w = small_cases()[case]
+    m = O.Mesh(w)
+    m.set_load(0.0, 0.0)  # no traction, pressure, rotation or activation
+    _, n = m.residual(np.zeros(m.ndof))
+    assert n < 1e-13
+
+
+@pytest.mark.parametrize("case", ["cook_p1", "cook_p2", "heart_p1"])
+def test_residual_frame_indifference(case):
+    w = strip_bc(small_cases()[case])
+    m = O.Mesh(w)
+    m.set_load(0.0, 0.0)
+    X = m.topology()["X"]
+    Q = rotation([0.3, -1.0, 0.5], 0.9)
+    d = (X @ Q.T - X).reshape(-1)
+    _, n = m.residual(d)
+    assert n < 1e-10 * max(1.0, np.abs(X).max())
+
+
+@pytest.mark.parametrize("case", ["cook_p1", "cook_p2", "twist_up"])
+def test_patch_test_affine(case):
+    # affine displacement -> constant F -> constant P: interior residual zero
+    w = strip_bc(small_cases()[case])
+    m = O.Mesh(w)
+    m.set_load(0.0, 0.0)
+    X = m.topology()["X"]
+    G = np.array([[0.05, 0.02, -0.01], [0.03, -0.04, 0.02], [0.0, 0.01, 0.06]])
+    d = np.zeros(m.ndof)
+    d[: 3 * m.nn] = (X @ G.T + np.array([0.1, -0.2, 0.3])).reshape(-1)
+    r, _ = m.residual(d)
+    bnd = np.zeros(m.nn, dtype=bool)
+    bf = W.boundary_faces(w["coords"], w["tets"])
+    bnd[np.unique(bf)] = True
+    if m.nen == 10:
+        conn = m.topology()["conn"]
+        loc = [(0, 1), (0, 2), (0, 3), (1, 2), (1, 3), (2, 3)]
+        bset = set(map(int, np.unique(bf)))
+        faceset = {tuple(sorted(f)) for f in bf}
+        for e in range(m.ne):
+            for k, (a, b) in enumerate(loc):
+                va, vb = conn[e, a], conn[e, b]
+                if any(va in f and vb in f for f in faceset if va in bset and vb in bset):
+                    bnd[conn[e, 4 + k]] = True
+    ru = r[: 3 * m.nn].reshape(-1, 3)
+    scale = np.abs(r).max()
+    assert scale > 1e-6
+    assert np.abs(ru[~bnd]).max() < 1e-12 * max(1.0, scale)
+
+
+def test_small_strain_K0_equals_linear_elastic_P1():
+    # K(0) = sum_e V_e B_e^T D B_e (textbook linear elasticity, Voigt form)
+    w = strip_bc(W.cook(2, 2, 1))
+    E, nu = 1.0, 0.49
+    m = O.Mesh(w)
+    m.set_load(0.0)
+    m.tangent(np.zeros(m.ndof))
+    K = oracle_dense_K(m, w)
+    mu = E / (2 * (1 + nu)); lam = 2 * mu * nu / (1 - 2 * nu)
+    D = lam * np.outer([1, 1, 1, 0, 0, 0], [1, 1, 1, 0, 0, 0]) + mu * np.diag([2, 2, 2, 1, 1, 1])
+    Kref = np.zeros_like(K)
+    X = w["coords"]
+    for t in w["tets"]:
+        M = np.ones((4, 4)); M[:, 1:] = X[t]
+        C = np.linalg.inv(M)  # rows: coefficients of the barycentric functions
+        g = C[1:, :].T  # gradients [4][3]
+        V = abs(np.linalg.det(M)) / 6
+        B = np.zeros((6, 12))
+        for a in range(4):
+            gx, gy, gz = g[a]
+            B[:, 3 * a:3 * a + 3] = [[gx, 0, 0], [0, gy, 0], [0, 0, gz],
+                                     [gy, gx, 0], [0, gz, gy], [gz, 0, gx]]
+        idx = np.concatenate([[3 * v, 3 * v + 1, 3 * v + 2] for v in t])
+        Kref[np.ix_(idx, idx)] += V * B.T @ D @ B
+    assert np.abs(K - Kref).max() < 1e-12 * np.abs(Kref).max()
+
+
+def _state(m, w, case, rng):
+    load, time = {"heart_p1": (0.7, 0.15)}.get(case, (0.6, 0.0))
+    m.set_load(load, time)
+    d = 0.02 * rng.standard_normal(m.ndof)
+    if case.startswith("cook"):
+        d *= 10.0
+    m.apply_dirichlet(d)
+    return d
+
+
+@pytest.mark.parametrize("case", list(small_cases()))
+def test_tangent_matches_fd_and_is_symmetric(case):
+    # Eq. "newton": K = dR/dd; dead loads keep it symmetric
+    w = small_cases()[case]
+    m = O.Mesh(w)
+    rng = np.random.default_rng(3)
+    d = _state(m, w, case, rng)
+    m.tangent(d)
+    K = oracle_dense_K(m, w)
+    assert np.abs(K - K.T).max() <= 1e-10 * np.abs(K).max()
+    # random direction vanishing at prescribed components
+    load, time = {"heart_p1": (0.7, 0.15)}.get(case, (0.6, 0.0))
+    probe = np.full(m.ndof, 3.25)
+    m.apply_dirichlet(probe)
+    free = probe == 3.25
+    e = rng.standard_normal(m.ndof) * free
+    h = 1e-6
+    rp, _ = m.residual(d + h * e)
+    rm, _ = m.residual(d - h * e)
+    fd = (rp - rm) / (2 * h)
+    Ke = K @ e
+    assert np.linalg.norm(Ke - fd) <= 1e-6 * np.linalg.norm(Ke)
+    del load, time
+
+
+@pytest.mark.parametrize("case", list(small_cases()))
+def test_residual_is_energy_gradient(case):
+    # R = dPi/dd (Eq. "minimization"), for free components
+    w = small_cases()[case]
+    m = O.Mesh(w)
+    rng = np.random.default_rng(4)
+    d = _state(m, w, case, rng)
+    r, _ = m.residual(d)
+    probe = np.full(m.ndof, 3.25)
+    m.apply_dirichlet(probe)
+    free = probe == 3.25
+    for trial in range(3):
+        e = rng.standard_normal(m.ndof) * free
+        h = 1e-6
+        fd = (m.energy(d + h * e) - m.energy(d - h * e)) / (2 * h)
+        assert abs(fd - r @ e) <= 1e-6 * max(1.0, abs(r @ e))
+
+
+def test_cook_total_traction():
+    # total load t A = (1/16) * (16 * 10) = 10 in y; P2: vertex 0, edge t A/3
+    for order in (1, 2):
+        w = W.cook(4, 4, 2, order=order)
+        m = O.Mesh(w)
+        m.set_load(1.0)
+        r, _ = m.residual(np.zeros(m.ndof))
+        ry = r[1::3][: m.nn]
+        assert abs(ry.sum() + 10.0) < 1e-12
+        assert np.abs(r[0::3]).max() < 1e-15 and np.abs(r[2::3]).max() < 1e-15
+        if order == 2:
+            nv = w["coords"].shape[0]
+            assert np.abs(ry[:nv]).max() < 1e-14
+            conn = m.topology()["conn"]
+            loc = [(0, 1), (0, 2), (0, 3), (1, 2), (1, 3), (2, 3)]
+            enode = {}
+            for e in range(m.ne):
+                for k, (a, b) in enumerate(loc):
+                    va, vb = conn[e, a], conn[e, b]
+                    enode[(min(va, vb), max(va, vb))] = conn[e, 4 + k]
+            expect = np.zeros(m.nn)
+            x = w["coords"][w["faces"]]
+            areas = 0.5 * np.linalg.norm(np.cross(x[:, 1] - x[:, 0], x[:, 2] - x[:, 0]), axis=1)
+            for f, A in zip(w["faces"], areas):
+                for a, b in ((0, 1), (1, 2), (0, 2)):
+                    expect[enode[(min(f[a], f[b]), max(f[a], f[b]))]] -= A / 16.0 / 3.0
+            assert np.abs(ry - expect).max() < 1e-14
+
+
+# ---------------------------------------------------------------- linear solvers
+def _cook_small_tangent(order=1):
+    w = W.cook(3, 3, 1, order=order)
+    m = O.Mesh(w)
+    m.set_load(1.0)
+    d = m.apply_dirichlet(np.zeros(m.ndof))
+    m.tangent(d)
+    return w, m
+
+
+def test_gmres_matches_dense_solve():
+    w, m = _cook_small_tangent()
+    K = oracle_dense_K(m, w)
+    rng = np.random.default_rng(5)
+    b = rng.standard_normal(m.ndof)
+    x, it, res = m.gmres(b, rtol=1e-13, atol=0.0, restart=m.ndof, max_it=10 * m.ndof)
+    xd = np.linalg.solve(K, b)
+    assert np.linalg.norm(x - xd) <= 1e-8 * np.linalg.norm(xd)
+    assert it <= 2 * m.ndof
+    assert np.linalg.norm(b - K @ x) <= 1e-12 * np.linalg.norm(b) * 10
+
+
+def test_gmres_restarted_reaches_target():
+    w, m = _cook_small_tangent()
+    K = oracle_dense_K(m, w)
+    b = np.random.default_rng(6).standard_normal(m.ndof)
+    x, it, res = m.gmres(b, rtol=1e-8, atol=0.0, restart=20, max_it=20000)
+    true = np.linalg.norm(b - K @ x)
+    assert true <= 1.01e-8 * np.linalg.norm(b) * 1.5
+    assert abs(true - res) <= 1e-6 * np.linalg.norm(b)
+
+
+def test_block_jacobi_and_schur():
+    w = small_cases()["twist_up"]
+    m = O.Mesh(w)
+    m.set_load(0.5)
+    d = m.apply_dirichlet(np.zeros(m.ndof))
+    d[3 * m.nn:] = 0.05
+    m.tangent(d)
+    K = oracle_dense_K(m, w)
+    _, _, dinv = m.tangent_copy()
+    nn = m.nn
+    for a in range(nn):
+        Db = K[3 * a:3 * a + 3, 3 * a:3 * a + 3]
+        assert np.abs(dinv[a] @ Db - np.eye(3)).max() < 1e-10
+    # lower Schur with SIMPLE diagonal: z_u = D^{-1} x_u; z_p = (x_p - B2 z_u)/S_diag
+    rng = np.random.default_rng(7)
+    x = rng.standard_normal(m.ndof)
+    zu = np.concatenate([dinv[a] @ x[3 * a:3 * a + 3] for a in range(nn)])
+    B1 = K[: 3 * nn, 3 * nn:]
+    B2 = K[3 * nn:, : 3 * nn]
+    Sd = -np.einsum("iv,i,iv->v", B1, 1.0 / np.diag(K)[: 3 * nn], B1)
+    zp = (x[3 * nn:] - B2 @ zu) / Sd
+    z = m.pc(x)
+    assert np.abs(z - np.concatenate([zu, zp])).max() <= 1e-10 * np.abs(z).max()
+    assert np.abs(B1 - B2.T).max() == 0.0
+    assert np.abs(K[3 * nn:, 3 * nn:]).max() == 0.0  # C = 0 (Taylor-Hood)
+
+
+def _bfgs_dense(H0, pairs):
+    # the paper's update: H+ = (I - rho s y^T) H (I - rho y s^T) + rho s s^T
+    H = H0.copy()
+    n = H.shape[0]
+    for s, y in pairs:
+        rho = 1.0 / (y @ s)
+        V = np.eye(n) - rho * np.outer(y, s)
+        H = V.T @ H @ V + rho * np.outer(s, s)
+    return H
+
+
+def test_twoloop_equals_dense_bfgs_update():
+    w = W.cook(1, 1, 1)
+    m = O.Mesh(w)
+    m.set_load(1.0)
+    d = m.apply_dirichlet(np.zeros(m.ndof))
+    m.tangent(d)
+    n = m.ndof
+    assert n <= 60
+    rng = np.random.default_rng(8)
+    A = rng.standard_normal((n, n))
+    A = A @ A.T + n * np.eye(n)
+    pairs = []
+    for _ in range(6):
+        s = rng.standard_normal(n)
+        pairs.append((s, A @ s))
+    S = np.array([p[0] for p in pairs]); Y = np.array([p[1] for p in pairs])
+    rho = 1.0 / np.einsum("ij,ij->i", S, Y)
+    q = rng.standard_normal(n)
+    for h0 in (1, 0):
+        if h0 == 1:
+            H0 = np.eye(n)
+        else:
+            _, _, dinv = m.tangent_copy()
+            H0 = np.zeros((n, n))
+            for a in range(m.nn):
+                H0[3 * a:3 * a + 3, 3 * a:3 * a + 3] = dinv[a]
+        Hd = _bfgs_dense(H0, pairs)
+        z = m.lbfgs_apply(S, Y, rho, q, h0=h0)
+        assert np.abs(z - Hd @ q).max() <= 1e-12 * np.abs(Hd @ q).max()
+        # secant equation for the newest pair: H y = s
+        zs = m.lbfgs_apply(S, Y, rho, Y[-1], h0=h0)
+        assert np.abs(zs - S[-1]).max() <= 1e-10 * np.abs(S[-1]).max()
+
+
+# ---------------------------------------------------------------- nonlinear solvers
+def _cook_solve(method, order=1, load=0.2, opts=None, tol=1e-8, n=(4, 4, 2), nu=0.3,
+                max_it=None):
+    w = W.cook(*n, order=order, nu=nu)
+    m = O.Mesh(w)
+    m.set_load(load)
+    d, st = m.solve(method, np.zeros(m.ndof), tol=tol, opts=opts, max_it=max_it)
+    return m, d, st
+
+
+def test_nk_quadratic_convergence():
+    # Newton converges quadratically near the solution (paper, Section "Theory")
+    _, _, st = _cook_solve("NK", opts=dict(ksp_rtol=1e-13, ksp_atol=0.0), tol=1e-12, load=0.6)
+    r = st["res_hist"]
+    assert st["status"] == 0
+    ratios = [r[k + 1] / r[k] ** 2 for k in range(len(r) - 1) if r[k + 1] > 1e-11 * r[0]
+              and r[k] < 1e-2 * r[0]]
+    assert ratios, r
+    assert max(ratios) < 50.0 / r[0]
+
+
+def test_all_methods_converge_and_agree():
+    sols = {}
+    for mth in ("NK", "iNK", "B", "iB"):
+        # atol 0: the Appendix A absolute tolerances would stop the Krylov
+        # solver before the 1e-12 relative nonlinear target
+        m, d, st = _cook_solve(mth, tol=1e-12, opts=dict(ksp_atol=0.0))
+        assert st["status"] == 0, (mth, st["res_hist"][-5:])
+        sols[mth] = d
+        if mth in ("B", "iB"):
+            assert st["assemblies"] == 1  # one Hessian assembly (Section "Numerical solvers")
+    for mth in ("iNK", "B", "iB"):
+        assert np.linalg.norm(sols[mth] - sols["NK"]) <= 1e-8 * np.linalg.norm(sols["NK"])
+
+
+def test_ink_forcing_bounded():
+    _, _, st = _cook_solve("iNK", load=0.6)
+    assert st["status"] == 0
+    eta = st["eta_hist"][1:]
+    assert abs(eta[0] - 0.1) < 1e-15 and (eta <= 0.1 + 1e-15).all() and (eta >= 0).all()
+
+
+def test_ib_first_step_is_newton_step():
+    # with an (almost) exact H0 = K(d_0)^{-1}, the first BFGS step is the Newton step
+    o = dict(ksp_rtol=1e-13, ksp_atol=0.0)
+    m1, d1, st1 = _cook_solve("NK", opts=o, load=0.6, max_it=1)
+    m2, d2, st2 = _cook_solve("iB", opts=o, load=0.6, max_it=1)
+    assert st1["nit"] == 1 and st2["nit"] == 1
+    assert np.linalg.norm(d1 - d2) <= 1e-9 * np.linalg.norm(d1)
+
+
+def test_small_load_linear_limit():
+    w = W.cook(3, 3, 1)
+    m = O.Mesh(w)
+    eps = 1e-6
+    m.set_load(eps)
+    d, st = m.solve("NK", np.zeros(m.ndof), tol=1e-12, opts=dict(ksp_rtol=1e-13, ksp_atol=0.0))
+    m.tangent(np.zeros(m.ndof))
+    r0, _ = m.residual(np.zeros(m.ndof))
+    from oracle_helpers import oracle_dense_K as odk
+    K0 = odk(m, w)
+    dlin = np.linalg.solve(K0, -r0)
+    assert np.linalg.norm(d - dlin) <= 10 * eps * np.linalg.norm(dlin)
+
+
+def test_rigid_rotation_patch_solve():
+    # every boundary vertex prescribed by a rigid rotation: the solution is
+    # that rotation everywhere (stress free), reproduced by the solver
+    w = W.twist(2, order=1, pressure=False)
+    w = strip_bc(w)
+    bf = np.unique(W.boundary_faces(w["coords"], w["tets"]))
+    w["dir_group"][bf] = 1
+    w["groups"] = [dict(mask=7, center=(0.5, 0.5, 0.0), angle=0.4, translation=(0.1, 0.0, 0.2))]
+    m = O.Mesh(w)
+    m.set_load(1.0)
+    d, st = m.solve("NK", np.zeros(m.ndof), tol=1e-12, opts=dict(ksp_rtol=1e-12, ksp_atol=0.0))
+    assert st["status"] == 0
+    X = w["coords"]
+    th = 0.4
+    R = np.array([[np.cos(th), -np.sin(th), 0], [np.sin(th), np.cos(th), 0], [0, 0, 1]])
+    c = np.array([0.5, 0.5, 0.0])
+    exact = ((X - c) @ R.T + c + np.array([0.1, 0.0, 0.2]) - X).reshape(-1)
+    assert np.abs(d - exact).max() < 1e-9
+
+
+def test_large_config_counts():
+    # Cook P2 64x64x8 and twist 32^3 Taylor-Hood: tets, nodes, DoF, blocks
+    w = W.cook(64, 64, 8, order=2)
+    m = O.Mesh(w)
+    assert (m.ne, m.nn, m.ndof, m.nnzb) == (196608, 282897, 848691, 7773249)
+    w = W.twist(32, order=2)
+    m = O.Mesh(w)
+    assert (m.nn, m.np_, m.ndof, m.nnzb) == (274625, 35937, 859812, 7678721)
