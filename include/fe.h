@@ -255,6 +255,33 @@ int fe_gmres(fe_mesh m, const double* b, double* x, double rtol, double atol,
 int fe_lbfgs_apply(fe_mesh m, const double* S, const double* Y, const double* rho,
                    int k, const double* q, double* z, int h0);
 
+/* ---- instrumentation ----------------------------------------------------
+ * Measurement support (no counterpart in the paper).  Every kernel launch
+ * of the library is counted per class; with timing on, each launch is also
+ * bracketed by CUDA events on the mesh's stream and credited with the
+ * algorithmic bytes it must move (inputs read once, outputs written once). */
+#define FE_PROF_CLASSES 8
+enum {
+  FE_PROF_RESIDUAL = 0, /* element residual + node gather */
+  FE_PROF_TANGENT = 1,  /* coloured tangent assembly, springs, diagonal inverse */
+  FE_PROF_SPMV = 2,     /* block-CSR SpMV */
+  FE_PROF_PC = 3,       /* block-Jacobi / Schur preconditioner */
+  FE_PROF_ARNOLDI = 4,  /* persistent MGS Arnoldi step */
+  FE_PROF_TWOLOOP = 5,  /* L-BFGS two-loop recursion */
+  FE_PROF_VECTOR = 6,   /* dots, axpys, copies, GMRES update */
+  FE_PROF_OTHER = 7
+};
+typedef struct {
+  int64_t launches[FE_PROF_CLASSES]; /* kernel launches since the last reset */
+  int64_t timed[FE_PROF_CLASSES];    /* launches timed with events */
+  double ms[FE_PROF_CLASSES];        /* summed event time of the timed launches */
+  double bytes[FE_PROF_CLASSES];     /* summed algorithmic bytes of the timed launches */
+} fe_profile_info;
+/* Zero the counters; timing = 1 also times every launch with CUDA events. */
+int fe_profile_reset(fe_mesh m, int timing);
+/* Synchronise the stream and read the counters (host out). */
+int fe_profile_read(fe_mesh m, fe_profile_info* out);
+
 /* Thread-local message describing the last error. */
 const char* fe_last_error(void);
 

@@ -1,0 +1,194 @@
+// fe_internal.h -- internal types shared by the translation units of libfe.so.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/fe.h"
+
+// ---------------------------------------------------------------- errors
+void fe_set_error(const char* fmt, ...);
+#define FE_CUDA(call)                                                                    \
+  do {                                                                                   \
+    cudaError_t e_ = (call);                                                             \
+    if (e_ != cudaSuccess) {                                                             \
+      fe_set_error("%s:%d %s: %s", __FILE__, __LINE__, #call, cudaGetErrorString(e_));   \
+      return FE_ERR_CUDA;                                                                \
+    }                                                                                    \
+  } while (0)
+#define FE_TRY(expr)            \
+  do {                          \
+    int r_ = (expr);            \
+    if (r_ != FE_OK) return r_; \
+  } while (0)
+
+// device error word values (written by kernels, read by the host)
+enum { DEV_OK = 0, DEV_ERR_TIMEOUT = 1, DEV_ERR_BOUNDS = 2, DEV_ERR_COLORS = 3 };
+
+// ---------------------------------------------------------------- material parameters
+struct MatParams {
+  int kind;
+  double mu, cvol;                // COOK_NH (mu, c_vol), TH_NH (mu)
+  double C, bf, bt, bfs, kappa;   // GUCCIONE
+  double gamma;                   // active tension at the current time
+};
+
+// ---------------------------------------------------------------- mesh object
+struct fe_mesh_s {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  int order = 1, pres = 0, nv = 0, ne = 0, nn = 0, np = 0, nen = 4, nq = 1;
+  int64_t ndof = 0;
+  fe_material mat{};
+  double load = 0.0, time = 0.0;
+  MatParams mp{};
+
+  // host copies kept for queries
+  std::vector<int> h_color_start;  // [ncolors+1] offsets into perm
+  int ncolors = 0;
+  int ngroups = 0;
+  std::vector<fe_dirichlet_group> groups;
+
+  // device topology / geometry
+  double* X = nullptr;        // [nn][3]
+  int* conn = nullptr;        // [ne][nen]
+  int* colors = nullptr;      // [ne]
+  int* perm = nullptr;        // [ne] element ids sorted by (colour, id)
+  double* geo = nullptr;      // [ne][10]: grad lambda_1..3 (rows, 9) + volume
+  double* fib = nullptr;      // [ne][9] or null
+  uint8_t* fixmask = nullptr; // [nn] bit c: component c prescribed
+  uint8_t* dgroup = nullptr;  // [nn]
+  fe_dirichlet_group* d_groups = nullptr;
+
+  // displacement block pattern
+  int64_t nnzb = 0;
+  int* row_ptr = nullptr;  // [nn+1]
+  int* col = nullptr;      // [nnzb]
+  int* diag_pos = nullptr; // [nn]
+  int* emap = nullptr;     // [ne][nen*nen]
+  // u-p coupling pattern (u rows, vertex columns) and its transpose
+  int64_t nnz_up = 0;
+  int* up_ptr = nullptr;   // [nn+1]
+  int* up_col = nullptr;   // [nnz_up]
+  int* upmap = nullptr;    // [ne][nen*4]
+  int* pu_ptr = nullptr;   // [np+1]
+  int* pu_col = nullptr;   // [nnz_up] u node of the entry
+  int* pu_src = nullptr;   // [nnz_up] index of the entry in the u-row storage
+
+  // residual gather lists: node -> (element*nen + local) ; vertex -> (element*4 + local)
+  int* node_ptr = nullptr;
+  int* node_list = nullptr;
+  int* vert_ptr = nullptr;
+  int* vert_list = nullptr;
+
+  // boundary data precomputed at creation (constant in d)
+  double* fext1 = nullptr;   // [nn][3] external load at load factor 1
+  int64_t nnz_ks = 0;
+  int* ks_ptr = nullptr;     // [nn+1] spring matrix (Robin faces)
+  int* ks_col = nullptr;
+  double* ks_val = nullptr;  // [nnz_ks][9]
+  int* ks_kpos = nullptr;    // [nnz_ks] block index in the tangent pattern
+
+  // tangent and preconditioner
+  int prec = -1;             // precision of the assembled tangent (-1 none)
+  double* K64 = nullptr;     // [nnzb][9]
+  float* K32 = nullptr;
+  __nv_bfloat16* K16 = nullptr;
+  double* B64 = nullptr;     // [nnz_up][3]
+  float* B32 = nullptr;
+  double* Dinv64 = nullptr;  // [nn][9]
+  float* Dinv32 = nullptr;
+  double* Sd = nullptr;      // [np] SIMPLE Schur diagonal
+
+  // workspace
+  double* rel = nullptr;     // [ne][nen*3] element-local residual contributions
+  double* relp = nullptr;    // [ne][4]
+  double* red = nullptr;     // reduction partials [RED_SLOTS]
+  unsigned* red_ticket = nullptr;
+  double* scal = nullptr;    // device scalars [64]
+  int* err = nullptr;        // device error word
+  unsigned* bar = nullptr;   // grid barrier words [2]
+  double* h_scal = nullptr;  // pinned host mirror [64]
+
+  // solver workspace (lazy)
+  int ws_restart = 0;
+  double* V = nullptr;       // [(restart+1)][ndof]
+  double* H = nullptr;       // [(restart+1)][restart] column-major by step
+  double* gv = nullptr;      // Givens: cs, sn, g, y [4][restart+1]
+  double* w64 = nullptr;     // [ndof]
+  double* t64 = nullptr;     // [ndof]
+  double* u64 = nullptr;     // [ndof]
+  void* zx = nullptr;        // [ndof] SpMV input (FP32 or FP64)
+  int lb_m = 0;
+  double* S = nullptr;       // [m][ndof]
+  double* Yv = nullptr;      // [m][ndof]
+  double* nl_R = nullptr, *nl_Rn = nullptr, *nl_dl = nullptr, *nl_t = nullptr;
+  double* rho_d = nullptr;   // [LBFGS_MAX] curvature scalars 1/(y.s) of the stored pairs
+  double* alpha_d = nullptr; // [LBFGS_MAX] two-loop coefficients alpha_i
+  double* lb_x = nullptr;    // [ndof] GMRES iterate of the inexact-BFGS H0
+
+  // instrumentation
+  int prof_timing = 0;
+  int64_t prof_launches[FE_PROF_CLASSES] = {};
+  int64_t prof_timed[FE_PROF_CLASSES] = {};
+  double prof_ms[FE_PROF_CLASSES] = {};
+  double prof_bytes[FE_PROF_CLASSES] = {};
+  struct ProfRec {
+    int cls;
+    cudaEvent_t a, b;
+    double bytes;
+  };
+  std::vector<ProfRec> prof_pending;
+  std::vector<cudaEvent_t> ev_free;
+
+  int coop_blocks = 0;       // co-resident blocks for the persistent kernels
+  int sm_count = 0;
+  int64_t device_bytes = 0;
+};
+
+constexpr int RED_SLOTS = 16384;
+constexpr int SCAL_N = 64;
+constexpr int LBFGS_MAX = 1000;  // largest number of stored secant pairs
+
+// Counts one kernel launch of class `cls` and, with timing on, brackets it
+// with events on the mesh stream: open the scope, launch, close the scope.
+struct LaunchScope {
+  fe_mesh m;
+  int cls;
+  double bytes;
+  cudaEvent_t a = nullptr;
+  LaunchScope(fe_mesh m_, int cls_, double bytes_);
+  ~LaunchScope();
+};
+#define FE_CAT2(a, b) a##b
+#define FE_CAT(a, b) FE_CAT2(a, b)
+#define FE_SCOPE(m, cls, bytes) LaunchScope FE_CAT(fe_scope_, __LINE__)(m, cls, (double)(bytes))
+
+// allocation helper that tracks the mesh's device footprint
+int fe_alloc(fe_mesh m, void** p, size_t bytes);
+template <class T>
+int fe_alloc_t(fe_mesh m, T** p, size_t count) {
+  return fe_alloc(m, reinterpret_cast<void**>(p), count * sizeof(T));
+}
+int fe_check_device_error(fe_mesh m);  // syncs the stream and reads the error word
+
+// ---------------------------------------------------------------- internal entry points
+// assembly (fe_assemble.cu)
+int fe_residual_dev(fe_mesh m, const double* d, double* r, bool want_norm);  // norm^2 -> scal[0]
+int fe_tangent_dev(fe_mesh m, const double* d, int precision);
+int fe_energy_dev(fe_mesh m, const double* d, double* out);
+// linear algebra (fe_krylov.cu)
+int fe_spmv_dev(fe_mesh m, const double* x, double* y);           // FP64 in/out, current tangent
+int fe_pc_dev(fe_mesh m, const double* x, double* y);             // FP64 in/out
+int fe_gmres_dev(fe_mesh m, const double* b, double* x, double rtol, double atol, int restart,
+                 int max_it, int* iters, double* res);
+int fe_dot_dev(fe_mesh m, const double* a, const double* b, int64_t n, double* out_host);
+int fe_axpby_dev(fe_mesh m, double a, const double* x, double b, double* y, int64_t n);
+int fe_lbfgs_dev(fe_mesh m, const double* S, const double* Y, const double* rho, int head, int mcap,
+                 int k, int64_t ld, const double* q, double* z, int h0, double ksp_rtol,
+                 double ksp_atol, int restart, int kmaxit, int* lit);
+int fe_workspace(fe_mesh m, int restart);

@@ -1,0 +1,944 @@
+// fe_krylov.cu -- block-CSR SpMV, nodal block-Jacobi and lower-Schur
+// preconditioners, reductions, GMRES with modified Gram-Schmidt Arnoldi
+// (paper: GMRES with MGS, Section "Test problems and solvers details"), and
+// the L-BFGS two-loop recursion (Section "Numerical solvers", BFGS method).
+//
+// The Arnoldi step is one persistent cooperative kernel: every thread keeps
+// its slice of w in registers for the whole MGS sweep, so each basis vector
+// v_i is read from HBM exactly once per step; the k sequential inner
+// products are reduced in a fixed order (block tree, then block partials in
+// block order) between bounded grid barriers.  The two-loop recursion uses
+// the same structure with q (or z) held in registers.
+#include <algorithm>
+#include <cmath>
+
+#include "fe_internal.h"
+
+__device__ __forceinline__ double warp_sum(double v) {
+  for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+  return v;
+}
+
+// block sum, result broadcast to all threads
+__device__ __forceinline__ double block_sum_all(double v, double* sh) {
+  v = warp_sum(v);
+  int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  __syncthreads();
+  if (lane == 0) sh[wid] = v;
+  __syncthreads();
+  int nw = blockDim.x >> 5;
+  double t = lane < nw ? sh[lane] : 0.0;
+  t = warp_sum(t);
+  return t;
+}
+
+// sum of the per-block partials in block order (every block gets the same value)
+__device__ __forceinline__ double sum_partials(const double* part, double* sh) {
+  double s = 0.0;
+  for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) s += ((volatile const double*)part)[b];
+  return block_sum_all(s, sh);
+}
+
+// ---------------------------------------------------------------- grid reduction with publish
+// Each block passes its block sum (valid in thread 0).  The last block to
+// arrive adds the partials in block order with one warp (deterministic for a
+// given grid), stores the total in *pub and releases the others; every
+// thread of every block returns the same total in `out`.  The wait is
+// bounded: after ~2^26 polls (seconds) the block records DEV_ERR_TIMEOUT and
+// returns false, and every later wait returns at once, so a launch always ends.
+__device__ __forceinline__ bool grid_reduce(double bsum, double* part, unsigned* bar, double* pub, int* err,
+                                            double& out) {
+  __shared__ int s_last, s_fail;
+  __shared__ unsigned s_gen;
+  __shared__ double s_val;
+  if (threadIdx.x == 0) {
+    s_fail = 0;
+    s_gen = *(volatile unsigned*)(bar + 1);
+    part[blockIdx.x] = bsum;
+    __threadfence();
+    s_last = atomicAdd(bar, 1u) == gridDim.x - 1;
+  }
+  __syncthreads();
+  if (s_last) {
+    if (threadIdx.x < 32) {
+      __threadfence();
+      double s = 0.0;
+      for (int b = threadIdx.x; b < (int)gridDim.x; b += 32) s += ((volatile double*)part)[b];
+      s = warp_sum(s);
+      if (threadIdx.x == 0) {
+        *(volatile double*)pub = s;
+        s_val = s;
+        atomicExch(bar, 0u);
+        __threadfence();
+        atomicAdd(bar + 1, 1u);
+      }
+    }
+  } else if (threadIdx.x == 0) {
+    unsigned spins = 0;
+    while (*(volatile unsigned*)(bar + 1) == s_gen) {
+      if (++spins > (1u << 26) || *(volatile int*)err != DEV_OK) {
+        atomicCAS(err, DEV_OK, DEV_ERR_TIMEOUT);
+        s_fail = 1;
+        break;
+      }
+    }
+    __threadfence();
+    s_val = *(volatile double*)pub;
+  }
+  __syncthreads();
+  out = s_val;
+  return s_fail == 0;
+}
+
+// block sum with the result in thread 0 (others: partial garbage)
+__device__ __forceinline__ double block_sum0(double v, double* sh) {
+  v = warp_sum(v);
+  int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  __syncthreads();
+  if (lane == 0) sh[wid] = v;
+  __syncthreads();
+  double t = 0.0;
+  if (wid == 0) {
+    int nw = blockDim.x >> 5;
+    t = lane < nw ? sh[lane] : 0.0;
+    t = warp_sum(t);
+  }
+  return t;
+}
+
+// ---------------------------------------------------------------- persistent Arnoldi (MGS)
+// Step j.  Block b owns the contiguous slice [b*S, min((b+1)*S, n)) of every
+// vector (S = NPT*blockDim, a multiple of 3 so that slices hold whole nodes);
+// w's slice lives in shared memory for the whole sweep.  For i = 0..j:
+// h_ij = <w, V_i> (one grid reduction), w -= h_ij V_i, with V_{i+1}'s slice
+// loaded into registers before the reduction's wait.  Then h_{j+1,j} = ||w||,
+// V_{j+1} = w / h_{j+1,j}, optionally z = D^{-1} V_{j+1} (nodal block-Jacobi,
+// the preconditioned vector the next SpMV needs), and block 0 applies the
+// previous Givens rotations to column j, forms the new one and updates g.
+template <int NPT, class DT, class ZT>
+__global__ void __launch_bounds__(NPT <= 8 ? 1024 : 512)
+    k_arnoldi(int64_t n, int j, double* __restrict__ V, int64_t ldv, const double* __restrict__ w,
+              double* __restrict__ Hcol, double* part, unsigned* bar, double* pub, int* err,
+              double* __restrict__ cs, double* __restrict__ sn, double* __restrict__ g, double* __restrict__ out,
+              const DT* __restrict__ Dinv, ZT* __restrict__ z) {
+  extern __shared__ __align__(16) double ws[];
+  __shared__ double sh[32];
+  const int64_t S = (int64_t)NPT * blockDim.x;
+  const int64_t base = (int64_t)blockIdx.x * S;
+  const int64_t len = base >= n ? 0 : (n - base < S ? n - base : S);
+  for (int64_t k = threadIdx.x; k < len; k += blockDim.x) ws[k] = w[base + k];
+  double vc[NPT], vn[NPT];
+#pragma unroll
+  for (int s = 0; s < NPT; s++) {
+    int64_t k = threadIdx.x + (int64_t)s * blockDim.x;
+    vc[s] = k < len ? V[base + k] : 0.0;
+  }
+  __syncthreads();
+  for (int i = 0; i <= j; i++) {
+    double loc = 0.0;
+#pragma unroll
+    for (int s = 0; s < NPT; s++) {
+      int64_t k = threadIdx.x + (int64_t)s * blockDim.x;
+      if (k < len) loc += ws[k] * vc[s];
+    }
+    double bs = block_sum0(loc, sh);
+    if (i < j) {
+      const double* vi = V + (int64_t)(i + 1) * ldv + base;
+#pragma unroll
+      for (int s = 0; s < NPT; s++) {
+        int64_t k = threadIdx.x + (int64_t)s * blockDim.x;
+        vn[s] = k < len ? vi[k] : 0.0;
+      }
+    }
+    double h;
+    if (!grid_reduce(bs, part, bar, pub, err, h)) return;
+    if (blockIdx.x == 0 && threadIdx.x == 0) Hcol[i] = h;
+#pragma unroll
+    for (int s = 0; s < NPT; s++) {
+      int64_t k = threadIdx.x + (int64_t)s * blockDim.x;
+      if (k < len) ws[k] -= h * vc[s];
+      vc[s] = vn[s];
+    }
+  }
+  double loc = 0.0;
+#pragma unroll
+  for (int s = 0; s < NPT; s++) {
+    int64_t k = threadIdx.x + (int64_t)s * blockDim.x;
+    if (k < len) loc += ws[k] * ws[k];
+  }
+  double bs = block_sum0(loc, sh);
+  double hn2;
+  if (!grid_reduce(bs, part, bar, pub, err, hn2)) return;
+  double hn = sqrt(hn2);
+  if (hn > 0.0) {
+    double inv = 1.0 / hn;
+    double* vnx = V + (int64_t)(j + 1) * ldv + base;
+    for (int64_t k = threadIdx.x; k < len; k += blockDim.x) {
+      double v = ws[k] * inv;
+      ws[k] = v;
+      vnx[k] = v;
+    }
+    if (z) {
+      __syncthreads();
+      for (int64_t a = threadIdx.x; a < len / 3; a += blockDim.x) {
+        const DT* D = Dinv + ((base / 3) + a) * 9;
+        double x0 = ws[3 * a], x1 = ws[3 * a + 1], x2 = ws[3 * a + 2];
+        ZT* zo = z + base + 3 * a;
+        if constexpr (sizeof(DT) == 8) {
+          zo[0] = (ZT)(D[0] * x0 + D[1] * x1 + D[2] * x2);
+          zo[1] = (ZT)(D[3] * x0 + D[4] * x1 + D[5] * x2);
+          zo[2] = (ZT)(D[6] * x0 + D[7] * x1 + D[8] * x2);
+        } else {
+          float f0 = (float)x0, f1 = (float)x1, f2 = (float)x2;
+          zo[0] = (ZT)(D[0] * f0 + D[1] * f1 + D[2] * f2);
+          zo[1] = (ZT)(D[3] * f0 + D[4] * f1 + D[5] * f2);
+          zo[2] = (ZT)(D[6] * f0 + D[7] * f1 + D[8] * f2);
+        }
+      }
+    }
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    Hcol[j + 1] = hn;
+    for (int i = 0; i < j; i++) {
+      double a = Hcol[i], c = Hcol[i + 1];
+      Hcol[i] = cs[i] * a + sn[i] * c;
+      Hcol[i + 1] = -sn[i] * a + cs[i] * c;
+    }
+    double a = Hcol[j], c = Hcol[j + 1];
+    double r = hypot(a, c);
+    cs[j] = a / r;
+    sn[j] = c / r;
+    Hcol[j] = r;
+    Hcol[j + 1] = 0.0;
+    g[j + 1] = -sn[j] * g[j];
+    g[j] = cs[j] * g[j];
+    out[0] = fabs(g[j + 1]);
+    out[1] = hn;
+  }
+}
+
+// ---------------------------------------------------------------- SpMV
+template <class V>
+__device__ __forceinline__ float ld_val(const V* p);
+template <>
+__device__ __forceinline__ float ld_val<float>(const float* p) { return __ldg(p); }
+template <>
+__device__ __forceinline__ float ld_val<__nv_bfloat16>(const __nv_bfloat16* p) {
+  return __bfloat162float(*p);
+}
+
+// y_u = K x_u (+ B1 x_p): one warp per block row.  The row's values are a
+// contiguous run of 9*nblk entries; per chunk of up to 32 blocks the warp
+// loads the column indices once (lane b holds the column of block b), then
+// every lane issues all 9 of its value loads and all 9 of its x gathers
+// (column taken from the owning lane by a shuffle) before accumulating, so
+// each warp keeps ~18 independent loads in flight instead of a dependent
+// val -> col -> x chain per entry.
+template <class VT, class XT, class AT>
+__global__ void __launch_bounds__(256) k_spmv(int nn, const int* __restrict__ row_ptr, const int* __restrict__ col,
+                                              const VT* __restrict__ val, const XT* __restrict__ x,
+                                              double* __restrict__ y, const int* __restrict__ up_ptr,
+                                              const int* __restrict__ up_col, const VT* __restrict__ B,
+                                              const XT* __restrict__ xp) {
+  int row = (int)(((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+  int lane = threadIdx.x & 31;
+  if (row >= nn) return;
+  const int rs = row_ptr[row], re = row_ptr[row + 1];
+  AT a0 = AT(0), a1 = AT(0), a2 = AT(0);
+  for (int base = rs; base < re; base += 32) {
+    const int cb = re - base < 32 ? re - base : 32;
+    const int nf = 9 * cb;
+    const int mycol = lane < cb ? __ldg(col + base + lane) : 0;
+    const VT* vb = val + (int64_t)base * 9;
+    AT v[9];
+#pragma unroll
+    for (int t = 0; t < 9; t++) {
+      int f = lane + 32 * t;
+      if constexpr (sizeof(VT) == 8) v[t] = f < nf ? vb[f] : AT(0);
+      else v[t] = f < nf ? (AT)ld_val<VT>(vb + f) : AT(0);
+    }
+    AT xv[9];
+#pragma unroll
+    for (int t = 0; t < 9; t++) {
+      int f = lane + 32 * t;
+      int blk = f / 9;
+      int c = (f - 9 * blk) % 3;
+      int cidx = __shfl_sync(0xffffffffu, mycol, blk & 31);
+      xv[t] = f < nf ? (AT)x[3 * (int64_t)cidx + c] : AT(0);
+    }
+#pragma unroll
+    for (int t = 0; t < 9; t++) {
+      int f = lane + 32 * t;
+      int r = (f % 9) / 3;
+      AT p = v[t] * xv[t];
+      a0 += r == 0 ? p : AT(0);
+      a1 += r == 1 ? p : AT(0);
+      a2 += r == 2 ? p : AT(0);
+    }
+  }
+  if (up_ptr) {
+    for (int k = up_ptr[row] + lane; k < up_ptr[row + 1]; k += 32) {
+      AT xv = (AT)xp[up_col[k]];
+      const VT* b = B + (int64_t)k * 3;
+      if constexpr (sizeof(VT) == 8) {
+        a0 += b[0] * xv;
+        a1 += b[1] * xv;
+        a2 += b[2] * xv;
+      } else {
+        a0 += (AT)ld_val<VT>(b) * xv;
+        a1 += (AT)ld_val<VT>(b + 1) * xv;
+        a2 += (AT)ld_val<VT>(b + 2) * xv;
+      }
+    }
+  }
+  for (int off = 16; off > 0; off >>= 1) {
+    a0 += __shfl_xor_sync(0xffffffffu, a0, off);
+    a1 += __shfl_xor_sync(0xffffffffu, a1, off);
+    a2 += __shfl_xor_sync(0xffffffffu, a2, off);
+  }
+  if (lane == 0) {
+    y[3 * (int64_t)row] = (double)a0;
+    y[3 * (int64_t)row + 1] = (double)a1;
+    y[3 * (int64_t)row + 2] = (double)a2;
+  }
+}
+
+// pressure rows: y_p[v] = sum over (u node a, v) of B[a,v] . x_u[a]  (B2 = B1^T)
+template <class VT, class XT, class AT>
+__global__ void __launch_bounds__(256) k_spmv_p(int np, const int* __restrict__ pu_ptr, const int* __restrict__ pu_col,
+                                                const int* __restrict__ pu_src, const VT* __restrict__ B,
+                                                const XT* __restrict__ xu, double* __restrict__ yp) {
+  int v = (int)(((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+  int lane = threadIdx.x & 31;
+  if (v >= np) return;
+  AT acc = AT(0);
+  for (int k = pu_ptr[v] + lane; k < pu_ptr[v + 1]; k += 32) {
+    const VT* b = B + (int64_t)pu_src[k] * 3;
+    const XT* u = xu + 3 * (int64_t)pu_col[k];
+    if constexpr (sizeof(VT) == 8) acc += b[0] * u[0] + b[1] * u[1] + b[2] * u[2];
+    else acc += (AT)ld_val<VT>(b) * (AT)u[0] + (AT)ld_val<VT>(b + 1) * (AT)u[1] + (AT)ld_val<VT>(b + 2) * (AT)u[2];
+  }
+  for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
+  if (lane == 0) yp[v] = (double)acc;
+}
+
+// ---------------------------------------------------------------- preconditioner
+// nodal block-Jacobi z_a = D_a^{-1} x_a (displacement part)
+template <class DT, class OT>
+__global__ void k_pc_bj(int nn, const DT* __restrict__ Dinv, const double* __restrict__ x, OT* __restrict__ z) {
+  int a = blockIdx.x * blockDim.x + threadIdx.x;
+  if (a >= nn) return;
+  const DT* D = Dinv + (int64_t)a * 9;
+  double x0 = x[3 * (int64_t)a], x1 = x[3 * (int64_t)a + 1], x2 = x[3 * (int64_t)a + 2];
+  if constexpr (sizeof(DT) == 8) {
+    z[3 * (int64_t)a] = (OT)(D[0] * x0 + D[1] * x1 + D[2] * x2);
+    z[3 * (int64_t)a + 1] = (OT)(D[3] * x0 + D[4] * x1 + D[5] * x2);
+    z[3 * (int64_t)a + 2] = (OT)(D[6] * x0 + D[7] * x1 + D[8] * x2);
+  } else {
+    float f0 = (float)x0, f1 = (float)x1, f2 = (float)x2;
+    z[3 * (int64_t)a] = (OT)(D[0] * f0 + D[1] * f1 + D[2] * f2);
+    z[3 * (int64_t)a + 1] = (OT)(D[3] * f0 + D[4] * f1 + D[5] * f2);
+    z[3 * (int64_t)a + 2] = (OT)(D[6] * f0 + D[7] * f1 + D[8] * f2);
+  }
+}
+
+// lower Schur (SIMPLE): z_p = S^{-1} (x_p - B2 z_u), point-Jacobi S
+template <class VT, class OT>
+__global__ void __launch_bounds__(256) k_pc_schur(int np, int nn, const int* __restrict__ pu_ptr,
+                                                  const int* __restrict__ pu_col, const int* __restrict__ pu_src,
+                                                  const VT* __restrict__ B, const double* __restrict__ Sd,
+                                                  const double* __restrict__ x, OT* __restrict__ z) {
+  int v = (int)(((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+  int lane = threadIdx.x & 31;
+  if (v >= np) return;
+  double acc = 0.0;
+  for (int k = pu_ptr[v] + lane; k < pu_ptr[v + 1]; k += 32) {
+    const VT* b = B + (int64_t)pu_src[k] * 3;
+    const OT* u = z + 3 * (int64_t)pu_col[k];
+    double b0, b1, b2;
+    if constexpr (sizeof(VT) == 8) {
+      b0 = b[0]; b1 = b[1]; b2 = b[2];
+    } else {
+      b0 = ld_val<VT>(b); b1 = ld_val<VT>(b + 1); b2 = ld_val<VT>(b + 2);
+    }
+    acc += b0 * (double)u[0] + b1 * (double)u[1] + b2 * (double)u[2];
+  }
+  acc = warp_sum(acc);
+  if (lane == 0) {
+    double t = x[3 * (int64_t)nn + v] - acc;
+    double s = Sd[v];
+    z[3 * (int64_t)nn + v] = (OT)(s != 0.0 ? t / s : t);
+  }
+}
+
+template <class OT>
+static int pc_apply_t(fe_mesh m, const double* x, OT* z) {
+  FE_SCOPE(m, FE_PROF_PC, (double)m->nn * (9.0 * (m->prec == FE_PREC_FP64 ? 8 : 4) + 24 + 3.0 * sizeof(OT)) +
+                              (m->pres ? (double)m->nnz_up * (8 + 12.0 * (m->prec == FE_PREC_FP64 ? 8 : 4)) + 24.0 * m->np
+                                       : 0.0));
+  if (m->prec == FE_PREC_FP64)
+    k_pc_bj<double, OT><<<(m->nn + 255) / 256, 256, 0, m->stream>>>(m->nn, m->Dinv64, x, z);
+  else
+    k_pc_bj<float, OT><<<(m->nn + 255) / 256, 256, 0, m->stream>>>(m->nn, m->Dinv32, x, z);
+  FE_CUDA(cudaGetLastError());
+  if (m->pres) {
+    unsigned grid = (unsigned)(((int64_t)m->np * 32 + 255) / 256);
+    if (m->prec == FE_PREC_FP64)
+      k_pc_schur<double, OT><<<grid, 256, 0, m->stream>>>(m->np, m->nn, m->pu_ptr, m->pu_col, m->pu_src, m->B64,
+                                                          m->Sd, x, z);
+    else
+      k_pc_schur<float, OT><<<grid, 256, 0, m->stream>>>(m->np, m->nn, m->pu_ptr, m->pu_col, m->pu_src, m->B32,
+                                                         m->Sd, x, z);
+    FE_CUDA(cudaGetLastError());
+  }
+  return FE_OK;
+}
+
+int fe_pc_dev(fe_mesh m, const double* x, double* y) { return pc_apply_t<double>(m, x, y); }
+
+// z (SpMV input type) = M^{-1} x
+static int pc_to_zx(fe_mesh m, const double* x) {
+  if (m->prec == FE_PREC_FP64) return pc_apply_t<double>(m, x, (double*)m->zx);
+  return pc_apply_t<float>(m, x, (float*)m->zx);
+}
+
+// y = K zx (zx already in the SpMV input type); the u-p coupling is kept in
+// the tangent's precision (FP64, or FP32 for the mixed form)
+static int spmv_zx(fe_mesh m, double* y) {
+  const double sv = m->prec == FE_PREC_FP64 ? 8 : (m->prec == FE_PREC_MIXED_BF16 ? 2 : 4);
+  const double sx = m->prec == FE_PREC_FP64 ? 8 : 4;
+  FE_SCOPE(m, FE_PROF_SPMV, (double)m->nnzb * (9 * sv + 4) + 4.0 * (m->nn + 1) + sx * (double)m->ndof + 8.0 * (double)m->ndof +
+                                (m->pres ? (double)m->nnz_up * 2 * (3 * sv + 8) + 4.0 * (m->nn + m->np + 2) : 0.0));
+  unsigned grid = (unsigned)(((int64_t)m->nn * 32 + 255) / 256);
+  unsigned gridp = (unsigned)(((int64_t)m->np * 32 + 255) / 256);
+  const int* upp = m->pres ? m->up_ptr : nullptr;
+  if (m->prec == FE_PREC_FP64) {
+    const double* x = (const double*)m->zx;
+    k_spmv<double, double, double><<<grid, 256, 0, m->stream>>>(m->nn, m->row_ptr, m->col, m->K64, x, y, upp,
+                                                                m->up_col, m->B64, x + 3 * (int64_t)m->nn);
+    if (m->pres)
+      k_spmv_p<double, double, double><<<gridp, 256, 0, m->stream>>>(m->np, m->pu_ptr, m->pu_col, m->pu_src, m->B64,
+                                                                     x, y + 3 * (int64_t)m->nn);
+  } else if (m->prec == FE_PREC_MIXED_BF16) {
+    const float* x = (const float*)m->zx;
+    k_spmv<__nv_bfloat16, float, float><<<grid, 256, 0, m->stream>>>(m->nn, m->row_ptr, m->col, m->K16, x, y,
+                                                                      nullptr, nullptr, nullptr, nullptr);
+  } else {
+    const float* x = (const float*)m->zx;
+    k_spmv<float, float, float><<<grid, 256, 0, m->stream>>>(m->nn, m->row_ptr, m->col, m->K32, x, y, upp,
+                                                             m->up_col, m->B32, x + 3 * (int64_t)m->nn);
+    if (m->pres)
+      k_spmv_p<float, float, float><<<gridp, 256, 0, m->stream>>>(m->np, m->pu_ptr, m->pu_col, m->pu_src, m->B32, x,
+                                                                  y + 3 * (int64_t)m->nn);
+  }
+  FE_CUDA(cudaGetLastError());
+  return FE_OK;
+}
+
+__global__ void k_narrow(int64_t n, const double* __restrict__ x, float* __restrict__ y) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) y[i] = (float)x[i];
+}
+__global__ void k_copy(int64_t n, const double* __restrict__ x, double* __restrict__ y) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) y[i] = x[i];
+}
+
+static int ensure_zx(fe_mesh m) {
+  if (!m->zx) FE_TRY(fe_alloc(m, &m->zx, (size_t)m->ndof * sizeof(double)));
+  return FE_OK;
+}
+
+// y = K x for FP64 x, y
+int fe_spmv_dev(fe_mesh m, const double* x, double* y) {
+  if (m->prec < 0) return fe_set_error("no tangent assembled"), FE_ERR_STATE;
+  FE_TRY(ensure_zx(m));
+  unsigned g = (unsigned)((m->ndof + 255) / 256);
+  FE_SCOPE(m, FE_PROF_VECTOR, (m->prec == FE_PREC_FP64 ? 16.0 : 12.0) * m->ndof);
+  if (m->prec == FE_PREC_FP64) k_copy<<<g, 256, 0, m->stream>>>(m->ndof, x, (double*)m->zx);
+  else k_narrow<<<g, 256, 0, m->stream>>>(m->ndof, x, (float*)m->zx);
+  FE_CUDA(cudaGetLastError());
+  return spmv_zx(m, y);
+}
+
+// ---------------------------------------------------------------- vectors
+__global__ void k_dot(int64_t n, const double* __restrict__ a, const double* __restrict__ b, double* red,
+                      unsigned* ticket, double* out) {
+  __shared__ double sh[32];
+  __shared__ bool last;
+  double s = 0.0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    s += a[i] * b[i];
+  s = block_sum_all(s, sh);
+  if (threadIdx.x == 0) {
+    red[blockIdx.x] = s;
+    __threadfence();
+    last = atomicAdd(ticket, 1u) == gridDim.x - 1;
+  }
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  double t = sum_partials(red, sh);
+  if (threadIdx.x == 0) {
+    *out = t;
+    *ticket = 0u;
+  }
+}
+
+static unsigned dot_grid(fe_mesh m) { return (unsigned)(m->sm_count * 4); }
+
+// dot product into device scalar slot `slot` (no host sync)
+static int dot_async(fe_mesh m, const double* a, const double* b, int64_t n, int slot) {
+  FE_SCOPE(m, FE_PROF_VECTOR, (a == b ? 8.0 : 16.0) * n);
+  k_dot<<<dot_grid(m), 256, 0, m->stream>>>(n, a, b, m->red, m->red_ticket, m->scal + slot);
+  FE_CUDA(cudaGetLastError());
+  return FE_OK;
+}
+
+int fe_dot_dev(fe_mesh m, const double* a, const double* b, int64_t n, double* out_host) {
+  FE_TRY(dot_async(m, a, b, n, 5));
+  FE_CUDA(cudaMemcpyAsync(m->h_scal + 5, m->scal + 5, sizeof(double), cudaMemcpyDeviceToHost, m->stream));
+  FE_CUDA(cudaStreamSynchronize(m->stream));
+  *out_host = m->h_scal[5];
+  return FE_OK;
+}
+
+// y = a x + b y
+__global__ void k_axpby(int64_t n, double a, const double* __restrict__ x, double b, double* __restrict__ y) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) y[i] = a * x[i] + b * y[i];
+}
+int fe_axpby_dev(fe_mesh m, double a, const double* x, double b, double* y, int64_t n) {
+  FE_SCOPE(m, FE_PROF_VECTOR, 24.0 * n);
+  k_axpby<<<(unsigned)((n + 255) / 256), 256, 0, m->stream>>>(n, a, x, b, y);
+  FE_CUDA(cudaGetLastError());
+  return FE_OK;
+}
+
+// v = (b - w) / beta? -> r = b - w
+__global__ void k_sub(int64_t n, const double* __restrict__ b, const double* __restrict__ w, double* __restrict__ r) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) r[i] = b[i] - w[i];
+}
+__global__ void k_scale(int64_t n, const double* __restrict__ s, double* __restrict__ v, double* __restrict__ g,
+                        int glen) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  double beta = sqrt(s[0]);
+  if (i < n) v[i] = v[i] / beta;
+  if (i < glen) g[i] = (i == 0) ? beta : 0.0;
+}
+
+// back substitution y = H^{-1} g on the k x k upper triangle (one block)
+__global__ void k_trisolve(int k, int ldh, const double* __restrict__ H, double* __restrict__ g,
+                           double* __restrict__ y) {
+  for (int i = k - 1; i >= 0; i--) {
+    __syncthreads();
+    double yi = g[i] / H[(int64_t)i * ldh + i];
+    if (threadIdx.x == 0) y[i] = yi;
+    for (int r = threadIdx.x; r < i; r += blockDim.x) g[r] -= H[(int64_t)i * ldh + r] * yi;
+  }
+}
+
+// u = sum_i y_i V_i
+__global__ void k_gemv(int64_t n, int k, const double* __restrict__ V, int64_t ldv, const double* __restrict__ y,
+                       double* __restrict__ u) {
+  __shared__ double ys[1024];
+  for (int i = threadIdx.x; i < k && i < 1024; i += blockDim.x) ys[i] = y[i];
+  __syncthreads();
+  int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= n) return;
+  double s = 0.0;
+  for (int i = 0; i < k; i++) s += ys[i] * V[(int64_t)i * ldv + idx];
+  u[idx] = s;
+}
+
+// ---------------------------------------------------------------- workspace
+int fe_workspace(fe_mesh m, int restart) {
+  FE_TRY(ensure_zx(m));
+  if (!m->w64) FE_TRY(fe_alloc_t(m, &m->w64, (size_t)m->ndof));
+  if (!m->t64) FE_TRY(fe_alloc_t(m, &m->t64, (size_t)m->ndof));
+  if (!m->u64) FE_TRY(fe_alloc_t(m, &m->u64, (size_t)m->ndof));
+  if (restart > m->ws_restart) {
+    if (m->V) {
+      cudaFree(m->V);
+      cudaFree(m->H);
+      cudaFree(m->gv);
+      m->device_bytes -= (int64_t)(m->ws_restart + 1) * m->ndof * 8 + (int64_t)(m->ws_restart + 1) * (m->ws_restart + 1) * 8 +
+                         (int64_t)4 * (m->ws_restart + 2) * 8;
+      m->V = m->H = m->gv = nullptr;
+    }
+    FE_TRY(fe_alloc_t(m, &m->V, (size_t)(restart + 1) * m->ndof));
+    FE_TRY(fe_alloc_t(m, &m->H, (size_t)(restart + 1) * (restart + 1)));
+    FE_TRY(fe_alloc_t(m, &m->gv, (size_t)4 * (restart + 2)));
+    m->ws_restart = restart;
+  }
+  return FE_OK;
+}
+
+// ---------------------------------------------------------------- persistent launch helpers
+struct CoopCfg {
+  int npt, grid;
+};
+
+template <int NPT, class DT, class ZT>
+static const void* arnoldi_fn() { return (const void*)k_arnoldi<NPT, DT, ZT>; }
+
+// Picks the smallest slice width (NPT values per thread, a multiple of 3)
+// whose grid of ceil(n / S) blocks can be co-resident, then launches the
+// step cooperatively.  fuse_pc: also write z = D^{-1} V_{j+1} into zx.
+template <class DT, class ZT>
+static int launch_arnoldi_t(fe_mesh m, int j, int kmax, bool fuse_pc, const DT* Dinv) {
+  const int64_t n = m->ndof;
+  const void* fns[4] = {arnoldi_fn<3, DT, ZT>(), arnoldi_fn<6, DT, ZT>(), arnoldi_fn<12, DT, ZT>(),
+                        arnoldi_fn<24, DT, ZT>()};
+  const int npts[4] = {3, 6, 12, 24};
+  const int bds[4] = {1024, 1024, 512, 512};
+  static bool attr[2][2][4] = {};
+  int which = -1, grid = 0;
+  for (int q = 0; q < 4; q++) {
+    size_t smem = (size_t)npts[q] * bds[q] * sizeof(double);
+    bool& done = attr[sizeof(DT) == 8][sizeof(ZT) == 8][q];
+    if (!done) {
+      FE_CUDA(cudaFuncSetAttribute(fns[q], cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+      done = true;
+    }
+    int per_sm = 0;
+    FE_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fns[q], bds[q], smem));
+    int64_t need = (n + (int64_t)npts[q] * bds[q] - 1) / ((int64_t)npts[q] * bds[q]);
+    if (per_sm >= 1 && need <= (int64_t)per_sm * m->sm_count && need <= RED_SLOTS) {
+      which = q;
+      grid = (int)need;
+      break;
+    }
+  }
+  if (which < 0) return fe_set_error("vector too long for the persistent Arnoldi kernel (n = %lld)", (long long)n), FE_ERR_ARG;
+  size_t smem = (size_t)npts[which] * bds[which] * sizeof(double);
+  double* V = m->V;
+  int64_t ldv = m->ndof;
+  double* Hcol = m->H + (int64_t)j * (kmax + 1);
+  double* cs = m->gv;
+  double* sn = m->gv + (kmax + 2);
+  double* g = m->gv + 2 * (kmax + 2);
+  double* out = m->scal + 3;
+  double* pub = m->scal + 7;
+  double* part = m->red;
+  const DT* D = fuse_pc ? Dinv : nullptr;
+  ZT* z = fuse_pc ? (ZT*)m->zx : nullptr;
+  void* args[] = {(void*)&n, (void*)&j, (void*)&V, (void*)&ldv, (void*)&m->w64, (void*)&Hcol, (void*)&part,
+                  (void*)&m->bar, (void*)&pub, (void*)&m->err, (void*)&cs, (void*)&sn, (void*)&g, (void*)&out,
+                  (void*)&D, (void*)&z};
+  FE_SCOPE(m, FE_PROF_ARNOLDI, 8.0 * (double)n * (j + 3) + (fuse_pc ? (double)n * (3.0 * sizeof(DT) + sizeof(ZT)) : 0.0));
+  FE_CUDA(cudaLaunchCooperativeKernel(fns[which], dim3(grid), dim3(bds[which]), args, smem, m->stream));
+  return FE_OK;
+}
+
+static int launch_arnoldi(fe_mesh m, int j, int kmax, bool fuse_pc) {
+  if (m->prec == FE_PREC_FP64) return launch_arnoldi_t<double, double>(m, j, kmax, fuse_pc, m->Dinv64);
+  return launch_arnoldi_t<float, float>(m, j, kmax, fuse_pc, m->Dinv32);
+}
+
+// ---------------------------------------------------------------- GMRES
+// Right-preconditioned GMRES(restart) with MGS Arnoldi and Givens rotations.
+// Stops when the residual estimate |g_{j+1}| <= max(rtol ||b||, atol), on a
+// lucky breakdown, or after max_it iterations; the iterate is updated at the
+// end of every cycle with x += M^{-1} V_j y.
+int fe_gmres_dev(fe_mesh m, const double* b, double* x, double rtol, double atol, int restart, int max_it,
+                 int* iters, double* res) {
+  if (m->prec < 0) return fe_set_error("no tangent assembled"), FE_ERR_STATE;
+  if (restart < 1 || restart > 1000) return fe_set_error("restart must be in [1, 1000]"), FE_ERR_ARG;
+  FE_TRY(fe_workspace(m, restart));
+  const int64_t n = m->ndof;
+  const unsigned g1 = (unsigned)((n + 255) / 256);
+  double bnorm2;
+  FE_TRY(fe_dot_dev(m, b, b, n, &bnorm2));
+  double bnorm = sqrt(bnorm2);
+  double target = fmax(rtol * bnorm, atol);
+  int it = 0;
+  double resid = 0.0;
+  const int kmax = restart;
+  double* cs = m->gv;
+  double* g = m->gv + 2 * (kmax + 2);
+  double* y = m->gv + 3 * (kmax + 2);
+  (void)cs;
+  for (;;) {
+    // r = b - K x -> V_0, beta = ||r||
+    FE_TRY(fe_spmv_dev(m, x, m->w64));
+    {
+      FE_SCOPE(m, FE_PROF_VECTOR, 24.0 * n);
+      k_sub<<<g1, 256, 0, m->stream>>>(n, b, m->w64, m->V);
+    }
+    FE_TRY(dot_async(m, m->V, m->V, n, 6));
+    FE_CUDA(cudaMemcpyAsync(m->h_scal + 6, m->scal + 6, sizeof(double), cudaMemcpyDeviceToHost, m->stream));
+    FE_CUDA(cudaStreamSynchronize(m->stream));
+    double beta = sqrt(m->h_scal[6]);
+    resid = beta;
+    if (beta <= target || it >= max_it || !std::isfinite(beta)) break;
+    unsigned gs = std::max<unsigned>(g1, (unsigned)((kmax + 1 + 255) / 256));
+    {
+      FE_SCOPE(m, FE_PROF_VECTOR, 16.0 * n);
+      k_scale<<<gs, 256, 0, m->stream>>>(n, m->scal + 6, m->V, g, kmax + 1);
+    }
+    FE_CUDA(cudaGetLastError());
+    int j = 0;
+    bool done = false;
+    // the block-Jacobi application is fused into the Arnoldi step (it writes
+    // z = D^{-1} V_{j+1} for the next SpMV); the u-p Schur preconditioner
+    // needs B2 z_u and runs as its own kernels
+    const bool fuse = !m->pres;
+    for (j = 0; j < kmax; j++) {
+      if (j == 0 || !fuse) FE_TRY(pc_to_zx(m, m->V + (int64_t)j * n));
+      FE_TRY(spmv_zx(m, m->w64));
+      FE_TRY(launch_arnoldi(m, j, kmax, fuse));
+      FE_CUDA(cudaMemcpyAsync(m->h_scal + 3, m->scal + 3, (SCAL_N - 3) * sizeof(double), cudaMemcpyDeviceToHost,
+                              m->stream));
+      FE_CUDA(cudaStreamSynchronize(m->stream));
+      if (*(const int*)(m->h_scal + SCAL_N - 1) != DEV_OK) FE_TRY(fe_check_device_error(m));
+      it++;
+      resid = m->h_scal[3];
+      double hn = m->h_scal[4];
+      if (resid <= target || it >= max_it || hn == 0.0 || !std::isfinite(resid)) {
+        done = true;
+        j++;
+        break;
+      }
+    }
+    if (!done) j = kmax;
+    {
+      FE_SCOPE(m, FE_PROF_VECTOR, 8.0 * j * (j + 1));
+      k_trisolve<<<1, 256, 0, m->stream>>>(j, kmax + 1, m->H, g, y);
+    }
+    {
+      FE_SCOPE(m, FE_PROF_VECTOR, 8.0 * n * (j + 1));
+      k_gemv<<<g1, 256, 0, m->stream>>>(n, j, m->V, n, y, m->u64);
+    }
+    FE_TRY(fe_pc_dev(m, m->u64, m->t64));
+    FE_TRY(fe_axpby_dev(m, 1.0, m->t64, 1.0, x, n));
+    FE_CUDA(cudaGetLastError());
+    if (done) break;
+  }
+  FE_CUDA(cudaStreamSynchronize(m->stream));
+  if (iters) *iters = it;
+  if (res) *res = resid;
+  return FE_OK;
+}
+
+// ---------------------------------------------------------------- L-BFGS two-loop
+// loop 1 (newest -> oldest): alpha_i = rho_i s_i . q ; q -= alpha_i y_i
+template <int NPT>
+__global__ void __launch_bounds__(256) k_twoloop1(int64_t n, int k, int head, int mcap, const double* __restrict__ S,
+                                                  const double* __restrict__ Y, int64_t ld,
+                                                  const double* __restrict__ rho, const double* __restrict__ qin,
+                                                  double* __restrict__ qout, double* __restrict__ alpha, double* part,
+                                                  unsigned* bar, double* pub, int* err) {
+  __shared__ double sh[32];
+  const int64_t T = (int64_t)gridDim.x * blockDim.x;
+  const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  double q[NPT];
+#pragma unroll
+  for (int s = 0; s < NPT; s++) {
+    int64_t idx = tid + s * T;
+    q[s] = idx < n ? qin[idx] : 0.0;
+  }
+  for (int c = k - 1; c >= 0; c--) {
+    int slot = (head + c) % mcap;
+    const double* si = S + (int64_t)slot * ld;
+    const double* yi = Y + (int64_t)slot * ld;
+    double loc = 0.0;
+#pragma unroll
+    for (int s = 0; s < NPT; s++) {
+      int64_t idx = tid + s * T;
+      if (idx < n) loc += si[idx] * q[s];
+    }
+    double bs = block_sum0(loc, sh);
+    double yv[NPT];  // loaded before the reduction's wait
+#pragma unroll
+    for (int s = 0; s < NPT; s++) {
+      int64_t idx = tid + s * T;
+      yv[s] = idx < n ? yi[idx] : 0.0;
+    }
+    double tot;
+    if (!grid_reduce(bs, part, bar, pub, err, tot)) return;
+    double a = rho[slot] * tot;
+    if (blockIdx.x == 0 && threadIdx.x == 0) alpha[c] = a;
+#pragma unroll
+    for (int s = 0; s < NPT; s++) q[s] -= a * yv[s];
+  }
+#pragma unroll
+  for (int s = 0; s < NPT; s++) {
+    int64_t idx = tid + s * T;
+    if (idx < n) qout[idx] = q[s];
+  }
+}
+
+// loop 2 (oldest -> newest): beta = rho_i y_i . z ; z += (alpha_i - beta) s_i
+template <int NPT>
+__global__ void __launch_bounds__(256) k_twoloop2(int64_t n, int k, int head, int mcap, const double* __restrict__ S,
+                                                  const double* __restrict__ Y, int64_t ld,
+                                                  const double* __restrict__ rho, const double* __restrict__ alpha,
+                                                  const double* __restrict__ zin, double* __restrict__ zout,
+                                                  double* part, unsigned* bar, double* pub, int* err) {
+  __shared__ double sh[32];
+  const int64_t T = (int64_t)gridDim.x * blockDim.x;
+  const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  double z[NPT];
+#pragma unroll
+  for (int s = 0; s < NPT; s++) {
+    int64_t idx = tid + s * T;
+    z[s] = idx < n ? zin[idx] : 0.0;
+  }
+  for (int c = 0; c < k; c++) {
+    int slot = (head + c) % mcap;
+    const double* si = S + (int64_t)slot * ld;
+    const double* yi = Y + (int64_t)slot * ld;
+    double loc = 0.0;
+#pragma unroll
+    for (int s = 0; s < NPT; s++) {
+      int64_t idx = tid + s * T;
+      if (idx < n) loc += yi[idx] * z[s];
+    }
+    double bs = block_sum0(loc, sh);
+    double sv[NPT];  // loaded before the reduction's wait
+#pragma unroll
+    for (int s = 0; s < NPT; s++) {
+      int64_t idx = tid + s * T;
+      sv[s] = idx < n ? si[idx] : 0.0;
+    }
+    double tot;
+    if (!grid_reduce(bs, part, bar, pub, err, tot)) return;
+    double beta = rho[slot] * tot;
+    double coef = alpha[c] - beta;
+#pragma unroll
+    for (int s = 0; s < NPT; s++) z[s] += coef * sv[s];
+  }
+#pragma unroll
+  for (int s = 0; s < NPT; s++) {
+    int64_t idx = tid + s * T;
+    if (idx < n) zout[idx] = z[s];
+  }
+}
+
+static int coop_grid(fe_mesh m, const void* fn, int* grid) {
+  int per_sm = 0;
+  FE_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, 256, 0));
+  if (per_sm < 1) return fe_set_error("persistent kernel does not fit on an SM"), FE_ERR_CUDA;
+  *grid = per_sm * m->sm_count;
+  if (*grid > RED_SLOTS) *grid = RED_SLOTS;
+  return FE_OK;
+}
+
+#define TL_FN(name, N) ((const void*)name<N>)
+
+static int launch_twoloop(fe_mesh m, int which, void** args) {
+  const void* f1[6] = {TL_FN(k_twoloop1, 1), TL_FN(k_twoloop1, 2), TL_FN(k_twoloop1, 4),
+                       TL_FN(k_twoloop1, 8), TL_FN(k_twoloop1, 16), TL_FN(k_twoloop1, 32)};
+  const void* f2[6] = {TL_FN(k_twoloop2, 1), TL_FN(k_twoloop2, 2), TL_FN(k_twoloop2, 4),
+                       TL_FN(k_twoloop2, 8), TL_FN(k_twoloop2, 16), TL_FN(k_twoloop2, 32)};
+  const int npts[6] = {1, 2, 4, 8, 16, 32};
+  const void** fns = which == 1 ? f1 : f2;
+  int64_t n = m->ndof;
+  int grid = 0, q = 0;
+  for (q = 0; q < 6; q++) {
+    FE_TRY(coop_grid(m, fns[q], &grid));
+    if ((int64_t)grid * 256 * npts[q] >= n) break;
+  }
+  if (q == 6) return fe_set_error("vector too long for the persistent two-loop kernel"), FE_ERR_ARG;
+  int64_t per_block = 256LL * npts[q];
+  int need = (int)((n + per_block - 1) / per_block);
+  if (need < grid) grid = need;
+  int k = *(int*)args[1];
+  FE_SCOPE(m, FE_PROF_TWOLOOP, 16.0 * (double)n * (k + 1));
+  FE_CUDA(cudaLaunchCooperativeKernel(fns[q], dim3(grid), dim3(256), args, 0, m->stream));
+  return FE_OK;
+}
+
+// z = H_k q with the pairs at ring slots (head + c) % mcap, c = 0..k-1 oldest
+// first; H0 = preconditioner (h0 = 0), identity (h0 = 1) or GMRES (h0 = 2).
+int fe_lbfgs_dev(fe_mesh m, const double* S, const double* Y, const double* rho, int head, int mcap, int k,
+                 int64_t ld, const double* q, double* z, int h0, double ksp_rtol, double ksp_atol, int restart,
+                 int kmaxit, int* lit) {
+  FE_TRY(fe_workspace(m, restart > 0 ? restart : 1));
+  int64_t n = m->ndof;
+  if (k > LBFGS_MAX) return fe_set_error("at most %d stored pairs", LBFGS_MAX), FE_ERR_ARG;
+  if (!m->alpha_d) FE_TRY(fe_alloc_t(m, &m->alpha_d, LBFGS_MAX));
+  double* alpha = m->alpha_d;
+  double* qbuf = m->t64;
+  double* part = m->red;
+  double* pub = m->scal + 9;
+  if (k > 0) {
+    void* a1[] = {(void*)&n, (void*)&k, (void*)&head, (void*)&mcap, (void*)&S, (void*)&Y, (void*)&ld, (void*)&rho,
+                  (void*)&q, (void*)&qbuf, (void*)&alpha, (void*)&part, (void*)&m->bar, (void*)&pub, (void*)&m->err};
+    FE_TRY(launch_twoloop(m, 1, a1));
+  } else {
+    FE_SCOPE(m, FE_PROF_VECTOR, 16.0 * n);
+    k_copy<<<(unsigned)((n + 255) / 256), 256, 0, m->stream>>>(n, q, qbuf);
+  }
+  double* zb = m->u64;
+  if (h0 == 0) {
+    FE_TRY(fe_pc_dev(m, qbuf, zb));
+  } else if (h0 == 1) {
+    FE_SCOPE(m, FE_PROF_VECTOR, 16.0 * n);
+    k_copy<<<(unsigned)((n + 255) / 256), 256, 0, m->stream>>>(n, qbuf, zb);
+  } else {
+    // GMRES needs t64/u64 itself: move q aside into z's storage first
+    {
+      FE_SCOPE(m, FE_PROF_VECTOR, 16.0 * n);
+      k_copy<<<(unsigned)((n + 255) / 256), 256, 0, m->stream>>>(n, qbuf, z);
+    }
+    if (!m->lb_x) FE_TRY(fe_alloc_t(m, &m->lb_x, (size_t)n));
+    double* xs = m->lb_x;
+    FE_CUDA(cudaMemsetAsync(xs, 0, n * sizeof(double), m->stream));
+    int its = 0;
+    double res = 0.0;
+    FE_TRY(fe_gmres_dev(m, z, xs, ksp_rtol, ksp_atol, restart, kmaxit, &its, &res));
+    if (lit) *lit += its;
+    FE_SCOPE(m, FE_PROF_VECTOR, 16.0 * n);
+    k_copy<<<(unsigned)((n + 255) / 256), 256, 0, m->stream>>>(n, xs, zb);
+  }
+  FE_CUDA(cudaGetLastError());
+  if (k > 0) {
+    void* a2[] = {(void*)&n, (void*)&k, (void*)&head, (void*)&mcap, (void*)&S, (void*)&Y, (void*)&ld,
+                  (void*)&rho, (void*)&alpha, (void*)&zb, (void*)&z, (void*)&part, (void*)&m->bar, (void*)&pub,
+                  (void*)&m->err};
+    FE_TRY(launch_twoloop(m, 2, a2));
+  } else {
+    FE_SCOPE(m, FE_PROF_VECTOR, 16.0 * n);
+    k_copy<<<(unsigned)((n + 255) / 256), 256, 0, m->stream>>>(n, zb, z);
+  }
+  FE_CUDA(cudaGetLastError());
+  return FE_OK;
+}
+
+// ---------------------------------------------------------------- C ABI
+extern "C" int fe_spmv(fe_mesh m, const double* x, double* y) {
+  if (!m || !x || !y) return fe_set_error("NULL argument"), FE_ERR_ARG;
+  FE_CUDA(cudaSetDevice(m->device));
+  FE_TRY(fe_spmv_dev(m, x, y));
+  return fe_check_device_error(m);
+}
+
+extern "C" int fe_pc_apply(fe_mesh m, const double* x, double* y) {
+  if (!m || !x || !y) return fe_set_error("NULL argument"), FE_ERR_ARG;
+  if (m->prec < 0) return fe_set_error("no tangent assembled"), FE_ERR_STATE;
+  FE_CUDA(cudaSetDevice(m->device));
+  FE_TRY(fe_pc_dev(m, x, y));
+  return fe_check_device_error(m);
+}
+
+extern "C" int fe_gmres(fe_mesh m, const double* b, double* x, double rtol, double atol, int restart, int max_it,
+                        int* iters, double* res_out) {
+  if (!m || !b || !x) return fe_set_error("NULL argument"), FE_ERR_ARG;
+  if (!(rtol >= 0.0) || !(atol >= 0.0) || max_it < 0) return fe_set_error("bad tolerances"), FE_ERR_ARG;
+  FE_CUDA(cudaSetDevice(m->device));
+  FE_TRY(fe_gmres_dev(m, b, x, rtol, atol, restart, max_it, iters, res_out));
+  return fe_check_device_error(m);
+}
+
+extern "C" int fe_lbfgs_apply(fe_mesh m, const double* S, const double* Y, const double* rho, int k,
+                              const double* q, double* z, int h0) {
+  if (!m || !q || !z || k < 0 || (k > 0 && (!S || !Y || !rho))) return fe_set_error("bad arguments"), FE_ERR_ARG;
+  if (h0 != 0 && h0 != 1) return fe_set_error("h0 must be 0 or 1"), FE_ERR_ARG;
+  if (h0 == 0 && m->prec < 0) return fe_set_error("no tangent assembled"), FE_ERR_STATE;
+  FE_CUDA(cudaSetDevice(m->device));
+  FE_TRY(fe_lbfgs_dev(m, S, Y, rho, 0, k > 0 ? k : 1, k, m->ndof, q, z, h0, 0.0, 0.0, 1, 1, nullptr));
+  return fe_check_device_error(m);
+}
