@@ -259,7 +259,8 @@ int fe_lbfgs_apply(fe_mesh m, const double* S, const double* Y, const double* rh
  * Measurement support (no counterpart in the paper).  Every kernel launch
  * of the library is counted per class; with timing on, each launch is also
  * bracketed by CUDA events on the mesh's stream and credited with the
- * algorithmic bytes it must move (inputs read once, outputs written once). */
+ * algorithmic bytes it must move (inputs read once, outputs written once)
+ * and the floating-point operations it must perform. */
 #define FE_PROF_CLASSES 8
 enum {
   FE_PROF_RESIDUAL = 0, /* element residual + node gather */
@@ -276,6 +277,7 @@ typedef struct {
   int64_t timed[FE_PROF_CLASSES];    /* launches timed with events */
   double ms[FE_PROF_CLASSES];        /* summed event time of the timed launches */
   double bytes[FE_PROF_CLASSES];     /* summed algorithmic bytes of the timed launches */
+  double flops[FE_PROF_CLASSES];     /* summed algorithmic floating-point operations (FMA = 2) */
 } fe_profile_info;
 /* Zero the counters; timing = 1 also times every launch with CUDA events. */
 int fe_profile_reset(fe_mesh m, int timing);

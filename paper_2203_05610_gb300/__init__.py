@@ -77,7 +77,7 @@ PROF_CLASSES = ["residual", "tangent", "spmv", "pc", "arnoldi", "twoloop", "vect
 
 class fe_profile_info(C.Structure):
     _fields_ = [("launches", C.c_int64 * 8), ("timed", C.c_int64 * 8), ("ms", C.c_double * 8),
-                ("bytes", C.c_double * 8)]
+                ("bytes", C.c_double * 8), ("flops", C.c_double * 8)]
 
 
 _lib = None
@@ -302,7 +302,7 @@ class Mesh:
         p = fe_profile_info()
         _check(lib().fe_profile_read(self.h, C.byref(p)))
         return {name: dict(launches=int(p.launches[i]), timed=int(p.timed[i]), ms=float(p.ms[i]),
-                           bytes=float(p.bytes[i])) for i, name in enumerate(PROF_CLASSES)}
+                           bytes=float(p.bytes[i]), flops=float(p.flops[i])) for i, name in enumerate(PROF_CLASSES)}
 
     def solve(self, method, d, tol=1e-8, max_it=None, opts=None):
         mth = METHODS[method] if isinstance(method, str) else int(method)

@@ -111,7 +111,7 @@ struct fe_mesh_s {
   unsigned* red_ticket = nullptr;
   double* scal = nullptr;    // device scalars [64]
   int* err = nullptr;        // device error word
-  unsigned* bar = nullptr;   // grid barrier words [2]
+  unsigned* bar = nullptr;   // grid reduction state: count, seq, slot[2] (u64)
   double* h_scal = nullptr;  // pinned host mirror [64]
 
   // solver workspace (lazy)
@@ -137,10 +137,11 @@ struct fe_mesh_s {
   int64_t prof_timed[FE_PROF_CLASSES] = {};
   double prof_ms[FE_PROF_CLASSES] = {};
   double prof_bytes[FE_PROF_CLASSES] = {};
+  double prof_flops[FE_PROF_CLASSES] = {};
   struct ProfRec {
     int cls;
     cudaEvent_t a, b;
-    double bytes;
+    double bytes, flops;
   };
   std::vector<ProfRec> prof_pending;
   std::vector<cudaEvent_t> ev_free;
@@ -159,14 +160,16 @@ constexpr int LBFGS_MAX = 1000;  // largest number of stored secant pairs
 struct LaunchScope {
   fe_mesh m;
   int cls;
-  double bytes;
+  double bytes, flops;
   cudaEvent_t a = nullptr;
-  LaunchScope(fe_mesh m_, int cls_, double bytes_);
+  LaunchScope(fe_mesh m_, int cls_, double bytes_, double flops_ = 0.0);
   ~LaunchScope();
 };
 #define FE_CAT2(a, b) a##b
 #define FE_CAT(a, b) FE_CAT2(a, b)
 #define FE_SCOPE(m, cls, bytes) LaunchScope FE_CAT(fe_scope_, __LINE__)(m, cls, (double)(bytes))
+#define FE_SCOPE_F(m, cls, bytes, flops) \
+  LaunchScope FE_CAT(fe_scope_, __LINE__)(m, cls, (double)(bytes), (double)(flops))
 
 // allocation helper that tracks the mesh's device footprint
 int fe_alloc(fe_mesh m, void** p, size_t bytes);
@@ -175,6 +178,7 @@ int fe_alloc_t(fe_mesh m, T** p, size_t count) {
   return fe_alloc(m, reinterpret_cast<void**>(p), count * sizeof(T));
 }
 int fe_check_device_error(fe_mesh m);  // syncs the stream and reads the error word
+int fe_reset_grid_sync(fe_mesh m);     // arrival counter, step sequence, published-value slots
 
 // ---------------------------------------------------------------- internal entry points
 // assembly (fe_assemble.cu)

@@ -40,54 +40,93 @@ __device__ __forceinline__ double sum_partials(const double* part, double* sh) {
 }
 
 // ---------------------------------------------------------------- grid reduction with publish
-// Each block passes its block sum (valid in thread 0).  The last block to
-// arrive adds the partials in block order with one warp (deterministic for a
-// given grid), stores the total in *pub and releases the others; every
-// thread of every block returns the same total in `out`.  The wait is
-// bounded: after ~2^26 polls (seconds) the block records DEV_ERR_TIMEOUT and
-// returns false, and every later wait returns at once, so a launch always ends.
-__device__ __forceinline__ bool grid_reduce(double bsum, double* part, unsigned* bar, double* pub, int* err,
-                                            double& out) {
-  __shared__ int s_last, s_fail;
-  __shared__ unsigned s_gen;
-  __shared__ double s_val;
-  if (threadIdx.x == 0) {
-    s_fail = 0;
-    s_gen = *(volatile unsigned*)(bar + 1);
-    part[blockIdx.x] = bsum;
-    __threadfence();
-    s_last = atomicAdd(bar, 1u) == gridDim.x - 1;
-  }
-  __syncthreads();
-  if (s_last) {
-    if (threadIdx.x < 32) {
-      __threadfence();
+// Sequential inner products of the persistent kernels, one grid-wide
+// reduction each.  Warp 0 of every block does the synchronisation:
+//   arrive : lane 0 stores the block partial and increments the arrival
+//            counter with acq_rel semantics (atom.inc wraps to 0 on the last
+//            arrival, so the counter needs no reset);
+//   publish: the last block to arrive adds the partials in block order
+//            (fixed order: deterministic for a given grid), resets the slot
+//            of the next step to a sentinel and stores the total with
+//            release semantics into this step's slot;
+//   wait   : the other blocks poll this step's slot (acquire loads) until it
+//            holds a value instead of the sentinel.
+// Two slots alternate by the global step sequence number seq, which lives in
+// device memory across launches.  The sentinel is a NaN payload that no
+// arithmetic produces.  The wait is bounded (2^26 polls, seconds): on
+// timeout the block records DEV_ERR_TIMEOUT and the kernel ends.
+constexpr unsigned long long kSentinel = 0x7FF4DEAD5EEDF00DULL;
+
+__device__ __forceinline__ unsigned atom_inc_acq_rel(unsigned* p, unsigned lim) {
+  unsigned old;
+  asm volatile("atom.acq_rel.gpu.global.inc.u32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(lim) : "memory");
+  return old;
+}
+__device__ __forceinline__ unsigned long long ld_acquire_u64(const unsigned long long* p) {
+  unsigned long long v;
+  asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_release_u64(unsigned long long* p, unsigned long long v) {
+  asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+__device__ __forceinline__ void st_relaxed_u64(unsigned long long* p, unsigned long long v) {
+  asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+__device__ __forceinline__ double ld_relaxed_f64(const double* p) {
+  double v;
+  asm volatile("ld.relaxed.gpu.global.f64 %0, [%1];" : "=d"(v) : "l"(p) : "memory");
+  return v;
+}
+
+struct GridSync {
+  unsigned* count;           // arrival counter
+  unsigned* seq;             // global step sequence
+  unsigned long long* slot;  // [2] published totals
+  int* err;
+};
+
+// lane 0 of warp 0 only: returns 1 for the last block to arrive
+__device__ __forceinline__ int grid_arrive(const GridSync& gs, double* part, double bsum) {
+  part[blockIdx.x] = bsum;
+  return atom_inc_acq_rel(gs.count, gridDim.x - 1) == gridDim.x - 1;
+}
+
+// warp 0: publish (last block) or wait; all threads: the total in `out`
+__device__ __forceinline__ bool grid_complete(const GridSync& gs, const double* part, unsigned seq, int last,
+                                              double* s_val, int* s_fail, double& out) {
+  if (threadIdx.x < 32) {
+    last = __shfl_sync(0xffffffffu, last, 0);
+    unsigned long long* slot = gs.slot + (seq & 1u);
+    if (last) {
+      asm volatile("fence.acq_rel.gpu;" ::: "memory");
       double s = 0.0;
-      for (int b = threadIdx.x; b < (int)gridDim.x; b += 32) s += ((volatile double*)part)[b];
+      for (int b = threadIdx.x; b < (int)gridDim.x; b += 32) s += ld_relaxed_f64(part + b);
       s = warp_sum(s);
       if (threadIdx.x == 0) {
-        *(volatile double*)pub = s;
-        s_val = s;
-        atomicExch(bar, 0u);
-        __threadfence();
-        atomicAdd(bar + 1, 1u);
+        st_relaxed_u64(gs.slot + ((seq + 1u) & 1u), kSentinel);
+        *(volatile unsigned*)gs.seq = seq + 1u;
+        st_release_u64(slot, (unsigned long long)__double_as_longlong(s));
+        *s_val = s;
+        *s_fail = 0;
       }
-    }
-  } else if (threadIdx.x == 0) {
-    unsigned spins = 0;
-    while (*(volatile unsigned*)(bar + 1) == s_gen) {
-      if (++spins > (1u << 26) || *(volatile int*)err != DEV_OK) {
-        atomicCAS(err, DEV_OK, DEV_ERR_TIMEOUT);
-        s_fail = 1;
-        break;
+    } else if (threadIdx.x == 0) {
+      unsigned spins = 0;
+      unsigned long long v;
+      *s_fail = 0;
+      while ((v = ld_acquire_u64(slot)) == kSentinel) {
+        if (++spins > (1u << 26) || *(volatile int*)gs.err != DEV_OK) {
+          atomicCAS(gs.err, DEV_OK, DEV_ERR_TIMEOUT);
+          *s_fail = 1;
+          break;
+        }
       }
+      *s_val = __longlong_as_double((long long)v);
     }
-    __threadfence();
-    s_val = *(volatile double*)pub;
   }
   __syncthreads();
-  out = s_val;
-  return s_fail == 0;
+  out = *s_val;
+  return *s_fail == 0;
 }
 
 // block sum with the result in thread 0 (others: partial garbage)
@@ -118,11 +157,16 @@ __device__ __forceinline__ double block_sum0(double v, double* sh) {
 template <int NPT, class DT, class ZT>
 __global__ void __launch_bounds__(NPT <= 8 ? 1024 : 512)
     k_arnoldi(int64_t n, int j, double* __restrict__ V, int64_t ldv, const double* __restrict__ w,
-              double* __restrict__ Hcol, double* part, unsigned* bar, double* pub, int* err,
+              double* __restrict__ Hcol, double* part, GridSync gs,
               double* __restrict__ cs, double* __restrict__ sn, double* __restrict__ g, double* __restrict__ out,
-              const DT* __restrict__ Dinv, ZT* __restrict__ z) {
+              const DT* __restrict__ Dinv, ZT* __restrict__ z, double target, int kmax, int it0, int max_it) {
   extern __shared__ __align__(16) double ws[];
   __shared__ double sh[32];
+  __shared__ int s_fail;
+  __shared__ double s_val;
+  // speculative batches: a step queued after the cycle ended does nothing
+  if (*(volatile double*)(out + 7) != 0.0) return;
+  unsigned seq = *(volatile unsigned*)gs.seq;  // no reduction completes before every block has read it
   const int64_t S = (int64_t)NPT * blockDim.x;
   const int64_t base = (int64_t)blockIdx.x * S;
   const int64_t len = base >= n ? 0 : (n - base < S ? n - base : S);
@@ -142,7 +186,8 @@ __global__ void __launch_bounds__(NPT <= 8 ? 1024 : 512)
       if (k < len) loc += ws[k] * vc[s];
     }
     double bs = block_sum0(loc, sh);
-    if (i < j) {
+    int last = threadIdx.x == 0 ? grid_arrive(gs, part, bs) : 0;
+    if (i < j) {  // the next basis vector streams in while the reduction completes
       const double* vi = V + (int64_t)(i + 1) * ldv + base;
 #pragma unroll
       for (int s = 0; s < NPT; s++) {
@@ -151,7 +196,7 @@ __global__ void __launch_bounds__(NPT <= 8 ? 1024 : 512)
       }
     }
     double h;
-    if (!grid_reduce(bs, part, bar, pub, err, h)) return;
+    if (!grid_complete(gs, part, seq++, last, &s_val, &s_fail, h)) return;
     if (blockIdx.x == 0 && threadIdx.x == 0) Hcol[i] = h;
 #pragma unroll
     for (int s = 0; s < NPT; s++) {
@@ -168,7 +213,8 @@ __global__ void __launch_bounds__(NPT <= 8 ? 1024 : 512)
   }
   double bs = block_sum0(loc, sh);
   double hn2;
-  if (!grid_reduce(bs, part, bar, pub, err, hn2)) return;
+  int last = threadIdx.x == 0 ? grid_arrive(gs, part, bs) : 0;
+  if (!grid_complete(gs, part, seq++, last, &s_val, &s_fail, hn2)) return;
   double hn = sqrt(hn2);
   if (hn > 0.0) {
     double inv = 1.0 / hn;
@@ -212,8 +258,11 @@ __global__ void __launch_bounds__(NPT <= 8 ? 1024 : 512)
     Hcol[j + 1] = 0.0;
     g[j + 1] = -sn[j] * g[j];
     g[j] = cs[j] * g[j];
-    out[0] = fabs(g[j + 1]);
+    double res = fabs(g[j + 1]);
+    out[0] = res;
     out[1] = hn;
+    out[8] = (double)(j + 1);  // steps completed in this cycle
+    if (!(res > target) || hn == 0.0 || j + 1 >= kmax || it0 + j + 1 >= max_it) out[7] = 1.0;
   }
 }
 
@@ -227,13 +276,12 @@ __device__ __forceinline__ float ld_val<__nv_bfloat16>(const __nv_bfloat16* p) {
   return __bfloat162float(*p);
 }
 
-// y_u = K x_u (+ B1 x_p): one warp per block row.  The row's values are a
-// contiguous run of 9*nblk entries; per chunk of up to 32 blocks the warp
-// loads the column indices once (lane b holds the column of block b), then
-// every lane issues all 9 of its value loads and all 9 of its x gathers
-// (column taken from the owning lane by a shuffle) before accumulating, so
-// each warp keeps ~18 independent loads in flight instead of a dependent
-// val -> col -> x chain per entry.
+// y_u = K x_u (+ B1 x_p): one warp per block row, one lane per 3x3 block.
+// A lane loads its block's column index, its 9 values (a contiguous 36-byte
+// run; the warp's 32 runs tile the row's value segment, so every sector is
+// used) and the 3 entries of x, then accumulates the 3 row sums; the warp
+// reduces them with shuffles.  Few registers keep the SM full of warps, which
+// is what hides the HBM latency of the value stream.
 template <class VT, class XT, class AT>
 __global__ void __launch_bounds__(256) k_spmv(int nn, const int* __restrict__ row_ptr, const int* __restrict__ col,
                                               const VT* __restrict__ val, const XT* __restrict__ x,
@@ -245,36 +293,20 @@ __global__ void __launch_bounds__(256) k_spmv(int nn, const int* __restrict__ ro
   if (row >= nn) return;
   const int rs = row_ptr[row], re = row_ptr[row + 1];
   AT a0 = AT(0), a1 = AT(0), a2 = AT(0);
-  for (int base = rs; base < re; base += 32) {
-    const int cb = re - base < 32 ? re - base : 32;
-    const int nf = 9 * cb;
-    const int mycol = lane < cb ? __ldg(col + base + lane) : 0;
-    const VT* vb = val + (int64_t)base * 9;
+  for (int k = rs + lane; k < re; k += 32) {
+    const int c = __ldg(col + k);
+    const VT* b = val + (int64_t)k * 9;
     AT v[9];
 #pragma unroll
     for (int t = 0; t < 9; t++) {
-      int f = lane + 32 * t;
-      if constexpr (sizeof(VT) == 8) v[t] = f < nf ? vb[f] : AT(0);
-      else v[t] = f < nf ? (AT)ld_val<VT>(vb + f) : AT(0);
+      if constexpr (sizeof(VT) == 8) v[t] = __ldg(b + t);
+      else v[t] = (AT)ld_val<VT>(b + t);
     }
-    AT xv[9];
-#pragma unroll
-    for (int t = 0; t < 9; t++) {
-      int f = lane + 32 * t;
-      int blk = f / 9;
-      int c = (f - 9 * blk) % 3;
-      int cidx = __shfl_sync(0xffffffffu, mycol, blk & 31);
-      xv[t] = f < nf ? (AT)x[3 * (int64_t)cidx + c] : AT(0);
-    }
-#pragma unroll
-    for (int t = 0; t < 9; t++) {
-      int f = lane + 32 * t;
-      int r = (f % 9) / 3;
-      AT p = v[t] * xv[t];
-      a0 += r == 0 ? p : AT(0);
-      a1 += r == 1 ? p : AT(0);
-      a2 += r == 2 ? p : AT(0);
-    }
+    const XT* xc = x + 3 * (int64_t)c;
+    AT x0 = (AT)xc[0], x1 = (AT)xc[1], x2 = (AT)xc[2];
+    a0 += v[0] * x0 + v[1] * x1 + v[2] * x2;
+    a1 += v[3] * x0 + v[4] * x1 + v[5] * x2;
+    a2 += v[6] * x0 + v[7] * x1 + v[8] * x2;
   }
   if (up_ptr) {
     for (int k = up_ptr[row] + lane; k < up_ptr[row + 1]; k += 32) {
@@ -407,8 +439,9 @@ static int pc_to_zx(fe_mesh m, const double* x) {
 static int spmv_zx(fe_mesh m, double* y) {
   const double sv = m->prec == FE_PREC_FP64 ? 8 : (m->prec == FE_PREC_MIXED_BF16 ? 2 : 4);
   const double sx = m->prec == FE_PREC_FP64 ? 8 : 4;
-  FE_SCOPE(m, FE_PROF_SPMV, (double)m->nnzb * (9 * sv + 4) + 4.0 * (m->nn + 1) + sx * (double)m->ndof + 8.0 * (double)m->ndof +
-                                (m->pres ? (double)m->nnz_up * 2 * (3 * sv + 8) + 4.0 * (m->nn + m->np + 2) : 0.0));
+  FE_SCOPE_F(m, FE_PROF_SPMV, (double)m->nnzb * (9 * sv + 4) + 4.0 * (m->nn + 1) + sx * (double)m->ndof + 8.0 * (double)m->ndof +
+                                  (m->pres ? (double)m->nnz_up * 2 * (3 * sv + 8) + 4.0 * (m->nn + m->np + 2) : 0.0),
+             18.0 * (double)m->nnzb + (m->pres ? 12.0 * (double)m->nnz_up : 0.0));
   unsigned grid = (unsigned)(((int64_t)m->nn * 32 + 255) / 256);
   unsigned gridp = (unsigned)(((int64_t)m->np * 32 + 255) / 256);
   const int* upp = m->pres ? m->up_ptr : nullptr;
@@ -580,6 +613,15 @@ struct CoopCfg {
   int npt, grid;
 };
 
+static GridSync grid_sync(fe_mesh m) {
+  GridSync gs;
+  gs.count = m->bar;
+  gs.seq = m->bar + 1;
+  gs.slot = (unsigned long long*)(m->bar + 2);
+  gs.err = m->err;
+  return gs;
+}
+
 template <int NPT, class DT, class ZT>
 static const void* arnoldi_fn() { return (const void*)k_arnoldi<NPT, DT, ZT>; }
 
@@ -587,7 +629,8 @@ static const void* arnoldi_fn() { return (const void*)k_arnoldi<NPT, DT, ZT>; }
 // whose grid of ceil(n / S) blocks can be co-resident, then launches the
 // step cooperatively.  fuse_pc: also write z = D^{-1} V_{j+1} into zx.
 template <class DT, class ZT>
-static int launch_arnoldi_t(fe_mesh m, int j, int kmax, bool fuse_pc, const DT* Dinv) {
+static int launch_arnoldi_t(fe_mesh m, int j, int kmax, bool fuse_pc, const DT* Dinv, double target, int it0,
+                            int max_it) {
   const int64_t n = m->ndof;
   const void* fns[4] = {arnoldi_fn<3, DT, ZT>(), arnoldi_fn<6, DT, ZT>(), arnoldi_fn<12, DT, ZT>(),
                         arnoldi_fn<24, DT, ZT>()};
@@ -620,21 +663,25 @@ static int launch_arnoldi_t(fe_mesh m, int j, int kmax, bool fuse_pc, const DT* 
   double* sn = m->gv + (kmax + 2);
   double* g = m->gv + 2 * (kmax + 2);
   double* out = m->scal + 3;
-  double* pub = m->scal + 7;
   double* part = m->red;
   const DT* D = fuse_pc ? Dinv : nullptr;
   ZT* z = fuse_pc ? (ZT*)m->zx : nullptr;
+  GridSync gs = grid_sync(m);
   void* args[] = {(void*)&n, (void*)&j, (void*)&V, (void*)&ldv, (void*)&m->w64, (void*)&Hcol, (void*)&part,
-                  (void*)&m->bar, (void*)&pub, (void*)&m->err, (void*)&cs, (void*)&sn, (void*)&g, (void*)&out,
-                  (void*)&D, (void*)&z};
-  FE_SCOPE(m, FE_PROF_ARNOLDI, 8.0 * (double)n * (j + 3) + (fuse_pc ? (double)n * (3.0 * sizeof(DT) + sizeof(ZT)) : 0.0));
+                  (void*)&gs, (void*)&cs, (void*)&sn, (void*)&g, (void*)&out,
+                  (void*)&D, (void*)&z, (void*)&target, (void*)&kmax, (void*)&it0, (void*)&max_it};
+  // flops: (j+1) inner products and axpys (4 per entry), the norm (2) and the scaling (1)
+  // per entry, plus 18 per node for the fused block-Jacobi product
+  FE_SCOPE_F(m, FE_PROF_ARNOLDI, 8.0 * (double)n * (j + 3) + (fuse_pc ? (double)n * (3.0 * sizeof(DT) + sizeof(ZT)) : 0.0),
+             (double)n * (4.0 * (j + 1) + 3.0) + (fuse_pc ? 6.0 * n : 0.0));
   FE_CUDA(cudaLaunchCooperativeKernel(fns[which], dim3(grid), dim3(bds[which]), args, smem, m->stream));
   return FE_OK;
 }
 
-static int launch_arnoldi(fe_mesh m, int j, int kmax, bool fuse_pc) {
-  if (m->prec == FE_PREC_FP64) return launch_arnoldi_t<double, double>(m, j, kmax, fuse_pc, m->Dinv64);
-  return launch_arnoldi_t<float, float>(m, j, kmax, fuse_pc, m->Dinv32);
+static int launch_arnoldi(fe_mesh m, int j, int kmax, bool fuse_pc, double target, int it0, int max_it) {
+  if (m->prec == FE_PREC_FP64)
+    return launch_arnoldi_t<double, double>(m, j, kmax, fuse_pc, m->Dinv64, target, it0, max_it);
+  return launch_arnoldi_t<float, float>(m, j, kmax, fuse_pc, m->Dinv32, target, it0, max_it);
 }
 
 // ---------------------------------------------------------------- GMRES
@@ -642,6 +689,8 @@ static int launch_arnoldi(fe_mesh m, int j, int kmax, bool fuse_pc) {
 // Stops when the residual estimate |g_{j+1}| <= max(rtol ||b||, atol), on a
 // lucky breakdown, or after max_it iterations; the iterate is updated at the
 // end of every cycle with x += M^{-1} V_j y.
+constexpr int GMRES_BATCH = 8;
+
 int fe_gmres_dev(fe_mesh m, const double* b, double* x, double rtol, double atol, int restart, int max_it,
                  int* iters, double* res) {
   if (m->prec < 0) return fe_set_error("no tangent assembled"), FE_ERR_STATE;
@@ -679,30 +728,38 @@ int fe_gmres_dev(fe_mesh m, const double* b, double* x, double rtol, double atol
       k_scale<<<gs, 256, 0, m->stream>>>(n, m->scal + 6, m->V, g, kmax + 1);
     }
     FE_CUDA(cudaGetLastError());
-    int j = 0;
-    bool done = false;
     // the block-Jacobi application is fused into the Arnoldi step (it writes
     // z = D^{-1} V_{j+1} for the next SpMV); the u-p Schur preconditioner
-    // needs B2 z_u and runs as its own kernels
+    // needs B2 z_u and runs as its own kernels.  Steps are queued in batches
+    // of GMRES_BATCH; the step that meets the stopping test raises a device
+    // flag that turns the rest of its batch into no-ops, so the host reads
+    // the scalars once per batch.
     const bool fuse = !m->pres;
-    for (j = 0; j < kmax; j++) {
-      if (j == 0 || !fuse) FE_TRY(pc_to_zx(m, m->V + (int64_t)j * n));
-      FE_TRY(spmv_zx(m, m->w64));
-      FE_TRY(launch_arnoldi(m, j, kmax, fuse));
+    FE_CUDA(cudaMemsetAsync(m->scal + 10, 0, 2 * sizeof(double), m->stream));  // out[7], out[8]
+    int batch = 1;
+    bool done = false;
+    int j = 0;
+    while (!done) {
+      const int jprev = j;
+      int jend = std::min(j + batch, kmax);
+      for (int jj = j; jj < jend; jj++) {
+        if (jj == 0 || !fuse) FE_TRY(pc_to_zx(m, m->V + (int64_t)jj * n));
+        FE_TRY(spmv_zx(m, m->w64));
+        FE_TRY(launch_arnoldi(m, jj, kmax, fuse, target, it, max_it));
+      }
       FE_CUDA(cudaMemcpyAsync(m->h_scal + 3, m->scal + 3, (SCAL_N - 3) * sizeof(double), cudaMemcpyDeviceToHost,
                               m->stream));
       FE_CUDA(cudaStreamSynchronize(m->stream));
       if (*(const int*)(m->h_scal + SCAL_N - 1) != DEV_OK) FE_TRY(fe_check_device_error(m));
-      it++;
+      done = m->h_scal[10] != 0.0;
+      j = (int)m->h_scal[11];
       resid = m->h_scal[3];
-      double hn = m->h_scal[4];
-      if (resid <= target || it >= max_it || hn == 0.0 || !std::isfinite(resid)) {
-        done = true;
-        j++;
-        break;
-      }
+      if (!std::isfinite(resid)) done = true;
+      if (!done && j <= jprev) return fe_set_error("GMRES made no progress in a batch"), FE_ERR_STATE;
+      batch = std::min(2 * batch, GMRES_BATCH);
     }
-    if (!done) j = kmax;
+    it += j;
+    done = resid <= target || it >= max_it || m->h_scal[4] == 0.0 || !std::isfinite(resid);
     {
       FE_SCOPE(m, FE_PROF_VECTOR, 8.0 * j * (j + 1));
       k_trisolve<<<1, 256, 0, m->stream>>>(j, kmax + 1, m->H, g, y);
@@ -729,8 +786,11 @@ __global__ void __launch_bounds__(256) k_twoloop1(int64_t n, int k, int head, in
                                                   const double* __restrict__ Y, int64_t ld,
                                                   const double* __restrict__ rho, const double* __restrict__ qin,
                                                   double* __restrict__ qout, double* __restrict__ alpha, double* part,
-                                                  unsigned* bar, double* pub, int* err) {
+                                                  GridSync gs) {
   __shared__ double sh[32];
+  __shared__ int s_fail;
+  __shared__ double s_val;
+  unsigned seq = *(volatile unsigned*)gs.seq;
   const int64_t T = (int64_t)gridDim.x * blockDim.x;
   const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   double q[NPT];
@@ -750,14 +810,15 @@ __global__ void __launch_bounds__(256) k_twoloop1(int64_t n, int k, int head, in
       if (idx < n) loc += si[idx] * q[s];
     }
     double bs = block_sum0(loc, sh);
-    double yv[NPT];  // loaded before the reduction's wait
+    int last = threadIdx.x == 0 ? grid_arrive(gs, part, bs) : 0;
+    double yv[NPT];  // streams in while the reduction completes
 #pragma unroll
     for (int s = 0; s < NPT; s++) {
       int64_t idx = tid + s * T;
       yv[s] = idx < n ? yi[idx] : 0.0;
     }
     double tot;
-    if (!grid_reduce(bs, part, bar, pub, err, tot)) return;
+    if (!grid_complete(gs, part, seq++, last, &s_val, &s_fail, tot)) return;
     double a = rho[slot] * tot;
     if (blockIdx.x == 0 && threadIdx.x == 0) alpha[c] = a;
 #pragma unroll
@@ -776,8 +837,11 @@ __global__ void __launch_bounds__(256) k_twoloop2(int64_t n, int k, int head, in
                                                   const double* __restrict__ Y, int64_t ld,
                                                   const double* __restrict__ rho, const double* __restrict__ alpha,
                                                   const double* __restrict__ zin, double* __restrict__ zout,
-                                                  double* part, unsigned* bar, double* pub, int* err) {
+                                                  double* part, GridSync gs) {
   __shared__ double sh[32];
+  __shared__ int s_fail;
+  __shared__ double s_val;
+  unsigned seq = *(volatile unsigned*)gs.seq;
   const int64_t T = (int64_t)gridDim.x * blockDim.x;
   const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   double z[NPT];
@@ -797,14 +861,15 @@ __global__ void __launch_bounds__(256) k_twoloop2(int64_t n, int k, int head, in
       if (idx < n) loc += yi[idx] * z[s];
     }
     double bs = block_sum0(loc, sh);
-    double sv[NPT];  // loaded before the reduction's wait
+    int last = threadIdx.x == 0 ? grid_arrive(gs, part, bs) : 0;
+    double sv[NPT];  // streams in while the reduction completes
 #pragma unroll
     for (int s = 0; s < NPT; s++) {
       int64_t idx = tid + s * T;
       sv[s] = idx < n ? si[idx] : 0.0;
     }
     double tot;
-    if (!grid_reduce(bs, part, bar, pub, err, tot)) return;
+    if (!grid_complete(gs, part, seq++, last, &s_val, &s_fail, tot)) return;
     double beta = rho[slot] * tot;
     double coef = alpha[c] - beta;
 #pragma unroll
@@ -846,7 +911,7 @@ static int launch_twoloop(fe_mesh m, int which, void** args) {
   int need = (int)((n + per_block - 1) / per_block);
   if (need < grid) grid = need;
   int k = *(int*)args[1];
-  FE_SCOPE(m, FE_PROF_TWOLOOP, 16.0 * (double)n * (k + 1));
+  FE_SCOPE_F(m, FE_PROF_TWOLOOP, 16.0 * (double)n * (k + 1), 4.0 * (double)n * k);
   FE_CUDA(cudaLaunchCooperativeKernel(fns[q], dim3(grid), dim3(256), args, 0, m->stream));
   return FE_OK;
 }
@@ -863,10 +928,10 @@ int fe_lbfgs_dev(fe_mesh m, const double* S, const double* Y, const double* rho,
   double* alpha = m->alpha_d;
   double* qbuf = m->t64;
   double* part = m->red;
-  double* pub = m->scal + 9;
+  GridSync gs = grid_sync(m);
   if (k > 0) {
     void* a1[] = {(void*)&n, (void*)&k, (void*)&head, (void*)&mcap, (void*)&S, (void*)&Y, (void*)&ld, (void*)&rho,
-                  (void*)&q, (void*)&qbuf, (void*)&alpha, (void*)&part, (void*)&m->bar, (void*)&pub, (void*)&m->err};
+                  (void*)&q, (void*)&qbuf, (void*)&alpha, (void*)&part, (void*)&gs};
     FE_TRY(launch_twoloop(m, 1, a1));
   } else {
     FE_SCOPE(m, FE_PROF_VECTOR, 16.0 * n);
@@ -897,8 +962,7 @@ int fe_lbfgs_dev(fe_mesh m, const double* S, const double* Y, const double* rho,
   FE_CUDA(cudaGetLastError());
   if (k > 0) {
     void* a2[] = {(void*)&n, (void*)&k, (void*)&head, (void*)&mcap, (void*)&S, (void*)&Y, (void*)&ld,
-                  (void*)&rho, (void*)&alpha, (void*)&zb, (void*)&z, (void*)&part, (void*)&m->bar, (void*)&pub,
-                  (void*)&m->err};
+                  (void*)&rho, (void*)&alpha, (void*)&zb, (void*)&z, (void*)&part, (void*)&gs};
     FE_TRY(launch_twoloop(m, 2, a2));
   } else {
     FE_SCOPE(m, FE_PROF_VECTOR, 16.0 * n);

@@ -40,14 +40,24 @@ int fe_alloc(fe_mesh m, void** p, size_t bytes) {
   return FE_OK;
 }
 
+// grid-reduction state of the persistent kernels: arrival counter, step
+// sequence, and two published-value slots holding the "not yet" sentinel
+int fe_reset_grid_sync(fe_mesh m) {
+  static const unsigned long long sentinel = 0x7FF4DEAD5EEDF00DULL;
+  unsigned long long init[4] = {0ull, sentinel, sentinel, 0ull};  // {count, seq}, slot0, slot1, pad
+  FE_CUDA(cudaMemcpyAsync(m->bar, init, sizeof(init), cudaMemcpyHostToDevice, m->stream));
+  FE_CUDA(cudaStreamSynchronize(m->stream));
+  return FE_OK;
+}
+
 int fe_check_device_error(fe_mesh m) {
   int h = 0;
   FE_CUDA(cudaMemcpyAsync(&h, m->err, sizeof(int), cudaMemcpyDeviceToHost, m->stream));
   FE_CUDA(cudaStreamSynchronize(m->stream));
   if (h == DEV_OK) return FE_OK;
-  // clear the error word and the barrier arrival counter for later calls
+  // clear the error word and the grid-synchronisation state for later calls
   cudaMemsetAsync(m->err, 0, sizeof(int), m->stream);
-  cudaMemsetAsync(m->bar, 0, sizeof(unsigned), m->stream);
+  fe_reset_grid_sync(m);
   cudaStreamSynchronize(m->stream);
   if (h == DEV_ERR_TIMEOUT) {
     fe_set_error("a bounded device wait ran out (grid barrier)");
@@ -75,6 +85,7 @@ static void prof_resolve(fe_mesh m) {
     if (cudaEventSynchronize(r.b) == cudaSuccess && cudaEventElapsedTime(&ms, r.a, r.b) == cudaSuccess) {
       m->prof_ms[r.cls] += ms;
       m->prof_bytes[r.cls] += r.bytes;
+      m->prof_flops[r.cls] += r.flops;
       m->prof_timed[r.cls]++;
     }
     m->ev_free.push_back(r.a);
@@ -83,7 +94,8 @@ static void prof_resolve(fe_mesh m) {
   m->prof_pending.clear();
 }
 
-LaunchScope::LaunchScope(fe_mesh m_, int cls_, double bytes_) : m(m_), cls(cls_), bytes(bytes_) {
+LaunchScope::LaunchScope(fe_mesh m_, int cls_, double bytes_, double flops_)
+    : m(m_), cls(cls_), bytes(bytes_), flops(flops_) {
   m->prof_launches[cls]++;
   if (m->prof_timing) {
     a = ev_get(m);
@@ -95,7 +107,7 @@ LaunchScope::~LaunchScope() {
   if (!a) return;
   cudaEvent_t b = ev_get(m);
   cudaEventRecord(b, m->stream);
-  m->prof_pending.push_back({cls, a, b, bytes});
+  m->prof_pending.push_back({cls, a, b, bytes, flops});
   if (m->prof_pending.size() > 50000) prof_resolve(m);
 }
 
@@ -106,7 +118,7 @@ extern "C" int fe_profile_reset(fe_mesh m, int timing) {
   prof_resolve(m);
   for (int c = 0; c < FE_PROF_CLASSES; c++) {
     m->prof_launches[c] = m->prof_timed[c] = 0;
-    m->prof_ms[c] = m->prof_bytes[c] = 0.0;
+    m->prof_ms[c] = m->prof_bytes[c] = m->prof_flops[c] = 0.0;
   }
   m->prof_timing = timing ? 1 : 0;
   return FE_OK;
@@ -122,6 +134,7 @@ extern "C" int fe_profile_read(fe_mesh m, fe_profile_info* out) {
     out->timed[c] = m->prof_timed[c];
     out->ms[c] = m->prof_ms[c];
     out->bytes[c] = m->prof_bytes[c];
+    out->flops[c] = m->prof_flops[c];
   }
   return FE_OK;
 }
@@ -566,8 +579,8 @@ static int create_impl(const fe_mesh_desc* desc, fe_mesh m) {
     FE_TRY(upload(m, &m->fib, fib));
   }
 
-  FE_TRY(fe_alloc_t(m, &m->bar, 4));
-  FE_CUDA(cudaMemsetAsync(m->bar, 0, 4 * sizeof(unsigned), m->stream));
+  FE_TRY(fe_alloc_t(m, &m->bar, 8));
+  FE_TRY(fe_reset_grid_sync(m));
   FE_TRY(fe_alloc_t(m, &m->red, RED_SLOTS));
   FE_TRY(fe_alloc_t(m, &m->red_ticket, 4));
   FE_CUDA(cudaMemsetAsync(m->red_ticket, 0, 4 * sizeof(unsigned), m->stream));
