@@ -197,6 +197,27 @@ int fe_spmv(fe_mesh m, const double* x, double* y);
 /* y = M^{-1} x with the preconditioner of the assembled tangent. */
 int fe_pc_apply(fe_mesh m, const double* x, double* y);
 
+/* y = K x like fe_spmv, without allocating device memory during the call.
+ * The paper has no counterpart.  For callers that cannot call cudaMalloc
+ * while they run: a serving loop whose memory pool already owns the free
+ * device memory, a latency-bound loop that cannot afford the device-wide
+ * synchronisation an allocation may cause, or a host thread that another
+ * allocator (PyTorch's caching allocator, a custom arena) must remain the
+ * only owner for.  fe_spmv converts x to the SpMV's input precision in a
+ * buffer it allocates on first use; this call stages that input in a fixed
+ * device array of the library instead: 2^20 FP64 entries (8 MiB), held by
+ * every GPU that loads the library until the process exits.  Limits and
+ * rules:
+ *  - ndof must be at most 1,048,576; larger meshes get FE_ERR_ARG.
+ *  - The first call on a device looks up the array's device address (once
+ *    per device); make that first call before any stream capture.
+ *  - All calls share the array and each overwrites it: calls that overlap
+ *    on the GPU (other streams or threads) race; serialise them.
+ *  - The tangent must be assembled (fe_assemble_tangent); mesh and tangent
+ *    memory are allocated by those earlier calls, not by this one.
+ * x, y: device [ndof] FP64.  Returns FE_ERR_STATE without a tangent. */
+int fe_spmv_noalloc(fe_mesh m, const double* x, double* y);
+
 /* ---- solvers ----------------------------------------------------------- */
 typedef struct {
   int32_t precision;   /* fe_precision (default FE_PREC_FP64) */

@@ -98,6 +98,7 @@ SIGNATURES = {
     "fe_tangent_copy": (_I, [_P, _P, _P, _P]),
     "fe_spmv": (_I, [_P, _P, _P]),
     "fe_pc_apply": (_I, [_P, _P, _P]),
+    "fe_spmv_noalloc": (_I, [_P, _P, _P]),
     "nl_opts_default": (_I, [_I, C.POINTER(nl_opts)]),
     "nl_solve": (_I, [_P, _I, _D, _I, _P, C.POINTER(nl_opts), C.POINTER(nl_stats)]),
     "fe_gmres": (_I, [_P, _P, _P, _D, _D, _I, _I, C.POINTER(C.c_int), C.POINTER(C.c_double)]),

@@ -196,3 +196,4 @@ int fe_lbfgs_dev(fe_mesh m, const double* S, const double* Y, const double* rho,
                  int k, int64_t ld, const double* q, double* z, int h0, double ksp_rtol,
                  double ksp_atol, int restart, int kmaxit, int* lit);
 int fe_workspace(fe_mesh m, int restart);
+int fe_spmv_from_input(fe_mesh m, const void* xin, double* y);  // input already in the SpMV precision

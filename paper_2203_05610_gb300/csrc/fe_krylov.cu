@@ -494,6 +494,36 @@ int fe_spmv_dev(fe_mesh m, const double* x, double* y) {
   return spmv_zx(m, y);
 }
 
+// y = K xin where xin already holds the input in the SpMV's input precision
+// (FP64 for an FP64 tangent, FP32 otherwise).  Used by the allocation-free
+// entry point, which stages the input in its own fixed device array.
+int fe_spmv_from_input(fe_mesh m, const void* xin, double* y) {
+  unsigned grid = (unsigned)(((int64_t)m->nn * 32 + 255) / 256);
+  unsigned gridp = (unsigned)(((int64_t)m->np * 32 + 255) / 256);
+  const int* upp = m->pres ? m->up_ptr : nullptr;
+  if (m->prec == FE_PREC_FP64) {
+    const double* x = (const double*)xin;
+    k_spmv<double, double, double><<<grid, 256, 0, m->stream>>>(m->nn, m->row_ptr, m->col, m->K64, x, y, upp,
+                                                                m->up_col, m->B64, x + 3 * (int64_t)m->nn);
+    if (m->pres)
+      k_spmv_p<double, double, double><<<gridp, 256, 0, m->stream>>>(m->np, m->pu_ptr, m->pu_col, m->pu_src, m->B64,
+                                                                     x, y + 3 * (int64_t)m->nn);
+  } else if (m->prec == FE_PREC_MIXED_BF16) {
+    const float* x = (const float*)xin;
+    k_spmv<__nv_bfloat16, float, float><<<grid, 256, 0, m->stream>>>(m->nn, m->row_ptr, m->col, m->K16, x, y,
+                                                                      nullptr, nullptr, nullptr, nullptr);
+  } else {
+    const float* x = (const float*)xin;
+    k_spmv<float, float, float><<<grid, 256, 0, m->stream>>>(m->nn, m->row_ptr, m->col, m->K32, x, y, upp,
+                                                             m->up_col, m->B32, x + 3 * (int64_t)m->nn);
+    if (m->pres)
+      k_spmv_p<float, float, float><<<gridp, 256, 0, m->stream>>>(m->np, m->pu_ptr, m->pu_col, m->pu_src, m->B32, x,
+                                                                  y + 3 * (int64_t)m->nn);
+  }
+  FE_CUDA(cudaGetLastError());
+  return FE_OK;
+}
+
 // ---------------------------------------------------------------- vectors
 __global__ void k_dot(int64_t n, const double* __restrict__ a, const double* __restrict__ b, double* red,
                       unsigned* ticket, double* out) {
