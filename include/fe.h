@@ -61,7 +61,8 @@ typedef enum {
   FE_PREC_FP64 = 0,       /* tangent, SpMV, preconditioner in FP64 */
   FE_PREC_MIXED_FP32 = 1, /* tangent assembled and stored in FP32; SpMV and
                              preconditioner in FP32; Arnoldi, residual,
-                             update and BFGS products stay FP64 */
+                             update and BFGS products stay FP64; Krylov
+                             relative tolerances are clamped at 1e-5 */
   FE_PREC_MIXED_BF16 = 2  /* as MIXED_FP32 with BF16 tangent storage */
 } fe_precision;
 typedef enum {
@@ -230,6 +231,10 @@ typedef struct {
   int32_t lbfgs_m;     /* stored secant pairs, default 50 */
   double dtol;         /* divergence: ||R|| > dtol*||R0||, default 1e4 */
   int32_t apply_dirichlet; /* 1 (default): write prescribed values into d first */
+  int32_t orthog;      /* Arnoldi orthogonalisation: 0 (default) the sequential modified
+                          Gram-Schmidt sweep the paper uses (j+2 grid reductions per step);
+                          1 the same MGS projections in compact-WY form (2 grid
+                          reductions per step, ~1.5x the FP64 work, restart <= 128) */
 } nl_opts;
 
 #define NL_HIST 1024
@@ -263,10 +268,12 @@ int nl_solve(fe_mesh m, int method, double tol, int max_it, double* d,
              const nl_opts* opts, nl_stats* stats);
 
 /* Solve K x = b with GMRES on the assembled tangent (device [ndof] FP64;
- * x holds the initial guess and is overwritten).  iters/res_out (host,
- * nullable) receive the iteration count and the final residual estimate. */
+ * x holds the initial guess and is overwritten); orthog as in nl_opts.
+ * iters/res_out (host, nullable) receive the iteration count and the final
+ * residual estimate.  Paper: GMRES with modified Gram-Schmidt (Section
+ * "Test problems and solvers details"), right preconditioning (reading). */
 int fe_gmres(fe_mesh m, const double* b, double* x, double rtol, double atol,
-             int restart, int max_it, int* iters, double* res_out);
+             int restart, int max_it, int orthog, int* iters, double* res_out);
 
 /* One L-BFGS two-loop application z = H q over k stored pairs (device
  * pointers: S, Y [k][ndof] row-major oldest first, rho [k], q, z [ndof]),

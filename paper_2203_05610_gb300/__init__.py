@@ -62,7 +62,7 @@ class nl_opts(C.Structure):
     _fields_ = [("precision", C.c_int32), ("ksp_rtol", C.c_double), ("ksp_atol", C.c_double),
                 ("ew_rtol0", C.c_double), ("ew_rtolmax", C.c_double), ("ksp_restart", C.c_int32),
                 ("ksp_max_it", C.c_int32), ("lbfgs_m", C.c_int32), ("dtol", C.c_double),
-                ("apply_dirichlet", C.c_int32)]
+                ("apply_dirichlet", C.c_int32), ("orthog", C.c_int32)]
 
 
 class nl_stats(C.Structure):
@@ -79,6 +79,23 @@ class fe_profile_info(C.Structure):
     _fields_ = [("launches", C.c_int64 * 8), ("timed", C.c_int64 * 8), ("ms", C.c_double * 8),
                 ("bytes", C.c_double * 8), ("flops", C.c_double * 8)]
 
+
+class fe_server_opts(C.Structure):
+    _fields_ = [("device", C.c_int32), ("hbm_budget", C.c_int64), ("max_active", C.c_int32)]
+
+
+class fe_request(C.Structure):
+    _fields_ = [("mesh", C.POINTER(fe_mesh_desc)), ("method", C.c_int32), ("tol", C.c_double),
+                ("max_it", C.c_int32), ("opts", C.POINTER(nl_opts)), ("load", C.c_double), ("time", C.c_double),
+                ("d0", C.c_void_p)]
+
+
+class fe_request_status(C.Structure):
+    _fields_ = [("state", C.c_int32), ("result", C.c_int32), ("ndof", C.c_int64), ("footprint", C.c_int64),
+                ("t_submit", C.c_double), ("t_start", C.c_double), ("t_end", C.c_double), ("stats", nl_stats)]
+
+
+REQ_STATES = {0: "queued", 1: "running", 2: "done", 3: "failed"}
 
 _lib = None
 _lock = threading.Lock()
@@ -101,10 +118,15 @@ SIGNATURES = {
     "fe_spmv_noalloc": (_I, [_P, _P, _P]),
     "nl_opts_default": (_I, [_I, C.POINTER(nl_opts)]),
     "nl_solve": (_I, [_P, _I, _D, _I, _P, C.POINTER(nl_opts), C.POINTER(nl_stats)]),
-    "fe_gmres": (_I, [_P, _P, _P, _D, _D, _I, _I, C.POINTER(C.c_int), C.POINTER(C.c_double)]),
+    "fe_gmres": (_I, [_P, _P, _P, _D, _D, _I, _I, _I, C.POINTER(C.c_int), C.POINTER(C.c_double)]),
     "fe_lbfgs_apply": (_I, [_P, _P, _P, _P, _I, _P, _P, _I]),
     "fe_profile_reset": (_I, [_P, _I]),
     "fe_profile_read": (_I, [_P, C.POINTER(fe_profile_info)]),
+    "serve_create": (_I, [C.POINTER(fe_server_opts), C.POINTER(C.c_void_p)]),
+    "serve_submit": (_I, [_P, C.POINTER(fe_request), C.POINTER(C.c_int64)]),
+    "serve_poll": (_I, [_P, C.c_int64, _I, C.POINTER(fe_request_status), _P]),
+    "serve_clock": (_D, [_P]),
+    "serve_destroy": (_I, [_P]),
     "fe_last_error": (C.c_char_p, []),
 }
 
@@ -155,6 +177,53 @@ def material_struct(m):
     return s
 
 
+def make_desc(w, device=0):
+    """fe_mesh_desc for a workload dict, with the arrays it points to."""
+    groups = (fe_dirichlet_group * max(len(w["groups"]), 1))()
+    for g, G in enumerate(w["groups"]):
+        groups[g].comp_mask = int(G["mask"])
+        groups[g].center[:] = [float(x) for x in G["center"]]
+        groups[g].angle = float(G["angle"])
+        groups[g].translation[:] = [float(x) for x in G["translation"]]
+    d = fe_mesh_desc()
+    d.order = int(w["order"])
+    d.pressure_order = int(w["pressure_order"])
+    d.nv = int(w["coords"].shape[0])
+    d.ne = int(w["tets"].shape[0])
+    keep = [np.ascontiguousarray(w["coords"], dtype=np.float64),
+            np.ascontiguousarray(w["tets"], dtype=np.int32),
+            np.ascontiguousarray(w["dir_group"], dtype=np.uint8),
+            np.ascontiguousarray(w["faces"], dtype=np.int32).reshape(-1, 3),
+            np.ascontiguousarray(w["face_kind"], dtype=np.int32).reshape(-1),
+            np.ascontiguousarray(w["face_data"], dtype=np.float64).reshape(-1, 3),
+            None if w["fibers"] is None else np.ascontiguousarray(w["fibers"], dtype=np.float64),
+            groups]
+    d.coords = _np_ptr(keep[0])
+    d.tets = _np_ptr(keep[1])
+    d.dir_group = _np_ptr(keep[2])
+    d.ngroups = len(w["groups"])
+    d.groups = C.cast(groups, C.c_void_p)
+    d.nf = int(keep[3].shape[0])
+    d.faces = _np_ptr(keep[3])
+    d.face_kind = _np_ptr(keep[4])
+    d.face_data = _np_ptr(keep[5])
+    d.material = material_struct(w["material"])
+    d.fibers = _np_ptr(keep[6])
+    d.device = int(device)
+    d.stream = None
+    return d, keep
+
+
+def _opts_struct(method, opts):
+    o = nl_opts()
+    _check(lib().nl_opts_default(method, C.byref(o)))
+    for k, v in (opts or {}).items():
+        if k == "precision" and isinstance(v, str):
+            v = PRECISIONS[v]
+        setattr(o, k, v)
+    return o
+
+
 class Mesh:
     """A mesh (and its solver state) resident on one GPU.
 
@@ -166,38 +235,7 @@ class Mesh:
         import torch
         L = lib()
         self.device = torch.device("cuda", device)
-        groups = (fe_dirichlet_group * max(len(w["groups"]), 1))()
-        for g, G in enumerate(w["groups"]):
-            groups[g].comp_mask = int(G["mask"])
-            groups[g].center[:] = [float(x) for x in G["center"]]
-            groups[g].angle = float(G["angle"])
-            groups[g].translation[:] = [float(x) for x in G["translation"]]
-        d = fe_mesh_desc()
-        d.order = int(w["order"])
-        d.pressure_order = int(w["pressure_order"])
-        d.nv = int(w["coords"].shape[0])
-        d.ne = int(w["tets"].shape[0])
-        self._keep = [np.ascontiguousarray(w["coords"], dtype=np.float64),
-                      np.ascontiguousarray(w["tets"], dtype=np.int32),
-                      np.ascontiguousarray(w["dir_group"], dtype=np.uint8),
-                      np.ascontiguousarray(w["faces"], dtype=np.int32).reshape(-1, 3),
-                      np.ascontiguousarray(w["face_kind"], dtype=np.int32).reshape(-1),
-                      np.ascontiguousarray(w["face_data"], dtype=np.float64).reshape(-1, 3),
-                      None if w["fibers"] is None else np.ascontiguousarray(w["fibers"], dtype=np.float64),
-                      groups]
-        d.coords = _np_ptr(self._keep[0])
-        d.tets = _np_ptr(self._keep[1])
-        d.dir_group = _np_ptr(self._keep[2])
-        d.ngroups = len(w["groups"])
-        d.groups = C.cast(groups, C.c_void_p)
-        d.nf = int(self._keep[3].shape[0])
-        d.faces = _np_ptr(self._keep[3])
-        d.face_kind = _np_ptr(self._keep[4])
-        d.face_data = _np_ptr(self._keep[5])
-        d.material = material_struct(w["material"])
-        d.fibers = _np_ptr(self._keep[6])
-        d.device = int(device)
-        d.stream = None
+        d, self._keep = make_desc(w, device)
         torch.cuda.init()
         h = C.c_void_p()
         _check(L.fe_mesh_create(C.byref(d), C.byref(h)))
@@ -277,12 +315,12 @@ class Mesh:
         _check(lib().fe_pc_apply(self.h, self._vec(x), self._vec(y, "y")))
         return y
 
-    def gmres(self, b, x=None, rtol=1e-6, atol=1e-10, restart=500, max_it=10000):
+    def gmres(self, b, x=None, rtol=1e-6, atol=1e-10, restart=500, max_it=10000, orthog=0):
         x = self.zeros() if x is None else x
         it = C.c_int()
         res = C.c_double()
         _check(lib().fe_gmres(self.h, self._vec(b, "b"), self._vec(x), float(rtol), float(atol), int(restart),
-                              int(max_it), C.byref(it), C.byref(res)))
+                              int(max_it), int(orthog), C.byref(it), C.byref(res)))
         return x, it.value, res.value
 
     def lbfgs_apply(self, S, Y, rho, q, h0=0):
@@ -309,12 +347,7 @@ class Mesh:
         mth = METHODS[method] if isinstance(method, str) else int(method)
         if max_it is None:
             max_it = 50 if mth < 2 else 1000
-        o = nl_opts()
-        _check(lib().nl_opts_default(mth, C.byref(o)))
-        for k, v in (opts or {}).items():
-            if k == "precision" and isinstance(v, str):
-                v = PRECISIONS[v]
-            setattr(o, k, v)
+        o = _opts_struct(mth, opts)
         st = nl_stats()
         rc = _check(lib().nl_solve(self.h, mth, float(tol), int(max_it), self._vec(d, "d"), C.byref(o),
                                    C.byref(st)))
@@ -323,3 +356,65 @@ class Mesh:
                      rfinal=st.rfinal, time_s=st.time_s, res_hist=np.array(st.res_hist[:n]),
                      lit_hist=np.array(st.lit_hist[:n]), eta_hist=np.array(st.eta_hist[:n]))
         return d, stats
+
+
+def _stats_dict(st):
+    n = st.hist_len
+    return dict(status=st.status, nit=st.nit, lit_total=int(st.lit_total), assemblies=st.assemblies, r0=st.r0,
+                rfinal=st.rfinal, time_s=st.time_s, res_hist=np.array(st.res_hist[:n]),
+                lit_hist=np.array(st.lit_hist[:n]), eta_hist=np.array(st.eta_hist[:n]))
+
+
+class Server:
+    """Continuous-batching request loop on one GPU (include/fe_serve.h)."""
+
+    def __init__(self, device=0, hbm_budget=0, max_active=8):
+        import torch
+        torch.cuda.init()
+        o = fe_server_opts(device=int(device), hbm_budget=int(hbm_budget), max_active=int(max_active))
+        h = C.c_void_p()
+        _check(lib().serve_create(C.byref(o), C.byref(h)))
+        self.h = h
+        self._ndof = {}
+
+    def submit(self, w, method, tol=1e-8, max_it=None, opts=None, load=1.0, time=0.0, d0=None):
+        mth = METHODS[method] if isinstance(method, str) else int(method)
+        if max_it is None:
+            max_it = 50 if mth < 2 else 1000
+        d, keep = make_desc(w)
+        o = _opts_struct(mth, opts)
+        d0a = None if d0 is None else np.ascontiguousarray(d0, dtype=np.float64)
+        q = fe_request(mesh=C.pointer(d), method=mth, tol=float(tol), max_it=int(max_it), opts=C.pointer(o),
+                       load=float(load), time=float(time), d0=_np_ptr(d0a))
+        rid = C.c_int64()
+        _check(lib().serve_submit(self.h, C.byref(q), C.byref(rid)))
+        del keep
+        return int(rid.value)
+
+    def poll(self, rid, wait=False):
+        st = fe_request_status()
+        _check(lib().serve_poll(self.h, int(rid), 1 if wait else 0, C.byref(st), None))
+        out = dict(state=REQ_STATES[st.state], result=st.result, ndof=int(st.ndof), footprint=int(st.footprint),
+                   t_submit=st.t_submit, t_start=st.t_start, t_end=st.t_end)
+        if st.state == 2:
+            x = np.zeros(int(st.ndof))
+            _check(lib().serve_poll(self.h, int(rid), 0, C.byref(st), _np_ptr(x)))
+            out["d"] = x
+            out["stats"] = _stats_dict(st.stats)
+        elif st.state == 3:
+            out["error"] = lib().fe_last_error().decode()
+        return out
+
+    def clock(self):
+        return float(lib().serve_clock(self.h))
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().serve_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

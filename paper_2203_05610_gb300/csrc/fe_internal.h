@@ -116,7 +116,13 @@ struct fe_mesh_s {
 
   // solver workspace (lazy)
   int ws_restart = 0;
-  double* V = nullptr;       // [(restart+1)][ndof]
+  double* V = nullptr;       // [(restart+1)][ldv], rows zero-padded
+  int64_t ldv = 0;           // leading dimension of V: ndof rounded up to 32
+  int orthog = 0;            // 0: sequential MGS sweep, 1: low-synchronisation MGS
+  double* Lmat = nullptr;    // [(restart+1)^2] strictly lower triangle of V^T V (low-sync MGS)
+  double* hpub = nullptr;    // [restart+1] published MGS coefficients
+  double* partv = nullptr;   // [partv_blocks][2 restart + 1] per-block inner products
+  int partv_blocks = 0;
   double* H = nullptr;       // [(restart+1)][restart] column-major by step
   double* gv = nullptr;      // Givens: cs, sn, g, y [4][restart+1]
   double* w64 = nullptr;     // [ndof]

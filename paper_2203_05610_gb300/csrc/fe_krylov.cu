@@ -89,12 +89,22 @@ struct GridSync {
 // lane 0 of warp 0 only: returns 1 for the last block to arrive
 __device__ __forceinline__ int grid_arrive(const GridSync& gs, double* part, double bsum) {
   part[blockIdx.x] = bsum;
+  if (gridDim.x == 1) return 1;  // one block: nothing to synchronise with
   return atom_inc_acq_rel(gs.count, gridDim.x - 1) == gridDim.x - 1;
 }
 
 // warp 0: publish (last block) or wait; all threads: the total in `out`
 __device__ __forceinline__ bool grid_complete(const GridSync& gs, const double* part, unsigned seq, int last,
                                               double* s_val, int* s_fail, double& out) {
+  if (gridDim.x == 1) {  // one block: its own partial is the total
+    if (threadIdx.x == 0) {
+      *s_val = part[0];
+      *s_fail = 0;
+    }
+    __syncthreads();
+    out = *s_val;
+    return true;
+  }
   if (threadIdx.x < 32) {
     last = __shfl_sync(0xffffffffu, last, 0);
     unsigned long long* slot = gs.slot + (seq & 1u);
@@ -147,30 +157,71 @@ __device__ __forceinline__ double block_sum0(double v, double* sh) {
 
 // ---------------------------------------------------------------- persistent Arnoldi (MGS)
 // Step j.  Block b owns the contiguous slice [b*S, min((b+1)*S, n)) of every
-// vector (S = NPT*blockDim, a multiple of 3 so that slices hold whole nodes);
-// w's slice lives in shared memory for the whole sweep.  For i = 0..j:
-// h_ij = <w, V_i> (one grid reduction), w -= h_ij V_i, with V_{i+1}'s slice
-// loaded into registers before the reduction's wait.  Then h_{j+1,j} = ||w||,
-// V_{j+1} = w / h_{j+1,j}, optionally z = D^{-1} V_{j+1} (nodal block-Jacobi,
-// the preconditioned vector the next SpMV needs), and block 0 applies the
+// vector (S = NPT*blockDim values, NPT a multiple of 3, so slices hold whole
+// nodes); w's slice lives in shared memory for the whole sweep.  For
+// i = 0..j: h_ij = <w, V_i> (warp sums -> one block barrier -> warp 0 adds the
+// warp sums and runs the grid reduction -> one block barrier), w -= h_ij V_i;
+// V_{i+1}'s slice is loaded into registers before the reduction.  Then
+// h_{j+1,j} = ||w||, V_{j+1} = w / h_{j+1,j}, optionally z = D^{-1} V_{j+1}
+// (nodal block-Jacobi, the input of the next SpMV), and block 0 applies the
 // previous Givens rotations to column j, forms the new one and updates g.
+// Rows of V have a leading dimension rounded up to 32 values (256 bytes).
+// warp 0 only: grid reduction of the block total `b` (valid in every lane);
+// publishes or waits; lane 0 leaves the total in *s_val
+__device__ __forceinline__ void grid_reduce_w0(const GridSync& gs, double* part, unsigned seq, double b, double* s_val,
+                                               int* s_fail) {
+  if (gridDim.x == 1) {  // one block: the block total is the result, no grid traffic
+    if (threadIdx.x == 0) *s_val = b;
+    return;
+  }
+  int last = 0;
+  if (threadIdx.x == 0) last = grid_arrive(gs, part, b);
+  last = __shfl_sync(0xffffffffu, last, 0);
+  unsigned long long* slot = gs.slot + (seq & 1u);
+  if (last) {
+    asm volatile("fence.acq_rel.gpu;" ::: "memory");
+    double s = 0.0;
+    for (int k = threadIdx.x; k < (int)gridDim.x; k += 32) s += ld_relaxed_f64(part + k);
+    s = warp_sum(s);
+    if (threadIdx.x == 0) {
+      st_relaxed_u64(gs.slot + ((seq + 1u) & 1u), kSentinel);
+      *(volatile unsigned*)gs.seq = seq + 1u;
+      st_release_u64(slot, (unsigned long long)__double_as_longlong(s));
+      *s_val = s;
+    }
+  } else if (threadIdx.x == 0) {
+    unsigned spins = 0;
+    unsigned long long v;
+    while ((v = ld_acquire_u64(slot)) == kSentinel) {
+      if (++spins > (1u << 26) || *(volatile int*)gs.err != DEV_OK) {
+        atomicCAS(gs.err, DEV_OK, DEV_ERR_TIMEOUT);
+        *s_fail = 1;
+        break;
+      }
+    }
+    *s_val = __longlong_as_double((long long)v);
+  }
+}
+
 template <int NPT, class DT, class ZT>
-__global__ void __launch_bounds__(NPT <= 8 ? 1024 : 512)
+__global__ void __launch_bounds__(NPT <= 6 ? 1024 : 512)
     k_arnoldi(int64_t n, int j, double* __restrict__ V, int64_t ldv, const double* __restrict__ w,
               double* __restrict__ Hcol, double* part, GridSync gs,
               double* __restrict__ cs, double* __restrict__ sn, double* __restrict__ g, double* __restrict__ out,
               const DT* __restrict__ Dinv, ZT* __restrict__ z, double target, int kmax, int it0, int max_it) {
   extern __shared__ __align__(16) double ws[];
-  __shared__ double sh[32];
-  __shared__ int s_fail;
+  __shared__ double wpart[32];
   __shared__ double s_val;
+  __shared__ int s_fail;
   // speculative batches: a step queued after the cycle ended does nothing
   if (*(volatile double*)(out + 7) != 0.0) return;
   unsigned seq = *(volatile unsigned*)gs.seq;  // no reduction completes before every block has read it
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
   const int64_t S = (int64_t)NPT * blockDim.x;
   const int64_t base = (int64_t)blockIdx.x * S;
-  const int64_t len = base >= n ? 0 : (n - base < S ? n - base : S);
-  for (int64_t k = threadIdx.x; k < len; k += blockDim.x) ws[k] = w[base + k];
+  const int64_t len = n - base < S ? n - base : S;
+  for (int64_t k = threadIdx.x; k < S; k += blockDim.x) ws[k] = k < len ? w[base + k] : 0.0;
+  if (threadIdx.x == 0) s_fail = 0;
   double vc[NPT], vn[NPT];
 #pragma unroll
   for (int s = 0; s < NPT; s++) {
@@ -181,13 +232,10 @@ __global__ void __launch_bounds__(NPT <= 8 ? 1024 : 512)
   for (int i = 0; i <= j; i++) {
     double loc = 0.0;
 #pragma unroll
-    for (int s = 0; s < NPT; s++) {
-      int64_t k = threadIdx.x + (int64_t)s * blockDim.x;
-      if (k < len) loc += ws[k] * vc[s];
-    }
-    double bs = block_sum0(loc, sh);
-    int last = threadIdx.x == 0 ? grid_arrive(gs, part, bs) : 0;
-    if (i < j) {  // the next basis vector streams in while the reduction completes
+    for (int s = 0; s < NPT; s++) loc += ws[threadIdx.x + s * blockDim.x] * vc[s];
+    loc = warp_sum(loc);
+    if (lane == 0) wpart[wid] = loc;
+    if (i < j) {
       const double* vi = V + (int64_t)(i + 1) * ldv + base;
 #pragma unroll
       for (int s = 0; s < NPT; s++) {
@@ -195,29 +243,34 @@ __global__ void __launch_bounds__(NPT <= 8 ? 1024 : 512)
         vn[s] = k < len ? vi[k] : 0.0;
       }
     }
-    double h;
-    if (!grid_complete(gs, part, seq++, last, &s_val, &s_fail, h)) return;
+    __syncthreads();
+    if (wid == 0) grid_reduce_w0(gs, part, seq, warp_sum(lane < nw ? wpart[lane] : 0.0), &s_val, &s_fail);
+    seq++;
+    __syncthreads();
+    if (s_fail) return;
+    const double h = s_val;
     if (blockIdx.x == 0 && threadIdx.x == 0) Hcol[i] = h;
 #pragma unroll
     for (int s = 0; s < NPT; s++) {
-      int64_t k = threadIdx.x + (int64_t)s * blockDim.x;
-      if (k < len) ws[k] -= h * vc[s];
+      ws[threadIdx.x + s * blockDim.x] -= h * vc[s];
       vc[s] = vn[s];
     }
   }
   double loc = 0.0;
 #pragma unroll
   for (int s = 0; s < NPT; s++) {
-    int64_t k = threadIdx.x + (int64_t)s * blockDim.x;
-    if (k < len) loc += ws[k] * ws[k];
+    double a = ws[threadIdx.x + s * blockDim.x];
+    loc += a * a;
   }
-  double bs = block_sum0(loc, sh);
-  double hn2;
-  int last = threadIdx.x == 0 ? grid_arrive(gs, part, bs) : 0;
-  if (!grid_complete(gs, part, seq++, last, &s_val, &s_fail, hn2)) return;
-  double hn = sqrt(hn2);
+  loc = warp_sum(loc);
+  if (lane == 0) wpart[wid] = loc;
+  __syncthreads();
+  if (wid == 0) grid_reduce_w0(gs, part, seq, warp_sum(lane < nw ? wpart[lane] : 0.0), &s_val, &s_fail);
+  __syncthreads();
+  if (s_fail) return;
+  const double hn = sqrt(s_val);
   if (hn > 0.0) {
-    double inv = 1.0 / hn;
+    const double inv = 1.0 / hn;
     double* vnx = V + (int64_t)(j + 1) * ldv + base;
     for (int64_t k = threadIdx.x; k < len; k += blockDim.x) {
       double v = ws[k] * inv;
@@ -262,6 +315,208 @@ __global__ void __launch_bounds__(NPT <= 8 ? 1024 : 512)
     out[0] = res;
     out[1] = hn;
     out[8] = (double)(j + 1);  // steps completed in this cycle
+    if (!(res > target) || hn == 0.0 || j + 1 >= kmax || it0 + j + 1 >= max_it) out[7] = 1.0;
+  }
+}
+
+// ---------------------------------------------------------------- low-synchronisation MGS step
+// Modified Gram-Schmidt in its compact-WY form: the product of the j+1 MGS
+// projectors (I - q_j q_j^T) ... (I - q_0 q_0^T) equals I - Q T Q^T with
+// T = (I + L)^{-1}, L the strictly lower triangle of Q^T Q, Q = [V_0 .. V_j].
+// The MGS coefficients are therefore h = (I + L)^{-1} Q^T w: one grid
+// reduction of the j+1 inner products Q^T w together with the j products
+// V_j^T V_i (row j of L), a triangular solve, and one more sweep w -= Q h.
+// In exact arithmetic the step equals the sequential MGS sweep; it takes 2
+// grid reductions instead of j + 2, at about 1.5x the FP64 work (published:
+// Swirydowicz, Langou, Ananthan, Yang and Thomas, low-synchronisation
+// Gram-Schmidt and GMRES, 2020).
+//
+// Block b owns the same contiguous slice as k_arnoldi; the slices of w and
+// V_j live in shared memory.  Per-warp partials of all 2j+1 inner products
+// go to shared memory without block barriers; the block sums go to
+// part[block][2j+1]; the last block to arrive adds them in block order,
+// stores row j of L, solves (I + L) h = s with one warp and publishes h.
+__device__ __forceinline__ void publish_seq(const GridSync& gs, unsigned seq) {
+  st_relaxed_u64(gs.slot + ((seq + 1u) & 1u), kSentinel);
+  *(volatile unsigned*)gs.seq = seq + 1u;
+  st_release_u64(gs.slot + (seq & 1u), (unsigned long long)seq);
+}
+
+__device__ __forceinline__ bool wait_seq(const GridSync& gs, unsigned seq) {
+  unsigned spins = 0;
+  while (ld_acquire_u64(gs.slot + (seq & 1u)) == kSentinel) {
+    if (++spins > (1u << 26) || *(volatile int*)gs.err != DEV_OK) {
+      atomicCAS(gs.err, DEV_OK, DEV_ERR_TIMEOUT);
+      return false;
+    }
+  }
+  return true;
+}
+
+template <int NPT, class DT, class ZT>
+__global__ void __launch_bounds__(NPT <= 6 ? 1024 : 512)
+    k_arnoldi_ls(int64_t n, int j, double* __restrict__ V, int64_t ldv, const double* __restrict__ w,
+                 double* __restrict__ Hcol, double* part, double* partv, GridSync gs, double* __restrict__ Lmat,
+                 int ldl, double* hpub, double* __restrict__ cs, double* __restrict__ sn, double* __restrict__ g,
+                 double* __restrict__ out, const DT* __restrict__ Dinv, ZT* __restrict__ z, double target, int kmax,
+                 int it0, int max_it) {
+  extern __shared__ __align__(16) double sm[];
+  __shared__ double wpart[32];
+  __shared__ double s_val;
+  __shared__ int s_fail, s_last;
+  if (*(volatile double*)(out + 7) != 0.0) return;
+  unsigned seq = *(volatile unsigned*)gs.seq;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const int64_t S = (int64_t)NPT * blockDim.x;
+  const int64_t base = (int64_t)blockIdx.x * S;
+  const int64_t len = n - base < S ? n - base : S;
+  const int nv = 2 * j + 1;  // s_0..s_j, then l_0..l_{j-1}
+  double* ws = sm;           // [S]  w
+  double* vj = sm + S;       // [S]  V_j
+  double* pw = sm + 2 * S;   // [nv][32] per-warp partials
+  for (int64_t k = threadIdx.x; k < S; k += blockDim.x) {
+    ws[k] = k < len ? w[base + k] : 0.0;
+    vj[k] = k < len ? V[(int64_t)j * ldv + base + k] : 0.0;
+  }
+  if (threadIdx.x == 0) s_fail = 0;
+  __syncthreads();
+  double vc[NPT], vn[NPT];
+#pragma unroll
+  for (int s = 0; s < NPT; s++) {
+    int64_t k = threadIdx.x + (int64_t)s * blockDim.x;
+    vc[s] = k < len ? V[base + k] : 0.0;
+  }
+  for (int i = 0; i <= j; i++) {
+    if (i < j) {
+      const double* vi = V + (int64_t)(i + 1) * ldv + base;
+#pragma unroll
+      for (int s = 0; s < NPT; s++) {
+        int64_t k = threadIdx.x + (int64_t)s * blockDim.x;
+        vn[s] = k < len ? vi[k] : 0.0;
+      }
+    }
+    double ps = 0.0, pl = 0.0;
+#pragma unroll
+    for (int s = 0; s < NPT; s++) {
+      const int64_t k = threadIdx.x + (int64_t)s * blockDim.x;
+      ps += ws[k] * vc[s];
+      pl += vj[k] * vc[s];
+    }
+    ps = warp_sum(ps);
+    if (i < j) pl = warp_sum(pl);
+    if (lane == 0) {
+      pw[i * 32 + wid] = ps;
+      if (i < j) pw[(j + 1 + i) * 32 + wid] = pl;
+    }
+#pragma unroll
+    for (int s = 0; s < NPT; s++) vc[s] = vn[s];
+  }
+  __syncthreads();
+  for (int v = threadIdx.x; v < nv; v += blockDim.x) {
+    double t = 0.0;
+    for (int q = 0; q < nw; q++) t += pw[v * 32 + q];
+    partv[(int64_t)blockIdx.x * nv + v] = t;
+    __threadfence();
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    s_last = gridDim.x == 1 ? 1 : (atom_inc_acq_rel(gs.count, gridDim.x - 1) == gridDim.x - 1);
+  }
+  __syncthreads();
+  if (s_last) {
+    asm volatile("fence.acq_rel.gpu;" ::: "memory");
+    for (int v = threadIdx.x; v < nv; v += blockDim.x) {
+      double t = 0.0;
+      for (int b = 0; b < (int)gridDim.x; b++) t += ld_relaxed_f64(partv + (int64_t)b * nv + v);
+      if (v <= j) hpub[v] = t;
+      else Lmat[(int64_t)j * ldl + (v - j - 1)] = t;
+    }
+    __threadfence();
+    __syncthreads();
+    if (wid == 0) {  // forward substitution (I + L) h = s, column by column
+      for (int i = 0; i <= j; i++) {
+        const double hi = ld_relaxed_f64(hpub + i);
+        for (int r = i + 1 + lane; r <= j; r += 32) hpub[r] -= ld_relaxed_f64(Lmat + (int64_t)r * ldl + i) * hi;
+        __threadfence();
+        __syncwarp();
+      }
+      if (lane == 0 && gridDim.x > 1) publish_seq(gs, seq);
+    }
+  } else if (threadIdx.x == 0) {
+    if (!wait_seq(gs, seq)) s_fail = 1;
+  }
+  if (gridDim.x > 1) seq++;
+  __syncthreads();
+  if (s_fail) return;
+  for (int i = 0; i <= j; i++) {  // w -= sum_i h_i V_i
+    const double hi = ld_relaxed_f64(hpub + i);
+    const double* vi = V + (int64_t)i * ldv + base;
+#pragma unroll
+    for (int s = 0; s < NPT; s++) {
+      const int64_t k = threadIdx.x + (int64_t)s * blockDim.x;
+      if (k < len) ws[k] -= hi * vi[k];
+    }
+  }
+  double loc = 0.0;
+#pragma unroll
+  for (int s = 0; s < NPT; s++) {
+    const int64_t k = threadIdx.x + (int64_t)s * blockDim.x;
+    loc += ws[k] * ws[k];
+  }
+  loc = warp_sum(loc);
+  if (lane == 0) wpart[wid] = loc;
+  __syncthreads();
+  if (wid == 0) grid_reduce_w0(gs, part, seq, warp_sum(lane < nw ? wpart[lane] : 0.0), &s_val, &s_fail);
+  __syncthreads();
+  if (s_fail) return;
+  const double hn = sqrt(s_val);
+  if (hn > 0.0) {
+    const double inv = 1.0 / hn;
+    double* vnx = V + (int64_t)(j + 1) * ldv + base;
+    for (int64_t k = threadIdx.x; k < len; k += blockDim.x) {
+      double v = ws[k] * inv;
+      ws[k] = v;
+      vnx[k] = v;
+    }
+    if (z) {
+      __syncthreads();
+      for (int64_t a = threadIdx.x; a < len / 3; a += blockDim.x) {
+        const DT* D = Dinv + ((base / 3) + a) * 9;
+        double x0 = ws[3 * a], x1 = ws[3 * a + 1], x2 = ws[3 * a + 2];
+        ZT* zo = z + base + 3 * a;
+        if constexpr (sizeof(DT) == 8) {
+          zo[0] = (ZT)(D[0] * x0 + D[1] * x1 + D[2] * x2);
+          zo[1] = (ZT)(D[3] * x0 + D[4] * x1 + D[5] * x2);
+          zo[2] = (ZT)(D[6] * x0 + D[7] * x1 + D[8] * x2);
+        } else {
+          float f0 = (float)x0, f1 = (float)x1, f2 = (float)x2;
+          zo[0] = (ZT)(D[0] * f0 + D[1] * f1 + D[2] * f2);
+          zo[1] = (ZT)(D[3] * f0 + D[4] * f1 + D[5] * f2);
+          zo[2] = (ZT)(D[6] * f0 + D[7] * f1 + D[8] * f2);
+        }
+      }
+    }
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    for (int i = 0; i <= j; i++) Hcol[i] = ld_relaxed_f64(hpub + i);
+    Hcol[j + 1] = hn;
+    for (int i = 0; i < j; i++) {
+      double a = Hcol[i], c = Hcol[i + 1];
+      Hcol[i] = cs[i] * a + sn[i] * c;
+      Hcol[i + 1] = -sn[i] * a + cs[i] * c;
+    }
+    double a = Hcol[j], c = Hcol[j + 1];
+    double r = hypot(a, c);
+    cs[j] = a / r;
+    sn[j] = c / r;
+    Hcol[j] = r;
+    Hcol[j + 1] = 0.0;
+    g[j + 1] = -sn[j] * g[j];
+    g[j] = cs[j] * g[j];
+    double res = fabs(g[j + 1]);
+    out[0] = res;
+    out[1] = hn;
+    out[8] = (double)(j + 1);
     if (!(res > target) || hn == 0.0 || j + 1 >= kmax || it0 + j + 1 >= max_it) out[7] = 1.0;
   }
 }
@@ -616,24 +871,41 @@ __global__ void k_gemv(int64_t n, int k, const double* __restrict__ V, int64_t l
 }
 
 // ---------------------------------------------------------------- workspace
+constexpr int LOWSYNC_MAX_RESTART = 128;  // shared memory holds 32 partials per inner product
 int fe_workspace(fe_mesh m, int restart) {
   FE_TRY(ensure_zx(m));
   if (!m->w64) FE_TRY(fe_alloc_t(m, &m->w64, (size_t)m->ndof));
   if (!m->t64) FE_TRY(fe_alloc_t(m, &m->t64, (size_t)m->ndof));
   if (!m->u64) FE_TRY(fe_alloc_t(m, &m->u64, (size_t)m->ndof));
   if (restart > m->ws_restart) {
+    // basis rows padded to a multiple of 32 values (256 bytes) and zeroed, so
+    // the Arnoldi kernel's 16-byte pair loads stay inside a row
+    const int64_t ldv = (m->ndof + 31) / 32 * 32;
     if (m->V) {
       cudaFree(m->V);
       cudaFree(m->H);
       cudaFree(m->gv);
-      m->device_bytes -= (int64_t)(m->ws_restart + 1) * m->ndof * 8 + (int64_t)(m->ws_restart + 1) * (m->ws_restart + 1) * 8 +
+      m->device_bytes -= (int64_t)(m->ws_restart + 1) * m->ldv * 8 + (int64_t)(m->ws_restart + 1) * (m->ws_restart + 1) * 8 +
                          (int64_t)4 * (m->ws_restart + 2) * 8;
       m->V = m->H = m->gv = nullptr;
     }
-    FE_TRY(fe_alloc_t(m, &m->V, (size_t)(restart + 1) * m->ndof));
+    FE_TRY(fe_alloc_t(m, &m->V, (size_t)(restart + 1) * ldv));
+    FE_CUDA(cudaMemsetAsync(m->V, 0, (size_t)(restart + 1) * ldv * sizeof(double), m->stream));
     FE_TRY(fe_alloc_t(m, &m->H, (size_t)(restart + 1) * (restart + 1)));
     FE_TRY(fe_alloc_t(m, &m->gv, (size_t)4 * (restart + 2)));
     m->ws_restart = restart;
+    m->ldv = ldv;
+    if (restart <= LOWSYNC_MAX_RESTART) {  // low-synchronisation MGS: L, h, per-block inner products
+      if (m->Lmat) {
+        cudaFree(m->Lmat);
+        cudaFree(m->hpub);
+        cudaFree(m->partv);
+      }
+      m->partv_blocks = 2 * m->sm_count;
+      FE_TRY(fe_alloc_t(m, &m->Lmat, (size_t)(restart + 1) * (restart + 1)));
+      FE_TRY(fe_alloc_t(m, &m->hpub, (size_t)(restart + 1)));
+      FE_TRY(fe_alloc_t(m, &m->partv, (size_t)m->partv_blocks * (2 * restart + 1)));
+    }
   }
   return FE_OK;
 }
@@ -662,13 +934,12 @@ template <class DT, class ZT>
 static int launch_arnoldi_t(fe_mesh m, int j, int kmax, bool fuse_pc, const DT* Dinv, double target, int it0,
                             int max_it) {
   const int64_t n = m->ndof;
-  const void* fns[4] = {arnoldi_fn<3, DT, ZT>(), arnoldi_fn<6, DT, ZT>(), arnoldi_fn<12, DT, ZT>(),
-                        arnoldi_fn<24, DT, ZT>()};
-  const int npts[4] = {3, 6, 12, 24};
-  const int bds[4] = {1024, 1024, 512, 512};
-  static bool attr[2][2][4] = {};
+  const void* fns[3] = {arnoldi_fn<6, DT, ZT>(), arnoldi_fn<12, DT, ZT>(), arnoldi_fn<24, DT, ZT>()};
+  const int npts[3] = {6, 12, 24};
+  const int bds[3] = {1024, 512, 512};
+  static bool attr[2][2][3] = {};
   int which = -1, grid = 0;
-  for (int q = 0; q < 4; q++) {
+  for (int q = 0; q < 3; q++) {
     size_t smem = (size_t)npts[q] * bds[q] * sizeof(double);
     bool& done = attr[sizeof(DT) == 8][sizeof(ZT) == 8][q];
     if (!done) {
@@ -687,7 +958,7 @@ static int launch_arnoldi_t(fe_mesh m, int j, int kmax, bool fuse_pc, const DT* 
   if (which < 0) return fe_set_error("vector too long for the persistent Arnoldi kernel (n = %lld)", (long long)n), FE_ERR_ARG;
   size_t smem = (size_t)npts[which] * bds[which] * sizeof(double);
   double* V = m->V;
-  int64_t ldv = m->ndof;
+  int64_t ldv = m->ldv;
   double* Hcol = m->H + (int64_t)j * (kmax + 1);
   double* cs = m->gv;
   double* sn = m->gv + (kmax + 2);
@@ -708,7 +979,71 @@ static int launch_arnoldi_t(fe_mesh m, int j, int kmax, bool fuse_pc, const DT* 
   return FE_OK;
 }
 
+template <int NPT, class DT, class ZT>
+static const void* arnoldi_ls_fn() { return (const void*)k_arnoldi_ls<NPT, DT, ZT>; }
+
+template <class DT, class ZT>
+static int launch_arnoldi_ls_t(fe_mesh m, int j, int kmax, bool fuse_pc, const DT* Dinv, double target, int it0,
+                               int max_it) {
+  const int64_t n = m->ndof;
+  const void* fns[3] = {arnoldi_ls_fn<6, DT, ZT>(), arnoldi_ls_fn<12, DT, ZT>(), arnoldi_ls_fn<24, DT, ZT>()};
+  const int npts[3] = {6, 12, 24};
+  const int bds[3] = {1024, 512, 512};
+  const size_t pw_max = (size_t)(2 * LOWSYNC_MAX_RESTART + 1) * 32 * sizeof(double);
+  static bool attr[2][2][3] = {};
+  int which = -1, grid = 0;
+  for (int q = 0; q < 3; q++) {
+    size_t smem = 2 * (size_t)npts[q] * bds[q] * sizeof(double) + pw_max;
+    bool& done = attr[sizeof(DT) == 8][sizeof(ZT) == 8][q];
+    if (!done) {
+      FE_CUDA(cudaFuncSetAttribute(fns[q], cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+      done = true;
+    }
+    int per_sm = 0;
+    FE_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fns[q], bds[q], smem));
+    int64_t need = (n + (int64_t)npts[q] * bds[q] - 1) / ((int64_t)npts[q] * bds[q]);
+    if (per_sm >= 1 && need <= (int64_t)per_sm * m->sm_count && need <= m->partv_blocks) {
+      which = q;
+      grid = (int)need;
+      break;
+    }
+  }
+  if (which < 0) return fe_set_error("vector too long for the low-synchronisation Arnoldi kernel"), FE_ERR_ARG;
+  const int nv = 2 * j + 1;
+  size_t smem = 2 * (size_t)npts[which] * bds[which] * sizeof(double) + (size_t)nv * 32 * sizeof(double);
+  double* V = m->V;
+  int64_t ldv = m->ldv;
+  double* Hcol = m->H + (int64_t)j * (kmax + 1);
+  double* cs = m->gv;
+  double* sn = m->gv + (kmax + 2);
+  double* g = m->gv + 2 * (kmax + 2);
+  double* out = m->scal + 3;
+  double* part = m->red;
+  double* partv = m->partv;
+  double* Lmat = m->Lmat;
+  int ldl = kmax + 1;
+  double* hpub = m->hpub;
+  const DT* D = fuse_pc ? Dinv : nullptr;
+  ZT* z = fuse_pc ? (ZT*)m->zx : nullptr;
+  GridSync gs = grid_sync(m);
+  void* args[] = {(void*)&n, (void*)&j, (void*)&V, (void*)&ldv, (void*)&m->w64, (void*)&Hcol, (void*)&part,
+                  (void*)&partv, (void*)&gs, (void*)&Lmat, (void*)&ldl, (void*)&hpub, (void*)&cs, (void*)&sn,
+                  (void*)&g, (void*)&out, (void*)&D, (void*)&z, (void*)&target, (void*)&kmax, (void*)&it0,
+                  (void*)&max_it};
+  // flops: 2 inner products per basis vector, then the update, the norm and the scaling
+  FE_SCOPE_F(m, FE_PROF_ARNOLDI,
+             8.0 * (double)n * (2.0 * (j + 1) + 3) + (fuse_pc ? (double)n * (3.0 * sizeof(DT) + sizeof(ZT)) : 0.0),
+             (double)n * (6.0 * (j + 1) + 3.0) + (fuse_pc ? 6.0 * n : 0.0));
+  FE_CUDA(cudaLaunchCooperativeKernel(fns[which], dim3(grid), dim3(bds[which]), args, smem, m->stream));
+  return FE_OK;
+}
+
 static int launch_arnoldi(fe_mesh m, int j, int kmax, bool fuse_pc, double target, int it0, int max_it) {
+  if (m->orthog == 1) {
+    if (m->prec == FE_PREC_FP64)
+      return launch_arnoldi_ls_t<double, double>(m, j, kmax, fuse_pc, m->Dinv64, target, it0, max_it);
+    return launch_arnoldi_ls_t<float, float>(m, j, kmax, fuse_pc, m->Dinv32, target, it0, max_it);
+  }
   if (m->prec == FE_PREC_FP64)
     return launch_arnoldi_t<double, double>(m, j, kmax, fuse_pc, m->Dinv64, target, it0, max_it);
   return launch_arnoldi_t<float, float>(m, j, kmax, fuse_pc, m->Dinv32, target, it0, max_it);
@@ -725,6 +1060,8 @@ int fe_gmres_dev(fe_mesh m, const double* b, double* x, double rtol, double atol
                  int* iters, double* res) {
   if (m->prec < 0) return fe_set_error("no tangent assembled"), FE_ERR_STATE;
   if (restart < 1 || restart > 1000) return fe_set_error("restart must be in [1, 1000]"), FE_ERR_ARG;
+  if (m->orthog == 1 && restart > LOWSYNC_MAX_RESTART)
+    return fe_set_error("low-synchronisation MGS supports restart <= %d", LOWSYNC_MAX_RESTART), FE_ERR_ARG;
   FE_TRY(fe_workspace(m, restart));
   const int64_t n = m->ndof;
   const unsigned g1 = (unsigned)((n + 255) / 256);
@@ -773,7 +1110,7 @@ int fe_gmres_dev(fe_mesh m, const double* b, double* x, double rtol, double atol
       const int jprev = j;
       int jend = std::min(j + batch, kmax);
       for (int jj = j; jj < jend; jj++) {
-        if (jj == 0 || !fuse) FE_TRY(pc_to_zx(m, m->V + (int64_t)jj * n));
+        if (jj == 0 || !fuse) FE_TRY(pc_to_zx(m, m->V + (int64_t)jj * m->ldv));
         FE_TRY(spmv_zx(m, m->w64));
         FE_TRY(launch_arnoldi(m, jj, kmax, fuse, target, it, max_it));
       }
@@ -796,7 +1133,7 @@ int fe_gmres_dev(fe_mesh m, const double* b, double* x, double rtol, double atol
     }
     {
       FE_SCOPE(m, FE_PROF_VECTOR, 8.0 * n * (j + 1));
-      k_gemv<<<g1, 256, 0, m->stream>>>(n, j, m->V, n, y, m->u64);
+      k_gemv<<<g1, 256, 0, m->stream>>>(n, j, m->V, m->ldv, y, m->u64);
     }
     FE_TRY(fe_pc_dev(m, m->u64, m->t64));
     FE_TRY(fe_axpby_dev(m, 1.0, m->t64, 1.0, x, n));
@@ -1019,10 +1356,12 @@ extern "C" int fe_pc_apply(fe_mesh m, const double* x, double* y) {
 }
 
 extern "C" int fe_gmres(fe_mesh m, const double* b, double* x, double rtol, double atol, int restart, int max_it,
-                        int* iters, double* res_out) {
+                        int orthog, int* iters, double* res_out) {
   if (!m || !b || !x) return fe_set_error("NULL argument"), FE_ERR_ARG;
   if (!(rtol >= 0.0) || !(atol >= 0.0) || max_it < 0) return fe_set_error("bad tolerances"), FE_ERR_ARG;
+  if (orthog != 0 && orthog != 1) return fe_set_error("orthog must be 0 or 1"), FE_ERR_ARG;
   FE_CUDA(cudaSetDevice(m->device));
+  m->orthog = orthog;
   FE_TRY(fe_gmres_dev(m, b, x, rtol, atol, restart, max_it, iters, res_out));
   return fe_check_device_error(m);
 }

@@ -669,7 +669,7 @@ static void free_all(fe_mesh m) {
                   m->ks_kpos, m->K64, m->K32, m->K16, m->B64, m->B32, m->Dinv64, m->Dinv32,
                   m->Sd, m->rel, m->relp, m->red, m->red_ticket, m->scal, m->bar, m->V,
                   m->H, m->gv, m->w64, m->t64, m->u64, m->zx, m->S, m->Yv, m->nl_R, m->nl_Rn,
-                  m->nl_dl, m->nl_t, m->rho_d, m->lb_x, m->alpha_d};
+                  m->nl_dl, m->nl_t, m->rho_d, m->lb_x, m->alpha_d, m->Lmat, m->hpub, m->partv};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (m->h_scal) cudaFreeHost(m->h_scal);

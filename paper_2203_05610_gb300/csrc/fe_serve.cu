@@ -1,0 +1,299 @@
+// fe_serve.cu -- continuous-batching request loop (include/fe_serve.h).
+//
+// A scheduler thread admits queued requests first-fit in arrival order when
+// a slot is free and the request's estimated device footprint fits the
+// remaining HBM budget; each admitted request runs in its own worker thread
+// on its own non-blocking CUDA stream with its own resident mesh, pattern,
+// tangent, Krylov and BFGS workspace, so admitted requests overlap on the
+// device.  A finished request frees its memory and its slot at once, and the
+// scheduler admits the next queued requests that now fit.
+#include <algorithm>
+#include <chrono>
+#include <condition_variable>
+#include <cstring>
+#include <deque>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <string>
+#include <thread>
+#include <vector>
+
+#include "../../include/fe_serve.h"
+#include "fe_internal.h"
+
+namespace {
+
+struct Request {
+  int64_t id = 0;
+  fe_mesh_desc desc{};
+  std::vector<double> coords, face_data, fibers, d0;
+  std::vector<int32_t> tets, faces, face_kind;
+  std::vector<uint8_t> dir_group;
+  std::vector<fe_dirichlet_group> groups;
+  int method = 0;
+  double tol = 1e-8;
+  int max_it = 50;
+  nl_opts opts{};
+  bool has_opts = false;
+  double load = 0.0, time = 0.0;
+  fe_request_status st{};
+  std::vector<double> result;
+  std::string error;
+};
+
+// device bytes a request will hold, estimated from its description before
+// anything is allocated (exact node count; block count from the measured
+// blocks per node of tetrahedral meshes, 28 for P2 and 16 for P1, with
+// margin)
+int64_t estimate_footprint(const Request& r, int64_t* ndof_out) {
+  const fe_mesh_desc& d = r.desc;
+  int64_t nv = d.nv, ne = d.ne, nn = nv;
+  if (d.order == 2) {
+    std::vector<uint64_t> keys((size_t)ne * 6);
+    static const int E[6][2] = {{0, 1}, {0, 2}, {0, 3}, {1, 2}, {1, 3}, {2, 3}};
+    for (int64_t e = 0; e < ne; e++)
+      for (int k = 0; k < 6; k++) {
+        uint64_t a = (uint64_t)d.tets[4 * e + E[k][0]], b = (uint64_t)d.tets[4 * e + E[k][1]];
+        keys[(size_t)e * 6 + k] = (std::min(a, b) << 32) | std::max(a, b);
+      }
+    std::sort(keys.begin(), keys.end());
+    nn += (int64_t)(std::unique(keys.begin(), keys.end()) - keys.begin());
+  }
+  const int64_t nen = d.order == 1 ? 4 : 10;
+  const int64_t ndof = 3 * nn + (d.pressure_order ? nv : 0);
+  const int64_t nnzb = (d.order == 1 ? 16 : 28) * nn;
+  nl_opts o = r.opts;
+  if (!r.has_opts) nl_opts_default((nl_method)r.method, &o);
+  const int64_t restart = o.ksp_restart > 0 ? o.ksp_restart : 500;
+  const int64_t mpairs = (r.method >= NL_B) ? (o.lbfgs_m > 0 ? o.lbfgs_m : 50) : 0;
+  const int64_t sval = o.precision == FE_PREC_FP64 ? 8 : 4;
+  int64_t b = 0;
+  b += 24 * nn + ne * (4 * nen + 8 + 80 + 4 * nen * nen + 24 * nen + 8 * nen) + 4 * nnzb + 16 * nn;  // mesh
+  if (d.fibers) b += 72 * ne;
+  if (d.pressure_order) b += ne * (4 * nen * 4 + 32) + 16 * 12 * nn;  // coupling pattern and values
+  b += 9 * sval * nnzb + 9 * sval * nn + (o.precision == FE_PREC_MIXED_BF16 ? 18 * nnzb : 0);  // tangent
+  b += 8 * ndof * (restart + 1) + 8 * (restart + 1) * (restart + 1);                             // Krylov basis
+  b += 8 * ndof * (2 * mpairs + 12);                                                              // BFGS pairs, vectors
+  *ndof_out = ndof;
+  return b + b / 8 + (64 << 20);
+}
+
+}  // namespace
+
+struct fe_server_s {
+  int device = 0;
+  int64_t budget = 0, used = 0;
+  int max_active = 8, active = 0;
+  bool stop = false;
+  int64_t next_id = 1;
+  std::mutex mu;
+  std::condition_variable cv;
+  std::deque<int64_t> queue;
+  std::map<int64_t, std::unique_ptr<Request>> reqs;
+  std::thread scheduler;
+  std::vector<std::thread> workers;
+  std::chrono::steady_clock::time_point t0 = std::chrono::steady_clock::now();
+  double now() const {
+    return std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  }
+};
+
+static void run_request(fe_server s, Request* r) {
+  int rc = FE_OK;
+  cudaStream_t stream = nullptr;
+  fe_mesh m = nullptr;
+  double* d = nullptr;
+  nl_stats stats{};
+  std::vector<double> out;
+  cudaSetDevice(s->device);
+  if (cudaStreamCreateWithFlags(&stream, cudaStreamNonBlocking) != cudaSuccess) {
+    rc = FE_ERR_CUDA;
+    fe_set_error("cudaStreamCreate failed");
+  }
+  fe_mesh_desc desc = r->desc;
+  desc.device = s->device;
+  desc.stream = stream;
+  if (rc == FE_OK) rc = fe_mesh_create(&desc, &m);
+  if (rc == FE_OK) rc = fe_set_load(m, r->load, r->time);
+  int64_t ndof = 0;
+  if (rc == FE_OK) {
+    fe_mesh_info info;
+    fe_mesh_get_info(m, &info);
+    ndof = info.ndof;
+    if (!r->d0.empty() && (int64_t)r->d0.size() != ndof) {
+      rc = FE_ERR_ARG;
+      fe_set_error("initial guess has %zu entries, mesh has %lld unknowns", r->d0.size(), (long long)ndof);
+    }
+  }
+  if (rc == FE_OK && cudaMalloc(&d, ndof * sizeof(double)) != cudaSuccess) {
+    rc = FE_ERR_OOM;
+    fe_set_error("cudaMalloc of the solution vector failed");
+  }
+  if (rc == FE_OK) {
+    if (r->d0.empty()) cudaMemsetAsync(d, 0, ndof * sizeof(double), stream);
+    else cudaMemcpyAsync(d, r->d0.data(), ndof * sizeof(double), cudaMemcpyHostToDevice, stream);
+    {
+      std::lock_guard<std::mutex> lk(s->mu);
+      r->st.t_start = s->now();
+      r->st.ndof = ndof;
+    }
+    rc = nl_solve(m, r->method, r->tol, r->max_it, d, r->has_opts ? &r->opts : nullptr, &stats);
+    if (rc >= 0) {
+      out.resize(ndof);
+      if (cudaMemcpyAsync(out.data(), d, ndof * sizeof(double), cudaMemcpyDeviceToHost, stream) != cudaSuccess ||
+          cudaStreamSynchronize(stream) != cudaSuccess) {
+        rc = FE_ERR_CUDA;
+        fe_set_error("copying the solution back failed");
+      }
+    }
+  }
+  std::string err = rc < 0 ? std::string(fe_last_error()) : std::string();
+  if (d) cudaFree(d);
+  if (m) fe_mesh_destroy(m);
+  if (stream) cudaStreamDestroy(stream);
+  {
+    std::lock_guard<std::mutex> lk(s->mu);
+    r->st.t_end = s->now();
+    r->st.state = rc < 0 ? FE_REQ_FAILED : FE_REQ_DONE;
+    r->st.result = rc;
+    r->st.stats = stats;
+    r->result.swap(out);
+    r->error = err;
+    s->used -= r->st.footprint;
+    s->active--;
+  }
+  s->cv.notify_all();
+}
+
+static void scheduler_loop(fe_server s) {
+  std::unique_lock<std::mutex> lk(s->mu);
+  for (;;) {
+    // first fit in arrival order
+    bool admitted = false;
+    for (auto it = s->queue.begin(); it != s->queue.end();) {
+      Request* r = s->reqs[*it].get();
+      if (r->st.footprint > s->budget) {  // can never fit: reject
+        r->st.state = FE_REQ_FAILED;
+        r->st.result = FE_ERR_OOM;
+        r->error = "request footprint exceeds the server's HBM budget";
+        r->st.t_start = r->st.t_end = s->now();
+        it = s->queue.erase(it);
+        s->cv.notify_all();
+        continue;
+      }
+      if (s->active < s->max_active && s->used + r->st.footprint <= s->budget) {
+        s->used += r->st.footprint;
+        s->active++;
+        r->st.state = FE_REQ_RUNNING;
+        it = s->queue.erase(it);
+        s->workers.emplace_back(run_request, s, r);
+        admitted = true;
+        continue;
+      }
+      ++it;
+    }
+    if (s->stop && s->queue.empty() && s->active == 0) break;
+    if (!admitted) s->cv.wait(lk);
+  }
+}
+
+extern "C" int serve_create(const fe_server_opts* opts, fe_server* out) {
+  if (!opts || !out) return fe_set_error("NULL argument"), FE_ERR_ARG;
+  *out = nullptr;
+  FE_CUDA(cudaSetDevice(opts->device));
+  size_t free_b = 0, total_b = 0;
+  FE_CUDA(cudaMemGetInfo(&free_b, &total_b));
+  fe_server s = new fe_server_s();
+  s->device = opts->device;
+  s->budget = opts->hbm_budget > 0 ? opts->hbm_budget : (int64_t)(0.8 * (double)free_b);
+  s->max_active = opts->max_active > 0 ? opts->max_active : 8;
+  s->scheduler = std::thread(scheduler_loop, s);
+  *out = s;
+  return FE_OK;
+}
+
+template <class T>
+static void copy_in(std::vector<T>& dst, const T* src, size_t n) {
+  if (src && n) dst.assign(src, src + n);
+  else dst.clear();
+}
+
+extern "C" int serve_submit(fe_server s, const fe_request* q, int64_t* id_out) {
+  if (!s || !q || !q->mesh || !id_out) return fe_set_error("NULL argument"), FE_ERR_ARG;
+  if (q->method < NL_NK || q->method > NL_IB || !(q->tol >= 0.0) || q->max_it < 0)
+    return fe_set_error("bad method, tol or max_it"), FE_ERR_ARG;
+  const fe_mesh_desc& d = *q->mesh;
+  if (d.nv < 4 || d.ne < 1 || !d.coords || !d.tets || d.nf < 0 || d.ngroups < 0)
+    return fe_set_error("bad mesh description"), FE_ERR_ARG;
+  auto r = std::make_unique<Request>();
+  copy_in(r->coords, d.coords, 3 * (size_t)d.nv);
+  copy_in(r->tets, d.tets, 4 * (size_t)d.ne);
+  copy_in(r->dir_group, d.dir_group, (size_t)d.nv);
+  copy_in(r->groups, d.groups, (size_t)d.ngroups);
+  copy_in(r->faces, d.faces, 3 * (size_t)d.nf);
+  copy_in(r->face_kind, d.face_kind, (size_t)d.nf);
+  copy_in(r->face_data, d.face_data, 3 * (size_t)d.nf);
+  copy_in(r->fibers, d.fibers, d.fibers ? 9 * (size_t)d.ne : 0);
+  r->desc = d;
+  r->desc.coords = r->coords.data();
+  r->desc.tets = r->tets.data();
+  r->desc.dir_group = d.dir_group ? r->dir_group.data() : nullptr;
+  r->desc.groups = d.ngroups ? r->groups.data() : nullptr;
+  r->desc.faces = d.nf ? r->faces.data() : nullptr;
+  r->desc.face_kind = d.nf ? r->face_kind.data() : nullptr;
+  r->desc.face_data = d.nf ? r->face_data.data() : nullptr;
+  r->desc.fibers = d.fibers ? r->fibers.data() : nullptr;
+  r->method = q->method;
+  r->tol = q->tol;
+  r->max_it = q->max_it;
+  if (q->opts) {
+    r->opts = *q->opts;
+    r->has_opts = true;
+  }
+  r->load = q->load;
+  r->time = q->time;
+  int64_t ndof = 0;
+  r->st.footprint = estimate_footprint(*r, &ndof);
+  if (q->d0) r->d0.assign(q->d0, q->d0 + ndof);
+  r->st.state = FE_REQ_QUEUED;
+  {
+    std::lock_guard<std::mutex> lk(s->mu);
+    r->id = s->next_id++;
+    r->st.t_submit = s->now();
+    *id_out = r->id;
+    s->queue.push_back(r->id);
+    s->reqs[r->id] = std::move(r);
+  }
+  s->cv.notify_all();
+  return FE_OK;
+}
+
+extern "C" int serve_poll(fe_server s, int64_t id, int wait, fe_request_status* status, double* d_out) {
+  if (!s || !status) return fe_set_error("NULL argument"), FE_ERR_ARG;
+  std::unique_lock<std::mutex> lk(s->mu);
+  auto it = s->reqs.find(id);
+  if (it == s->reqs.end()) return fe_set_error("unknown request id %lld", (long long)id), FE_ERR_ARG;
+  Request* r = it->second.get();
+  if (wait)
+    s->cv.wait(lk, [r] { return r->st.state == FE_REQ_DONE || r->st.state == FE_REQ_FAILED; });
+  *status = r->st;
+  if (r->st.state == FE_REQ_FAILED && !r->error.empty()) fe_set_error("%s", r->error.c_str());
+  if (d_out && r->st.state == FE_REQ_DONE) std::memcpy(d_out, r->result.data(), r->result.size() * sizeof(double));
+  return FE_OK;
+}
+
+extern "C" double serve_clock(fe_server s) { return s ? s->now() : 0.0; }
+
+extern "C" int serve_destroy(fe_server s) {
+  if (!s) return FE_OK;
+  {
+    std::lock_guard<std::mutex> lk(s->mu);
+    s->stop = true;
+  }
+  s->cv.notify_all();
+  s->scheduler.join();
+  for (auto& t : s->workers) t.join();
+  delete s;
+  return FE_OK;
+}

@@ -8,6 +8,7 @@
 // All four use the basic line search (full step) and the test
 // ||R_k|| <= tol ||R_0||; divergence when ||R_k|| > dtol ||R_0|| or non-finite.
 // The host only sequences kernels and reads one scalar per convergence test.
+#include <algorithm>
 #include <chrono>
 #include <cmath>
 #include <cstring>
@@ -28,6 +29,7 @@ extern "C" int nl_opts_default(nl_method method, nl_opts* o) {
   o->lbfgs_m = 50;
   o->dtol = 1e4;
   o->apply_dirichlet = 1;
+  o->orthog = 0;
   return FE_OK;
 }
 
@@ -63,6 +65,7 @@ static int solve_impl(fe_mesh m, int method, double tol, int max_it, double* d, 
   if (!m->nl_dl) FE_TRY(fe_alloc_t(m, &m->nl_dl, (size_t)n));
   if (!m->nl_t) FE_TRY(fe_alloc_t(m, &m->nl_t, (size_t)n));
   if (!m->rho_d) FE_TRY(fe_alloc_t(m, &m->rho_d, LBFGS_MAX));
+  m->orthog = o.orthog;
   FE_TRY(fe_workspace(m, o.ksp_restart));
   if (o.apply_dirichlet) FE_TRY(fe_apply_dirichlet(m, d));
   double* R = m->nl_R;
@@ -87,8 +90,13 @@ static int solve_impl(fe_mesh m, int method, double tol, int max_it, double* d, 
     st.rfinal = 0.0;
     return FE_OK;
   }
+  // FP32 SpMV/preconditioner rows sum ~30 single-precision products, so the
+  // mixed forms cannot resolve relative linear residuals much below 1e-6:
+  // their Krylov tolerance is clamped at 1e-5 instead of letting GMRES run
+  // to its iteration cap
+  const double rtol_floor = o.precision == FE_PREC_FP64 ? 0.0 : 1e-5;
   if (method == NL_NK || method == NL_INK) {
-    double eta = method == NL_NK ? o.ksp_rtol : o.ew_rtol0;
+    double eta = std::max(method == NL_NK ? o.ksp_rtol : o.ew_rtol0, rtol_floor);
     const double alpha2 = 0.5 * (1.0 + sqrt(5.0));
     for (int k = 1; k <= max_it; k++) {
       FE_TRY(fe_tangent_dev(m, d, o.precision));
@@ -98,7 +106,8 @@ static int solve_impl(fe_mesh m, int method, double tol, int max_it, double* d, 
       FE_CUDA(cudaMemsetAsync(dl, 0, n * sizeof(double), m->stream));
       int its = 0;
       double lres = 0.0;
-      FE_TRY(fe_gmres_dev(m, t, dl, eta, o.ksp_atol, o.ksp_restart, o.ksp_max_it, &its, &lres));
+      FE_TRY(fe_gmres_dev(m, t, dl, std::max(eta, rtol_floor), o.ksp_atol, o.ksp_restart, o.ksp_max_it, &its,
+                          &lres));
       st.lit_total += its;
       if (k < NL_HIST) {
         st.lit_hist[k] = its;
@@ -148,8 +157,8 @@ static int solve_impl(fe_mesh m, int method, double tol, int max_it, double* d, 
     int head = 0, np = 0;
     for (int k = 1; k <= max_it; k++) {
       int lit = 0;
-      FE_TRY(fe_lbfgs_dev(m, m->S, m->Yv, m->rho_d, head, mcap, np, n, R, t, method == NL_B ? 0 : 2, o.ksp_rtol,
-                          o.ksp_atol, o.ksp_restart, o.ksp_max_it, &lit));
+      FE_TRY(fe_lbfgs_dev(m, m->S, m->Yv, m->rho_d, head, mcap, np, n, R, t, method == NL_B ? 0 : 2,
+                          std::max(o.ksp_rtol, rtol_floor), o.ksp_atol, o.ksp_restart, o.ksp_max_it, &lit));
       st.lit_total += lit;
       if (k < NL_HIST) {
         st.lit_hist[k] = lit;
@@ -216,7 +225,9 @@ extern "C" int nl_solve(fe_mesh m, int method, double tol, int max_it, double* d
     if (opts->lbfgs_m > 0) o.lbfgs_m = opts->lbfgs_m;
     if (opts->dtol > 0) o.dtol = opts->dtol;
     o.apply_dirichlet = opts->apply_dirichlet;
+    o.orthog = opts->orthog;
   }
+  if (o.orthog != 0 && o.orthog != 1) return fe_set_error("orthog must be 0 or 1"), FE_ERR_ARG;
   if (o.precision < 0 || o.precision > 2) return fe_set_error("bad precision"), FE_ERR_ARG;
   FE_CUDA(cudaSetDevice(m->device));
   nl_stats local;

@@ -321,3 +321,36 @@ def test_config2_residual_and_tangent_full_size(fe):
     assert _rel(vg, v) < 1e-12
     x = np.random.default_rng(12).standard_normal(om.ndof)
     assert _rel(m.spmv(torch.from_numpy(x).cuda()).cpu().numpy(), om.spmv(x)) < 1e-12
+
+
+# ---------------------------------------------------------------- low-synchronisation MGS
+@pytest.mark.parametrize("case", ["cook_p2", "twist_up"])
+def test_gmres_lowsync_mgs(fe, case):
+    # the compact-WY form of MGS gives the MGS projections: same iterates as
+    # the oracle's sequential sweep up to rounding
+    w = small_cases()[case]
+    m, om = _pair(fe, w)
+    d, dg = _state(m, om, case, 13, amp=0.05)
+    om.tangent(d)
+    m.tangent(dg)
+    b = np.random.default_rng(14).standard_normal(om.ndof)
+    bn = np.linalg.norm(b)
+    for restart in (128, 20):
+        x, it, res = om.gmres(b, rtol=1e-10, atol=0.0, restart=restart, max_it=20000)
+        xg, itg, resg = m.gmres(torch.from_numpy(b).cuda(), rtol=1e-10, atol=0.0, restart=restart,
+                                max_it=20000, orthog=1)
+        true = np.linalg.norm(b - om.spmv(xg.cpu().numpy()))
+        assert resg <= 1e-10 * bn and true <= 2e-10 * bn, (restart, resg / bn, true / bn)
+        assert abs(itg - it) <= max(2, it // 10), (restart, itg, it)
+
+
+@pytest.mark.parametrize("method", ["NK", "iB"])
+def test_nl_solve_lowsync_mgs(fe, method):
+    w = small_cases()["cook_p2"]
+    m, om = _pair(fe, w)
+    m.set_load(0.4)
+    om.set_load(0.4)
+    x, so = om.solve(method, np.zeros(om.ndof), tol=1e-11, opts=dict(ksp_atol=0.0, ksp_restart=60))
+    xg, sg = m.solve(method, m.zeros(), tol=1e-11, opts=dict(ksp_atol=0.0, ksp_restart=60, orthog=1))
+    assert so["status"] == 0 and sg["status"] == 0
+    assert np.linalg.norm(xg.cpu().numpy() - x) <= 1e-10 * np.linalg.norm(x)

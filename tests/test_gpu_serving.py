@@ -1,0 +1,75 @@
+"""Serving loop: continuous batching of nonlinear solves on one GPU.
+
+Each request's result must be the same alone and in the mix (same kernels,
+same launch shapes, deterministic reductions: compared at 1e-12 relative);
+admitted requests overlap on the device; requests that can never fit the
+HBM budget are rejected at admission.
+"""
+import numpy as np
+import pytest
+
+import workloads as W
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def fe():
+    import __graft_entry__ as g
+    g.build()
+    import paper_2203_05610_gb300 as fe
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    return fe
+
+
+def _requests():
+    return [
+        (W.cook(4, 4, 2, order=1, nu=0.3), "NK", dict(precision="fp64", ksp_atol=0.0), (0.4, 0.0)),
+        (W.cook(3, 3, 1, order=2, nu=0.3), "iB", dict(precision="mixed_fp32"), (0.4, 0.0)),
+        (W.twist(2, order=2), "iNK", dict(precision="fp64"), (0.3, 0.0)),
+        (W.heart(nr=2, nc=8, nl=6), "B", dict(precision="fp64"), (0.2, 0.01)),
+        (W.cook(8, 8, 2, order=1, nu=0.49), "iNK", dict(precision="mixed_fp32"), (0.2, 0.0)),
+        (W.cook(6, 6, 2, order=2, nu=0.3), "NK", dict(precision="mixed_fp32"), (0.2, 0.0)),
+    ]
+
+
+def test_alone_and_in_the_mix_agree(fe):
+    reqs = _requests()
+    alone = []
+    for w, meth, opts, (load, tm) in reqs:
+        m = fe.Mesh(w)
+        m.set_load(load, tm)
+        d, st = m.solve(meth, m.zeros(), tol=1e-8, opts=opts)
+        assert st["status"] == 0, (meth, st["res_hist"][-3:])
+        alone.append(d.cpu().numpy())
+        m.close()
+    srv = fe.Server(max_active=4)
+    ids = [srv.submit(w, meth, tol=1e-8, opts=opts, load=load, time=tm) for w, meth, opts, (load, tm) in reqs]
+    res = [srv.poll(i, wait=True) for i in ids]
+    srv.close()
+    for r, a, (w, meth, _, _) in zip(res, alone, reqs):
+        assert r["state"] == "done" and r["result"] == 0, (meth, r)
+        assert np.abs(r["d"] - a).max() <= 1e-12 * np.abs(a).max(), meth
+    # admitted requests overlap on the device: some request started before another ended
+    spans = sorted((r["t_start"], r["t_end"]) for r in res)
+    assert any(spans[k + 1][0] < spans[k][1] for k in range(len(spans) - 1))
+
+
+def test_one_slot_runs_requests_one_after_another(fe):
+    srv = fe.Server(max_active=1)
+    w = W.cook(4, 4, 2, order=1, nu=0.3)
+    ids = [srv.submit(w, "NK", load=0.1 * (k + 1)) for k in range(3)]
+    res = [srv.poll(i, wait=True) for i in ids]
+    srv.close()
+    assert all(r["state"] == "done" for r in res)
+    for a, b in zip(res, res[1:]):
+        assert b["t_start"] >= a["t_end"] - 1e-6
+
+
+def test_admission_rejects_requests_beyond_the_budget(fe):
+    srv = fe.Server(hbm_budget=1 << 20, max_active=2)  # 1 MiB: no mesh fits
+    rid = srv.submit(W.cook(4, 4, 2, order=1), "NK", load=0.1)
+    r = srv.poll(rid, wait=True)
+    srv.close()
+    assert r["state"] == "failed" and r["result"] == -2 and "budget" in r["error"]
