@@ -46,8 +46,9 @@ def parse():
     p.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     p.add_argument("--methods", default="iB")
     p.add_argument("--restart", type=int, default=50)
-    p.add_argument("--orthog", type=int, default=0, choices=[0, 1],
-                   help="Arnoldi: 0 sequential MGS sweep (paper), 1 low-synchronisation MGS")
+    p.add_argument("--orthog", type=int, default=0, choices=[0, 1, 2],
+                   help="Arnoldi: 0 sequential MGS sweep (paper), 1 low-synchronisation MGS, "
+                        "2 blocked MGS (8 basis vectors per grid reduction)")
     p.add_argument("--precision", default="mixed_fp32", choices=["fp64", "mixed_fp32", "mixed_bf16"])
     p.add_argument("--nu", type=float, default=0.3)
     p.add_argument("--traction", type=float, default=1.0)
@@ -363,7 +364,7 @@ def run_serving(args):
                vs_baseline=None, dtype="f32+f64", data="synthetic",
                config=dict(workload="serving_mix", requests=len(jobs), seed=20220311,
                            dofs_range=[1e3, args.serve_max_dofs], slots=args.serve_slots, ksp_restart=args.restart,
-                           orthog=["mgs", "mgs_lowsync"][args.orthog], method="iNK",
+                           orthog=["mgs", "mgs_lowsync", "mgs_blocked"][args.orthog], method="iNK",
                            arrival_rate_x_capacity=args.serve_rate, precision="mixed_fp32",
                            families={n: sum(1 for j in jobs if j[4].startswith(n)) for n in ("cook", "twist", "heart")}),
                p50_latency_s=round(float(np.percentile(lat, 50)), 4) if len(lat) else None,
@@ -506,7 +507,7 @@ def main():
                    data="synthetic",
                    config=dict(workload=name, dofs=m.ndof, blocks=m.nnzb, nu=args.nu, traction=args.traction,
                                load_step=f"step 1 of {len(w['steps'])} from rest", methods=methods, precision=args.precision, tol=TOL,
-                               ksp_restart=args.restart, orthog=["mgs", "mgs_lowsync"][args.orthog],
+                               ksp_restart=args.restart, orthog=["mgs", "mgs_lowsync", "mgs_blocked"][args.orthog],
                                l2="working set > L2 (tangent and Krylov basis), no flush",
                                parallelism=f"replicas x{world}"),
                    methods=per_method, roofline=roof, roofline_spmv=roof_spmv,

@@ -234,7 +234,11 @@ typedef struct {
   int32_t orthog;      /* Arnoldi orthogonalisation: 0 (default) the sequential modified
                           Gram-Schmidt sweep the paper uses (j+2 grid reductions per step);
                           1 the same MGS projections in compact-WY form (2 grid
-                          reductions per step, ~1.5x the FP64 work, restart <= 128) */
+                          reductions per step, ~1.5x the FP64 work, restart <= 128);
+                          2 MGS over blocks of 8 basis vectors, the block's
+                          coefficients from its cached Gram entries (ceil((j+1)/8)+1
+                          grid reductions per step, same FP64 work; vectors too long
+                          for one co-resident grid take the sequential sweep) */
 } nl_opts;
 
 #define NL_HIST 1024

@@ -625,18 +625,18 @@ __global__ void __launch_bounds__(256) k_elem_tangent(
     int na = sconn[le][a], nb = sconn[le][b];
     uint8_t fa = fixmask[na], fb = fixmask[nb];
     const int* em = emap + (size_t)e * NEN * NEN;
-    T* Kab = K + (size_t)em[a * NEN + b] * 9;
+    const int pab = em[a * NEN + b];
     for (int kk = 0; kk < 3; kk++) {
       T v = w * acc[kk];
       if (((fa >> i) & 1) || ((fb >> kk) & 1)) v = T(0);
-      Kab[3 * i + kk] += v;
+      K[kv_index(pab, 3 * i + kk)] += v;
     }
     if (a != b) {
-      T* Kba = K + (size_t)em[b * NEN + a] * 9;
+      const int pba = em[b * NEN + a];
       for (int kk = 0; kk < 3; kk++) {
         T v = w * acc[kk];
         if (((fa >> i) & 1) || ((fb >> kk) & 1)) v = T(0);
-        Kba[3 * kk + i] += v;
+        K[kv_index(pba, 3 * kk + i)] += v;
       }
     }
   }
@@ -670,10 +670,10 @@ __global__ void k_add_springs(int nn, const int* __restrict__ ks_ptr, const int*
   if (a >= nn) return;
   for (int k = ks_ptr[a]; k < ks_ptr[a + 1]; k++) {
     uint8_t fa = fixmask[a], fb = fixmask[ks_col[k]];
-    T* Kb = K + (size_t)ks_kpos[k] * 9;
+    const int p = ks_kpos[k];
     for (int i = 0; i < 3; i++)
       for (int j = 0; j < 3; j++)
-        if (!((fa >> i) & 1) && !((fb >> j) & 1)) Kb[3 * i + j] += (T)ks_val[(size_t)k * 9 + 3 * i + j];
+        if (!((fa >> i) & 1) && !((fb >> j) & 1)) K[kv_index(p, 3 * i + j)] += (T)ks_val[(size_t)k * 9 + 3 * i + j];
   }
 }
 
@@ -683,12 +683,12 @@ __global__ void k_diag_inverse(int nn, const int* __restrict__ diag_pos, const u
                                T* K, DT* Dinv) {
   int a = blockIdx.x * blockDim.x + threadIdx.x;
   if (a >= nn) return;
-  T* Kd = K + (size_t)diag_pos[a] * 9;
+  const int p = diag_pos[a];
   uint8_t fm = fixmask[a];
   for (int i = 0; i < 3; i++)
-    if ((fm >> i) & 1) Kd[4 * i] = T(1);
+    if ((fm >> i) & 1) K[kv_index(p, 4 * i)] = T(1);
   T M[9];
-  for (int k = 0; k < 9; k++) M[k] = Kd[k];
+  for (int k = 0; k < 9; k++) M[k] = K[kv_index(p, k)];
   T c0 = M[4] * M[8] - M[5] * M[7];
   T c1 = M[5] * M[6] - M[3] * M[8];
   T c2 = M[3] * M[7] - M[4] * M[6];
@@ -715,9 +715,9 @@ __global__ void k_schur_diag(int np, const int* __restrict__ pu_ptr, const int* 
   if (v >= np) return;
   double s = 0.0;
   for (int k = pu_ptr[v]; k < pu_ptr[v + 1]; k++) {
-    const T* Kd = K + (size_t)diag_pos[pu_col[k]] * 9;
+    const int p = diag_pos[pu_col[k]];
     const T* b = B + (size_t)pu_src[k] * 3;
-    for (int i = 0; i < 3; i++) s -= (double)b[i] * (double)b[i] / (double)Kd[4 * i];
+    for (int i = 0; i < 3; i++) s -= (double)b[i] * (double)b[i] / (double)K[kv_index(p, 4 * i)];
   }
   Sd[v] = s;
 }
@@ -756,7 +756,7 @@ int fe_tangent_dev(fe_mesh m, const double* d, int precision) {
   if (precision < 0 || precision > 2) return fe_set_error("bad precision %d", precision), FE_ERR_ARG;
   if (precision == FE_PREC_MIXED_BF16 && m->pres)
     return fe_set_error("BF16 tangent storage is offered for the displacement form only"), FE_ERR_ARG;
-  const size_t nval = (size_t)m->nnzb * 9;
+  const size_t nval = kv_count(m->nnzb);  // tiles of 32 blocks (the last one zero-padded)
   const size_t nb = (size_t)(m->nnz_up > 0 ? m->nnz_up : 1) * 3;
   if (precision == FE_PREC_FP64) {
     if (!m->K64) FE_TRY(fe_alloc_t(m, &m->K64, nval));
@@ -875,7 +875,13 @@ extern "C" int fe_tangent_copy(fe_mesh m, double* val, double* bup, double* dinv
   FE_CUDA(cudaStreamSynchronize(m->stream));
   bool f64 = m->prec == FE_PREC_FP64;
   bool b16 = m->prec == FE_PREC_MIXED_BF16;
-  FE_TRY(copy_out(m, val, f64 ? m->K64 : nullptr, f64 ? nullptr : m->K32, b16 ? m->K16 : nullptr, m->nnzb * 9));
+  if (val) {  // device values are tiled (kv_index); the copy is block-major [nnzb][3][3]
+    std::vector<double> tv(kv_count(m->nnzb));
+    FE_TRY(copy_out(m, tv.data(), f64 ? m->K64 : nullptr, f64 ? nullptr : m->K32, b16 ? m->K16 : nullptr,
+                    (int64_t)tv.size()));
+    for (int64_t p = 0; p < m->nnzb; p++)
+      for (int c = 0; c < 9; c++) val[p * 9 + c] = tv[kv_index(p, c)];
+  }
   if (m->pres) FE_TRY(copy_out(m, bup, f64 ? m->B64 : nullptr, f64 ? nullptr : m->B32, nullptr, m->nnz_up * 3));
   FE_TRY(copy_out(m, dinv, f64 ? m->Dinv64 : nullptr, f64 ? nullptr : m->Dinv32, nullptr, (int64_t)m->nn * 9));
   return FE_OK;

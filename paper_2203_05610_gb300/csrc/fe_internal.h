@@ -95,7 +95,7 @@ struct fe_mesh_s {
 
   // tangent and preconditioner
   int prec = -1;             // precision of the assembled tangent (-1 none)
-  double* K64 = nullptr;     // [nnzb][9]
+  double* K64 = nullptr;     // [kv_count(nnzb)] tiles of 32 blocks, component-major inside a tile (kv_index)
   float* K32 = nullptr;
   __nv_bfloat16* K16 = nullptr;
   double* B64 = nullptr;     // [nnz_up][3]
@@ -111,18 +111,19 @@ struct fe_mesh_s {
   unsigned* red_ticket = nullptr;
   double* scal = nullptr;    // device scalars [64]
   int* err = nullptr;        // device error word
-  unsigned* bar = nullptr;   // grid reduction state: count, seq, slot[2] (u64)
+  unsigned* bar = nullptr;   // grid reduction state [BAR_WORDS]: count, seq, slot[2] (u64); blocked-MGS seq, pub[2][8] (u64)
   double* h_scal = nullptr;  // pinned host mirror [64]
 
   // solver workspace (lazy)
   int ws_restart = 0;
   double* V = nullptr;       // [(restart+1)][ldv], rows zero-padded
   int64_t ldv = 0;           // leading dimension of V: ndof rounded up to 32
-  int orthog = 0;            // 0: sequential MGS sweep, 1: low-synchronisation MGS
+  int orthog = 0;            // 0: sequential MGS sweep, 1: low-synchronisation MGS, 2: blocked MGS
   double* Lmat = nullptr;    // [(restart+1)^2] strictly lower triangle of V^T V (low-sync MGS)
   double* hpub = nullptr;    // [restart+1] published MGS coefficients
   double* partv = nullptr;   // [partv_blocks][2 restart + 1] per-block inner products
   int partv_blocks = 0;
+  double* Tbm = nullptr;     // [(restart+2)][BMGS_P] strictly lower rows of (I + L_B)^{-1} (blocked MGS)
   double* H = nullptr;       // [(restart+1)][restart] column-major by step
   double* gv = nullptr;      // Givens: cs, sn, g, y [4][restart+1]
   double* w64 = nullptr;     // [ndof]
@@ -160,6 +161,17 @@ struct fe_mesh_s {
 constexpr int RED_SLOTS = 16384;
 constexpr int SCAL_N = 64;
 constexpr int LBFGS_MAX = 1000;  // largest number of stored secant pairs
+constexpr int BMGS_P = 8;        // basis vectors per block of the blocked MGS step
+constexpr int BAR_WORDS = 64;    // u32 words of the grid reduction state
+
+// Tangent values: tiles of 32 consecutive blocks, component-major inside a
+// tile.  Entry c = 3i + k of block p lives at (p / 32) 288 + 32 c + p % 32,
+// so a warp reading one component of 32 consecutive blocks reads at most two
+// 128-byte runs of one 1,152-byte tile region (block-major storage made each
+// such load touch the warp's whole value segment; fully component-major
+// storage spread the warp over 9 distant DRAM pages).
+__host__ __device__ __forceinline__ int64_t kv_index(int64_t p, int c) { return (p >> 5) * 288 + 32 * c + (p & 31); }
+inline size_t kv_count(int64_t nnzb) { return (size_t)((nnzb + 31) / 32) * 288; }
 
 // Counts one kernel launch of class `cls` and, with timing on, brackets it
 // with events on the mesh stream: open the scope, launch, close the scope.

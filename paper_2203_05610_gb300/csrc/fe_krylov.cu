@@ -204,7 +204,7 @@ __device__ __forceinline__ void grid_reduce_w0(const GridSync& gs, double* part,
 }
 
 template <int NPT, class DT, class ZT>
-__global__ void __launch_bounds__(NPT <= 6 ? 1024 : 512)
+__global__ void __launch_bounds__(NPT <= 6 ? 1024 : (NPT <= 12 ? 512 : 256))
     k_arnoldi(int64_t n, int j, double* __restrict__ V, int64_t ldv, const double* __restrict__ w,
               double* __restrict__ Hcol, double* part, GridSync gs,
               double* __restrict__ cs, double* __restrict__ sn, double* __restrict__ g, double* __restrict__ out,
@@ -354,7 +354,7 @@ __device__ __forceinline__ bool wait_seq(const GridSync& gs, unsigned seq) {
 }
 
 template <int NPT, class DT, class ZT>
-__global__ void __launch_bounds__(NPT <= 6 ? 1024 : 512)
+__global__ void __launch_bounds__(NPT <= 6 ? 1024 : (NPT <= 12 ? 512 : 256))
     k_arnoldi_ls(int64_t n, int j, double* __restrict__ V, int64_t ldv, const double* __restrict__ w,
                  double* __restrict__ Hcol, double* part, double* partv, GridSync gs, double* __restrict__ Lmat,
                  int ldl, double* hpub, double* __restrict__ cs, double* __restrict__ sn, double* __restrict__ g,
@@ -521,7 +521,333 @@ __global__ void __launch_bounds__(NPT <= 6 ? 1024 : 512)
   }
 }
 
+// ---------------------------------------------------------------- blocked MGS step
+// Modified Gram-Schmidt over the basis in blocks of P vectors.  Inside a
+// block the sequential MGS coefficients follow from the block's inner
+// products with the current w and from the block's own Gram entries:
+//   <w - sum_{l<m} h_l v_l, v_m> = <w, v_m> - sum_{l<m} h_l <v_l, v_m>,
+// i.e. h_B = (I + L_B)^{-1} V_B^T w with L_B the strictly lower triangle of
+// V_B^T V_B (the compact-WY identity of the low-synchronisation step,
+// applied per block; equal to the MGS coefficients in exact arithmetic, the
+// sequential MGS sweep for P = 1).  Between blocks w is updated before the
+// next block's inner products, as in MGS.  The entries <v_{j+1}, v_l>, v_l in
+// the block of v_{j+1}, are reduced together with ||w||^2 at the end of step
+// j, and the new row of T_B = (I + L_B)^{-1} is stored, so step j takes
+// ceil((j+1)/P) + 1 grid reductions instead of j + 2, at the same 2 FMAs per
+// entry and basis vector (plus at most P - 1 inner products for the Gram
+// row).  w stays in registers; each sweep applies the previous block's
+// update and accumulates the current block's inner products, one vector per
+// pass, with the next pass's vector loaded while the current one is used.
+//
+// The reductions have their own step sequence and two sets of P published
+// slots (bar[6], bar[8..]) so that other persistent kernels' use of the
+// shared slots cannot leave a stale value in a slot this kernel polls.
+struct BlockSync {
+  unsigned* count;           // arrival counter (shared with GridSync)
+  unsigned* seq;             // this kernel's step sequence
+  unsigned long long* pub;   // [2][BMGS_P] published values, kSentinel when not yet
+  int* err;
+};
+
+// Warp reduce-scatter of P values per lane: returns, in every lane, the warp
+// total of value index lane / (32 / P).  Each of the first log2(P) exchange
+// steps halves the values a lane carries (it keeps the half selected by its
+// lane bit and adds the partner's copy of that half), then plain xor steps
+// finish the sum: P - 1 + 5 - log2(P) shuffles instead of 5 P.
+template <int P>
+__device__ __forceinline__ double warp_reduce_scatter(double (&v)[P], int lane) {
+#pragma unroll
+  for (int cnt = P, o = 16; cnt > 1; cnt >>= 1, o >>= 1) {
+    const bool up = (lane & o) != 0;
+#pragma unroll
+    for (int k = 0; k < cnt / 2; k++) {
+      const double send = up ? v[k] : v[k + cnt / 2];
+      const double keep = up ? v[k + cnt / 2] : v[k];
+      v[k] = keep + __shfl_xor_sync(0xffffffffu, send, o);
+    }
+  }
+  double t = v[0];
+#pragma unroll
+  for (int o = 16 / P; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+  return t;
+}
+
+// warp 0 of every block.  Lane l holds the block total of value l % P.  The
+// last block to arrive adds the partials of all blocks in block order, and
+// when `solve` is set (lane m < nc: row m of T_B, entries l < m, in trow)
+// turns the totals s into h = T_B s; lanes m < P of every block end with the
+// value m in out_sh[m].  false: the wait timed out (error word set).
+template <int P>
+__device__ __forceinline__ bool bm_reduce_w0(const BlockSync& bs, double* part, unsigned seq, double t,
+                                             const double (&trow)[P], bool solve, int nc, double* out_sh) {
+  const int lane = threadIdx.x & 31;
+  if (gridDim.x > 1) {
+    if (lane < P) part[(int64_t)blockIdx.x * P + lane] = t;
+    __threadfence();
+    __syncwarp();
+    int last = 0;
+    if (lane == 0) last = atom_inc_acq_rel(bs.count, gridDim.x - 1) == gridDim.x - 1;
+    last = __shfl_sync(0xffffffffu, last, 0);
+    if (!last) {
+      bool ok = true;
+      if (lane < P) {
+        const unsigned long long* slot = bs.pub + (seq & 1u) * BMGS_P + lane;
+        unsigned spins = 0;
+        unsigned long long u;
+        while ((u = ld_acquire_u64(slot)) == kSentinel) {
+          if (++spins > (1u << 26) || *(volatile int*)bs.err != DEV_OK) {
+            atomicCAS(bs.err, DEV_OK, DEV_ERR_TIMEOUT);
+            ok = false;
+            break;
+          }
+        }
+        out_sh[lane] = __longlong_as_double((long long)u);
+      }
+      return __all_sync(0xffffffffu, ok);
+    }
+    asm volatile("fence.acq_rel.gpu;" ::: "memory");
+    t = 0.0;
+    for (int b = lane / P; b < (int)gridDim.x; b += 32 / P) t += ld_relaxed_f64(part + (int64_t)b * P + (lane % P));
+#pragma unroll
+    for (int o = P; o < 32; o <<= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+  }
+  if (solve) {  // h_m = s_m + sum_{l<m} T[m][l] s_l
+    double h = t;
+#pragma unroll
+    for (int l = 0; l < P - 1; l++) {
+      const double sl = __shfl_sync(0xffffffffu, t, l);
+      if (lane > l && lane < nc) h += trow[l] * sl;
+    }
+    t = h;
+  }
+  if (lane < P) {
+    out_sh[lane] = t;
+    if (gridDim.x > 1) {
+      st_relaxed_u64(bs.pub + ((seq + 1u) & 1u) * BMGS_P + lane, kSentinel);
+      st_release_u64(bs.pub + (seq & 1u) * BMGS_P + lane, (unsigned long long)__double_as_longlong(t));
+    }
+  }
+  if (lane == 0 && gridDim.x > 1) *(volatile unsigned*)bs.seq = seq + 1u;
+  return true;
+}
+
+__device__ __forceinline__ void prefetch_l2(const double* p, int64_t count) {
+  // bulk L2 prefetch of a 16-byte aligned run (rows of V are 256-byte aligned
+  // and zero-padded, so rounding the size up stays inside the row)
+  const uint32_t bytes = (uint32_t)(((count * 8) + 15) & ~(int64_t)15);
+  if (bytes) asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
+}
+
+// this thread's NPT values of a vector slice (0 past its end)
+template <int NPT>
+__device__ __forceinline__ void load_slice(double (&r)[NPT], const double* __restrict__ v, int64_t len) {
+#pragma unroll
+  for (int s = 0; s < NPT; s++) {
+    const int64_t k = threadIdx.x + (int64_t)s * blockDim.x;
+    r[s] = k < len ? __ldcg(v + k) : 0.0;
+  }
+}
+
+template <int NPT, int P, class DT, class ZT>
+__global__ void __launch_bounds__(NPT <= 12 ? 512 : 256)
+    k_arnoldi_bm(int64_t n, int j, double* __restrict__ V, int64_t ldv, const double* __restrict__ w,
+                 double* __restrict__ Hcol, double* part, BlockSync bs, double* __restrict__ T,
+                 double* __restrict__ cs, double* __restrict__ sn, double* __restrict__ g, double* __restrict__ out,
+                 const DT* __restrict__ Dinv, ZT* __restrict__ z, double target, int kmax, int it0, int max_it) {
+  static_assert(P == 2 || P == 4 || P == 8, "block of 2, 4 or 8 basis vectors");
+  extern __shared__ __align__(16) double ws[];
+  __shared__ double wpart[P][32];
+  __shared__ double s_h[P];
+  __shared__ int s_fail;
+  if (*(volatile double*)(out + 7) != 0.0) return;
+  unsigned seq = *(volatile unsigned*)bs.seq;  // no reduction completes before every block has read it
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const int64_t S = (int64_t)NPT * blockDim.x;
+  const int64_t base = (int64_t)blockIdx.x * S;
+  const int64_t len = n - base < S ? n - base : S;
+  const int nb = j / P + 1;                // blocks of the basis v_0..v_j
+  const int nlast = j + 1 - (nb - 1) * P;  // vectors in the last block
+  const int ng = (j + 1) % P ? nlast : 0;  // Gram entries of v_{j+1} (its block is the last one)
+  if (threadIdx.x == 0) s_fail = 0;
+  if (threadIdx.x < P && (int)threadIdx.x <= j) prefetch_l2(V + (int64_t)threadIdx.x * ldv + base, len);
+  double wr[NPT];
+#pragma unroll
+  for (int s = 0; s < NPT; s++) {
+    const int64_t k = threadIdx.x + (int64_t)s * blockDim.x;
+    wr[s] = k < len ? w[base + k] : 0.0;
+  }
+  double hp[P];
+#pragma unroll
+  for (int m = 0; m < P; m++) hp[m] = 0.0;
+  double cur[NPT], nxt[NPT];
+#pragma unroll
+  for (int s = 0; s < NPT; s++) nxt[s] = 0.0;
+  load_slice<NPT>(cur, V + base, len);  // first pass: the inner product with v_0
+  for (int kb = 0; kb <= nb; kb++) {
+    const int np = kb == 0 ? 0 : (kb == nb ? nlast : P);        // previous block: update
+    const int nc = kb == nb ? ng : (kb == nb - 1 ? nlast : P);  // current block (final sweep: Gram row)
+    const double* Vp = V + (int64_t)(kb > 0 ? kb - 1 : 0) * P * ldv + base;
+    const double* Vc = kb < nb ? V + (int64_t)kb * P * ldv + base : Vp;
+    // Passes over one vector each: np update passes (w -= h_m v_m, block B-1),
+    // then nc inner-product passes (block B; final sweep: the Gram row against
+    // block B-1).  The slice of the next pass's vector is loaded into registers
+    // while the current one is used.
+    const int nq = np + nc;
+#pragma unroll
+    for (int m = 0; m < P; m++) {
+      if (m < np) {
+        if (m + 1 < nq) load_slice<NPT>(nxt, m + 1 < np ? Vp + (int64_t)(m + 1) * ldv : Vc, len);
+        const double h = hp[m];
+#pragma unroll
+        for (int s = 0; s < NPT; s++) wr[s] -= h * cur[s];
+#pragma unroll
+        for (int s = 0; s < NPT; s++) cur[s] = nxt[s];
+      }
+    }
+    double loc[P];
+#pragma unroll
+    for (int m = 0; m < P; m++) loc[m] = 0.0;
+#pragma unroll
+    for (int m = 0; m < P; m++) {
+      if (m < nc) {
+        if (m + 1 < nc) load_slice<NPT>(nxt, Vc + (int64_t)(m + 1) * ldv, len);
+        double a[4] = {0.0, 0.0, 0.0, 0.0};  // four chains: the FP64 pipe is shared by few warps
+#pragma unroll
+        for (int s = 0; s < NPT; s++) a[s & 3] += wr[s] * cur[s];
+        loc[m] = (a[0] + a[1]) + (a[2] + a[3]);
+#pragma unroll
+        for (int s = 0; s < NPT; s++) cur[s] = nxt[s];
+      }
+    }
+    if (kb == nb) {  // final sweep: [||w||^2, Gram row]
+      double a[4] = {0.0, 0.0, 0.0, 0.0};
+#pragma unroll
+      for (int s = 0; s < NPT; s++) a[s & 3] += wr[s] * wr[s];
+#pragma unroll
+      for (int m = P - 1; m > 0; m--) loc[m] = loc[m - 1];
+      loc[0] = (a[0] + a[1]) + (a[2] + a[3]);
+    } else {
+      // first pass of the next sweep: the update with this block's v_{kb P}
+      load_slice<NPT>(cur, V + (int64_t)kb * P * ldv + base, len);
+    }
+    // the next block's vectors are read from HBM by the next sweep: start them now
+    if (kb + 1 < nb && threadIdx.x < P && (kb + 1) * P + (int)threadIdx.x <= j)
+      prefetch_l2(V + (int64_t)((kb + 1) * P + threadIdx.x) * ldv + base, len);
+    // T rows of the current block (lane m: row kb P + m, entries l < m)
+    double trow[P];
+#pragma unroll
+    for (int l = 0; l < P; l++) trow[l] = 0.0;
+    const bool solve = kb < nb;
+    if (wid == 0 && solve && lane < nc) {
+      const double* tr = T + (int64_t)(kb * P + lane) * P;
+#pragma unroll
+      for (int l = 0; l < P - 1; l++)
+        if (l < lane) trow[l] = tr[l];
+    }
+    const double r = warp_reduce_scatter<P>(loc, lane);
+    if ((lane & (32 / P - 1)) == 0) wpart[lane / (32 / P)][wid] = r;
+    __syncthreads();
+    if (wid == 0) {
+      double t = 0.0;
+      for (int q = lane / P; q < nw; q += 32 / P) t += wpart[lane % P][q];
+#pragma unroll
+      for (int x = P; x < 32; x <<= 1) t += __shfl_xor_sync(0xffffffffu, t, x);
+      if (!bm_reduce_w0<P>(bs, part, seq, t, trow, solve, nc, s_h) && lane == 0) s_fail = 1;
+    }
+    if (gridDim.x > 1) seq++;
+    __syncthreads();
+    if (s_fail) return;
+#pragma unroll
+    for (int m = 0; m < P; m++) hp[m] = s_h[m];
+    if (solve && blockIdx.x == 0 && threadIdx.x < nc) Hcol[kb * P + threadIdx.x] = s_h[threadIdx.x];
+  }
+  // hp[0] = ||w||^2, hp[1..ng] = <w, v_l> for the last block's vectors
+  const double hn = sqrt(hp[0]);
+  if (hn > 0.0) {
+    const double inv = 1.0 / hn;
+    double* vnx = V + (int64_t)(j + 1) * ldv + base;
+#pragma unroll
+    for (int s = 0; s < NPT; s++) {
+      const int64_t k = threadIdx.x + (int64_t)s * blockDim.x;
+      const double v = wr[s] * inv;
+      ws[k] = v;
+      if (k < len) vnx[k] = v;
+    }
+    if (z) {
+      __syncthreads();
+      for (int64_t a = threadIdx.x; a < len / 3; a += blockDim.x) {
+        const DT* D = Dinv + ((base / 3) + a) * 9;
+        double x0 = ws[3 * a], x1 = ws[3 * a + 1], x2 = ws[3 * a + 2];
+        ZT* zo = z + base + 3 * a;
+        if constexpr (sizeof(DT) == 8) {
+          zo[0] = (ZT)(D[0] * x0 + D[1] * x1 + D[2] * x2);
+          zo[1] = (ZT)(D[3] * x0 + D[4] * x1 + D[5] * x2);
+          zo[2] = (ZT)(D[6] * x0 + D[7] * x1 + D[8] * x2);
+        } else {
+          float f0 = (float)x0, f1 = (float)x1, f2 = (float)x2;
+          zo[0] = (ZT)(D[0] * f0 + D[1] * f1 + D[2] * f2);
+          zo[1] = (ZT)(D[3] * f0 + D[4] * f1 + D[5] * f2);
+          zo[2] = (ZT)(D[6] * f0 + D[7] * f1 + D[8] * f2);
+        }
+      }
+    }
+    // new row of T_B: T[j+1][c] = -(g_c + sum_{c<l<ng} g_l T[b0+l][c]), g_l = <v_{j+1}, v_{b0+l}>
+    if (blockIdx.x == 0 && threadIdx.x < ng) {
+      const int c = threadIdx.x, b0 = (nb - 1) * P;
+      double acc = s_h[1 + c] * inv;
+      for (int l = c + 1; l < ng; l++) acc += s_h[1 + l] * inv * T[(int64_t)(b0 + l) * P + c];
+      T[(int64_t)(j + 1) * P + c] = -acc;
+    }
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    Hcol[j + 1] = hn;
+    for (int i = 0; i < j; i++) {
+      double a = Hcol[i], c = Hcol[i + 1];
+      Hcol[i] = cs[i] * a + sn[i] * c;
+      Hcol[i + 1] = -sn[i] * a + cs[i] * c;
+    }
+    double a = Hcol[j], c = Hcol[j + 1];
+    double r = hypot(a, c);
+    cs[j] = a / r;
+    sn[j] = c / r;
+    Hcol[j] = r;
+    Hcol[j + 1] = 0.0;
+    g[j + 1] = -sn[j] * g[j];
+    g[j] = cs[j] * g[j];
+    double res = fabs(g[j + 1]);
+    out[0] = res;
+    out[1] = hn;
+    out[8] = (double)(j + 1);
+    if (!(res > target) || hn == 0.0 || j + 1 >= kmax || it0 + j + 1 >= max_it) out[7] = 1.0;
+  }
+}
+
 // ---------------------------------------------------------------- SpMV
+// float -> double widening with integer operations only.  GB300's FP64 pipe
+// issues ~2 lane-operations per clock per SM, so the three hardware
+// conversions of every row result of the FP32 SpMV cost about half of the
+// kernel's time.  The conversion is exact for every float: normal numbers
+// rebias the exponent (+896) and shift the mantissa (<< 29), subnormals are
+// normalised with a leading-zero count, zeros keep their sign, infinities
+// and NaNs map to the all-ones exponent with the payload in place.
+__device__ __forceinline__ double widen(float f) {
+  const uint32_t u = __float_as_uint(f);
+  const uint32_t e = (u >> 23) & 0xffu;
+  uint32_t mant = u & 0x7fffffu;
+  uint32_t de;                           // biased double exponent
+  if (e == 0xffu) de = 0x7ffu;           // Inf / NaN (payload and quiet bit keep their place)
+  else if (e != 0u) de = e + 896u;       // normal: rebias 127 -> 1023
+  else if (mant == 0u) de = 0u;          // signed zero
+  else {                                 // subnormal: normalise; value = mant 2^-149
+    const uint32_t lz = __clz(mant);     // >= 9; leading one moves to bit 23
+    de = 905u - lz;
+    mant = (mant << (lz - 8u)) & 0x7fffffu;
+  }
+  const uint64_t bits = ((uint64_t)(u >> 31) << 63) | ((uint64_t)de << 52) | ((uint64_t)mant << 29);
+  return __longlong_as_double((long long)bits);
+}
+__device__ __forceinline__ double widen(double d) { return d; }
+
 template <class V>
 __device__ __forceinline__ float ld_val(const V* p);
 template <>
@@ -532,11 +858,14 @@ __device__ __forceinline__ float ld_val<__nv_bfloat16>(const __nv_bfloat16* p) {
 }
 
 // y_u = K x_u (+ B1 x_p): one warp per block row, one lane per 3x3 block.
-// A lane loads its block's column index, its 9 values (a contiguous 36-byte
-// run; the warp's 32 runs tile the row's value segment, so every sector is
-// used) and the 3 entries of x, then accumulates the 3 row sums; the warp
-// reduces them with shuffles.  Few registers keep the SM full of warps, which
-// is what hides the HBM latency of the value stream.
+// A lane loads its block's column index, its 9 values and the 3 entries of
+// x, then accumulates the 3 row sums; the warp reduces them with shuffles.
+// The values are tiled (kv_index: 32 blocks per tile, component-major
+// inside it), so each of the 9 value loads of a warp reads at most two
+// 128-byte runs: with block-major storage every load touched the warp's
+// whole 1,152-byte segment and the L1 request rate, not HBM, bounded the
+// kernel (ncu: 9x more L1 sectors than DRAM sectors).  Few registers keep
+// the SM full of warps, which hides the HBM latency.
 template <class VT, class XT, class AT>
 __global__ void __launch_bounds__(256) k_spmv(int nn, const int* __restrict__ row_ptr, const int* __restrict__ col,
                                               const VT* __restrict__ val, const XT* __restrict__ x,
@@ -550,12 +879,12 @@ __global__ void __launch_bounds__(256) k_spmv(int nn, const int* __restrict__ ro
   AT a0 = AT(0), a1 = AT(0), a2 = AT(0);
   for (int k = rs + lane; k < re; k += 32) {
     const int c = __ldg(col + k);
-    const VT* b = val + (int64_t)k * 9;
+    const VT* b = val + kv_index(k, 0);
     AT v[9];
 #pragma unroll
     for (int t = 0; t < 9; t++) {
-      if constexpr (sizeof(VT) == 8) v[t] = __ldg(b + t);
-      else v[t] = (AT)ld_val<VT>(b + t);
+      if constexpr (sizeof(VT) == 8) v[t] = __ldg(b + 32 * t);
+      else v[t] = (AT)ld_val<VT>(b + 32 * t);
     }
     const XT* xc = x + 3 * (int64_t)c;
     AT x0 = (AT)xc[0], x1 = (AT)xc[1], x2 = (AT)xc[2];
@@ -584,9 +913,9 @@ __global__ void __launch_bounds__(256) k_spmv(int nn, const int* __restrict__ ro
     a2 += __shfl_xor_sync(0xffffffffu, a2, off);
   }
   if (lane == 0) {
-    y[3 * (int64_t)row] = (double)a0;
-    y[3 * (int64_t)row + 1] = (double)a1;
-    y[3 * (int64_t)row + 2] = (double)a2;
+    y[3 * (int64_t)row] = widen(a0);
+    y[3 * (int64_t)row + 1] = widen(a1);
+    y[3 * (int64_t)row + 2] = widen(a2);
   }
 }
 
@@ -606,7 +935,7 @@ __global__ void __launch_bounds__(256) k_spmv_p(int np, const int* __restrict__ 
     else acc += (AT)ld_val<VT>(b) * (AT)u[0] + (AT)ld_val<VT>(b + 1) * (AT)u[1] + (AT)ld_val<VT>(b + 2) * (AT)u[2];
   }
   for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
-  if (lane == 0) yp[v] = (double)acc;
+  if (lane == 0) yp[v] = widen(acc);
 }
 
 // ---------------------------------------------------------------- preconditioner
@@ -822,9 +1151,11 @@ int fe_dot_dev(fe_mesh m, const double* a, const double* b, int64_t n, double* o
 }
 
 // y = a x + b y
+// y = a x + b y; b == 0 overwrites y (the BLAS convention), so a NaN left in
+// y by an earlier solve cannot leak into y through 0 * NaN
 __global__ void k_axpby(int64_t n, double a, const double* __restrict__ x, double b, double* __restrict__ y) {
   int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < n) y[i] = a * x[i] + b * y[i];
+  if (i < n) y[i] = b == 0.0 ? a * x[i] : a * x[i] + b * y[i];
 }
 int fe_axpby_dev(fe_mesh m, double a, const double* x, double b, double* y, int64_t n) {
   FE_SCOPE(m, FE_PROF_VECTOR, 24.0 * n);
@@ -888,6 +1219,9 @@ int fe_workspace(fe_mesh m, int restart) {
       m->device_bytes -= (int64_t)(m->ws_restart + 1) * m->ldv * 8 + (int64_t)(m->ws_restart + 1) * (m->ws_restart + 1) * 8 +
                          (int64_t)4 * (m->ws_restart + 2) * 8;
       m->V = m->H = m->gv = nullptr;
+      cudaFree(m->Tbm);
+      m->device_bytes -= (int64_t)(m->ws_restart + 2) * BMGS_P * 8;
+      m->Tbm = nullptr;
     }
     FE_TRY(fe_alloc_t(m, &m->V, (size_t)(restart + 1) * ldv));
     FE_CUDA(cudaMemsetAsync(m->V, 0, (size_t)(restart + 1) * ldv * sizeof(double), m->stream));
@@ -895,6 +1229,7 @@ int fe_workspace(fe_mesh m, int restart) {
     FE_TRY(fe_alloc_t(m, &m->gv, (size_t)4 * (restart + 2)));
     m->ws_restart = restart;
     m->ldv = ldv;
+    FE_TRY(fe_alloc_t(m, &m->Tbm, (size_t)(restart + 2) * BMGS_P));
     if (restart <= LOWSYNC_MAX_RESTART) {  // low-synchronisation MGS: L, h, per-block inner products
       if (m->Lmat) {
         cudaFree(m->Lmat);
@@ -934,9 +1269,9 @@ template <class DT, class ZT>
 static int launch_arnoldi_t(fe_mesh m, int j, int kmax, bool fuse_pc, const DT* Dinv, double target, int it0,
                             int max_it) {
   const int64_t n = m->ndof;
-  const void* fns[3] = {arnoldi_fn<6, DT, ZT>(), arnoldi_fn<12, DT, ZT>(), arnoldi_fn<24, DT, ZT>()};
-  const int npts[3] = {6, 12, 24};
-  const int bds[3] = {1024, 512, 512};
+  const void* fns[3] = {arnoldi_fn<24, DT, ZT>(), arnoldi_fn<12, DT, ZT>(), arnoldi_fn<6, DT, ZT>()};
+  const int npts[3] = {24, 12, 6};
+  const int bds[3] = {256, 512, 1024};
   static bool attr[2][2][3] = {};
   int which = -1, grid = 0;
   for (int q = 0; q < 3; q++) {
@@ -986,9 +1321,9 @@ template <class DT, class ZT>
 static int launch_arnoldi_ls_t(fe_mesh m, int j, int kmax, bool fuse_pc, const DT* Dinv, double target, int it0,
                                int max_it) {
   const int64_t n = m->ndof;
-  const void* fns[3] = {arnoldi_ls_fn<6, DT, ZT>(), arnoldi_ls_fn<12, DT, ZT>(), arnoldi_ls_fn<24, DT, ZT>()};
-  const int npts[3] = {6, 12, 24};
-  const int bds[3] = {1024, 512, 512};
+  const void* fns[3] = {arnoldi_ls_fn<24, DT, ZT>(), arnoldi_ls_fn<12, DT, ZT>(), arnoldi_ls_fn<6, DT, ZT>()};
+  const int npts[3] = {24, 12, 6};
+  const int bds[3] = {256, 512, 1024};
   const size_t pw_max = (size_t)(2 * LOWSYNC_MAX_RESTART + 1) * 32 * sizeof(double);
   static bool attr[2][2][3] = {};
   int which = -1, grid = 0;
@@ -1038,7 +1373,80 @@ static int launch_arnoldi_ls_t(fe_mesh m, int j, int kmax, bool fuse_pc, const D
   return FE_OK;
 }
 
+template <int NPT, class DT, class ZT>
+static const void* arnoldi_bm_fn() { return (const void*)k_arnoldi_bm<NPT, BMGS_P, DT, ZT>; }
+
+static BlockSync block_sync(fe_mesh m) {
+  BlockSync bs;
+  bs.count = m->bar;
+  bs.seq = m->bar + 6;
+  bs.pub = (unsigned long long*)(m->bar + 8);
+  bs.err = m->err;
+  return bs;
+}
+
+// Slice selection as in launch_arnoldi_t (w, the current and the next basis
+// slice live in registers); returns 1 without launching when no co-resident
+// grid exists, and the caller takes the sequential sweep.
+template <class DT, class ZT>
+static int launch_arnoldi_bm_t(fe_mesh m, int j, int kmax, bool fuse_pc, const DT* Dinv, double target, int it0,
+                               int max_it) {
+  const int64_t n = m->ndof;
+  // 512 threads of 12 values first: four warps per SM sub-partition keep
+  // the FP64 pipe busier than two
+  const void* fns[2] = {arnoldi_bm_fn<12, DT, ZT>(), arnoldi_bm_fn<24, DT, ZT>()};
+  const int npts[2] = {12, 24};
+  const int bds[2] = {512, 256};
+  static bool attr[2][2][2] = {};
+  int which = -1, grid = 0;
+  for (int q = 0; q < 2; q++) {
+    size_t smem = (size_t)npts[q] * bds[q] * sizeof(double);
+    bool& done = attr[sizeof(DT) == 8][sizeof(ZT) == 8][q];
+    if (!done) {
+      FE_CUDA(cudaFuncSetAttribute(fns[q], cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+      done = true;
+    }
+    int per_sm = 0;
+    FE_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fns[q], bds[q], smem));
+    int64_t need = (n + (int64_t)npts[q] * bds[q] - 1) / ((int64_t)npts[q] * bds[q]);
+    if (per_sm >= 1 && need <= (int64_t)per_sm * m->sm_count && need * BMGS_P <= RED_SLOTS) {
+      which = q;
+      grid = (int)need;
+      break;
+    }
+  }
+  if (which < 0) return 1;
+  size_t smem = (size_t)npts[which] * bds[which] * sizeof(double);
+  double* V = m->V;
+  int64_t ldv = m->ldv;
+  double* Hcol = m->H + (int64_t)j * (kmax + 1);
+  double* cs = m->gv;
+  double* sn = m->gv + (kmax + 2);
+  double* g = m->gv + 2 * (kmax + 2);
+  double* out = m->scal + 3;
+  double* part = m->red;
+  double* T = m->Tbm;
+  const DT* D = fuse_pc ? Dinv : nullptr;
+  ZT* z = fuse_pc ? (ZT*)m->zx : nullptr;
+  BlockSync bs = block_sync(m);
+  void* args[] = {(void*)&n, (void*)&j, (void*)&V, (void*)&ldv, (void*)&m->w64, (void*)&Hcol, (void*)&part,
+                  (void*)&bs, (void*)&T, (void*)&cs, (void*)&sn, (void*)&g, (void*)&out,
+                  (void*)&D, (void*)&z, (void*)&target, (void*)&kmax, (void*)&it0, (void*)&max_it};
+  const int ng = (j + 1) % BMGS_P;
+  // same algorithmic bytes as the sequential sweep; flops add the Gram row
+  FE_SCOPE_F(m, FE_PROF_ARNOLDI, 8.0 * (double)n * (j + 3) + (fuse_pc ? (double)n * (3.0 * sizeof(DT) + sizeof(ZT)) : 0.0),
+             (double)n * (4.0 * (j + 1) + 3.0 + 2.0 * ng) + (fuse_pc ? 6.0 * n : 0.0));
+  FE_CUDA(cudaLaunchCooperativeKernel(fns[which], dim3(grid), dim3(bds[which]), args, smem, m->stream));
+  return FE_OK;
+}
+
 static int launch_arnoldi(fe_mesh m, int j, int kmax, bool fuse_pc, double target, int it0, int max_it) {
+  if (m->orthog == 2) {
+    int r = m->prec == FE_PREC_FP64
+                ? launch_arnoldi_bm_t<double, double>(m, j, kmax, fuse_pc, m->Dinv64, target, it0, max_it)
+                : launch_arnoldi_bm_t<float, float>(m, j, kmax, fuse_pc, m->Dinv32, target, it0, max_it);
+    if (r <= 0) return r;
+  }
   if (m->orthog == 1) {
     if (m->prec == FE_PREC_FP64)
       return launch_arnoldi_ls_t<double, double>(m, j, kmax, fuse_pc, m->Dinv64, target, it0, max_it);
@@ -1359,7 +1767,7 @@ extern "C" int fe_gmres(fe_mesh m, const double* b, double* x, double rtol, doub
                         int orthog, int* iters, double* res_out) {
   if (!m || !b || !x) return fe_set_error("NULL argument"), FE_ERR_ARG;
   if (!(rtol >= 0.0) || !(atol >= 0.0) || max_it < 0) return fe_set_error("bad tolerances"), FE_ERR_ARG;
-  if (orthog != 0 && orthog != 1) return fe_set_error("orthog must be 0 or 1"), FE_ERR_ARG;
+  if (orthog < 0 || orthog > 2) return fe_set_error("orthog must be 0, 1 or 2"), FE_ERR_ARG;
   FE_CUDA(cudaSetDevice(m->device));
   m->orthog = orthog;
   FE_TRY(fe_gmres_dev(m, b, x, rtol, atol, restart, max_it, iters, res_out));

@@ -41,10 +41,13 @@ int fe_alloc(fe_mesh m, void** p, size_t bytes) {
 }
 
 // grid-reduction state of the persistent kernels: arrival counter, step
-// sequence, and two published-value slots holding the "not yet" sentinel
+// sequence, and two published-value slots holding the "not yet" sentinel;
+// then the blocked-MGS step's own sequence and its two sets of 8 slots
 int fe_reset_grid_sync(fe_mesh m) {
   static const unsigned long long sentinel = 0x7FF4DEAD5EEDF00DULL;
-  unsigned long long init[4] = {0ull, sentinel, sentinel, 0ull};  // {count, seq}, slot0, slot1, pad
+  unsigned long long init[BAR_WORDS / 2] = {};
+  init[1] = init[2] = sentinel;                                 // {count, seq}, slot0, slot1
+  for (int i = 4; i < 4 + 2 * BMGS_P; i++) init[i] = sentinel;  // {bseq, pad}, pub[2][8]
   FE_CUDA(cudaMemcpyAsync(m->bar, init, sizeof(init), cudaMemcpyHostToDevice, m->stream));
   FE_CUDA(cudaStreamSynchronize(m->stream));
   return FE_OK;
@@ -579,7 +582,7 @@ static int create_impl(const fe_mesh_desc* desc, fe_mesh m) {
     FE_TRY(upload(m, &m->fib, fib));
   }
 
-  FE_TRY(fe_alloc_t(m, &m->bar, 8));
+  FE_TRY(fe_alloc_t(m, &m->bar, BAR_WORDS));
   FE_TRY(fe_reset_grid_sync(m));
   FE_TRY(fe_alloc_t(m, &m->red, RED_SLOTS));
   FE_TRY(fe_alloc_t(m, &m->red_ticket, 4));
@@ -669,7 +672,7 @@ static void free_all(fe_mesh m) {
                   m->ks_kpos, m->K64, m->K32, m->K16, m->B64, m->B32, m->Dinv64, m->Dinv32,
                   m->Sd, m->rel, m->relp, m->red, m->red_ticket, m->scal, m->bar, m->V,
                   m->H, m->gv, m->w64, m->t64, m->u64, m->zx, m->S, m->Yv, m->nl_R, m->nl_Rn,
-                  m->nl_dl, m->nl_t, m->rho_d, m->lb_x, m->alpha_d, m->Lmat, m->hpub, m->partv};
+                  m->nl_dl, m->nl_t, m->rho_d, m->lb_x, m->alpha_d, m->Lmat, m->hpub, m->partv, m->Tbm};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (m->h_scal) cudaFreeHost(m->h_scal);

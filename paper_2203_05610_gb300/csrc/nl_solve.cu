@@ -227,7 +227,7 @@ extern "C" int nl_solve(fe_mesh m, int method, double tol, int max_it, double* d
     o.apply_dirichlet = opts->apply_dirichlet;
     o.orthog = opts->orthog;
   }
-  if (o.orthog != 0 && o.orthog != 1) return fe_set_error("orthog must be 0 or 1"), FE_ERR_ARG;
+  if (o.orthog < 0 || o.orthog > 2) return fe_set_error("orthog must be 0, 1 or 2"), FE_ERR_ARG;
   if (o.precision < 0 || o.precision > 2) return fe_set_error("bad precision"), FE_ERR_ARG;
   FE_CUDA(cudaSetDevice(m->device));
   nl_stats local;

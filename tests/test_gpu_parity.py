@@ -121,6 +121,11 @@ def test_tangent_mixed_fp32(fe, case):
     v, _, _ = om.tangent_copy()
     vg, _, _ = m.tangent_copy()
     assert _rel(vg, v) < 2e-5  # FP32 arithmetic and storage
+    # FP32 SpMV (FP32 input and sums, exact widening of the row results)
+    x = np.random.default_rng(41).standard_normal(om.ndof)
+    y = om.spmv(x)
+    yg = m.spmv(torch.from_numpy(x).cuda()).cpu().numpy()
+    assert np.abs(yg - y).max() <= 1e-5 * np.abs(y).max()
 
 
 def test_tangent_bf16_storage(fe):
@@ -135,8 +140,9 @@ def test_tangent_bf16_storage(fe):
 
 
 # ---------------------------------------------------------------- Krylov and two-loop
+@pytest.mark.parametrize("orthog", [0, 2])
 @pytest.mark.parametrize("case", ["cook_p1", "twist_up"])
-def test_gmres(fe, case):
+def test_gmres(fe, case, orthog):
     # a mildly deformed state keeps the tangent definite, so GMRES converges
     # at both restart lengths instead of stagnating
     w = small_cases()[case]
@@ -148,14 +154,16 @@ def test_gmres(fe, case):
     bn = np.linalg.norm(b)
     # full-length cycle: same Krylov space, same iterates up to rounding
     x, it, res = om.gmres(b, rtol=1e-11, atol=0.0, restart=500, max_it=20000)
-    xg, itg, resg = m.gmres(torch.from_numpy(b).cuda(), rtol=1e-11, atol=0.0, restart=500, max_it=20000)
+    xg, itg, resg = m.gmres(torch.from_numpy(b).cuda(), rtol=1e-11, atol=0.0, restart=500, max_it=20000,
+                            orthog=orthog)
     assert res <= 1e-11 * bn and resg <= 1e-11 * bn
     assert abs(itg - it) <= max(2, it // 50), (itg, it)
     assert np.linalg.norm(xg.cpu().numpy() - x) <= 1e-7 * np.linalg.norm(x)
     # restarted: rounding changes the restart points' iterates, so compare the
     # property both must meet (true residual at the target) and the effort
     x, it, res = om.gmres(b, rtol=1e-9, atol=0.0, restart=40, max_it=20000)
-    xg, itg, resg = m.gmres(torch.from_numpy(b).cuda(), rtol=1e-9, atol=0.0, restart=40, max_it=20000)
+    xg, itg, resg = m.gmres(torch.from_numpy(b).cuda(), rtol=1e-9, atol=0.0, restart=40, max_it=20000,
+                            orthog=orthog)
     true = np.linalg.norm(b - om.spmv(xg.cpu().numpy()))
     assert resg <= 1e-9 * bn and true <= 2e-9 * bn, (resg / bn, true / bn)
     assert abs(itg - it) <= max(2, it // 5), (itg, it)
@@ -354,3 +362,93 @@ def test_nl_solve_lowsync_mgs(fe, method):
     xg, sg = m.solve(method, m.zeros(), tol=1e-11, opts=dict(ksp_atol=0.0, ksp_restart=60, orthog=1))
     assert so["status"] == 0 and sg["status"] == 0
     assert np.linalg.norm(xg.cpu().numpy() - x) <= 1e-10 * np.linalg.norm(x)
+
+
+# ---------------------------------------------------------------- blocked MGS and multi-block grids
+# Cook P2 16x16x4: 29,403 unknowns, i.e. several blocks of the persistent
+# Arnoldi kernels' 6,144-value slices, the last one ragged.
+MID = {}
+
+
+def _mid():
+    if "w" not in MID:
+        MID["w"] = W.cook(16, 16, 4, order=2, nu=0.3)
+    return MID["w"]
+
+
+@pytest.mark.parametrize("orthog", [0, 1, 2])
+@pytest.mark.parametrize("restart", [120, 30])
+def test_gmres_multiblock_grid(fe, orthog, restart):
+    # several grid blocks and a ragged tail.  This system needs thousands of
+    # iterations to converge, so both sides run exactly 120 iterations (one
+    # cycle, or four cycles of 30): with the MGS projections (sequential,
+    # compact-WY or blocked) the iterates agree up to rounding (two FP64
+    # summation orders differ by ~1e-12 here)
+    w = _mid()
+    m, om = _pair(fe, w)
+    assert om.ndof == 29403
+    d, dg = _state(m, om, "cook_mid", 21, amp=0.05)
+    om.tangent(d)
+    m.tangent(dg)
+    b = np.random.default_rng(22).standard_normal(om.ndof)
+    x, it, res = om.gmres(b, rtol=1e-14, atol=0.0, restart=restart, max_it=120)
+    xg, itg, resg = m.gmres(torch.from_numpy(b).cuda(), rtol=1e-14, atol=0.0, restart=restart, max_it=120,
+                            orthog=orthog)
+    assert it == itg == 120
+    assert abs(resg - res) <= 1e-8 * res, (resg, res)
+    assert np.linalg.norm(xg.cpu().numpy() - x) <= 1e-9 * np.linalg.norm(x)
+
+
+@pytest.mark.parametrize("method", ["NK", "iB"])
+def test_nl_solve_blocked_mgs(fe, method):
+    # default restart (500 >= the 441 unknowns): every Krylov solve converges
+    # within one cycle, so both sides follow the same Newton path (with a
+    # short restart this problem's GMRES stalls at its iteration cap and the
+    # Newton path becomes rounding-sensitive)
+    w = small_cases()["cook_p2"]
+    m, om = _pair(fe, w)
+    m.set_load(0.4)
+    om.set_load(0.4)
+    x, so = om.solve(method, np.zeros(om.ndof), tol=1e-11, opts=dict(ksp_atol=0.0))
+    xg, sg = m.solve(method, m.zeros(), tol=1e-11, opts=dict(ksp_atol=0.0, orthog=2))
+    assert so["status"] == 0 and sg["status"] == 0
+    assert np.linalg.norm(xg.cpu().numpy() - x) <= 1e-10 * np.linalg.norm(x)
+
+
+def test_nl_solve_multiblock_ib(fe):
+    # iB on Cook P1 24x24x6 (13,125 unknowns: three grid blocks, the last
+    # one 837 values), FP64 and mixed precision, sequential and blocked MGS,
+    # against the oracle's FP64 solve
+    w = W.cook(24, 24, 6, order=1, nu=0.3)
+    m, om = _pair(fe, w)
+    m.set_load(0.2)
+    om.set_load(0.2)
+    xref, so = om.solve("iB", np.zeros(om.ndof), tol=1e-11, opts=dict(ksp_restart=50))
+    assert so["status"] == 0
+    errs = {}
+    for prec in ("fp64", "mixed_fp32"):
+        for orthog in (0, 2):
+            xg, sg = m.solve("iB", m.zeros(), tol=1e-8, opts=dict(ksp_restart=50, orthog=orthog, precision=prec))
+            assert sg["status"] == 0, (prec, orthog, sg["status"])
+            assert sg["rfinal"] <= 1e-8 * sg["r0"]
+            errs[prec, orthog] = np.linalg.norm(xg.cpu().numpy() - xref) / np.linalg.norm(xref)
+    assert errs["fp64", 0] <= 1e-6, errs
+    assert max(errs.values()) <= 10 * max(errs["fp64", 0], 1e-12), errs
+
+
+def test_solve_after_nonfinite_solve(fe):
+    # a solve that ends non-finite leaves NaN in the library's work vectors;
+    # the next solve on the same mesh must not pick it up (NK's right-hand
+    # side is formed as -R + 0 * t, which must overwrite t)
+    w = small_cases()["cook_p1"]
+    m, om = _pair(fe, w)
+    m.set_load(50.0)
+    _, sb = m.solve("B", m.zeros(), tol=1e-8, max_it=200)
+    assert sb["status"] in (1, 3), sb["status"]  # diverged or non-finite at this load
+    m.set_load(0.4)
+    om.set_load(0.4)
+    x, so = om.solve("NK", np.zeros(om.ndof), tol=1e-10)
+    xg, sg = m.solve("NK", m.zeros(), tol=1e-10)
+    assert so["status"] == 0 and sg["status"] == 0
+    assert sg["lit_total"] > 0
+    assert np.linalg.norm(xg.cpu().numpy() - x) <= 1e-8 * np.linalg.norm(x)
