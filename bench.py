@@ -46,7 +46,7 @@ def parse():
     p.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     p.add_argument("--methods", default="iB")
     p.add_argument("--restart", type=int, default=50)
-    p.add_argument("--orthog", type=int, default=0, choices=[0, 1, 2],
+    p.add_argument("--orthog", type=int, default=2, choices=[0, 1, 2],
                    help="Arnoldi: 0 sequential MGS sweep (paper), 1 low-synchronisation MGS, "
                         "2 blocked MGS (8 basis vectors per grid reduction)")
     p.add_argument("--precision", default="mixed_fp32", choices=["fp64", "mixed_fp32", "mixed_bf16"])

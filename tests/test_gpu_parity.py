@@ -332,23 +332,31 @@ def test_config2_residual_and_tangent_full_size(fe):
 
 
 # ---------------------------------------------------------------- low-synchronisation MGS
-@pytest.mark.parametrize("case", ["cook_p2", "twist_up"])
+LOWSYNC_CASES = {"cook_p1_96": lambda: W.cook(3, 3, 1, order=1, nu=0.3), "twist_up": lambda: small_cases()["twist_up"]}
+
+
+@pytest.mark.parametrize("case", list(LOWSYNC_CASES))
 def test_gmres_lowsync_mgs(fe, case):
     # the compact-WY form of MGS gives the MGS projections: same iterates as
-    # the oracle's sequential sweep up to rounding
-    w = small_cases()[case]
+    # the oracle's sequential sweep up to rounding.  A cycle of 128 (the
+    # form's limit; the whole space for the 96-unknown Cook case) must reach
+    # 1e-10; a short restart is checked at a tolerance both reach (on a
+    # larger system with kappa ~ 1e6 restarted GMRES(128) stalls near 1e-8
+    # with either form, the oracle's sequential sweep included)
+    w = LOWSYNC_CASES[case]()
     m, om = _pair(fe, w)
     d, dg = _state(m, om, case, 13, amp=0.05)
     om.tangent(d)
     m.tangent(dg)
     b = np.random.default_rng(14).standard_normal(om.ndof)
     bn = np.linalg.norm(b)
-    for restart in (128, 20):
-        x, it, res = om.gmres(b, rtol=1e-10, atol=0.0, restart=restart, max_it=20000)
-        xg, itg, resg = m.gmres(torch.from_numpy(b).cuda(), rtol=1e-10, atol=0.0, restart=restart,
+    for restart, rtol in ((128, 1e-10), (20, 1e-6)):
+        x, it, res = om.gmres(b, rtol=rtol, atol=0.0, restart=restart, max_it=20000)
+        xg, itg, resg = m.gmres(torch.from_numpy(b).cuda(), rtol=rtol, atol=0.0, restart=restart,
                                 max_it=20000, orthog=1)
+        assert res <= rtol * bn, (restart, res / bn)
         true = np.linalg.norm(b - om.spmv(xg.cpu().numpy()))
-        assert resg <= 1e-10 * bn and true <= 2e-10 * bn, (restart, resg / bn, true / bn)
+        assert resg <= rtol * bn and true <= 2 * rtol * bn, (restart, resg / bn, true / bn)
         assert abs(itg - it) <= max(2, it // 10), (restart, itg, it)
 
 
