@@ -10,6 +10,7 @@
 // block order) between bounded grid barriers.  The two-loop recursion uses
 // the same structure with q (or z) held in registers.
 #include <algorithm>
+#include <climits>
 #include <cmath>
 
 #include "fe_internal.h"
@@ -574,12 +575,12 @@ __device__ __forceinline__ double warp_reduce_scatter(double (&v)[P], int lane) 
 
 // warp 0 of every block.  Lane l holds the block total of value l % P.  The
 // last block to arrive adds the partials of all blocks in block order, and
-// when `solve` is set (lane m < nc: row m of T_B, entries l < m, in trow)
+// when `solve` is set (trow[m][l], l < m < nc: the block's rows of T_B)
 // turns the totals s into h = T_B s; lanes m < P of every block end with the
 // value m in out_sh[m].  false: the wait timed out (error word set).
 template <int P>
 __device__ __forceinline__ bool bm_reduce_w0(const BlockSync& bs, double* part, unsigned seq, double t,
-                                             const double (&trow)[P], bool solve, int nc, double* out_sh) {
+                                             const double (*trow)[P], bool solve, int nc, double* out_sh) {
   const int lane = threadIdx.x & 31;
   if (gridDim.x > 1) {
     if (lane < P) part[(int64_t)blockIdx.x * P + lane] = t;
@@ -616,7 +617,7 @@ __device__ __forceinline__ bool bm_reduce_w0(const BlockSync& bs, double* part, 
 #pragma unroll
     for (int l = 0; l < P - 1; l++) {
       const double sl = __shfl_sync(0xffffffffu, t, l);
-      if (lane > l && lane < nc) h += trow[l] * sl;
+      if (lane > l && lane < nc) h += trow[lane][l] * sl;
     }
     t = h;
   }
@@ -638,13 +639,26 @@ __device__ __forceinline__ void prefetch_l2(const double* p, int64_t count) {
   if (bytes) asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
 }
 
+// A thread owns NPT / 2 pairs of consecutive values of its block's slice:
+// values s = 2q, 2q + 1 sit at slice offset bm_off(q) and bm_off(q) + 1, so
+// each pair is one 16-byte load (slices start at even offsets of 256-byte
+// aligned rows).
+__device__ __forceinline__ int64_t bm_off(int q) { return 2 * (threadIdx.x + (int64_t)q * blockDim.x); }
+
 // this thread's NPT values of a vector slice (0 past its end)
 template <int NPT>
 __device__ __forceinline__ void load_slice(double (&r)[NPT], const double* __restrict__ v, int64_t len) {
 #pragma unroll
-  for (int s = 0; s < NPT; s++) {
-    const int64_t k = threadIdx.x + (int64_t)s * blockDim.x;
-    r[s] = k < len ? __ldcg(v + k) : 0.0;
+  for (int q = 0; q < NPT / 2; q++) {
+    const int64_t k = bm_off(q);
+    if (k + 1 < len) {
+      const double2 p = __ldcg(reinterpret_cast<const double2*>(v + k));
+      r[2 * q] = p.x;
+      r[2 * q + 1] = p.y;
+    } else {
+      r[2 * q] = k < len ? __ldcg(v + k) : 0.0;
+      r[2 * q + 1] = 0.0;
+    }
   }
 }
 
@@ -657,7 +671,8 @@ __global__ void __launch_bounds__(NPT <= 12 ? 512 : 256)
   static_assert(P == 2 || P == 4 || P == 8, "block of 2, 4 or 8 basis vectors");
   extern __shared__ __align__(16) double ws[];
   __shared__ double wpart[P][32];
-  __shared__ double s_h[P];
+  __shared__ double s_h[P];       // the last reduction's results (h of the block, or the final norm/Gram row)
+  __shared__ double s_trow[P][P];
   __shared__ int s_fail;
   if (*(volatile double*)(out + 7) != 0.0) return;
   unsigned seq = *(volatile unsigned*)bs.seq;  // no reduction completes before every block has read it
@@ -669,16 +684,10 @@ __global__ void __launch_bounds__(NPT <= 12 ? 512 : 256)
   const int nlast = j + 1 - (nb - 1) * P;  // vectors in the last block
   const int ng = (j + 1) % P ? nlast : 0;  // Gram entries of v_{j+1} (its block is the last one)
   if (threadIdx.x == 0) s_fail = 0;
+  if (threadIdx.x < P) s_h[threadIdx.x] = 0.0;
   if (threadIdx.x < P && (int)threadIdx.x <= j) prefetch_l2(V + (int64_t)threadIdx.x * ldv + base, len);
   double wr[NPT];
-#pragma unroll
-  for (int s = 0; s < NPT; s++) {
-    const int64_t k = threadIdx.x + (int64_t)s * blockDim.x;
-    wr[s] = k < len ? w[base + k] : 0.0;
-  }
-  double hp[P];
-#pragma unroll
-  for (int m = 0; m < P; m++) hp[m] = 0.0;
+  load_slice<NPT>(wr, w + base, len);
   double cur[NPT], nxt[NPT];
 #pragma unroll
   for (int s = 0; s < NPT; s++) nxt[s] = 0.0;
@@ -697,7 +706,7 @@ __global__ void __launch_bounds__(NPT <= 12 ? 512 : 256)
     for (int m = 0; m < P; m++) {
       if (m < np) {
         if (m + 1 < nq) load_slice<NPT>(nxt, m + 1 < np ? Vp + (int64_t)(m + 1) * ldv : Vc, len);
-        const double h = hp[m];
+        const double h = s_h[m];
 #pragma unroll
         for (int s = 0; s < NPT; s++) wr[s] -= h * cur[s];
 #pragma unroll
@@ -734,15 +743,12 @@ __global__ void __launch_bounds__(NPT <= 12 ? 512 : 256)
     if (kb + 1 < nb && threadIdx.x < P && (kb + 1) * P + (int)threadIdx.x <= j)
       prefetch_l2(V + (int64_t)((kb + 1) * P + threadIdx.x) * ldv + base, len);
     // T rows of the current block (lane m: row kb P + m, entries l < m)
-    double trow[P];
-#pragma unroll
-    for (int l = 0; l < P; l++) trow[l] = 0.0;
     const bool solve = kb < nb;
     if (wid == 0 && solve && lane < nc) {
       const double* tr = T + (int64_t)(kb * P + lane) * P;
 #pragma unroll
       for (int l = 0; l < P - 1; l++)
-        if (l < lane) trow[l] = tr[l];
+        if (l < lane) s_trow[lane][l] = tr[l];
     }
     const double r = warp_reduce_scatter<P>(loc, lane);
     if ((lane & (32 / P - 1)) == 0) wpart[lane / (32 / P)][wid] = r;
@@ -752,26 +758,27 @@ __global__ void __launch_bounds__(NPT <= 12 ? 512 : 256)
       for (int q = lane / P; q < nw; q += 32 / P) t += wpart[lane % P][q];
 #pragma unroll
       for (int x = P; x < 32; x <<= 1) t += __shfl_xor_sync(0xffffffffu, t, x);
-      if (!bm_reduce_w0<P>(bs, part, seq, t, trow, solve, nc, s_h) && lane == 0) s_fail = 1;
+      __syncwarp();
+      if (!bm_reduce_w0<P>(bs, part, seq, t, s_trow, solve, nc, s_h) && lane == 0) s_fail = 1;
     }
     if (gridDim.x > 1) seq++;
     __syncthreads();
     if (s_fail) return;
-#pragma unroll
-    for (int m = 0; m < P; m++) hp[m] = s_h[m];
     if (solve && blockIdx.x == 0 && threadIdx.x < nc) Hcol[kb * P + threadIdx.x] = s_h[threadIdx.x];
   }
-  // hp[0] = ||w||^2, hp[1..ng] = <w, v_l> for the last block's vectors
-  const double hn = sqrt(hp[0]);
+  // s_h[0] = ||w||^2, s_h[1..ng] = <w, v_l> for the last block's vectors
+  const double hn = sqrt(s_h[0]);
   if (hn > 0.0) {
     const double inv = 1.0 / hn;
     double* vnx = V + (int64_t)(j + 1) * ldv + base;
 #pragma unroll
-    for (int s = 0; s < NPT; s++) {
-      const int64_t k = threadIdx.x + (int64_t)s * blockDim.x;
-      const double v = wr[s] * inv;
-      ws[k] = v;
-      if (k < len) vnx[k] = v;
+    for (int q = 0; q < NPT / 2; q++) {
+      const int64_t k = bm_off(q);
+      const double v0 = wr[2 * q] * inv, v1 = wr[2 * q + 1] * inv;
+      ws[k] = v0;
+      ws[k + 1] = v1;
+      if (k + 1 < len) *reinterpret_cast<double2*>(vnx + k) = make_double2(v0, v1);
+      else if (k < len) vnx[k] = v0;
     }
     if (z) {
       __syncthreads();
@@ -919,6 +926,114 @@ __global__ void __launch_bounds__(256) k_spmv(int nn, const int* __restrict__ ro
   }
 }
 
+// y = K x for the displacement form, streamed: a warp takes groups of 16
+// consecutive block rows, whose blocks are contiguous in memory, and walks
+// each group in chunks of 32 blocks (one block per lane) regardless of where
+// rows start.  The grid is one wave of resident blocks; warps stride over
+// the groups, so no half-empty second wave idles the SMs.
+// Row sums are formed by a segmented inclusive scan across the lanes (segment
+// heads = row starts inside the chunk, found from the warp's 32 row
+// pointers); the last lane of each segment writes its row, and a row that
+// runs past the chunk carries its partial sum into the next chunk.  The next
+// chunk's column indices and values are loaded before the current chunk's x
+// gather, so each warp keeps HBM requests in flight across its rows instead
+// of one dependent row-pointer -> values -> x chain per row, and no lane idles
+// on rows shorter than 32 blocks.  Summation order is fixed by the chunking,
+// so results are deterministic.
+constexpr int SPMV_RPW = 16;  // block rows per group (<= 32)
+
+template <class VT, class AT>
+__device__ __forceinline__ void spmv_load_chunk(const int* __restrict__ col, const VT* __restrict__ val, int64_t k,
+                                                int64_t kend, int& c, AT (&v)[9]) {
+  if (k < kend) {
+    c = __ldg(col + k);
+    const VT* b = val + kv_index(k, 0);
+#pragma unroll
+    for (int t = 0; t < 9; t++) {
+      if constexpr (sizeof(VT) == 8) v[t] = __ldg(b + 32 * t);
+      else v[t] = (AT)ld_val<VT>(b + 32 * t);
+    }
+  } else {
+    c = -1;
+#pragma unroll
+    for (int t = 0; t < 9; t++) v[t] = AT(0);
+  }
+}
+
+template <class VT, class XT, class AT>
+__global__ void __launch_bounds__(256) k_spmv_stream(int nn, const int* __restrict__ row_ptr,
+                                                     const int* __restrict__ col, const VT* __restrict__ val,
+                                                     const XT* __restrict__ x, double* __restrict__ y) {
+  const int lane = threadIdx.x & 31;
+  const int ngroups = (nn + SPMV_RPW - 1) / SPMV_RPW;
+  const int nwarps = (int)(((int64_t)gridDim.x * blockDim.x) >> 5);
+  for (int g = (int)((((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5)); g < ngroups; g += nwarps) {
+    const int r0 = g * SPMV_RPW;
+    const int nr = min(SPMV_RPW, nn - r0);
+    const int rpl = lane < nr ? __ldg(row_ptr + r0 + lane) : INT_MAX;  // start of row r0 + lane
+    const int kstart = __shfl_sync(0xffffffffu, rpl, 0);
+    const int kend = __ldg(row_ptr + r0 + nr);
+    int c;
+    AT v[9];
+    spmv_load_chunk<VT, AT>(col, val, (int64_t)kstart + lane, kend, c, v);
+    AT carry0 = AT(0), carry1 = AT(0), carry2 = AT(0);
+    int rowbase = r0 - 1;  // the row in progress before the current chunk
+    for (int kc = kstart; kc < kend; kc += 32) {
+      int cn;
+      AT vn[9];
+      spmv_load_chunk<VT, AT>(col, val, (int64_t)kc + 32 + lane, kend, cn, vn);
+      AT p0 = AT(0), p1 = AT(0), p2 = AT(0);
+      if (c >= 0) {
+        const XT* xc = x + 3 * (int64_t)c;
+        const AT x0 = (AT)xc[0], x1 = (AT)xc[1], x2 = (AT)xc[2];
+        p0 = v[0] * x0 + v[1] * x1 + v[2] * x2;
+        p1 = v[3] * x0 + v[4] * x1 + v[5] * x2;
+        p2 = v[6] * x0 + v[7] * x1 + v[8] * x2;
+      }
+      // row starts inside the chunk, and this lane's segment start (-1: before the chunk)
+      const unsigned bit = (rpl >= kc && rpl - kc < 32) ? (1u << (rpl - kc)) : 0u;
+      const unsigned heads = __reduce_or_sync(0xffffffffu, bit);
+      const unsigned below = heads & (0xffffffffu >> (31 - lane));
+      const int sstart = below ? 31 - __clz(below) : -1;
+#pragma unroll
+      for (int off = 1; off < 32; off <<= 1) {
+        const AT t0 = __shfl_up_sync(0xffffffffu, p0, off);
+        const AT t1 = __shfl_up_sync(0xffffffffu, p1, off);
+        const AT t2 = __shfl_up_sync(0xffffffffu, p2, off);
+        if (lane >= off && lane - off >= sstart) {
+          p0 += t0;
+          p1 += t1;
+          p2 += t2;
+        }
+      }
+      const int nvalid = min(32, kend - kc);
+      const bool cont = nvalid == 32 && kc + 32 < kend && !__any_sync(0xffffffffu, rpl == kc + 32);
+      const bool tail = lane < nvalid && ((lane < 31 && ((heads >> (lane + 1)) & 1u)) || (lane == nvalid - 1 && !cont));
+      if (tail) {
+        const int row = rowbase + __popc(below);
+        const bool add = sstart < 0;
+        y[3 * (int64_t)row] = widen(p0 + (add ? carry0 : AT(0)));
+        y[3 * (int64_t)row + 1] = widen(p1 + (add ? carry1 : AT(0)));
+        y[3 * (int64_t)row + 2] = widen(p2 + (add ? carry2 : AT(0)));
+      }
+      const AT l0 = __shfl_sync(0xffffffffu, p0, 31), l1 = __shfl_sync(0xffffffffu, p1, 31),
+               l2 = __shfl_sync(0xffffffffu, p2, 31);
+      if (cont) {
+        const bool whole = heads == 0u;  // lane 31's segment started before this chunk
+        carry0 = l0 + (whole ? carry0 : AT(0));
+        carry1 = l1 + (whole ? carry1 : AT(0));
+        carry2 = l2 + (whole ? carry2 : AT(0));
+      } else {
+        carry0 = carry1 = carry2 = AT(0);
+      }
+      rowbase += __popc(heads);
+      c = cn;
+#pragma unroll
+      for (int t = 0; t < 9; t++) v[t] = vn[t];
+    }
+  }
+}
+
 // pressure rows: y_p[v] = sum over (u node a, v) of B[a,v] . x_u[a]  (B2 = B1^T)
 template <class VT, class XT, class AT>
 __global__ void __launch_bounds__(256) k_spmv_p(int np, const int* __restrict__ pu_ptr, const int* __restrict__ pu_col,
@@ -1018,38 +1133,67 @@ static int pc_to_zx(fe_mesh m, const double* x) {
   return pc_apply_t<float>(m, x, (float*)m->zx);
 }
 
-// y = K zx (zx already in the SpMV input type); the u-p coupling is kept in
-// the tangent's precision (FP64, or FP32 for the mixed form)
+// one wave of the streamed SpMV: resident 256-thread blocks on every SM, but
+// no more warps than row groups
+template <class VT, class XT, class AT>
+static unsigned stream_grid_t(fe_mesh m) {
+  static int per_sm = 0;
+  if (!per_sm && cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_spmv_stream<VT, XT, AT>, 256, 0) != cudaSuccess)
+    per_sm = 4;
+  const int64_t groups = ((int64_t)m->nn + SPMV_RPW - 1) / SPMV_RPW;
+  const int64_t need = (groups + 7) / 8;
+  return (unsigned)std::max<int64_t>(1, std::min<int64_t>(need, (int64_t)std::max(per_sm, 1) * m->sm_count));
+}
+static unsigned spmv_stream_grid(fe_mesh m) {
+  if (m->prec == FE_PREC_FP64) return stream_grid_t<double, double, double>(m);
+  if (m->prec == FE_PREC_MIXED_BF16) return stream_grid_t<__nv_bfloat16, float, float>(m);
+  return stream_grid_t<float, float, float>(m);
+}
+
+// y = K xin with xin in the SpMV input type (FP64 for an FP64 tangent, FP32
+// otherwise).  The displacement form streams its blocks (k_spmv_stream);
+// the u-p form adds the coupling B1 x_p per row (k_spmv) and the pressure
+// rows (k_spmv_p); the u-p coupling is kept in the tangent's precision.
+static int launch_spmv(fe_mesh m, const void* xin, double* y) {
+  const unsigned grid = (unsigned)(((int64_t)m->nn * 32 + 255) / 256);
+  const unsigned gridp = (unsigned)(((int64_t)m->np * 32 + 255) / 256);
+  const unsigned grids = spmv_stream_grid(m);
+  if (m->prec == FE_PREC_FP64) {
+    const double* x = (const double*)xin;
+    if (!m->pres) {
+      k_spmv_stream<double, double, double><<<grids, 256, 0, m->stream>>>(m->nn, m->row_ptr, m->col, m->K64, x, y);
+    } else {
+      k_spmv<double, double, double><<<grid, 256, 0, m->stream>>>(m->nn, m->row_ptr, m->col, m->K64, x, y, m->up_ptr,
+                                                                  m->up_col, m->B64, x + 3 * (int64_t)m->nn);
+      k_spmv_p<double, double, double><<<gridp, 256, 0, m->stream>>>(m->np, m->pu_ptr, m->pu_col, m->pu_src, m->B64,
+                                                                     x, y + 3 * (int64_t)m->nn);
+    }
+  } else if (m->prec == FE_PREC_MIXED_BF16) {
+    const float* x = (const float*)xin;
+    k_spmv_stream<__nv_bfloat16, float, float><<<grids, 256, 0, m->stream>>>(m->nn, m->row_ptr, m->col, m->K16, x, y);
+  } else {
+    const float* x = (const float*)xin;
+    if (!m->pres) {
+      k_spmv_stream<float, float, float><<<grids, 256, 0, m->stream>>>(m->nn, m->row_ptr, m->col, m->K32, x, y);
+    } else {
+      k_spmv<float, float, float><<<grid, 256, 0, m->stream>>>(m->nn, m->row_ptr, m->col, m->K32, x, y, m->up_ptr,
+                                                               m->up_col, m->B32, x + 3 * (int64_t)m->nn);
+      k_spmv_p<float, float, float><<<gridp, 256, 0, m->stream>>>(m->np, m->pu_ptr, m->pu_col, m->pu_src, m->B32, x,
+                                                                  y + 3 * (int64_t)m->nn);
+    }
+  }
+  FE_CUDA(cudaGetLastError());
+  return FE_OK;
+}
+
+// y = K zx (zx already in the SpMV input type)
 static int spmv_zx(fe_mesh m, double* y) {
   const double sv = m->prec == FE_PREC_FP64 ? 8 : (m->prec == FE_PREC_MIXED_BF16 ? 2 : 4);
   const double sx = m->prec == FE_PREC_FP64 ? 8 : 4;
   FE_SCOPE_F(m, FE_PROF_SPMV, (double)m->nnzb * (9 * sv + 4) + 4.0 * (m->nn + 1) + sx * (double)m->ndof + 8.0 * (double)m->ndof +
                                   (m->pres ? (double)m->nnz_up * 2 * (3 * sv + 8) + 4.0 * (m->nn + m->np + 2) : 0.0),
              18.0 * (double)m->nnzb + (m->pres ? 12.0 * (double)m->nnz_up : 0.0));
-  unsigned grid = (unsigned)(((int64_t)m->nn * 32 + 255) / 256);
-  unsigned gridp = (unsigned)(((int64_t)m->np * 32 + 255) / 256);
-  const int* upp = m->pres ? m->up_ptr : nullptr;
-  if (m->prec == FE_PREC_FP64) {
-    const double* x = (const double*)m->zx;
-    k_spmv<double, double, double><<<grid, 256, 0, m->stream>>>(m->nn, m->row_ptr, m->col, m->K64, x, y, upp,
-                                                                m->up_col, m->B64, x + 3 * (int64_t)m->nn);
-    if (m->pres)
-      k_spmv_p<double, double, double><<<gridp, 256, 0, m->stream>>>(m->np, m->pu_ptr, m->pu_col, m->pu_src, m->B64,
-                                                                     x, y + 3 * (int64_t)m->nn);
-  } else if (m->prec == FE_PREC_MIXED_BF16) {
-    const float* x = (const float*)m->zx;
-    k_spmv<__nv_bfloat16, float, float><<<grid, 256, 0, m->stream>>>(m->nn, m->row_ptr, m->col, m->K16, x, y,
-                                                                      nullptr, nullptr, nullptr, nullptr);
-  } else {
-    const float* x = (const float*)m->zx;
-    k_spmv<float, float, float><<<grid, 256, 0, m->stream>>>(m->nn, m->row_ptr, m->col, m->K32, x, y, upp,
-                                                             m->up_col, m->B32, x + 3 * (int64_t)m->nn);
-    if (m->pres)
-      k_spmv_p<float, float, float><<<gridp, 256, 0, m->stream>>>(m->np, m->pu_ptr, m->pu_col, m->pu_src, m->B32, x,
-                                                                  y + 3 * (int64_t)m->nn);
-  }
-  FE_CUDA(cudaGetLastError());
-  return FE_OK;
+  return launch_spmv(m, m->zx, y);
 }
 
 __global__ void k_narrow(int64_t n, const double* __restrict__ x, float* __restrict__ y) {
@@ -1081,32 +1225,7 @@ int fe_spmv_dev(fe_mesh m, const double* x, double* y) {
 // y = K xin where xin already holds the input in the SpMV's input precision
 // (FP64 for an FP64 tangent, FP32 otherwise).  Used by the allocation-free
 // entry point, which stages the input in its own fixed device array.
-int fe_spmv_from_input(fe_mesh m, const void* xin, double* y) {
-  unsigned grid = (unsigned)(((int64_t)m->nn * 32 + 255) / 256);
-  unsigned gridp = (unsigned)(((int64_t)m->np * 32 + 255) / 256);
-  const int* upp = m->pres ? m->up_ptr : nullptr;
-  if (m->prec == FE_PREC_FP64) {
-    const double* x = (const double*)xin;
-    k_spmv<double, double, double><<<grid, 256, 0, m->stream>>>(m->nn, m->row_ptr, m->col, m->K64, x, y, upp,
-                                                                m->up_col, m->B64, x + 3 * (int64_t)m->nn);
-    if (m->pres)
-      k_spmv_p<double, double, double><<<gridp, 256, 0, m->stream>>>(m->np, m->pu_ptr, m->pu_col, m->pu_src, m->B64,
-                                                                     x, y + 3 * (int64_t)m->nn);
-  } else if (m->prec == FE_PREC_MIXED_BF16) {
-    const float* x = (const float*)xin;
-    k_spmv<__nv_bfloat16, float, float><<<grid, 256, 0, m->stream>>>(m->nn, m->row_ptr, m->col, m->K16, x, y,
-                                                                      nullptr, nullptr, nullptr, nullptr);
-  } else {
-    const float* x = (const float*)xin;
-    k_spmv<float, float, float><<<grid, 256, 0, m->stream>>>(m->nn, m->row_ptr, m->col, m->K32, x, y, upp,
-                                                             m->up_col, m->B32, x + 3 * (int64_t)m->nn);
-    if (m->pres)
-      k_spmv_p<float, float, float><<<gridp, 256, 0, m->stream>>>(m->np, m->pu_ptr, m->pu_col, m->pu_src, m->B32, x,
-                                                                  y + 3 * (int64_t)m->nn);
-  }
-  FE_CUDA(cudaGetLastError());
-  return FE_OK;
-}
+int fe_spmv_from_input(fe_mesh m, const void* xin, double* y) { return launch_spmv(m, xin, y); }
 
 // ---------------------------------------------------------------- vectors
 __global__ void k_dot(int64_t n, const double* __restrict__ a, const double* __restrict__ b, double* red,
