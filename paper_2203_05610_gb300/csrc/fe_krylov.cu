@@ -720,10 +720,10 @@ __global__ void __launch_bounds__(NPT <= 12 ? 512 : 256)
     for (int m = 0; m < P; m++) {
       if (m < nc) {
         if (m + 1 < nc) load_slice<NPT>(nxt, Vc + (int64_t)(m + 1) * ldv, len);
-        double a[4] = {0.0, 0.0, 0.0, 0.0};  // four chains: the FP64 pipe is shared by few warps
+        double a[2] = {0.0, 0.0};  // two chains: each extra one costs an FP64 add per vector
 #pragma unroll
-        for (int s = 0; s < NPT; s++) a[s & 3] += wr[s] * cur[s];
-        loc[m] = (a[0] + a[1]) + (a[2] + a[3]);
+        for (int s = 0; s < NPT; s++) a[s & 1] += wr[s] * cur[s];
+        loc[m] = a[0] + a[1];
 #pragma unroll
         for (int s = 0; s < NPT; s++) cur[s] = nxt[s];
       }
@@ -930,16 +930,17 @@ __global__ void __launch_bounds__(256) k_spmv(int nn, const int* __restrict__ ro
 // consecutive block rows, whose blocks are contiguous in memory, and walks
 // each group in chunks of 32 blocks (one block per lane) regardless of where
 // rows start.  The grid is one wave of resident blocks; warps stride over
-// the groups, so no half-empty second wave idles the SMs.
-// Row sums are formed by a segmented inclusive scan across the lanes (segment
-// heads = row starts inside the chunk, found from the warp's 32 row
-// pointers); the last lane of each segment writes its row, and a row that
-// runs past the chunk carries its partial sum into the next chunk.  The next
-// chunk's column indices and values are loaded before the current chunk's x
-// gather, so each warp keeps HBM requests in flight across its rows instead
-// of one dependent row-pointer -> values -> x chain per row, and no lane idles
-// on rows shorter than 32 blocks.  Summation order is fixed by the chunking,
-// so results are deterministic.
+// the groups, so no half-empty second wave idles the SMs.  Row sums are
+// formed by a segmented inclusive scan across the lanes (segment heads = row
+// starts inside the chunk, found from the group's row pointers); the last
+// lane of each segment writes its row, and a row that runs past the chunk
+// carries its partial sum into the next chunk.  Loads run two chunks ahead:
+// while chunk i is multiplied and reduced, the x gather of chunk i + 1 and
+// the column indices and values of chunk i + 2 are in flight, so each warp
+// keeps HBM and L2 requests outstanding across its rows instead of one
+// dependent row-pointer -> values -> x chain per row, and no lane idles on
+// rows shorter than 32 blocks.  Summation order is fixed by the chunking, so
+// results are deterministic.
 constexpr int SPMV_RPW = 16;  // block rows per group (<= 32)
 
 template <class VT, class AT>
@@ -960,6 +961,18 @@ __device__ __forceinline__ void spmv_load_chunk(const int* __restrict__ col, con
   }
 }
 
+template <class XT, class AT>
+__device__ __forceinline__ void spmv_load_x(const XT* __restrict__ x, int c, AT& x0, AT& x1, AT& x2) {
+  if (c >= 0) {
+    const XT* xc = x + 3 * (int64_t)c;
+    x0 = (AT)xc[0];
+    x1 = (AT)xc[1];
+    x2 = (AT)xc[2];
+  } else {
+    x0 = x1 = x2 = AT(0);
+  }
+}
+
 template <class VT, class XT, class AT>
 __global__ void __launch_bounds__(256) k_spmv_stream(int nn, const int* __restrict__ row_ptr,
                                                      const int* __restrict__ col, const VT* __restrict__ val,
@@ -973,22 +986,28 @@ __global__ void __launch_bounds__(256) k_spmv_stream(int nn, const int* __restri
     const int rpl = lane < nr ? __ldg(row_ptr + r0 + lane) : INT_MAX;  // start of row r0 + lane
     const int kstart = __shfl_sync(0xffffffffu, rpl, 0);
     const int kend = __ldg(row_ptr + r0 + nr);
-    int c;
-    AT v[9];
-    spmv_load_chunk<VT, AT>(col, val, (int64_t)kstart + lane, kend, c, v);
+    // three chunks in flight: the current one (values and x in registers), the
+    // next one (values in registers, x gather issued) and the one after (column
+    // indices and values issued)
+    int c0, c1;
+    AT v0[9], v1[9];
+    spmv_load_chunk<VT, AT>(col, val, (int64_t)kstart + lane, kend, c0, v0);
+    spmv_load_chunk<VT, AT>(col, val, (int64_t)kstart + 32 + lane, kend, c1, v1);
+    AT xa0, xa1, xa2;
+    spmv_load_x<XT, AT>(x, c0, xa0, xa1, xa2);
     AT carry0 = AT(0), carry1 = AT(0), carry2 = AT(0);
     int rowbase = r0 - 1;  // the row in progress before the current chunk
     for (int kc = kstart; kc < kend; kc += 32) {
-      int cn;
-      AT vn[9];
-      spmv_load_chunk<VT, AT>(col, val, (int64_t)kc + 32 + lane, kend, cn, vn);
+      int c2;
+      AT v2[9];
+      spmv_load_chunk<VT, AT>(col, val, (int64_t)kc + 64 + lane, kend, c2, v2);
+      AT xb0, xb1, xb2;
+      spmv_load_x<XT, AT>(x, c1, xb0, xb1, xb2);
       AT p0 = AT(0), p1 = AT(0), p2 = AT(0);
-      if (c >= 0) {
-        const XT* xc = x + 3 * (int64_t)c;
-        const AT x0 = (AT)xc[0], x1 = (AT)xc[1], x2 = (AT)xc[2];
-        p0 = v[0] * x0 + v[1] * x1 + v[2] * x2;
-        p1 = v[3] * x0 + v[4] * x1 + v[5] * x2;
-        p2 = v[6] * x0 + v[7] * x1 + v[8] * x2;
+      if (c0 >= 0) {
+        p0 = v0[0] * xa0 + v0[1] * xa1 + v0[2] * xa2;
+        p1 = v0[3] * xa0 + v0[4] * xa1 + v0[5] * xa2;
+        p2 = v0[6] * xa0 + v0[7] * xa1 + v0[8] * xa2;
       }
       // row starts inside the chunk, and this lane's segment start (-1: before the chunk)
       const unsigned bit = (rpl >= kc && rpl - kc < 32) ? (1u << (rpl - kc)) : 0u;
@@ -1027,9 +1046,16 @@ __global__ void __launch_bounds__(256) k_spmv_stream(int nn, const int* __restri
         carry0 = carry1 = carry2 = AT(0);
       }
       rowbase += __popc(heads);
-      c = cn;
+      c0 = c1;
+      c1 = c2;
 #pragma unroll
-      for (int t = 0; t < 9; t++) v[t] = vn[t];
+      for (int t = 0; t < 9; t++) {
+        v0[t] = v1[t];
+        v1[t] = v2[t];
+      }
+      xa0 = xb0;
+      xa1 = xb1;
+      xa2 = xb2;
     }
   }
 }
