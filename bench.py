@@ -83,6 +83,25 @@ def workload(args):
     return w, f"cook_p2_{nx}x{ny}x{nz}"
 
 
+def world_reduce(x, dist=None, device="cpu", op="max"):
+    """x reduced over the ranks of the job (max or sum); x itself without a
+    process group.  The timed region's duration is the max over ranks and
+    the solves are summed, so `value` is whole-job throughput."""
+    if dist is None:
+        return x
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX if op == "max" else dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+def job_throughput(converged_local, ms_local, dist=None, device="cpu"):
+    """(solves of all ranks, max duration over ranks in ms, solves/s)."""
+    ms = world_reduce(ms_local, dist, device, "max")
+    solves = world_reduce(converged_local, dist, device, "sum")
+    return solves, ms, solves / (ms / 1e3)
+
+
 def dist_env():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -436,17 +455,12 @@ def main():
     torch.cuda.synchronize()
     prof = m.profile_read()
     clocks = sampler.stop()
-    ms = ev0.elapsed_time(ev1)
-    if dist:
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-        dist.barrier()
     # only converged solves count (a solve that stops at max_it or diverges is
     # reported per method with its status)
     converged = sum(1 for meth in methods for st in stats[meth] if st["status"] == 0)
-    solves = converged * world
-    value = solves / (ms / 1e3)
+    solves, ms, value = job_throughput(converged, ev0.elapsed_time(ev1), dist, dev)
+    if dist:
+        dist.barrier()
 
     # end to end through the C ABI with host buffers: pinned initial guess in,
     # solution out, every step
@@ -460,11 +474,7 @@ def main():
             m.solve(meth, d, tol=TOL, opts=opts)
             h_out.copy_(d, non_blocking=True)
             torch.cuda.synchronize()
-    e2e_s = time.perf_counter() - t0
-    if dist:
-        t = torch.tensor([e2e_s], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
+    e2e_s = world_reduce(time.perf_counter() - t0, dist, dev, "max")
 
     if rank == 0:
         pk, src = peaks()
