@@ -1323,13 +1323,28 @@ __global__ void k_scale(int64_t n, const double* __restrict__ s, double* __restr
 }
 
 // back substitution y = H^{-1} g on the k x k upper triangle (one block)
-__global__ void k_trisolve(int k, int ldh, const double* __restrict__ H, double* __restrict__ g,
-                           double* __restrict__ y) {
+// back substitution R y = g (R upper triangular, column j at H + j ldh), one
+// block of 1024 threads, thread r owns row r (k <= 1000): g and the diagonal
+// sit in shared memory and each thread loads its entry of the next column
+// while the current one is applied, so a column costs one block barrier
+// instead of a global-memory round trip
+__global__ void __launch_bounds__(1024) k_trisolve(int k, int ldh, const double* __restrict__ H,
+                                                   const double* __restrict__ g, double* __restrict__ y) {
+  __shared__ double gs[1024], dg[1024];
+  const int r = threadIdx.x;
+  if (r < k) {
+    gs[r] = g[r];
+    dg[r] = H[(int64_t)r * ldh + r];
+  }
+  double h = (r < k - 1) ? H[(int64_t)(k - 1) * ldh + r] : 0.0;
+  __syncthreads();
   for (int i = k - 1; i >= 0; i--) {
+    const double yi = gs[i] / dg[i];
+    const double hn = (i >= 1 && r < i - 1) ? H[(int64_t)(i - 1) * ldh + r] : 0.0;
+    if (r < i) gs[r] -= h * yi;
+    if (r == 0) y[i] = yi;
+    h = hn;
     __syncthreads();
-    double yi = g[i] / H[(int64_t)i * ldh + i];
-    if (threadIdx.x == 0) y[i] = yi;
-    for (int r = threadIdx.x; r < i; r += blockDim.x) g[r] -= H[(int64_t)i * ldh + r] * yi;
   }
 }
 
@@ -1342,6 +1357,7 @@ __global__ void k_gemv(int64_t n, int k, const double* __restrict__ V, int64_t l
   int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= n) return;
   double s = 0.0;
+#pragma unroll 8
   for (int i = 0; i < k; i++) s += ys[i] * V[(int64_t)i * ldv + idx];
   u[idx] = s;
 }
@@ -1682,7 +1698,7 @@ int fe_gmres_dev(fe_mesh m, const double* b, double* x, double rtol, double atol
     done = resid <= target || it >= max_it || m->h_scal[4] == 0.0 || !std::isfinite(resid);
     {
       FE_SCOPE(m, FE_PROF_VECTOR, 8.0 * j * (j + 1));
-      k_trisolve<<<1, 256, 0, m->stream>>>(j, kmax + 1, m->H, g, y);
+      k_trisolve<<<1, 1024, 0, m->stream>>>(j, kmax + 1, m->H, g, y);
     }
     {
       FE_SCOPE(m, FE_PROF_VECTOR, 8.0 * n * (j + 1));
