@@ -57,7 +57,8 @@ def parse():
                    help="cook: Cook P2 (--mesh hexes); cook1: Cook P1 8x8x2; twist: Taylor-Hood cube 32^3; "
                         "heart: prolate shell, 149,760 P1 tets")
     p.add_argument("--no-cpu-baseline", action="store_true")
-    p.add_argument("--cpu-sample-iters", type=int, default=20)
+    p.add_argument("--cpu-sample-iters", type=int, default=0,
+                   help="GMRES iterations of the oracle's timed sample (0 = one full restart cycle)")
     p.add_argument("--serve", type=int, default=0,
                    help="serving mix: number of requests of the seeded Poisson stream (0 = off)")
     p.add_argument("--serve-max-dofs", type=float, default=5e4)
@@ -66,7 +67,10 @@ def parse():
                    help="offered load: arrival rate as a multiple of the measured one-at-a-time capacity "
                         "(above 1 the queue fills and the served rate is the server's capacity)")
     p.add_argument("--serve-precision", default="mixed_fp32", choices=["fp64", "mixed_fp32"])
-    return p.parse_args()
+    a = p.parse_args()
+    if a.cpu_sample_iters <= 0:
+        a.cpu_sample_iters = a.restart
+    return a
 
 
 def workload(args):
