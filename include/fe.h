@@ -239,6 +239,14 @@ typedef struct {
                           coefficients from its cached Gram entries (ceil((j+1)/8)+1
                           grid reductions per step, same FP64 work; vectors too long
                           for one co-resident grid take the sequential sweep) */
+  int32_t jac_lag;     /* NK/iNK: assemble the tangent (and its block-Jacobi) only at
+                          iterations 1, 1+L, 1+2L, ... and solve with the last one in
+                          between (Jacobian lagging, named as an extension in the
+                          paper's conclusions); 1 (default, 0 means 1) = every iteration */
+  int32_t hess_reassemble; /* B/iB: every R iterations re-assemble the tangent at the
+                          current d (new H0) and restart the L-BFGS memory (the
+                          conclusions' occasional Jacobian re-assembly for BFGS);
+                          0 (default) = only at d_0 */
 } nl_opts;
 
 #define NL_HIST 1024

@@ -1061,6 +1061,7 @@ int om_solve(om_mesh* m, int method, double tol, int max_it, double* d, const do
   double ksp_rtol = opts[1], ksp_atol = opts[2], ew0 = opts[3], ewmax = opts[4];
   int restart = (int)opts[5], kmaxit = (int)opts[6], mm = (int)opts[7];
   double dtol = opts[8];
+  int jac_lag = (int)opts[10] > 0 ? (int)opts[10] : 1, hess_re = (int)opts[11];
   double* res_hist = stats + 6;
   double* lit_hist = stats + 6 + OM_HIST;
   double* eta_hist = stats + 6 + 2 * OM_HIST;
@@ -1086,8 +1087,13 @@ int om_solve(om_mesh* m, int method, double tol, int max_it, double* d, const do
     double eta = method == 0 ? ksp_rtol : ew0, eta_prev = eta;
     const double alpha2 = 0.5 * (1.0 + sqrt(5.0));
     for (int k = 1; k <= max_it; k++) {
-      om_tangent(m, d);
-      assemblies++;
+      /* Jacobian lagging (conclusions: an extension for the Newton methods):
+       * the tangent is assembled at iterations 1, 1 + L, 1 + 2L, ... and the
+       * linear solves in between use the last one */
+      if ((k - 1) % jac_lag == 0) {
+        om_tangent(m, d);
+        assemblies++;
+      }
       /* K delta = -R */
       for (long i = 0; i < n; i++) t[i] = -R[i];
       memset(dl, 0, sizeof(double) * n);
@@ -1131,6 +1137,13 @@ int om_solve(om_mesh* m, int method, double tol, int max_it, double* d, const do
     double* rho = (double*)xcalloc(mm, sizeof(double));
     int np = 0;
     for (int k = 1; k <= max_it; k++) {
+      /* occasional re-assembly for BFGS (conclusions): a new H0 from the
+       * tangent at the current iterate, and the memory starts again */
+      if (hess_re > 0 && k > 1 && (k - 1) % hess_re == 0) {
+        om_tangent(m, d);
+        assemblies++;
+        np = 0;
+      }
       long long lit0 = m->lit;
       twoloop(m, S, Y, rho, np, R, t, method == 2 ? 0 : 2, ksp_rtol, ksp_atol, restart, kmaxit);
       if (k < OM_HIST) {

@@ -30,6 +30,8 @@ extern "C" int nl_opts_default(nl_method method, nl_opts* o) {
   o->dtol = 1e4;
   o->apply_dirichlet = 1;
   o->orthog = 0;
+  o->jac_lag = 1;
+  o->hess_reassemble = 0;
   return FE_OK;
 }
 
@@ -99,8 +101,10 @@ static int solve_impl(fe_mesh m, int method, double tol, int max_it, double* d, 
     double eta = std::max(method == NL_NK ? o.ksp_rtol : o.ew_rtol0, rtol_floor);
     const double alpha2 = 0.5 * (1.0 + sqrt(5.0));
     for (int k = 1; k <= max_it; k++) {
-      FE_TRY(fe_tangent_dev(m, d, o.precision));
-      st.assemblies++;
+      if ((k - 1) % o.jac_lag == 0) {  // Jacobian lagging: reuse the tangent in between
+        FE_TRY(fe_tangent_dev(m, d, o.precision));
+        st.assemblies++;
+      }
       // K delta = -R
       FE_TRY(fe_axpby_dev(m, -1.0, R, 0.0, t, n));
       FE_CUDA(cudaMemsetAsync(dl, 0, n * sizeof(double), m->stream));
@@ -156,6 +160,14 @@ static int solve_impl(fe_mesh m, int method, double tol, int max_it, double* d, 
     st.assemblies = 1;
     int head = 0, np = 0;
     for (int k = 1; k <= max_it; k++) {
+      if (o.hess_reassemble > 0 && k > 1 && (k - 1) % o.hess_reassemble == 0) {
+        // new H0 from the tangent at the current iterate; the stored pairs
+        // belonged to the old one, so the memory restarts
+        FE_TRY(fe_tangent_dev(m, d, o.precision));
+        st.assemblies++;
+        head = 0;
+        np = 0;
+      }
       int lit = 0;
       FE_TRY(fe_lbfgs_dev(m, m->S, m->Yv, m->rho_d, head, mcap, np, n, R, t, method == NL_B ? 0 : 2,
                           std::max(o.ksp_rtol, rtol_floor), o.ksp_atol, o.ksp_restart, o.ksp_max_it, &lit));
@@ -226,7 +238,11 @@ extern "C" int nl_solve(fe_mesh m, int method, double tol, int max_it, double* d
     if (opts->dtol > 0) o.dtol = opts->dtol;
     o.apply_dirichlet = opts->apply_dirichlet;
     o.orthog = opts->orthog;
+    o.jac_lag = opts->jac_lag > 0 ? opts->jac_lag : 1;
+    o.hess_reassemble = opts->hess_reassemble;
   }
+  if (o.jac_lag < 1 || o.hess_reassemble < 0)
+    return fe_set_error("jac_lag must be >= 1 (0 = 1) and hess_reassemble >= 0"), FE_ERR_ARG;
   if (o.orthog < 0 || o.orthog > 2) return fe_set_error("orthog must be 0, 1 or 2"), FE_ERR_ARG;
   if (o.precision < 0 || o.precision > 2) return fe_set_error("bad precision"), FE_ERR_ARG;
   FE_CUDA(cudaSetDevice(m->device));

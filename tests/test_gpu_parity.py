@@ -463,3 +463,27 @@ def test_solve_after_nonfinite_solve(fe):
     assert so["status"] == 0 and sg["status"] == 0
     assert sg["lit_total"] > 0
     assert np.linalg.norm(xg.cpu().numpy() - x) <= 1e-8 * np.linalg.norm(x)
+
+
+# ---------------------------------------------------------------- Jacobian lagging, BFGS re-assembly
+@pytest.mark.parametrize("method,extra", [("NK", dict(jac_lag=3)), ("iNK", dict(jac_lag=2)),
+                                          ("iB", dict(hess_reassemble=5))])
+def test_nl_solve_lagging_and_reassembly(fe, method, extra):
+    # the conclusions' extensions: lagged tangents for the Newton methods,
+    # periodic re-assembly (with a memory restart) for BFGS; same iterations,
+    # assemblies and solution as the oracle.  Cook P1 at 0.4 of the traction:
+    # on the P2 case at that load lagged NK steps invert elements (the oracle
+    # too), and B restarted every few steps never builds enough curvature
+    w = small_cases()["cook_p1"]
+    m, om = _pair(fe, w)
+    m.set_load(0.4)
+    om.set_load(0.4)
+    tol, xtol = 1e-11, 1e-10
+    o = dict(ksp_atol=0.0, **extra)
+    x, so = om.solve(method, np.zeros(om.ndof), tol=tol, opts=o)
+    xg, sg = m.solve(method, m.zeros(), tol=tol, opts=o)
+    assert so["status"] == 0 and sg["status"] == 0, (so["status"], sg["status"])
+    assert abs(sg["nit"] - so["nit"]) <= max(1, so["nit"] // 10), (sg["nit"], so["nit"])
+    if sg["nit"] == so["nit"]:
+        assert sg["assemblies"] == so["assemblies"]
+    assert np.linalg.norm(xg.cpu().numpy() - x) <= xtol * np.linalg.norm(x)

@@ -513,6 +513,54 @@ def test_ib_first_step_is_newton_step():
     assert np.linalg.norm(d1 - d2) <= 1e-9 * np.linalg.norm(d1)
 
 
+def test_jacobian_lagging_is_the_chord_iteration():
+    # Jacobian lagging (the conclusions' extension for the Newton methods):
+    # with exact linear solves, lag L is the chord method restarted every L
+    # steps, d_{k+1} = d_k - K(d_{L floor(k/L)})^{-1} R(d_k); written out here
+    # with dense numpy solves on the oracle's residual and tangent
+    w = W.cook(3, 3, 1, order=1, nu=0.3)
+    m = O.Mesh(w)
+    m.set_load(0.5)
+    lag, steps = 3, 7
+    o = dict(ksp_rtol=1e-14, ksp_atol=0.0, ksp_restart=500, jac_lag=lag)
+    d = np.zeros(m.ndof)
+    m.apply_dirichlet(d)
+    ref = [d.copy()]
+    K = None
+    for k in range(steps):
+        if k % lag == 0:
+            m.tangent(d)
+            K = oracle_dense_K(m, w)
+        r, _ = m.residual(d)
+        d = d - np.linalg.solve(K, r)
+        ref.append(d.copy())
+    for nit in (1, 2, 3, 4, steps):
+        dl, st = m.solve("NK", np.zeros(m.ndof), tol=1e-30, max_it=nit, opts=o)
+        assert st["nit"] == nit and st["assemblies"] == len(range(0, nit, lag))
+        assert np.linalg.norm(dl - ref[nit]) <= 1e-9 * np.linalg.norm(ref[nit]), nit
+    # lag 1 is plain Newton
+    d1, s1 = m.solve("NK", np.zeros(m.ndof), tol=1e-10, opts=dict(ksp_atol=0.0, jac_lag=1))
+    d0, s0 = m.solve("NK", np.zeros(m.ndof), tol=1e-10, opts=dict(ksp_atol=0.0))
+    assert s1["nit"] == s0["nit"] and np.array_equal(d1, d0)
+
+
+def test_bfgs_reassembled_every_step_is_newton():
+    # re-assembling the tangent every iteration and restarting the memory
+    # leaves iB with no secant pairs and H0 = K(d_k)^{-1} (quasi-exact GMRES):
+    # every step is the Newton step, so the iterates equal NK's
+    o = dict(ksp_rtol=1e-13, ksp_atol=0.0)
+    _, dn, sn = _cook_solve("NK", opts=o, load=0.6, tol=1e-11)
+    _, db, sb = _cook_solve("iB", opts=dict(o, hess_reassemble=1), load=0.6, tol=1e-11)
+    assert sn["status"] == 0 and sb["status"] == 0
+    assert sb["nit"] == sn["nit"] and sb["assemblies"] == sb["nit"]
+    assert np.allclose(sb["res_hist"], sn["res_hist"], rtol=1e-6, atol=1e-12 * sn["r0"])
+    assert np.linalg.norm(db - dn) <= 1e-9 * np.linalg.norm(dn)
+    # periodic re-assembly still converges to the same solution
+    _, dp, sp = _cook_solve("iB", opts=dict(ksp_atol=0.0, hess_reassemble=4), load=0.6, tol=1e-11)
+    assert sp["status"] == 0 and sp["assemblies"] == 1 + (sp["nit"] - 1) // 4
+    assert np.linalg.norm(dp - dn) <= 1e-8 * np.linalg.norm(dn)
+
+
 def test_small_load_linear_limit():
     w = W.cook(3, 3, 1)
     m = O.Mesh(w)
