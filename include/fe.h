@@ -247,6 +247,12 @@ typedef struct {
                           current d (new H0) and restart the L-BFGS memory (the
                           conclusions' occasional Jacobian re-assembly for BFGS);
                           0 (default) = only at d_0 */
+  int32_t ib_adaptive; /* iB: 1 = adaptive H0 tolerance of Eisenstat-Walker type (the
+                          alternative to the fixed 1e-2 that the paper leaves for future
+                          work), reading: EW choice 2, eta_1 = ksp_rtol,
+                          eta_k = min(ew_rtolmax, max(0.9 (|R_{k-1}|/|R_{k-2}|)^a,
+                          0.9 eta_{k-1}^a if that exceeds 0.1)), a = (1+sqrt 5)/2;
+                          0 (default) = fixed ksp_rtol */
 } nl_opts;
 
 #define NL_HIST 1024

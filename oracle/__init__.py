@@ -136,7 +136,7 @@ def splitmix64(x):
 
 def default_opts(method):
     """Appendix A defaults, with the readings: restart 500, m = 50."""
-    o = np.zeros(12)
+    o = np.zeros(13)
     o[0] = 0
     o[1] = {0: 1e-6, 1: 1e-2, 2: 0.0, 3: 1e-2}[method]
     o[2] = {0: 1e-10, 1: 1e-14, 2: 0.0, 3: 1e-14}[method]
@@ -149,6 +149,7 @@ def default_opts(method):
     o[9] = 1
     o[10] = 1  # jac_lag
     o[11] = 0  # hess_reassemble
+    o[12] = 0  # ib_adaptive
     return o
 
 
@@ -260,7 +261,8 @@ class Mesh:
         o = default_opts(mth)
         if opts:
             keys = ["precision", "ksp_rtol", "ksp_atol", "ew_rtol0", "ew_rtolmax", "ksp_restart",
-                    "ksp_max_it", "lbfgs_m", "dtol", "apply_dirichlet", "jac_lag", "hess_reassemble"]
+                    "ksp_max_it", "lbfgs_m", "dtol", "apply_dirichlet", "jac_lag", "hess_reassemble",
+                    "ib_adaptive"]
             for k, v in opts.items():
                 o[keys.index(k)] = v
         d = np.ascontiguousarray(d, dtype=np.float64)

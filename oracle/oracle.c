@@ -1062,6 +1062,7 @@ int om_solve(om_mesh* m, int method, double tol, int max_it, double* d, const do
   int restart = (int)opts[5], kmaxit = (int)opts[6], mm = (int)opts[7];
   double dtol = opts[8];
   int jac_lag = (int)opts[10] > 0 ? (int)opts[10] : 1, hess_re = (int)opts[11];
+  int ib_adaptive = (int)opts[12];
   double* res_hist = stats + 6;
   double* lit_hist = stats + 6 + OM_HIST;
   double* eta_hist = stats + 6 + 2 * OM_HIST;
@@ -1136,7 +1137,19 @@ int om_solve(om_mesh* m, int method, double tol, int max_it, double* d, const do
     double* Y = (double*)xcalloc((size_t)mm * n, sizeof(double));
     double* rho = (double*)xcalloc(mm, sizeof(double));
     int np = 0;
+    /* adaptive H0 tolerance for iB (the paper leaves an Eisenstat-Walker type
+     * tolerance for future work); reading: EW choice 2 on the nonlinear
+     * residual norms, eta_1 = ksp_rtol,
+     *   eta_k = min(ew_rtolmax, max(0.9 (r_{k-1} / r_{k-2})^a, 0.9 eta_{k-1}^a
+     *           when the latter exceeds 0.1)),  a = (1 + sqrt 5) / 2 */
+    double eta = ksp_rtol, r_km2 = 0.0;
     for (int k = 1; k <= max_it; k++) {
+      if (method == 3 && ib_adaptive && k > 1) {
+        double eta_prev = eta, a = 0.5 * (1.0 + sqrt(5.0));
+        eta = 0.9 * pow(rk / r_km2, a);
+        if (0.9 * pow(eta_prev, a) > 0.1) eta = fmax(eta, 0.9 * pow(eta_prev, a));
+        eta = fmin(eta, ewmax);
+      }
       /* occasional re-assembly for BFGS (conclusions): a new H0 from the
        * tangent at the current iterate, and the memory starts again */
       if (hess_re > 0 && k > 1 && (k - 1) % hess_re == 0) {
@@ -1145,11 +1158,12 @@ int om_solve(om_mesh* m, int method, double tol, int max_it, double* d, const do
         np = 0;
       }
       long long lit0 = m->lit;
-      twoloop(m, S, Y, rho, np, R, t, method == 2 ? 0 : 2, ksp_rtol, ksp_atol, restart, kmaxit);
+      twoloop(m, S, Y, rho, np, R, t, method == 2 ? 0 : 2, eta, ksp_atol, restart, kmaxit);
       if (k < OM_HIST) {
         lit_hist[k] = (double)(m->lit - lit0);
-        eta_hist[k] = method == 2 ? 0.0 : ksp_rtol;
+        eta_hist[k] = method == 2 ? 0.0 : eta;
       }
+      r_km2 = rk;
       for (long i = 0; i < n; i++) {
         dl[i] = -t[i];
         d[i] += dl[i];

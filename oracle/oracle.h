@@ -14,12 +14,13 @@
  *   [9] kappa  [10] Ta_peak  [11] period
  * Dirichlet group array groups[ngroups][8]:
  *   mask, center x, y, z, angle, translation x, y, z
- * Solver option array opts[12]:
+ * Solver option array opts[13]:
  *   precision(ignored: FP64), ksp_rtol, ksp_atol, ew_rtol0, ew_rtolmax,
  *   ksp_restart, ksp_max_it, lbfgs_m, dtol, apply_dirichlet,
  *   jac_lag (NK/iNK: tangent assembled every jac_lag iterations, >= 1),
  *   hess_reassemble (B/iB: tangent re-assembled and memory restarted every
- *   hess_reassemble iterations, 0 = never)
+ *   hess_reassemble iterations, 0 = never),
+ *   ib_adaptive (iB: 1 = Eisenstat-Walker choice-2 tolerance for the H0 solve)
  * Stats array (6 + 3*OM_HIST doubles):
  *   status, nit, lit_total, assemblies, r0, rfinal,
  *   res_hist[OM_HIST], lit_hist[OM_HIST], eta_hist[OM_HIST]

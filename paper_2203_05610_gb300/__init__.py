@@ -63,7 +63,7 @@ class nl_opts(C.Structure):
                 ("ew_rtol0", C.c_double), ("ew_rtolmax", C.c_double), ("ksp_restart", C.c_int32),
                 ("ksp_max_it", C.c_int32), ("lbfgs_m", C.c_int32), ("dtol", C.c_double),
                 ("apply_dirichlet", C.c_int32), ("orthog", C.c_int32), ("jac_lag", C.c_int32),
-                ("hess_reassemble", C.c_int32)]
+                ("hess_reassemble", C.c_int32), ("ib_adaptive", C.c_int32)]
 
 
 class nl_stats(C.Structure):

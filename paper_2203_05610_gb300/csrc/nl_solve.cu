@@ -32,6 +32,7 @@ extern "C" int nl_opts_default(nl_method method, nl_opts* o) {
   o->orthog = 0;
   o->jac_lag = 1;
   o->hess_reassemble = 0;
+  o->ib_adaptive = 0;
   return FE_OK;
 }
 
@@ -159,7 +160,16 @@ static int solve_impl(fe_mesh m, int method, double tol, int max_it, double* d, 
     FE_TRY(fe_tangent_dev(m, d, o.precision));  // the one Hessian assembly at d_0
     st.assemblies = 1;
     int head = 0, np = 0;
+    double eta = o.ksp_rtol, rprev2 = 0.0;  // iB H0 tolerance; ||R_{k-2}||
+    const double alpha2 = 0.5 * (1.0 + sqrt(5.0));
     for (int k = 1; k <= max_it; k++) {
+      if (method == NL_IB && o.ib_adaptive && k > 1) {  // EW choice 2 on the nonlinear residuals
+        const double eta_prev = eta;
+        eta = 0.9 * pow(rk / rprev2, alpha2);
+        const double sg = 0.9 * pow(eta_prev, alpha2);
+        if (sg > 0.1) eta = fmax(eta, sg);
+        eta = fmin(eta, o.ew_rtolmax);
+      }
       if (o.hess_reassemble > 0 && k > 1 && (k - 1) % o.hess_reassemble == 0) {
         // new H0 from the tangent at the current iterate; the stored pairs
         // belonged to the old one, so the memory restarts
@@ -170,12 +180,13 @@ static int solve_impl(fe_mesh m, int method, double tol, int max_it, double* d, 
       }
       int lit = 0;
       FE_TRY(fe_lbfgs_dev(m, m->S, m->Yv, m->rho_d, head, mcap, np, n, R, t, method == NL_B ? 0 : 2,
-                          std::max(o.ksp_rtol, rtol_floor), o.ksp_atol, o.ksp_restart, o.ksp_max_it, &lit));
+                          std::max(eta, rtol_floor), o.ksp_atol, o.ksp_restart, o.ksp_max_it, &lit));
       st.lit_total += lit;
       if (k < NL_HIST) {
         st.lit_hist[k] = lit;
-        st.eta_hist[k] = method == NL_B ? 0.0 : o.ksp_rtol;
+        st.eta_hist[k] = method == NL_B ? 0.0 : eta;
       }
+      rprev2 = rk;
       {
         FE_SCOPE(m, FE_PROF_VECTOR, 32.0 * n);
         k_step<<<g1, 256, 0, m->stream>>>(n, t, dl, d);  // delta = -H R; d += delta
@@ -240,6 +251,7 @@ extern "C" int nl_solve(fe_mesh m, int method, double tol, int max_it, double* d
     o.orthog = opts->orthog;
     o.jac_lag = opts->jac_lag > 0 ? opts->jac_lag : 1;
     o.hess_reassemble = opts->hess_reassemble;
+    o.ib_adaptive = opts->ib_adaptive;
   }
   if (o.jac_lag < 1 || o.hess_reassemble < 0)
     return fe_set_error("jac_lag must be >= 1 (0 = 1) and hess_reassemble >= 0"), FE_ERR_ARG;

@@ -467,11 +467,12 @@ def test_solve_after_nonfinite_solve(fe):
 
 # ---------------------------------------------------------------- Jacobian lagging, BFGS re-assembly
 @pytest.mark.parametrize("method,extra", [("NK", dict(jac_lag=3)), ("iNK", dict(jac_lag=2)),
-                                          ("iB", dict(hess_reassemble=5))])
+                                          ("iB", dict(hess_reassemble=5)), ("iB", dict(ib_adaptive=1))])
 def test_nl_solve_lagging_and_reassembly(fe, method, extra):
     # the conclusions' extensions: lagged tangents for the Newton methods,
-    # periodic re-assembly (with a memory restart) for BFGS; same iterations,
-    # assemblies and solution as the oracle.  Cook P1 at 0.4 of the traction:
+    # periodic re-assembly (with a memory restart) for BFGS, and the adaptive
+    # H0 tolerance for iB; same iterations, assemblies and solution as the
+    # oracle.  Cook P1 at 0.4 of the traction:
     # on the P2 case at that load lagged NK steps invert elements (the oracle
     # too), and B restarted every few steps never builds enough curvature
     w = small_cases()["cook_p1"]

@@ -561,6 +561,25 @@ def test_bfgs_reassembled_every_step_is_newton():
     assert np.linalg.norm(dp - dn) <= 1e-8 * np.linalg.norm(dn)
 
 
+def test_adaptive_ib_tolerance():
+    # adaptive H0 tolerance for iB (the paper's future-work alternative to the
+    # fixed 1e-2; Eisenstat-Walker choice 2 is a reading): eta starts at
+    # ksp_rtol, stays within (0, ew_rtolmax], tightens as the nonlinear
+    # residual drops fast, and the solve reaches the same solution as NK
+    _, dn, sn = _cook_solve("NK", opts=dict(ksp_atol=0.0), load=0.4, tol=1e-11)
+    _, da, sa = _cook_solve("iB", opts=dict(ksp_atol=0.0, ib_adaptive=1), load=0.4, tol=1e-11)
+    _, df, sf = _cook_solve("iB", opts=dict(ksp_atol=0.0), load=0.4, tol=1e-11)
+    assert sn["status"] == sa["status"] == sf["status"] == 0
+    eta = sa["eta_hist"][1:]
+    assert eta[0] == 1e-2 and (eta > 0).all() and (eta <= 0.1 + 1e-15).all()
+    assert (sf["eta_hist"][1:] == 1e-2).all()
+    r = sa["res_hist"]
+    fast = [k for k in range(2, len(eta)) if r[k - 1] / r[k - 2] < 0.1 and 0.9 * eta[k - 2] ** 1.618 <= 0.1]
+    assert all(eta[k - 1] < 0.9 * (r[k - 1] / r[k - 2]) ** 1.6 for k in fast)
+    assert np.linalg.norm(da - dn) <= 1e-8 * np.linalg.norm(dn)
+    assert np.linalg.norm(df - dn) <= 1e-8 * np.linalg.norm(dn)
+
+
 def test_small_load_linear_limit():
     w = W.cook(3, 3, 1)
     m = O.Mesh(w)
