@@ -331,7 +331,23 @@ def test_config2_residual_and_tangent_full_size(fe):
     vg, _, dig = m.tangent_copy()
     assert _rel(vg, v) < 1e-12
     x = np.random.default_rng(12).standard_normal(om.ndof)
-    assert _rel(m.spmv(torch.from_numpy(x).cuda()).cpu().numpy(), om.spmv(x)) < 1e-12
+    y = om.spmv(x)
+    assert _rel(m.spmv(torch.from_numpy(x).cuda()).cpu().numpy(), y) < 1e-12
+    # restarted GMRES(50) at this size, blocked MGS: the Arnoldi relation
+    # makes the residual estimate the true residual of the returned iterate
+    b = np.random.default_rng(13).standard_normal(om.ndof)
+    bn = np.linalg.norm(b)
+    xg, itg, resg = m.gmres(torch.from_numpy(b).cuda(), rtol=1e-14, atol=0.0, restart=50, max_it=100, orthog=2)
+    true = np.linalg.norm(b - om.spmv(xg.cpu().numpy()))
+    assert itg == 100 and resg < bn and abs(true - resg) <= 1e-9 * bn, (resg / bn, true / bn)
+    # the bench's mixed form: FP32 tangent and SpMV against the FP64 oracle
+    m.tangent(dg, "mixed_fp32")
+    vg32, _, _ = m.tangent_copy()
+    assert _rel(vg32, v) < 2e-5
+    assert np.abs(m.spmv(torch.from_numpy(x).cuda()).cpu().numpy() - y).max() <= 1e-5 * np.abs(y).max()
+    xg, itg, resg = m.gmres(torch.from_numpy(b).cuda(), rtol=1e-14, atol=0.0, restart=50, max_it=100, orthog=2)
+    true = np.linalg.norm(b - om.spmv(xg.cpu().numpy()))
+    assert itg == 100 and resg < bn and abs(true - resg) <= 1e-4 * bn, (resg / bn, true / bn)
 
 
 # ---------------------------------------------------------------- low-synchronisation MGS
