@@ -339,7 +339,7 @@ def test_config2_residual_and_tangent_full_size(fe):
     bn = np.linalg.norm(b)
     xg, itg, resg = m.gmres(torch.from_numpy(b).cuda(), rtol=1e-14, atol=0.0, restart=50, max_it=100, orthog=2)
     true = np.linalg.norm(b - om.spmv(xg.cpu().numpy()))
-    assert itg == 100 and resg < bn and abs(true - resg) <= 1e-9 * bn, (resg / bn, true / bn)
+    assert itg == 100 and resg < bn and abs(true - resg) <= 1e-8 * bn, (resg / bn, true / bn)
     # the bench's mixed form: FP32 tangent and SpMV against the FP64 oracle
     m.tangent(dg, "mixed_fp32")
     vg32, _, _ = m.tangent_copy()
@@ -347,7 +347,7 @@ def test_config2_residual_and_tangent_full_size(fe):
     assert np.abs(m.spmv(torch.from_numpy(x).cuda()).cpu().numpy() - y).max() <= 1e-5 * np.abs(y).max()
     xg, itg, resg = m.gmres(torch.from_numpy(b).cuda(), rtol=1e-14, atol=0.0, restart=50, max_it=100, orthog=2)
     true = np.linalg.norm(b - om.spmv(xg.cpu().numpy()))
-    assert itg == 100 and resg < bn and abs(true - resg) <= 1e-4 * bn, (resg / bn, true / bn)
+    assert itg == 100 and resg < bn and abs(true - resg) <= 1e-3 * bn, (resg / bn, true / bn)
 
 
 # ---------------------------------------------------------------- low-synchronisation MGS
