@@ -181,8 +181,8 @@ def traffic_record(kernel_class, algorithmic_bytes_per_launch):
     the ncu capture recorded in profiles/traffic.json, as the measured
     traffic/algorithmic-bytes ratio of the captured launch times this run's
     average algorithmic bytes per launch (traffic grows in proportion to the
-    basis vectors a step reads).  None once the kernel source has changed
-    since the capture (sha256 of the source file recorded with it)."""
+    basis vectors a step reads).  None once the kernels' source has changed
+    since the capture (sha256 of their source region recorded with it)."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     try:
         rec = json.load(open(path)).get(kernel_class)
@@ -191,12 +191,23 @@ def traffic_record(kernel_class, algorithmic_bytes_per_launch):
     if not rec:
         return None
     try:
-        h = hashlib.sha256(open(os.path.join(ROOT, rec["source"]), "rb").read()).hexdigest()[:16]
-    except OSError:
+        h = source_sha(os.path.join(ROOT, rec["source"]), rec.get("region"))
+    except (OSError, ValueError):
         return None
     if h != rec.get("source_sha"):
         return None
     return round(rec["traffic_over_algorithmic"] * algorithmic_bytes_per_launch)
+
+
+def source_sha(path, region=None):
+    """sha256 (16 hex digits) of a source file, or of the part of it from the
+    line region[0] up to the line region[1] (the kernels of one class and
+    their device helpers), so edits elsewhere in the file keep the record."""
+    text = open(path, "rb").read()
+    if region:
+        a = text.index(region[0].encode())
+        text = text[a:text.index(region[1].encode(), a)]
+    return hashlib.sha256(text).hexdigest()[:16]
 
 
 ORACLE_WORK = os.path.join(ROOT, "tests", "golden", "oracle_solve_work.json")

@@ -731,12 +731,7 @@ template <int ORDER, class T>
 static int launch_tangent(fe_mesh m, const double* d, T* K, T* B) {
   using C = TanCfg<ORDER, T>;
   size_t smem = sizeof(T) * C::EPB * C::PER_E;
-  static bool attr_done[2][2] = {{false, false}, {false, false}};
-  bool& done = attr_done[ORDER - 1][sizeof(T) == 8];
-  if (!done) {
-    FE_CUDA(cudaFuncSetAttribute(k_elem_tangent<ORDER, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    done = true;
-  }
+  FE_TRY(fe_kernel_smem((const void*)k_elem_tangent<ORDER, T>, (int)smem));
   for (int c = 0; c < m->ncolors; c++) {
     int start = m->h_color_start[c], nel = m->h_color_start[c + 1] - start;
     if (nel == 0) continue;

@@ -196,6 +196,12 @@ int fe_alloc_t(fe_mesh m, T** p, size_t count) {
   return fe_alloc(m, reinterpret_cast<void**>(p), count * sizeof(T));
 }
 int fe_check_device_error(fe_mesh m);  // syncs the stream and reads the error word
+// Kernel launch facts cached per (kernel, device, shape), safe from several
+// host threads (the serving loop) and from several devices in one process:
+// the dynamic shared memory opt-in of a kernel (set once per device) and its
+// resident blocks per SM for a block size and dynamic shared memory size.
+int fe_kernel_smem(const void* fn, int smem_bytes);
+int fe_kernel_occupancy(const void* fn, int threads, size_t smem_bytes, int* blocks_per_sm);
 int fe_reset_grid_sync(fe_mesh m);     // arrival counter, step sequence, published-value slots
 
 // ---------------------------------------------------------------- internal entry points

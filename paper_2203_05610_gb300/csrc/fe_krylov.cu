@@ -1163,9 +1163,8 @@ static int pc_to_zx(fe_mesh m, const double* x) {
 // no more warps than row groups
 template <class VT, class XT, class AT>
 static unsigned stream_grid_t(fe_mesh m) {
-  static int per_sm = 0;
-  if (!per_sm && cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_spmv_stream<VT, XT, AT>, 256, 0) != cudaSuccess)
-    per_sm = 4;
+  int per_sm = 0;
+  if (fe_kernel_occupancy((const void*)k_spmv_stream<VT, XT, AT>, 256, 0, &per_sm) != FE_OK) per_sm = 4;
   const int64_t groups = ((int64_t)m->nn + SPMV_RPW - 1) / SPMV_RPW;
   const int64_t need = (groups + 7) / 8;
   return (unsigned)std::max<int64_t>(1, std::min<int64_t>(need, (int64_t)std::max(per_sm, 1) * m->sm_count));
@@ -1433,17 +1432,12 @@ static int launch_arnoldi_t(fe_mesh m, int j, int kmax, bool fuse_pc, const DT* 
   const void* fns[3] = {arnoldi_fn<24, DT, ZT>(), arnoldi_fn<12, DT, ZT>(), arnoldi_fn<6, DT, ZT>()};
   const int npts[3] = {24, 12, 6};
   const int bds[3] = {256, 512, 1024};
-  static bool attr[2][2][3] = {};
   int which = -1, grid = 0;
   for (int q = 0; q < 3; q++) {
     size_t smem = (size_t)npts[q] * bds[q] * sizeof(double);
-    bool& done = attr[sizeof(DT) == 8][sizeof(ZT) == 8][q];
-    if (!done) {
-      FE_CUDA(cudaFuncSetAttribute(fns[q], cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-      done = true;
-    }
+    FE_TRY(fe_kernel_smem(fns[q], (int)smem));
     int per_sm = 0;
-    FE_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fns[q], bds[q], smem));
+    FE_TRY(fe_kernel_occupancy(fns[q], bds[q], smem, &per_sm));
     int64_t need = (n + (int64_t)npts[q] * bds[q] - 1) / ((int64_t)npts[q] * bds[q]);
     if (per_sm >= 1 && need <= (int64_t)per_sm * m->sm_count && need <= RED_SLOTS) {
       which = q;
@@ -1486,17 +1480,12 @@ static int launch_arnoldi_ls_t(fe_mesh m, int j, int kmax, bool fuse_pc, const D
   const int npts[3] = {24, 12, 6};
   const int bds[3] = {256, 512, 1024};
   const size_t pw_max = (size_t)(2 * LOWSYNC_MAX_RESTART + 1) * 32 * sizeof(double);
-  static bool attr[2][2][3] = {};
   int which = -1, grid = 0;
   for (int q = 0; q < 3; q++) {
     size_t smem = 2 * (size_t)npts[q] * bds[q] * sizeof(double) + pw_max;
-    bool& done = attr[sizeof(DT) == 8][sizeof(ZT) == 8][q];
-    if (!done) {
-      FE_CUDA(cudaFuncSetAttribute(fns[q], cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-      done = true;
-    }
+    FE_TRY(fe_kernel_smem(fns[q], (int)smem));
     int per_sm = 0;
-    FE_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fns[q], bds[q], smem));
+    FE_TRY(fe_kernel_occupancy(fns[q], bds[q], smem, &per_sm));
     int64_t need = (n + (int64_t)npts[q] * bds[q] - 1) / ((int64_t)npts[q] * bds[q]);
     if (per_sm >= 1 && need <= (int64_t)per_sm * m->sm_count && need <= m->partv_blocks) {
       which = q;
@@ -1558,17 +1547,12 @@ static int launch_arnoldi_bm_t(fe_mesh m, int j, int kmax, bool fuse_pc, const D
   const void* fns[2] = {arnoldi_bm_fn<12, DT, ZT>(), arnoldi_bm_fn<24, DT, ZT>()};
   const int npts[2] = {12, 24};
   const int bds[2] = {512, 256};
-  static bool attr[2][2][2] = {};
   int which = -1, grid = 0;
   for (int q = 0; q < 2; q++) {
     size_t smem = (size_t)npts[q] * bds[q] * sizeof(double);
-    bool& done = attr[sizeof(DT) == 8][sizeof(ZT) == 8][q];
-    if (!done) {
-      FE_CUDA(cudaFuncSetAttribute(fns[q], cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-      done = true;
-    }
+    FE_TRY(fe_kernel_smem(fns[q], (int)smem));
     int per_sm = 0;
-    FE_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fns[q], bds[q], smem));
+    FE_TRY(fe_kernel_occupancy(fns[q], bds[q], smem, &per_sm));
     int64_t need = (n + (int64_t)npts[q] * bds[q] - 1) / ((int64_t)npts[q] * bds[q]);
     if (per_sm >= 1 && need <= (int64_t)per_sm * m->sm_count && need * BMGS_P <= RED_SLOTS) {
       which = q;
@@ -1820,7 +1804,7 @@ __global__ void __launch_bounds__(256) k_twoloop2(int64_t n, int k, int head, in
 
 static int coop_grid(fe_mesh m, const void* fn, int* grid) {
   int per_sm = 0;
-  FE_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, 256, 0));
+  FE_TRY(fe_kernel_occupancy(fn, 256, 0, &per_sm));
   if (per_sm < 1) return fe_set_error("persistent kernel does not fit on an SM"), FE_ERR_CUDA;
   *grid = per_sm * m->sm_count;
   if (*grid > RED_SLOTS) *grid = RED_SLOTS;

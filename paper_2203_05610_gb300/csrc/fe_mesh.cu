@@ -13,6 +13,7 @@
 #include <algorithm>
 #include <array>
 #include <map>
+#include <mutex>
 #include <numeric>
 
 #include "fe_internal.h"
@@ -50,6 +51,50 @@ int fe_reset_grid_sync(fe_mesh m) {
   for (int i = 4; i < 4 + 2 * BMGS_P; i++) init[i] = sentinel;  // {bseq, pad}, pub[2][8]
   FE_CUDA(cudaMemcpyAsync(m->bar, init, sizeof(init), cudaMemcpyHostToDevice, m->stream));
   FE_CUDA(cudaStreamSynchronize(m->stream));
+  return FE_OK;
+}
+
+namespace {
+struct KernelKey {
+  const void* fn;
+  int device, threads;
+  size_t smem;
+  bool operator<(const KernelKey& o) const {
+    if (fn != o.fn) return fn < o.fn;
+    if (device != o.device) return device < o.device;
+    if (threads != o.threads) return threads < o.threads;
+    return smem < o.smem;
+  }
+};
+std::mutex g_kernel_mu;
+std::map<KernelKey, int> g_kernel_cache;  // smem opt-ins (threads = -1) and occupancies
+}  // namespace
+
+int fe_kernel_smem(const void* fn, int smem_bytes) {
+  int dev = 0;
+  FE_CUDA(cudaGetDevice(&dev));
+  std::lock_guard<std::mutex> lk(g_kernel_mu);
+  KernelKey k{fn, dev, -1, (size_t)smem_bytes};
+  if (g_kernel_cache.count(k)) return FE_OK;
+  FE_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes));
+  g_kernel_cache[k] = 1;
+  return FE_OK;
+}
+
+int fe_kernel_occupancy(const void* fn, int threads, size_t smem_bytes, int* blocks_per_sm) {
+  int dev = 0;
+  FE_CUDA(cudaGetDevice(&dev));
+  std::lock_guard<std::mutex> lk(g_kernel_mu);
+  KernelKey k{fn, dev, threads, smem_bytes};
+  auto it = g_kernel_cache.find(k);
+  if (it != g_kernel_cache.end()) {
+    *blocks_per_sm = it->second;
+    return FE_OK;
+  }
+  int b = 0;
+  FE_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, fn, threads, smem_bytes));
+  g_kernel_cache[k] = b;
+  *blocks_per_sm = b;
   return FE_OK;
 }
 
