@@ -1625,10 +1625,8 @@ int fe_gmres_dev(fe_mesh m, const double* b, double* x, double rtol, double atol
   int it = 0;
   double resid = 0.0;
   const int kmax = restart;
-  double* cs = m->gv;
-  double* g = m->gv + 2 * (kmax + 2);
+  double* g = m->gv + 2 * (kmax + 2);  // Givens arrays: cs, sn, g, y
   double* y = m->gv + 3 * (kmax + 2);
-  (void)cs;
   for (;;) {
     // r = b - K x -> V_0, beta = ||r||
     FE_TRY(fe_spmv_dev(m, x, m->w64));
