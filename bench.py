@@ -58,6 +58,8 @@ def parse():
     p.add_argument("--workload", default="cook", choices=["cook", "cook1", "twist", "heart"],
                    help="cook: Cook P2 (--mesh hexes); cook1: Cook P1 8x8x2; twist: Taylor-Hood cube 32^3; "
                         "heart: prolate shell, 149,760 P1 tets")
+    p.add_argument("--twist-material", default="neo_hookean", choices=["neo_hookean", "polyconvex"],
+                   help="twist: Taylor-Hood neo-Hookean stand-in, or the paper's polyconvex potential")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--cpu-sample-iters", type=int, default=0,
                    help="GMRES iterations of the oracle's timed sample (0 = one full restart cycle)")
@@ -81,6 +83,8 @@ def workload(args):
     if args.workload == "cook1":
         return W.cook(8, 8, 2, order=1, nu=args.nu, traction_scale=args.traction), "cook_p1_8x8x2"
     if args.workload == "twist":
+        if args.twist_material == "polyconvex":
+            return W.twist(32, order=2, material="polyconvex"), "twist_p2p1_32_polyconvex"
         return W.twist(32, order=2), "twist_p2p1_32"
     if args.workload == "heart":
         return W.heart(), "heart_p1_4x80x78"

@@ -74,12 +74,17 @@ typedef enum {
   FE_MAT_TH_NH = 1,    /* Psi = mu/2 (tr(F^T F) - 3) - mu ln J - p (J - 1); with
                           pressure_order = 1 this is the Taylor-Hood u-p form
                           (twist test stand-in).  Without pressure, p = 0. */
-  FE_MAT_GUCCIONE = 2  /* Psi = C/2 (e^Q - 1) + kappa/2 (J - 1) ln J, Q in the fibre
+  FE_MAT_GUCCIONE = 2, /* Psi = C/2 (e^Q - 1) + kappa/2 (J - 1) ln J, Q in the fibre
                           frame with b_ff = bf, b_ss = b_nn = b_sn = bt,
                           b_fs = b_fn = bfs; plus active stress
                           P_act = gamma(t) (F f) x f / |F f|,
                           gamma(t) = Ta_peak max(sin(2 pi t / period), 0).
                           Paper: Heartbeat test. */
+  FE_MAT_POLYCONVEX = 3 /* Psi = alpha_p (F:F - 3) + beta_p (cof F : cof F - 3)
+                          - c_log ln J - p (J - 1), cof F = J F^{-T}; the paper's
+                          twist potential (Section "Test problems", Psi_Twist, with
+                          c_log = 4 beta_s + 2 alpha_s and its "log(F)" read as
+                          ln det F).  With pressure_order = 1 the u-p form. */
 } fe_material_kind;
 typedef enum {
   FE_FACE_TRACTION = 0, /* dead traction t = load * data[0..2] per unit reference area */
@@ -95,6 +100,7 @@ typedef struct {
   double E, nu;        /* COOK_NH */
   double mu;           /* TH_NH */
   double C, bf, bt, bfs, kappa, Ta_peak, period; /* GUCCIONE */
+  double alpha_p, beta_p, c_log;                 /* POLYCONVEX */
 } fe_material;
 
 typedef struct {

@@ -86,7 +86,7 @@ def _p(a):
 def matp(material):
     """Material dict (workloads) -> the oracle's parameter array."""
     m = material
-    a = np.zeros(12)
+    a = np.zeros(15)
     a[0] = m["kind"]
     a[1] = m.get("vol_literal", 0)
     a[2] = m.get("E", 0.0)
@@ -99,6 +99,9 @@ def matp(material):
     a[9] = m.get("kappa", 0.0)
     a[10] = m.get("Ta_peak", 0.0)
     a[11] = m.get("period", 1.0)
+    a[12] = m.get("alpha_p", 0.0)
+    a[13] = m.get("beta_p", 0.0)
+    a[14] = m.get("c_log", 0.0)
     return a
 
 

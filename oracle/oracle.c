@@ -222,6 +222,57 @@ void om_material(const double* matp, const double* F, const double* fib, double 
     return;
   }
 
+  if (kind == 3) {
+    /* Polyconvex u-p potential of the paper's twist test (Section "Test
+     * problems", Psi_Twist):
+     *   Psi = a (F:F - 3) + b (cof F : cof F - 3) - c ln J - p (J - 1),
+     * cof F = J F^{-T}, c = 4 beta_s + 2 alpha_s; the printed "log(F)" is read
+     * as ln det F.  With C = F^T F, cof F : cof F = ((tr C)^2 - tr(C^2)) / 2,
+     * whose derivative is 2 F (tr C I - C). */
+    double a = matp[12], b = matp[13], c = matp[14];
+    double Cm[3][3], Bl[3][3], FC[3][3], trC2 = 0.0;
+    for (int M = 0; M < 3; M++)
+      for (int N = 0; N < 3; N++) {
+        double s = 0.0, t = 0.0;
+        for (int q = 0; q < 3; q++) {
+          s += F[IDX(q, M)] * F[IDX(q, N)];
+          t += F[IDX(M, q)] * F[IDX(N, q)];
+        }
+        Cm[M][N] = s;
+        Bl[M][N] = t;
+      }
+    for (int M = 0; M < 3; M++)
+      for (int N = 0; N < 3; N++) trC2 += Cm[M][N] * Cm[N][M];
+    for (int i = 0; i < 3; i++)
+      for (int N = 0; N < 3; N++) {
+        double s = 0.0;
+        for (int M = 0; M < 3; M++) s += F[IDX(i, M)] * Cm[M][N];
+        FC[i][N] = s;
+      }
+    double I2 = 0.5 * (I1 * I1 - trC2);
+    if (psi) *psi = a * (I1 - 3.0) + b * (I2 - 3.0) - c * log(J) - p * (J - 1.0);
+    for (int i = 0; i < 3; i++)
+      for (int Jj = 0; Jj < 3; Jj++)
+        P[IDX(i, Jj)] = 2.0 * a * F[IDX(i, Jj)] + 2.0 * b * (I1 * F[IDX(i, Jj)] - FC[i][Jj]) -
+                        c * H[IDX(i, Jj)] - p * J * H[IDX(i, Jj)];
+    if (dPdp)
+      for (int k = 0; k < 9; k++) dPdp[k] = -J * H[k];
+    if (A) {
+      for (int i = 0; i < 3; i++)
+        for (int Jj = 0; Jj < 3; Jj++)
+          for (int k = 0; k < 3; k++)
+            for (int L = 0; L < 3; L++) {
+              double dik = (i == k), dJL = (Jj == L);
+              double hh = H[IDX(i, L)] * H[IDX(k, Jj)];
+              double cof = 2.0 * F[IDX(k, L)] * F[IDX(i, Jj)] + I1 * dik * dJL - dik * Cm[L][Jj] -
+                           F[IDX(i, L)] * F[IDX(k, Jj)] - Bl[i][k] * dJL;
+              A[9 * IDX(i, Jj) + IDX(k, L)] = 2.0 * a * dik * dJL + 2.0 * b * cof + c * hh -
+                                              p * J * (H[IDX(i, Jj)] * H[IDX(k, L)] - hh);
+            }
+    }
+    return;
+  }
+
   /* kind 2: Guccione, Psi = C/2 (e^Q - 1) + kappa/2 (J - 1) ln J + gamma |F f|,
    * Q = sum_ab b_ab E_ab^2 in the fibre frame {f, s, n}, E = (F^T F - I)/2.
    * The active stress gamma (Ff) x f / |Ff| is the derivative of gamma |Ff|. */
@@ -336,7 +387,7 @@ struct om_mesh {
   int* fnodes; /* [nf][6] face nodes (3 vertices, then 3 edge nodes for P2) */
   int* fkind;
   double* fdata;
-  double matp[12];
+  double matp[15];
   double* fib; /* [ne][9] or NULL */
   double load, time;
   /* tangent */
@@ -417,7 +468,7 @@ om_mesh* om_create(int order, int pressure_order, int nv, int ne, const double* 
   m->nv = nv;
   m->ne = ne;
   m->nen = order == 1 ? 4 : 10;
-  memcpy(m->matp, matp, 12 * sizeof(double));
+  memcpy(m->matp, matp, 15 * sizeof(double));
   /* P2: unique edges sorted by (min, max) vertex id, numbered after vertices */
   long long* edges = NULL;
   long nedge = 0;

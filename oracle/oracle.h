@@ -8,10 +8,12 @@
  * inputs.  Every function follows the paper's definitions step by step
  * with plain loops, in the paper's order, so that it can be checked by eye.
  *
- * Material parameter array matp[12]:
- *   [0] kind (0 Cook neo-Hookean, 1 Taylor-Hood neo-Hookean, 2 Guccione)
+ * Material parameter array matp[15]:
+ *   [0] kind (0 Cook neo-Hookean, 1 Taylor-Hood neo-Hookean, 2 Guccione,
+ *       3 polyconvex twist potential)
  *   [1] vol_literal  [2] E  [3] nu  [4] mu  [5] C  [6] bf  [7] bt  [8] bfs
- *   [9] kappa  [10] Ta_peak  [11] period
+ *   [9] kappa  [10] Ta_peak  [11] period  [12] alpha_p  [13] beta_p
+ *   [14] c_log = 4 beta_s + 2 alpha_s
  * Dirichlet group array groups[ngroups][8]:
  *   mask, center x, y, z, angle, translation x, y, z
  * Solver option array opts[13]:

@@ -36,7 +36,8 @@ class FEError(RuntimeError):
 class fe_material(C.Structure):
     _fields_ = [("kind", C.c_int32), ("vol_literal", C.c_int32), ("E", C.c_double), ("nu", C.c_double),
                 ("mu", C.c_double), ("C", C.c_double), ("bf", C.c_double), ("bt", C.c_double),
-                ("bfs", C.c_double), ("kappa", C.c_double), ("Ta_peak", C.c_double), ("period", C.c_double)]
+                ("bfs", C.c_double), ("kappa", C.c_double), ("Ta_peak", C.c_double), ("period", C.c_double),
+                ("alpha_p", C.c_double), ("beta_p", C.c_double), ("c_log", C.c_double)]
 
 
 class fe_dirichlet_group(C.Structure):
@@ -171,7 +172,7 @@ def material_struct(m):
     s = fe_material()
     s.kind = int(m["kind"])
     s.vol_literal = int(m.get("vol_literal", 0))
-    for k in ("E", "nu", "mu", "C", "bf", "bt", "bfs", "kappa", "Ta_peak", "period"):
+    for k in ("E", "nu", "mu", "C", "bf", "bt", "bfs", "kappa", "Ta_peak", "period", "alpha_p", "beta_p", "c_log"):
         setattr(s, k, float(m.get(k, 0.0)))
     if s.period == 0.0:
         s.period = 1.0

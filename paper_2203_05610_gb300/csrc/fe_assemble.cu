@@ -108,6 +108,13 @@ __device__ void qp_prepare(const MatParams& mp, const double* __restrict__ fib, 
   s.an = dsqrt(an2);
 }
 
+// C = F^T F (row-major 3x3)
+template <class T>
+__device__ __forceinline__ void poly_C(const T* F, T* Cm) {
+  for (int M = 0; M < 3; M++)
+    for (int N = 0; N < 3; N++) Cm[3 * M + N] = F[M] * F[N] + F[3 + M] * F[3 + N] + F[6 + M] * F[6 + N];
+}
+
 // first Piola stress P = dPsi/dF
 template <class T>
 __device__ void qp_stress(const MatParams& mp, const double* __restrict__ fib, const QPState<T>& s, T* P) {
@@ -120,6 +127,17 @@ __device__ void qp_stress(const MatParams& mp, const double* __restrict__ fib, c
   } else if (mp.kind == FE_MAT_TH_NH) {
     T mu = (T)mp.mu;
     for (int k = 0; k < 9; k++) P[k] = mu * (s.F[k] - s.H[k]) - s.p * s.J * s.H[k];
+  } else if (mp.kind == FE_MAT_POLYCONVEX) {
+    // P = 2a F + 2b F (tr C I - C) - c H - p J H, C = F^T F
+    const T a = (T)mp.ap, b = (T)mp.bp, c = (T)mp.clog;
+    T Cm[9];
+    poly_C(s.F, Cm);
+    for (int i = 0; i < 3; i++)
+      for (int Jj = 0; Jj < 3; Jj++) {
+        const T fc = s.F[3 * i] * Cm[Jj] + s.F[3 * i + 1] * Cm[3 + Jj] + s.F[3 * i + 2] * Cm[6 + Jj];
+        P[3 * i + Jj] = T(2) * a * s.F[3 * i + Jj] + T(2) * b * (s.I1 * s.F[3 * i + Jj] - fc) -
+                        (c + s.p * s.J) * s.H[3 * i + Jj];
+      }
   } else {
     T kap = (T)mp.kappa, g = (T)mp.gamma;
     T phi = T(0.5) * kap * (s.J * dlog(s.J) + s.J - T(1));
@@ -138,6 +156,14 @@ __device__ T qp_energy(const MatParams& mp, const QPState<T>& s) {
     return T(0.5) * (T)mp.mu * (s.I1 / (j13 * j13) - T(3)) + (T)mp.cvol * (s.J * s.J - T(1) - T(2) * dlog(s.J));
   } else if (mp.kind == FE_MAT_TH_NH) {
     return T(0.5) * (T)mp.mu * (s.I1 - T(3)) - (T)mp.mu * dlog(s.J) - s.p * (s.J - T(1));
+  } else if (mp.kind == FE_MAT_POLYCONVEX) {
+    // cof F : cof F = ((tr C)^2 - tr(C^2)) / 2
+    T Cm[9], trC2 = T(0);
+    poly_C(s.F, Cm);
+    for (int M = 0; M < 3; M++)
+      for (int N = 0; N < 3; N++) trC2 += Cm[3 * M + N] * Cm[3 * N + M];
+    const T I2 = T(0.5) * (s.I1 * s.I1 - trC2);
+    return (T)mp.ap * (s.I1 - T(3)) + (T)mp.bp * (I2 - T(3)) - (T)mp.clog * dlog(s.J) - s.p * (s.J - T(1));
   }
   return T(0.5) * (T)mp.C * (s.eQ - T(1)) + T(0.5) * (T)mp.kappa * (s.J - T(1)) * dlog(s.J) + (T)mp.gamma * s.an;
 }
@@ -167,6 +193,24 @@ __device__ void qp_tangent_col(const MatParams& mp, const double* __restrict__ f
       for (int Jj = 0; Jj < 3; Jj++) {
         T hh = H[3 * i + L] * H[3 * k + Jj];
         col[3 * i + Jj] = mu * (((i == k && Jj == L) ? T(1) : T(0)) + hh) - pJ * (H[3 * i + Jj] * H[3 * k + L] - hh);
+      }
+  } else if (mp.kind == FE_MAT_POLYCONVEX) {
+    // A_iJkL = 2a d_ik d_JL + 2b (2 F_kL F_iJ + I1 d_ik d_JL - d_ik C_LJ - F_iL F_kJ
+    //          - (F F^T)_ik d_JL) + c H_iL H_kJ - p J (H_iJ H_kL - H_iL H_kJ)
+    const T a = (T)mp.ap, b = (T)mp.bp, c = (T)mp.clog, pJ = s.p * s.J;
+    T CL[3], Bk[3];  // row L of C = F^T F, column k of F F^T
+    for (int q = 0; q < 3; q++) {
+      CL[q] = F[L] * F[q] + F[3 + L] * F[3 + q] + F[6 + L] * F[6 + q];
+      Bk[q] = F[3 * q] * F[3 * k] + F[3 * q + 1] * F[3 * k + 1] + F[3 * q + 2] * F[3 * k + 2];
+    }
+    const T FkL = F[3 * k + L];
+    for (int i = 0; i < 3; i++)
+      for (int Jj = 0; Jj < 3; Jj++) {
+        const T dik = i == k ? T(1) : T(0), dJL = Jj == L ? T(1) : T(0);
+        const T hh = H[3 * i + L] * H[3 * k + Jj];
+        const T cof = T(2) * FkL * F[3 * i + Jj] + s.I1 * dik * dJL - dik * CL[Jj] - F[3 * i + L] * F[3 * k + Jj] -
+                      Bk[i] * dJL;
+        col[3 * i + Jj] = T(2) * a * dik * dJL + T(2) * b * cof + c * hh - pJ * (H[3 * i + Jj] * H[3 * k + L] - hh);
       }
   } else {
     T fr[9];

@@ -35,6 +35,7 @@ struct MatParams {
   double mu, cvol;                // COOK_NH (mu, c_vol), TH_NH (mu)
   double C, bf, bt, bfs, kappa;   // GUCCIONE
   double gamma;                   // active tension at the current time
+  double ap, bp, clog;            // POLYCONVEX: alpha_p, beta_p, c_log
 };
 
 // ---------------------------------------------------------------- mesh object

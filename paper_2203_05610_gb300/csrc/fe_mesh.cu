@@ -337,6 +337,10 @@ static MatParams make_params(const fe_material& mt, double time) {
     p.cvol = mt.vol_literal ? kap : 0.25 * kap;
   } else if (mt.kind == FE_MAT_TH_NH) {
     p.mu = mt.mu;
+  } else if (mt.kind == FE_MAT_POLYCONVEX) {
+    p.ap = mt.alpha_p;
+    p.bp = mt.beta_p;
+    p.clog = mt.c_log;
   } else {
     p.C = mt.C;
     p.bf = mt.bf;
@@ -374,11 +378,12 @@ static int validate(const fe_mesh_desc* d) {
   if (d->order != 1 && d->order != 2) return fe_set_error("order must be 1 or 2"), FE_ERR_ARG;
   if (d->pressure_order != 0 && d->pressure_order != 1)
     return fe_set_error("pressure_order must be 0 or 1"), FE_ERR_ARG;
-  if (d->pressure_order == 1 && (d->order != 2 || d->material.kind != FE_MAT_TH_NH))
-    return fe_set_error("P1 pressure needs order 2 and the TH_NH material"), FE_ERR_ARG;
+  if (d->pressure_order == 1 &&
+      (d->order != 2 || (d->material.kind != FE_MAT_TH_NH && d->material.kind != FE_MAT_POLYCONVEX)))
+    return fe_set_error("P1 pressure needs order 2 and the TH_NH or POLYCONVEX material"), FE_ERR_ARG;
   if (d->nv < 4 || d->ne < 1 || !d->coords || !d->tets)
     return fe_set_error("need nv >= 4, ne >= 1, coords and tets"), FE_ERR_ARG;
-  if (d->material.kind < 0 || d->material.kind > 2) return fe_set_error("bad material kind"), FE_ERR_ARG;
+  if (d->material.kind < 0 || d->material.kind > 3) return fe_set_error("bad material kind"), FE_ERR_ARG;
   if (d->material.kind == FE_MAT_GUCCIONE && !d->fibers)
     return fe_set_error("GUCCIONE needs fibers"), FE_ERR_ARG;
   if (d->material.kind == FE_MAT_COOK_NH && !(d->material.nu < 0.5 && d->material.nu > -1.0))

@@ -68,5 +68,6 @@ def small_cases():
         "cook_p1": W.cook(4, 4, 2, order=1),
         "cook_p2": W.cook(3, 3, 1, order=2),
         "twist_up": W.twist(2, order=2),
+        "twist_poly": W.twist(2, order=2, material="polyconvex"),
         "heart_p1": W.heart(nr=2, nc=8, nl=6),
     }

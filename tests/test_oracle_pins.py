@@ -131,6 +131,8 @@ MATS = {
     "th": dict(kind=W.MAT_TH_NH, mu=1.0),
     "gucc": dict(kind=W.MAT_GUCCIONE, C=0.88, bf=18.5, bt=3.58, bfs=1.63, kappa=1e3,
                  Ta_peak=60.0, period=0.8),
+    # distinct coefficients so that every term of the polyconvex potential shows
+    "poly": dict(kind=W.MAT_POLYCONVEX, alpha_p=1.0, beta_p=1.5, c_log=4 * 1.2 + 2 * 0.7),
 }
 
 
@@ -151,7 +153,7 @@ def test_material_derivatives(name):
     for trial in range(4):
         F = _rand_F(rng)
         fib = _fib(rng)
-        gam, p = (7.0 if name == "gucc" else 0.0), (0.3 if name == "th" else 0.0)
+        gam, p = (7.0 if name == "gucc" else 0.0), (0.3 if name in ("th", "poly") else 0.0)
         psi, P, A, dPdp = O.material_point(mat, F, fib, gam, p)
         h = 1e-6
         Pfd = np.zeros((3, 3))
@@ -166,7 +168,7 @@ def test_material_derivatives(name):
         assert np.abs(P - Pfd).max() <= 1e-6 * max(1.0, np.abs(P).max())
         assert np.abs(A - Afd).max() <= 1e-6 * max(1.0, np.abs(A).max())
         assert np.abs(A - A.T).max() <= 1e-9 * max(1.0, np.abs(A).max())  # major symmetry
-        if name == "th":
+        if name in ("th", "poly"):
             _, Pp, _, _ = O.material_point(mat, F, fib, gam, p + h)
             _, Pm, _, _ = O.material_point(mat, F, fib, gam, p - h)
             assert np.abs((Pp - Pm) / (2 * h) - dPdp).max() < 1e-8
@@ -183,6 +185,30 @@ def test_material_frame_indifference(name):
     psiq, Pq, _, _ = O.material_point(mat, Q @ F, fib, 5.0, 0.2)
     assert abs(psi - psiq) < 1e-10 * max(1, abs(psi))
     assert np.abs(Q @ P - Pq).max() < 1e-10 * max(1, np.abs(P).max())
+
+
+def test_polyconvex_twist_potential():
+    # the paper's twist potential (Section "Test problems", Psi_Twist) against
+    # its definition with the cofactor computed directly (cof F = det F F^-T;
+    # the oracle uses (tr C)^2 - tr C^2 = 2 |cof F|^2), and the stress-free
+    # reference configuration with the paper's coefficients (all 9000)
+    rng = np.random.default_rng(5)
+    mat = MATS["poly"]
+    for _ in range(3):
+        F = _rand_F(rng)
+        p = 0.4
+        cof = np.linalg.det(F) * np.linalg.inv(F).T
+        J = np.linalg.det(F)
+        psi_def = (mat["alpha_p"] * (np.sum(F * F) - 3) + mat["beta_p"] * (np.sum(cof * cof) - 3)
+                   - mat["c_log"] * np.log(J) - p * (J - 1))
+        psi, _, _, _ = O.material_point(mat, F, None, 0.0, p)
+        assert abs(psi - psi_def) <= 1e-12 * max(1.0, abs(psi_def))
+    paper = W.twist(2, material="polyconvex")["material"]
+    psi0, P0, A0, _ = O.material_point(paper, np.eye(3), None, 0.0, 0.0)
+    assert abs(psi0) < 1e-9 and np.abs(P0).max() < 1e-9
+    # the reference tangent is positive definite on the deviatoric directions
+    dev = np.eye(9) - np.outer(np.eye(3).reshape(9), np.eye(3).reshape(9)) / 3.0
+    assert np.linalg.eigvalsh(dev @ A0 @ dev).max() > 0
 
 
 def test_cook_tangent_at_identity_is_linear_elastic():

@@ -27,6 +27,7 @@ import numpy as np
 MAT_COOK_NH = 0
 MAT_TH_NH = 1
 MAT_GUCCIONE = 2
+MAT_POLYCONVEX = 3
 FACE_TRACTION = 0
 FACE_PRESSURE = 1
 FACE_ROBIN = 2
@@ -157,12 +158,18 @@ def cook(nx=8, ny=8, nz=2, order=1, E=1.0, nu=0.49, traction_scale=1.0,
                      nx=nx, ny=ny, nz=nz)
 
 
-def twist(n=32, order=2, mu=1.0, total_angle=math.pi / 2, nsteps=10, pressure=True):
+def twist(n=32, order=2, mu=1.0, total_angle=math.pi / 2, nsteps=10, pressure=True, material="neo_hookean",
+          alpha_p=9000.0, beta_p=9000.0, alpha_s=9000.0, beta_s=9000.0):
     """Twist test stand-in: unit cube n^3 hexes, Taylor-Hood P2-P1 (u, p).
 
     Bottom z = 0 clamped (group 1, all components); top z = 1 (group 2):
     x and y components follow the rotation by load*total_angle about the
     vertical axis through (0.5, 0.5); the z component is free.
+    material "neo_hookean": Psi = mu/2 (I1 - 3) - mu ln J - p (J - 1);
+    "polyconvex": the paper's twist potential alpha_p (F:F - 3) +
+    beta_p (cof F : cof F - 3) - (4 beta_s + 2 alpha_s) ln J - p (J - 1)
+    (all four coefficients 9000 in the paper; stress-free at F = I when
+    2 alpha_p + 4 beta_p = 4 beta_s + 2 alpha_s).
     """
     t1 = np.linspace(0.0, 1.0, n + 1)
     Z, Y, X = np.meshgrid(t1, t1, t1, indexing="ij")
@@ -180,7 +187,10 @@ def twist(n=32, order=2, mu=1.0, total_angle=math.pi / 2, nsteps=10, pressure=Tr
               dict(mask=3, center=(0.5, 0.5, 0.0), angle=total_angle,
                    translation=(0.0, 0.0, 0.0))]
     empty = np.zeros((0, 3))
-    material = dict(kind=MAT_TH_NH, mu=mu)
+    if material == "polyconvex":
+        material = dict(kind=MAT_POLYCONVEX, alpha_p=alpha_p, beta_p=beta_p, c_log=4.0 * beta_s + 2.0 * alpha_s)
+    else:
+        material = dict(kind=MAT_TH_NH, mu=mu)
     steps = [((s + 1) / nsteps, 0.0) for s in range(nsteps)]
     return _workload(f"twist_p{order}p1_{n}", coords, tets, order, 1 if pressure else 0,
                      dir_group, groups, empty.astype(np.int32), np.zeros(0), empty,
