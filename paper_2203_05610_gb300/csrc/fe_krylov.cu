@@ -3,12 +3,15 @@
 // (paper: GMRES with MGS, Section "Test problems and solvers details"), and
 // the L-BFGS two-loop recursion (Section "Numerical solvers", BFGS method).
 //
-// The Arnoldi step is one persistent cooperative kernel: every thread keeps
-// its slice of w in registers for the whole MGS sweep, so each basis vector
-// v_i is read from HBM exactly once per step; the k sequential inner
-// products are reduced in a fixed order (block tree, then block partials in
-// block order) between bounded grid barriers.  The two-loop recursion uses
-// the same structure with q (or z) held in registers.
+// The Arnoldi step is one persistent cooperative kernel: each block keeps
+// its slice of w on chip (shared memory for the sequential sweep, registers
+// for the blocked one) for the whole orthogonalisation, so each basis vector
+// v_i leaves HBM once per step; the inner products are reduced in a fixed
+// order (block tree, then block partials in block order) between bounded
+// grid barriers -- one per inner product for the sequential MGS sweep, one
+// per block of 8 basis vectors for the blocked form.  The SpMV streams block
+// rows in 32-block chunks with a segmented row-sum scan.  The two-loop
+// recursion uses the persistent structure with q (or z) held in registers.
 #include <algorithm>
 #include <climits>
 #include <cmath>
