@@ -648,3 +648,27 @@ def test_large_config_counts():
     w = W.twist(32, order=2)
     m = O.Mesh(w)
     assert (m.nn, m.np_, m.ndof, m.nnzb) == (274625, 35937, 859812, 7678721)
+
+
+# ---------------------------------------------------------------- synthetic inputs
+def test_heart_fibres_and_loads():
+    # cardiac shell (Section "Test problems", heartbeat): fibre frames are
+    # orthonormal and right-handed, and the load factor of the 100 steps over
+    # one period follows max(sin(2 pi t / T), 0)
+    w = W.heart(nr=2, nc=8, nl=6)
+    fib = np.asarray(w["fibers"]).reshape(-1, 3, 3)
+    G = np.einsum("eij,ekj->eik", fib, fib)
+    assert np.abs(G - np.eye(3)).max() < 1e-12
+    assert np.abs(np.linalg.det(fib) - 1.0).max() < 1e-12
+    assert all(abs(load - max(math.sin(2 * math.pi * t / 0.8), 0.0)) < 1e-15 for load, t in w["steps"])
+    assert len(w["steps"]) == 100
+
+
+def test_serving_stream_is_seeded_and_in_range():
+    a = W.serving_stream(nreq=64)
+    b = W.serving_stream(nreq=64)
+    assert a == b
+    arr = [r["arrival"] for r in a]
+    assert all(x < y for x, y in zip(arr, arr[1:]))
+    assert all(1e3 <= r["dofs"] <= 1e6 and 0.3 <= r["nu"] <= 0.4999 and 1.0 <= r["load"] <= 16.0 for r in a)
+    assert {r["family"] for r in a} == {0, 1, 2}
