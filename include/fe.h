@@ -112,7 +112,9 @@ typedef struct {
 
 typedef struct {
   int32_t order;          /* displacement order: 1 (P1) or 2 (P2) */
-  int32_t pressure_order; /* 0: displacement only; 1: P1 pressure (needs order 2 and TH_NH) */
+  int32_t pressure_order; /* 0: displacement only; 1: P1 pressure (vertex values, Taylor-Hood);
+                             2: P0 pressure (one constant per element, the paper's P2-P0
+                             twist pair); 1 and 2 need order 2 and TH_NH or POLYCONVEX */
   int32_t nv;             /* number of vertices */
   int32_t ne;             /* number of tetrahedra */
   const double* coords;   /* host [nv][3] vertex coordinates */

@@ -377,7 +377,7 @@ struct om_mesh {
   int* row_ptr; /* [nn+1] */
   int* col;     /* [nnzb] */
   long nnzb;
-  int* up_ptr; /* [nn+1] u-p coupling rows (u nodes), columns = vertices */
+  int* up_ptr; /* [nn+1] u-p coupling rows (u nodes), columns = pressure dofs */
   int* up_col;
   long nnz_up;
   unsigned char* dgroup; /* [nn] */
@@ -484,7 +484,9 @@ om_mesh* om_create(int order, int pressure_order, int nv, int ne, const double* 
       if (i == 0 || edges[i] != edges[i - 1]) edges[nedge++] = edges[i];
   }
   m->nn = nv + (int)nedge;
-  m->np = pressure_order ? nv : 0;
+  /* pressure space: 1 = P1 (vertex values, Taylor-Hood), 2 = P0 (one constant
+   * per element, the paper's P2-P0 twist discretisation) */
+  m->np = pressure_order == 1 ? nv : (pressure_order == 2 ? ne : 0);
   m->ndof = 3L * m->nn + m->np;
   m->X = (double*)xcalloc(3L * m->nn, sizeof(double));
   memcpy(m->X, coords, 3L * nv * sizeof(double));
@@ -579,8 +581,14 @@ om_mesh* om_create(int order, int pressure_order, int nv, int ne, const double* 
   /* block pattern */
   build_pattern(m->nn, m->nn, m->conn, ne, m->nen, m->nen, m->conn, m->nen, &m->row_ptr, &m->col,
                 &m->nnzb);
-  if (m->pres)
+  if (m->pres == 1)
     build_pattern(m->nn, nv, m->conn, ne, m->nen, 4, tets, 4, &m->up_ptr, &m->up_col, &m->nnz_up);
+  if (m->pres == 2) {
+    int* eid = (int*)xcalloc(ne, sizeof(int));
+    for (int e = 0; e < ne; e++) eid[e] = e;
+    build_pattern(m->nn, ne, m->conn, ne, m->nen, 1, eid, 1, &m->up_ptr, &m->up_col, &m->nnz_up);
+    free(eid);
+  }
   m->K = (double*)xcalloc(9 * m->nnzb, sizeof(double));
   m->B1 = (double*)xcalloc(3 * (m->nnz_up > 0 ? m->nnz_up : 1), sizeof(double));
   m->Dinv = (double*)xcalloc(9L * m->nn, sizeof(double));
@@ -712,6 +720,14 @@ static int face_terms(const om_mesh* m, int f, double fvec[6][3], double M[6][6]
   return nfn;
 }
 
+/* pressure space of element e: the number of local pressure values, their
+ * global indices and their shape functions at barycentric point lamq
+ * (P1: the 4 vertices with the barycentric shapes; P0: the element's one
+ * constant) */
+static int p_count(const om_mesh* m) { return m->pres == 2 ? 1 : 4; }
+static int p_index(const om_mesh* m, int e, const int* c, int v) { return m->pres == 2 ? e : c[v]; }
+static double p_shape(const om_mesh* m, const double* lamq, int v) { return m->pres == 2 ? 1.0 : lamq[v]; }
+
 double om_residual(om_mesh* m, const double* d, double* r) {
   memset(r, 0, sizeof(double) * m->ndof);
   int nen = m->nen;
@@ -733,7 +749,7 @@ double om_residual(om_mesh* m, const double* d, double* r) {
         }
       double p = 0.0;
       if (m->pres)
-        for (int a = 0; a < 4; a++) p += d[3L * m->nn + c[a]] * lam[4 * q + a];
+        for (int a = 0; a < p_count(m); a++) p += d[3L * m->nn + p_index(m, e, c, a)] * p_shape(m, lam + 4 * q, a);
       double P[9];
       om_material(m->matp, F, m->fib ? m->fib + 9L * e : NULL, gam, p, NULL, P, NULL, NULL);
       double wq = w[q] * vol;
@@ -747,7 +763,8 @@ double om_residual(om_mesh* m, const double* d, double* r) {
         double det, H[9];
         cofactor_H(F, &det, H);
         /* R_p = -int (J - 1) q_h */
-        for (int a = 0; a < 4; a++) r[3L * m->nn + c[a]] -= wq * (det - 1.0) * lam[4 * q + a];
+        for (int a = 0; a < p_count(m); a++)
+          r[3L * m->nn + p_index(m, e, c, a)] -= wq * (det - 1.0) * p_shape(m, lam + 4 * q, a);
       }
     }
   }
@@ -791,7 +808,7 @@ double om_energy(om_mesh* m, const double* d) {
         }
       double p = 0.0;
       if (m->pres)
-        for (int a = 0; a < 4; a++) p += d[3L * m->nn + c[a]] * lam[4 * q + a];
+        for (int a = 0; a < p_count(m); a++) p += d[3L * m->nn + p_index(m, e, c, a)] * p_shape(m, lam + 4 * q, a);
       double psi, P[9];
       om_material(m->matp, F, m->fib ? m->fib + 9L * e : NULL, gam, p, &psi, P, NULL, NULL);
       Pi += w[q] * vol * psi;
@@ -843,7 +860,7 @@ void om_tangent(om_mesh* m, const double* d) {
         }
       double p = 0.0;
       if (m->pres)
-        for (int a = 0; a < 4; a++) p += d[3L * m->nn + c[a]] * lam[4 * q + a];
+        for (int a = 0; a < p_count(m); a++) p += d[3L * m->nn + p_index(m, e, c, a)] * p_shape(m, lam + 4 * q, a);
       double P[9];
       om_material(m->matp, F, m->fib ? m->fib + 9L * e : NULL, gam, p, NULL, P, A, dPdp);
       double wq = w[q] * vol;
@@ -860,11 +877,11 @@ void om_tangent(om_mesh* m, const double* d) {
       /* coupling dR_u(a,i)/dp_v = w sum_J dPdp[iJ] dN_a[J] lambda_v */
       if (m->pres)
         for (int a = 0; a < nen; a++)
-          for (int v = 0; v < 4; v++)
+          for (int v = 0; v < p_count(m); v++)
             for (int i = 0; i < 3; i++) {
               double s = 0.0;
               for (int J = 0; J < 3; J++) s += dPdp[IDX(i, J)] * dN[a][J];
-              Be[a][v][i] += wq * s * lam[4 * q + v];
+              Be[a][v][i] += wq * s * p_shape(m, lam + 4 * q, v);
             }
     }
     for (int a = 0; a < nen; a++)
@@ -875,8 +892,8 @@ void om_tangent(om_mesh* m, const double* d) {
       }
     if (m->pres)
       for (int a = 0; a < nen; a++)
-        for (int v = 0; v < 4; v++) {
-          long k = find_block(m->up_ptr, m->up_col, c[a], c[v]);
+        for (int v = 0; v < p_count(m); v++) {
+          long k = find_block(m->up_ptr, m->up_col, c[a], p_index(m, e, c, v));
           for (int i = 0; i < 3; i++) m->B1[3 * k + i] += Be[a][v][i];
         }
   }

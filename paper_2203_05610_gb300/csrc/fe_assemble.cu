@@ -321,8 +321,10 @@ __global__ void __launch_bounds__(128) k_elem_residual(int ne, const int* __rest
     }
   }
   s.p = 0.0;
-  if (pres)
+  if (pres == 1)  // P1: vertex pressures with the barycentric shapes
     for (int v = 0; v < 4; v++) s.p += d[3 * (size_t)nn + c[v]] * lam[v];
+  else if (pres == 2)  // P0: the element's constant pressure
+    s.p = d[3 * (size_t)nn + e];
   const double* fe = fib ? fib + (size_t)e * 9 : nullptr;
   qp_prepare(mp, fe, s);
   double P[9];
@@ -334,8 +336,9 @@ __global__ void __launch_bounds__(128) k_elem_residual(int ne, const int* __rest
     shape_grad<ORDER>(a, lam, G, g);
     for (int i = 0; i < 3; i++) r[3 * a + i] = wq * (P[3 * i] * g[0] + P[3 * i + 1] * g[1] + P[3 * i + 2] * g[2]);
   }
-  double rp[4];
-  for (int v = 0; v < 4; v++) rp[v] = pres ? -wq * (s.J - 1.0) * lam[v] : 0.0;
+  double rp[4];  // R_p = -int (J - 1) q_h: P1 slots per vertex, P0 all in slot 0
+  for (int v = 0; v < 4; v++)
+    rp[v] = pres == 1 ? -wq * (s.J - 1.0) * lam[v] : (pres == 2 && v == 0 ? -wq * (s.J - 1.0) : 0.0);
   if (NQ > 1) {
 #pragma unroll
     for (int off = 1; off < NQ; off <<= 1) {
@@ -487,8 +490,10 @@ __global__ void __launch_bounds__(128) k_elem_energy(int ne, const int* __restri
         for (int J = 0; J < 3; J++) s.F[3 * i + J] += d[3 * (size_t)c[a] + i] * g[J];
     }
     s.p = 0.0;
-    if (pres)
+    if (pres == 1)
       for (int v = 0; v < 4; v++) s.p += d[3 * (size_t)nn + c[v]] * lam[v];
+    else if (pres == 2)
+      s.p = d[3 * (size_t)nn + e];
     const double* fe = fib ? fib + (size_t)e * 9 : nullptr;
     qp_prepare(mp, fe, s);
     val = vol / NQ * qp_energy(mp, s);
@@ -606,11 +611,14 @@ __global__ void __launch_bounds__(256) k_elem_tangent(
         for (int J = 0; J < 3; J++) s.F[3 * i + J] += (T)u[i] * g[J];
     }
     s.p = T(0);
-    if (pres)
+    if (pres == 1)
       for (int v = 0; v < 4; v++) s.p += (T)d[3 * (size_t)nn + sconn[le][v]] * lam[v];
+    else if (pres == 2)
+      s.p = (T)d[3 * (size_t)nn + selem[le]];
     qp_prepare(mp, fib ? fib + (size_t)e * 9 : nullptr, s);
     T* lb = Lbuf(le, q);
-    for (int c = 0; c < 4; c++) lb[c] = lam[c];
+    // pressure shape functions: P1 the barycentric ones, P0 the constant
+    for (int c = 0; c < 4; c++) lb[c] = pres == 2 ? (c == 0 ? T(1) : T(0)) : lam[c];
     if (q == 0) Wbuf(le)[0] = vol / NQ;
     if (pres) {
       T* dp = DPbuf(le, q);
@@ -684,10 +692,12 @@ __global__ void __launch_bounds__(256) k_elem_tangent(
       }
     }
   }
-  // u-p coupling B[a][v][i] = sum_q w sum_J dPdp[iJ] g_a[J] lambda_v
+  // u-p coupling B[a][v][i] = sum_q w sum_J dPdp[iJ] g_a[J] lambda_v over the
+  // element's local pressure values (P1: 4 vertices, P0: 1)
   if (pres) {
-    for (int k = threadIdx.x; k < EPB * NEN * 4; k += blockDim.x) {
-      int v = k % 4, a = (k / 4) % NEN, le = k / (4 * NEN);
+    const int npl = pres == 2 ? 1 : 4;
+    for (int k = threadIdx.x; k < EPB * NEN * npl; k += blockDim.x) {
+      int v = k % npl, a = (k / npl) % NEN, le = k / (npl * NEN);
       int e = selem[le];
       if (e < 0) continue;
       T w = Wbuf(le)[0];
@@ -699,7 +709,7 @@ __global__ void __launch_bounds__(256) k_elem_tangent(
         for (int i = 0; i < 3; i++) acc[i] += lv * (dp[3 * i] * ga[0] + dp[3 * i + 1] * ga[1] + dp[3 * i + 2] * ga[2]);
       }
       uint8_t fa = fixmask[sconn[le][a]];
-      T* Bv = B + (size_t)upmap[(size_t)e * NEN * 4 + a * 4 + v] * 3;
+      T* Bv = B + (size_t)upmap[((size_t)e * NEN + a) * npl + v] * 3;
       for (int i = 0; i < 3; i++) Bv[i] += ((fa >> i) & 1) ? T(0) : w * acc[i];
     }
   }

@@ -270,7 +270,7 @@ __global__ void k_geometry(int ne, int nen, const int* __restrict__ conn,
 // position of block (conn[e][a], conn[e][b]) in the pattern (binary search)
 __global__ void k_emap(int ne, int nen, int ncolk, const int* __restrict__ conn,
                        const int* __restrict__ ptr, const int* __restrict__ col, int* map,
-                       int* err) {
+                       int* err, int col_is_element) {
   int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   int64_t total = (int64_t)ne * nen * ncolk;
   if (t >= total) return;
@@ -278,7 +278,8 @@ __global__ void k_emap(int ne, int nen, int ncolk, const int* __restrict__ conn,
   int ab = (int)(t % (nen * ncolk));
   int a = ab / ncolk, b = ab % ncolk;
   int r = conn[(size_t)e * nen + a];
-  int c = conn[(size_t)e * nen + b];  // b < 4 for the u-p map: a vertex id
+  // u-p map: a vertex id (P1 pressure) or the element itself (P0)
+  int c = col_is_element ? e : conn[(size_t)e * nen + b];
   int lo = ptr[r], hi = ptr[r + 1] - 1, pos = -1;
   while (lo <= hi) {
     int mid = (lo + hi) >> 1;
@@ -376,11 +377,11 @@ static void build_rows(int nrow, const std::vector<int>& nptr, const std::vector
 static int validate(const fe_mesh_desc* d) {
   if (!d) return fe_set_error("desc is NULL"), FE_ERR_ARG;
   if (d->order != 1 && d->order != 2) return fe_set_error("order must be 1 or 2"), FE_ERR_ARG;
-  if (d->pressure_order != 0 && d->pressure_order != 1)
-    return fe_set_error("pressure_order must be 0 or 1"), FE_ERR_ARG;
-  if (d->pressure_order == 1 &&
+  if (d->pressure_order < 0 || d->pressure_order > 2)
+    return fe_set_error("pressure_order must be 0, 1 (P1) or 2 (P0)"), FE_ERR_ARG;
+  if (d->pressure_order != 0 &&
       (d->order != 2 || (d->material.kind != FE_MAT_TH_NH && d->material.kind != FE_MAT_POLYCONVEX)))
-    return fe_set_error("P1 pressure needs order 2 and the TH_NH or POLYCONVEX material"), FE_ERR_ARG;
+    return fe_set_error("a pressure space needs order 2 and the TH_NH or POLYCONVEX material"), FE_ERR_ARG;
   if (d->nv < 4 || d->ne < 1 || !d->coords || !d->tets)
     return fe_set_error("need nv >= 4, ne >= 1, coords and tets"), FE_ERR_ARG;
   if (d->material.kind < 0 || d->material.kind > 3) return fe_set_error("bad material kind"), FE_ERR_ARG;
@@ -453,7 +454,7 @@ static int create_impl(const fe_mesh_desc* desc, fe_mesh m) {
   };
   const int nn = nv + (int)ekeys.size();
   m->nn = nn;
-  m->np = m->pres ? nv : 0;
+  m->np = m->pres == 1 ? nv : (m->pres == 2 ? ne : 0);  // P1: vertex values; P0: one per element
   m->ndof = 3LL * nn + m->np;
   std::vector<int> conn((size_t)ne * m->nen);
   for (int e = 0; e < ne; e++) {
@@ -514,12 +515,18 @@ static int create_impl(const fe_mesh_desc* desc, fe_mesh m) {
     diag[a] = (int)(std::lower_bound(col.begin() + row_ptr[a], col.begin() + row_ptr[a + 1], a) - col.begin());
   std::vector<int> up_ptr, up_col, pu_ptr, pu_col, pu_src;
   if (m->pres) {
-    build_rows(nn, nptr, nlist, conn, m->nen, m->nen, 4, up_ptr, up_col);
+    if (m->pres == 1) {
+      build_rows(nn, nptr, nlist, conn, m->nen, m->nen, 4, up_ptr, up_col);  // columns: the element's vertices
+    } else {
+      std::vector<int> eid(ne);
+      for (int e = 0; e < ne; e++) eid[e] = e;
+      build_rows(nn, nptr, nlist, eid, m->nen, 1, 1, up_ptr, up_col);  // columns: the element itself
+    }
     m->nnz_up = (int64_t)up_col.size();
-    // transpose: vertex rows, u-node columns, with the index of the source entry
-    pu_ptr.assign(nv + 1, 0);
+    // transpose: pressure rows, u-node columns, with the index of the source entry
+    pu_ptr.assign(m->np + 1, 0);
     for (int64_t k = 0; k < m->nnz_up; k++) pu_ptr[up_col[k] + 1]++;
-    for (int v = 0; v < nv; v++) pu_ptr[v + 1] += pu_ptr[v];
+    for (int v = 0; v < m->np; v++) pu_ptr[v + 1] += pu_ptr[v];
     pu_col.resize(m->nnz_up);
     pu_src.resize(m->nnz_up);
     std::vector<int> fill(pu_ptr.begin(), pu_ptr.end() - 1);
@@ -624,8 +631,16 @@ static int create_impl(const fe_mesh_desc* desc, fe_mesh m) {
     FE_TRY(upload(m, &m->pu_ptr, pu_ptr));
     FE_TRY(upload(m, &m->pu_col, pu_col));
     FE_TRY(upload(m, &m->pu_src, pu_src));
-    FE_TRY(upload(m, &m->vert_ptr, vptr));
-    FE_TRY(upload(m, &m->vert_list, vlist));
+    if (m->pres == 1) {  // pressure residual gather: vertex -> (element, local vertex) slots
+      FE_TRY(upload(m, &m->vert_ptr, vptr));
+      FE_TRY(upload(m, &m->vert_list, vlist));
+    } else {  // P0: element e's pressure residual sits in its slot 0
+      std::vector<int> pptr(ne + 1), plist(ne);
+      for (int e = 0; e <= ne; e++) pptr[e] = e;
+      for (int e = 0; e < ne; e++) plist[e] = 4 * e;
+      FE_TRY(upload(m, &m->vert_ptr, pptr));
+      FE_TRY(upload(m, &m->vert_list, plist));
+    }
   }
   if (desc->fibers) {
     std::vector<double> fib(desc->fibers, desc->fibers + 9 * (size_t)ne);
@@ -696,15 +711,16 @@ static int create_impl(const fe_mesh_desc* desc, fe_mesh m) {
   {
     FE_SCOPE(m, FE_PROF_OTHER, 0);
     k_emap<<<(unsigned)((tot + 255) / 256), 256, 0, m->stream>>>(ne, m->nen, m->nen, m->conn, m->row_ptr,
-                                                                 m->col, m->emap, m->err);
+                                                                 m->col, m->emap, m->err, 0);
   }
   FE_CUDA(cudaGetLastError());
   if (m->pres) {
-    int64_t tu = (int64_t)ne * m->nen * 4;
+    const int npl = m->pres == 2 ? 1 : 4;  // local pressure values per element
+    int64_t tu = (int64_t)ne * m->nen * npl;
     FE_TRY(fe_alloc_t(m, &m->upmap, (size_t)tu));
     FE_SCOPE(m, FE_PROF_OTHER, 0);
-    k_emap<<<(unsigned)((tu + 255) / 256), 256, 0, m->stream>>>(ne, m->nen, 4, m->conn, m->up_ptr,
-                                                                m->up_col, m->upmap, m->err);
+    k_emap<<<(unsigned)((tu + 255) / 256), 256, 0, m->stream>>>(ne, m->nen, npl, m->conn, m->up_ptr,
+                                                                m->up_col, m->upmap, m->err, m->pres == 2);
     FE_CUDA(cudaGetLastError());
   }
   FE_TRY(fe_check_device_error(m));

@@ -61,7 +61,7 @@ int64_t estimate_footprint(const Request& r, int64_t* ndof_out) {
     nn += (int64_t)(std::unique(keys.begin(), keys.end()) - keys.begin());
   }
   const int64_t nen = d.order == 1 ? 4 : 10;
-  const int64_t ndof = 3 * nn + (d.pressure_order ? nv : 0);
+  const int64_t ndof = 3 * nn + (d.pressure_order == 1 ? nv : (d.pressure_order == 2 ? ne : 0));
   const int64_t nnzb = (d.order == 1 ? 16 : 28) * nn;
   nl_opts o = r.opts;
   if (!r.has_opts) nl_opts_default((nl_method)r.method, &o);

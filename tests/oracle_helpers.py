@@ -31,12 +31,13 @@ def dense_from_bcsr(nn, row_ptr, col, val, np_=0, up_ptr=None, up_col=None, bup=
     return K
 
 
-def up_pattern(conn, tets, nn):
-    """Brute-force pattern of the u-p coupling (u node rows, vertex columns)."""
+def up_pattern(conn, tets, nn, pressure_order=1):
+    """Brute-force pattern of the u-p coupling: u node rows; columns are the
+    element's vertices (P1 pressure) or the element itself (P0)."""
     rows = [set() for _ in range(nn)]
     for e in range(conn.shape[0]):
         for a in conn[e]:
-            rows[a].update(int(v) for v in tets[e])
+            rows[a].update([e] if pressure_order == 2 else [int(v) for v in tets[e]])
     ptr = np.zeros(nn + 1, dtype=np.int64)
     cols = []
     for a in range(nn):
@@ -50,7 +51,7 @@ def oracle_dense_K(m, w):
     topo = m.topology()
     val, bup, _ = m.tangent_copy()
     if m.np_:
-        up_ptr, up_col = up_pattern(topo["conn"], w["tets"], m.nn)
+        up_ptr, up_col = up_pattern(topo["conn"], w["tets"], m.nn, w["pressure_order"])
         return dense_from_bcsr(m.nn, topo["row_ptr"], topo["col"], val, m.np_, up_ptr, up_col, bup)
     return dense_from_bcsr(m.nn, topo["row_ptr"], topo["col"], val)
 
@@ -69,5 +70,6 @@ def small_cases():
         "cook_p2": W.cook(3, 3, 1, order=2),
         "twist_up": W.twist(2, order=2),
         "twist_poly": W.twist(2, order=2, material="polyconvex"),
+        "twist_p0": W.twist(2, order=2, pressure="P0", material="polyconvex"),
         "heart_p1": W.heart(nr=2, nc=8, nl=6),
     }

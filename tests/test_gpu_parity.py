@@ -212,6 +212,7 @@ SOLVE_CASES = [("cook_p1", m) for m in ("NK", "iNK", "B", "iB")] + \
               [("cook_p2", m) for m in ("NK", "iNK", "iB")] + \
               [("twist_up", m) for m in ("NK", "iNK")] + \
               [("twist_poly", m) for m in ("NK", "iNK")] + \
+              [("twist_p0", m) for m in ("NK", "iNK")] + \
               [("heart_p1", m) for m in ("NK", "iNK", "B", "iB")]
 
 
@@ -221,7 +222,8 @@ def test_nl_solve_fp64(fe, case, method):
     # 2e-12 relative (the oracle stalls there as well)
     w = small_cases()[case]
     m, om = _pair(fe, w)
-    load, time = {"heart_p1": (0.2, 0.01), "twist_up": (0.3, 0.0), "twist_poly": (0.3, 0.0)}.get(case, (0.4, 0.0))
+    load, time = {"heart_p1": (0.2, 0.01), "twist_up": (0.3, 0.0), "twist_poly": (0.3, 0.0),
+                  "twist_p0": (0.3, 0.0)}.get(case, (0.4, 0.0))
     m.set_load(load, time)
     om.set_load(load, time)
     opts = dict(ksp_atol=0.0)

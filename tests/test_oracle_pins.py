@@ -672,3 +672,24 @@ def test_serving_stream_is_seeded_and_in_range():
     assert all(x < y for x, y in zip(arr, arr[1:]))
     assert all(1e3 <= r["dofs"] <= 1e6 and 0.3 <= r["nu"] <= 0.4999 and 1.0 <= r["load"] <= 16.0 for r in a)
     assert {r["family"] for r in a} == {0, 1, 2}
+
+
+def test_p0_pressure_residual_is_element_volume_change():
+    # P2-P0 (the paper's twist pair): the pressure residual of element e is
+    # -int_e (J - 1); under an affine map x = (I + G) X, J = det(I + G) on
+    # every element, so R_p(e) = -|e| (det(I + G) - 1) exactly
+    w = strip_bc(W.twist(2, order=2, pressure="P0", material="polyconvex"))
+    m = O.Mesh(w)
+    m.set_load(0.0)
+    X = m.topology()["X"]
+    G = np.array([[0.05, 0.02, -0.01], [0.0, -0.03, 0.04], [0.01, 0.0, 0.02]])
+    d = np.zeros(m.ndof)
+    d[:3 * m.nn] = (X @ G.T).reshape(-1)
+    r, _ = m.residual(d)
+    tets = np.asarray(w["tets"])
+    Xv = np.asarray(w["coords"])
+    vol = np.abs(np.einsum("eij,eij->e", np.cross(Xv[tets[:, 1]] - Xv[tets[:, 0]], Xv[tets[:, 2]] - Xv[tets[:, 0]])[:, None, :],
+                           (Xv[tets[:, 3]] - Xv[tets[:, 0]])[:, None, :])) / 6.0
+    expect = -vol * (np.linalg.det(np.eye(3) + G) - 1.0)
+    assert m.np_ == len(tets)
+    assert np.abs(r[3 * m.nn:] - expect).max() <= 1e-13 * np.abs(expect).max()

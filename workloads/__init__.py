@@ -162,6 +162,9 @@ def twist(n=32, order=2, mu=1.0, total_angle=math.pi / 2, nsteps=10, pressure=Tr
           alpha_p=9000.0, beta_p=9000.0, alpha_s=9000.0, beta_s=9000.0):
     """Twist test stand-in: unit cube n^3 hexes, Taylor-Hood P2-P1 (u, p).
 
+    pressure: True or "P1" (vertex pressures, Taylor-Hood), "P0" (one
+    constant pressure per element: the paper's P2-P0 pair), False (none).
+
     Bottom z = 0 clamped (group 1, all components); top z = 1 (group 2):
     x and y components follow the rotation by load*total_angle about the
     vertical axis through (0.5, 0.5); the z component is free.
@@ -192,7 +195,8 @@ def twist(n=32, order=2, mu=1.0, total_angle=math.pi / 2, nsteps=10, pressure=Tr
     else:
         material = dict(kind=MAT_TH_NH, mu=mu)
     steps = [((s + 1) / nsteps, 0.0) for s in range(nsteps)]
-    return _workload(f"twist_p{order}p1_{n}", coords, tets, order, 1 if pressure else 0,
+    pspace = {True: 1, "P1": 1, "P0": 2, False: 0, None: 0}[pressure]
+    return _workload(f"twist_p{order}p{'0' if pspace == 2 else '1'}_{n}", coords, tets, order, pspace,
                      dir_group, groups, empty.astype(np.int32), np.zeros(0), empty,
                      material, None, steps, n=n)
 
