@@ -60,6 +60,8 @@ def parse():
                         "heart: prolate shell, 149,760 P1 tets")
     p.add_argument("--twist-material", default="neo_hookean", choices=["neo_hookean", "polyconvex"],
                    help="twist: Taylor-Hood neo-Hookean stand-in, or the paper's polyconvex potential")
+    p.add_argument("--twist-pressure", default="P1", choices=["P1", "P0"],
+                   help="twist pressure space: P1 (Taylor-Hood) or P0 (the paper's P2-P0 pair)")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--cpu-sample-iters", type=int, default=0,
                    help="GMRES iterations of the oracle's timed sample (0 = one full restart cycle)")
@@ -83,9 +85,8 @@ def workload(args):
     if args.workload == "cook1":
         return W.cook(8, 8, 2, order=1, nu=args.nu, traction_scale=args.traction), "cook_p1_8x8x2"
     if args.workload == "twist":
-        if args.twist_material == "polyconvex":
-            return W.twist(32, order=2, material="polyconvex"), "twist_p2p1_32_polyconvex"
-        return W.twist(32, order=2), "twist_p2p1_32"
+        w = W.twist(32, order=2, material=args.twist_material, pressure=args.twist_pressure)
+        return w, w["name"] + ("_polyconvex" if args.twist_material == "polyconvex" else "")
     if args.workload == "heart":
         return W.heart(), "heart_p1_4x80x78"
     nx, ny, nz = (int(v) for v in args.mesh.split(","))
