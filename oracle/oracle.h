@@ -37,6 +37,8 @@ extern "C" {
 
 typedef struct om_mesh om_mesh;
 
+/* pressure_order: 0 none, 1 P1 (vertex values, Taylor-Hood), 2 P0 (one
+ * constant per element, the paper's P2-P0 twist pair) */
 om_mesh* om_create(int order, int pressure_order, int nv, int ne, const double* coords,
                    const int* tets, const unsigned char* dir_group, int ngroups,
                    const double* groups, int nf, const int* faces, const int* face_kind,
