@@ -1134,7 +1134,8 @@ int om_solve(om_mesh* m, int method, double tol, int max_it, double* d, const do
   double* res_hist = stats + 6;
   double* lit_hist = stats + 6 + OM_HIST;
   double* eta_hist = stats + 6 + 2 * OM_HIST;
-  for (int i = 0; i < 6 + 3 * OM_HIST; i++) stats[i] = 0.0;
+  double* lres_hist = stats + 6 + 3 * OM_HIST;
+  for (int i = 0; i < 6 + 4 * OM_HIST; i++) stats[i] = 0.0;
   if ((int)opts[9]) om_apply_dirichlet(m, d);
   double* R = (double*)xcalloc(n, sizeof(double));
   double* Rn = (double*)xcalloc(n, sizeof(double));
@@ -1176,6 +1177,7 @@ int om_solve(om_mesh* m, int method, double tol, int max_it, double* d, const do
       om_spmv(m, dl, Rn);
       for (long i = 0; i < n; i++) Rn[i] += R[i];
       double lnorm = nrm2(Rn, n);
+      if (k < OM_HIST) lres_hist[k] = lnorm;
       for (long i = 0; i < n; i++) d[i] += dl[i]; /* basic line search: full step */
       double rprev = rk;
       rk = om_residual(m, d, R);

@@ -23,9 +23,11 @@
  *   hess_reassemble (B/iB: tangent re-assembled and memory restarted every
  *   hess_reassemble iterations, 0 = never),
  *   ib_adaptive (iB: 1 = Eisenstat-Walker choice-2 tolerance for the H0 solve)
- * Stats array (6 + 3*OM_HIST doubles):
+ * Stats array (6 + 4*OM_HIST doubles):
  *   status, nit, lit_total, assemblies, r0, rfinal,
- *   res_hist[OM_HIST], lit_hist[OM_HIST], eta_hist[OM_HIST]
+ *   res_hist[OM_HIST], lit_hist[OM_HIST], eta_hist[OM_HIST],
+ *   lres_hist[OM_HIST] (NK/iNK: linear residual ||R_{k-1} + K_{k-1} delta_k||
+ *   of iteration k, the second norm of the Eisenstat-Walker forcing term)
  */
 #ifndef ORACLE_H
 #define ORACLE_H
