@@ -12,6 +12,7 @@
 #include <cstring>
 #include <algorithm>
 #include <array>
+#include <climits>
 #include <map>
 #include <mutex>
 #include <numeric>
@@ -750,12 +751,22 @@ extern "C" int fe_mesh_create(const fe_mesh_desc* desc, fe_mesh* out) {
   FE_TRY(validate(desc));
   fe_mesh m = new fe_mesh_s();
   int rc = create_impl(desc, m);
+  // bring the fixed array of fe_spmv_noalloc and the kernels it launches
+  // into memory now, while allocating is allowed (see fe_noalloc.cu)
+  if (rc == FE_OK) rc = fe_noalloc_prepare(m);
   if (rc != FE_OK) {
     free_all(m);
     delete m;
     return rc;
   }
   *out = m;
+  return FE_OK;
+}
+
+extern "C" int fe_set_wait_limit(fe_mesh m, int64_t polls) {
+  if (!m) return fe_set_error("NULL mesh"), FE_ERR_ARG;
+  if (polls > (int64_t)UINT32_MAX) return fe_set_error("polls must be < 2^32"), FE_ERR_ARG;
+  m->wait_limit = polls < 0 ? (1u << 26) : (unsigned)polls;
   return FE_OK;
 }
 
