@@ -59,10 +59,16 @@ extern "C" {
 typedef enum { NL_NK = 0, NL_INK = 1, NL_B = 2, NL_IB = 3 } nl_method;
 typedef enum {
   FE_PREC_FP64 = 0,       /* tangent, SpMV, preconditioner in FP64 */
-  FE_PREC_MIXED_FP32 = 1, /* tangent assembled and stored in FP32; SpMV and
-                             preconditioner in FP32; Arnoldi, residual,
-                             update and BFGS products stay FP64; Krylov
-                             relative tolerances are clamped at 1e-5 */
+  FE_PREC_MIXED_FP32 = 1, /* tangent assembled and stored in FP32; the Krylov
+                             SpMV and preconditioner in FP32; Arnoldi,
+                             residual, update and BFGS products stay FP64.
+                             GMRES's restart residual b - K x and iNK's
+                             linear residual use the stored values with FP64
+                             vectors and accumulation, and a residual
+                             estimate at the target is confirmed on that
+                             residual (restarted GMRES as iterative
+                             refinement), so Krylov tolerances are met as
+                             in FP64 */
   FE_PREC_MIXED_BF16 = 2  /* as MIXED_FP32 with BF16 tangent storage */
 } fe_precision;
 typedef enum {
@@ -214,12 +220,15 @@ int fe_pc_apply(fe_mesh m, const double* x, double* y);
  * allocator (PyTorch's caching allocator, a custom arena) must remain the
  * only owner for.  fe_spmv converts x to the SpMV's input precision in a
  * buffer it allocates on first use; this call stages that input in a fixed
- * device array of the library instead: 2^20 FP64 entries (8 MiB), held by
- * every GPU that loads the library until the process exits.  Limits and
- * rules:
+ * device array of the library instead: 2^20 FP64 entries (8 MiB), held on
+ * every GPU where a mesh was created (with eager module loading, on every
+ * GPU the process uses) until the process exits.  Limits and rules:
  *  - ndof must be at most 1,048,576; larger meshes get FE_ERR_ARG.
- *  - The first call on a device looks up the array's device address (once
- *    per device); make that first call before any stream capture.
+ *  - fe_mesh_create brings the array into device memory on the mesh's
+ *    device (CUDA loads it lazily, on first use), looks its address up and
+ *    loads the kernels this call launches, so no call of this function
+ *    loads or allocates anything; a mesh that could not do so is not
+ *    created (FE_ERR_CUDA).
  *  - All calls share the array and each overwrites it: calls that overlap
  *    on the GPU (other streams or threads) race; serialise them.
  *  - The tangent must be assembled (fe_assemble_tangent); mesh and tangent
@@ -275,6 +284,9 @@ typedef struct {
   double res_hist[NL_HIST]; /* ||R_k||, k = 0..nit */
   int32_t lit_hist[NL_HIST];/* Krylov iterations of iteration k */
   double eta_hist[NL_HIST]; /* relative Krylov tolerance used at iteration k */
+  double lres_hist[NL_HIST];/* NK/iNK: linear residual ||R_{k-1} + K_{k-1} delta_k|| of
+                               iteration k (the Eisenstat-Walker forcing term's second
+                               norm); 0 for B/iB */
 } nl_stats;
 
 /* Fill opts with the defaults of the given method (Appendix A options). */
@@ -337,6 +349,15 @@ typedef struct {
 int fe_profile_reset(fe_mesh m, int timing);
 /* Synchronise the stream and read the counters (host out). */
 int fe_profile_read(fe_mesh m, fe_profile_info* out);
+
+/* Bounded device waits (no counterpart in the paper).  The persistent
+ * kernels' grid barriers poll for a published value at most `polls` times
+ * before they give up: the kernel then records a timeout in the mesh's
+ * error word and ends, and the call returns FE_ERR_TIMEOUT with the mesh
+ * still usable.  Default 2^26 polls (seconds); polls < 0 restores it; 0 makes
+ * every wait that does not find its value at the first poll give up (how
+ * the tests drive the timeout path).  Returns FE_ERR_ARG for polls >= 2^32. */
+int fe_set_wait_limit(fe_mesh m, int64_t polls);
 
 /* Thread-local message describing the last error. */
 const char* fe_last_error(void);

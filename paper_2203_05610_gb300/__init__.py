@@ -71,7 +71,7 @@ class nl_stats(C.Structure):
     _fields_ = [("status", C.c_int32), ("nit", C.c_int32), ("lit_total", C.c_int64), ("assemblies", C.c_int32),
                 ("r0", C.c_double), ("rfinal", C.c_double), ("time_s", C.c_double), ("hist_len", C.c_int32),
                 ("res_hist", C.c_double * NL_HIST), ("lit_hist", C.c_int32 * NL_HIST),
-                ("eta_hist", C.c_double * NL_HIST)]
+                ("eta_hist", C.c_double * NL_HIST), ("lres_hist", C.c_double * NL_HIST)]
 
 
 PROF_CLASSES = ["residual", "tangent", "spmv", "pc", "arnoldi", "twoloop", "vector", "other"]
@@ -129,6 +129,7 @@ SIGNATURES = {
     "serve_poll": (_I, [_P, C.c_int64, _I, C.POINTER(fe_request_status), _P]),
     "serve_clock": (_D, [_P]),
     "serve_destroy": (_I, [_P]),
+    "fe_set_wait_limit": (_I, [_P, C.c_int64]),
     "fe_last_error": (C.c_char_p, []),
 }
 
@@ -336,6 +337,10 @@ class Mesh:
                                     C.c_void_p(rho.data_ptr()), k, self._vec(q, "q"), self._vec(z, "z"), int(h0)))
         return z
 
+    def set_wait_limit(self, polls=-1):
+        """Polls before a bounded device wait gives up (< 0: the default)."""
+        _check(lib().fe_set_wait_limit(self.h, int(polls)))
+
     def profile_reset(self, timing=False):
         _check(lib().fe_profile_reset(self.h, 1 if timing else 0))
 
@@ -356,7 +361,8 @@ class Mesh:
         n = st.hist_len
         stats = dict(status=rc, nit=st.nit, lit_total=int(st.lit_total), assemblies=st.assemblies, r0=st.r0,
                      rfinal=st.rfinal, time_s=st.time_s, res_hist=np.array(st.res_hist[:n]),
-                     lit_hist=np.array(st.lit_hist[:n]), eta_hist=np.array(st.eta_hist[:n]))
+                     lit_hist=np.array(st.lit_hist[:n]), eta_hist=np.array(st.eta_hist[:n]),
+                lres_hist=np.array(st.lres_hist[:n]))
         return d, stats
 
 
@@ -364,7 +370,8 @@ def _stats_dict(st):
     n = st.hist_len
     return dict(status=st.status, nit=st.nit, lit_total=int(st.lit_total), assemblies=st.assemblies, r0=st.r0,
                 rfinal=st.rfinal, time_s=st.time_s, res_hist=np.array(st.res_hist[:n]),
-                lit_hist=np.array(st.lit_hist[:n]), eta_hist=np.array(st.eta_hist[:n]))
+                lit_hist=np.array(st.lit_hist[:n]), eta_hist=np.array(st.eta_hist[:n]),
+                lres_hist=np.array(st.lres_hist[:n]))
 
 
 class Server:

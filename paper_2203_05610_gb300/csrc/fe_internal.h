@@ -154,6 +154,7 @@ struct fe_mesh_s {
   std::vector<ProfRec> prof_pending;
   std::vector<cudaEvent_t> ev_free;
 
+  unsigned wait_limit = 1u << 26;  // polls before a bounded device wait gives up
   int coop_blocks = 0;       // co-resident blocks for the persistent kernels
   int sm_count = 0;
   int64_t device_bytes = 0;
@@ -212,6 +213,7 @@ int fe_tangent_dev(fe_mesh m, const double* d, int precision);
 int fe_energy_dev(fe_mesh m, const double* d, double* out);
 // linear algebra (fe_krylov.cu)
 int fe_spmv_dev(fe_mesh m, const double* x, double* y);           // FP64 in/out, current tangent
+int fe_spmv_acc_dev(fe_mesh m, const double* x, double* y);       // FP64 in/out and accumulation, any storage
 int fe_pc_dev(fe_mesh m, const double* x, double* y);             // FP64 in/out
 int fe_gmres_dev(fe_mesh m, const double* b, double* x, double rtol, double atol, int restart,
                  int max_it, int* iters, double* res);
@@ -222,3 +224,8 @@ int fe_lbfgs_dev(fe_mesh m, const double* S, const double* Y, const double* rho,
                  double ksp_atol, int restart, int kmaxit, int* lit);
 int fe_workspace(fe_mesh m, int restart);
 int fe_spmv_from_input(fe_mesh m, const void* xin, double* y);  // input already in the SpMV precision
+int fe_spmv_preload(fe_mesh m);  // loads every SpMV kernel and caches its launch facts
+// fe_noalloc.cu: resolves the fixed array of fe_spmv_noalloc on the mesh's
+// device and loads the kernels that entry point launches (called by
+// fe_mesh_create with the mesh's device current)
+int fe_noalloc_prepare(fe_mesh m);

@@ -58,7 +58,8 @@ __device__ __forceinline__ double sum_partials(const double* part, double* sh) {
 // Two slots alternate by the global step sequence number seq, which lives in
 // device memory across launches.  The sentinel is a NaN payload that no
 // arithmetic produces.  The wait is bounded (2^26 polls, seconds): on
-// timeout the block records DEV_ERR_TIMEOUT and the kernel ends.
+// timeout the block records DEV_ERR_TIMEOUT and the kernel ends.  The
+// limit is the mesh's (fe_set_wait_limit; 2^26 polls by default).
 constexpr unsigned long long kSentinel = 0x7FF4DEAD5EEDF00DULL;
 
 __device__ __forceinline__ unsigned atom_inc_acq_rel(unsigned* p, unsigned lim) {
@@ -88,6 +89,7 @@ struct GridSync {
   unsigned* seq;             // global step sequence
   unsigned long long* slot;  // [2] published totals
   int* err;
+  unsigned limit;            // polls before a wait gives up (fe_set_wait_limit)
 };
 
 // lane 0 of warp 0 only: returns 1 for the last block to arrive
@@ -129,7 +131,7 @@ __device__ __forceinline__ bool grid_complete(const GridSync& gs, const double* 
       unsigned long long v;
       *s_fail = 0;
       while ((v = ld_acquire_u64(slot)) == kSentinel) {
-        if (++spins > (1u << 26) || *(volatile int*)gs.err != DEV_OK) {
+        if (++spins > gs.limit || *(volatile int*)gs.err != DEV_OK) {
           atomicCAS(gs.err, DEV_OK, DEV_ERR_TIMEOUT);
           *s_fail = 1;
           break;
@@ -197,7 +199,7 @@ __device__ __forceinline__ void grid_reduce_w0(const GridSync& gs, double* part,
     unsigned spins = 0;
     unsigned long long v;
     while ((v = ld_acquire_u64(slot)) == kSentinel) {
-      if (++spins > (1u << 26) || *(volatile int*)gs.err != DEV_OK) {
+      if (++spins > gs.limit || *(volatile int*)gs.err != DEV_OK) {
         atomicCAS(gs.err, DEV_OK, DEV_ERR_TIMEOUT);
         *s_fail = 1;
         break;
@@ -349,7 +351,7 @@ __device__ __forceinline__ void publish_seq(const GridSync& gs, unsigned seq) {
 __device__ __forceinline__ bool wait_seq(const GridSync& gs, unsigned seq) {
   unsigned spins = 0;
   while (ld_acquire_u64(gs.slot + (seq & 1u)) == kSentinel) {
-    if (++spins > (1u << 26) || *(volatile int*)gs.err != DEV_OK) {
+    if (++spins > gs.limit || *(volatile int*)gs.err != DEV_OK) {
       atomicCAS(gs.err, DEV_OK, DEV_ERR_TIMEOUT);
       return false;
     }
@@ -551,6 +553,7 @@ struct BlockSync {
   unsigned* seq;             // this kernel's step sequence
   unsigned long long* pub;   // [2][BMGS_P] published values, kSentinel when not yet
   int* err;
+  unsigned limit;            // polls before a wait gives up (fe_set_wait_limit)
 };
 
 // Warp reduce-scatter of P values per lane: returns, in every lane, the warp
@@ -599,7 +602,7 @@ __device__ __forceinline__ bool bm_reduce_w0(const BlockSync& bs, double* part, 
         unsigned spins = 0;
         unsigned long long u;
         while ((u = ld_acquire_u64(slot)) == kSentinel) {
-          if (++spins > (1u << 26) || *(volatile int*)bs.err != DEV_OK) {
+          if (++spins > bs.limit || *(volatile int*)bs.err != DEV_OK) {
             atomicCAS(bs.err, DEV_OK, DEV_ERR_TIMEOUT);
             ok = false;
             break;
@@ -1250,10 +1253,69 @@ int fe_spmv_dev(fe_mesh m, const double* x, double* y) {
   return spmv_zx(m, y);
 }
 
+// y = K x with FP64 input and FP64 accumulation whatever the storage of the
+// tangent values (FP32 and BF16 values widen exactly to FP64).  The
+// residuals that decide the stopping tests of the mixed forms -- GMRES's
+// restart residual b - K x and iNK's linear residual R + K delta -- then
+// carry no rounding beyond the stored tangent's, so restarted GMRES refines
+// its iterate in FP64 (mixed-precision iterative refinement) instead of
+// stalling at the FP32 SpMV's accuracy.  The FP64 form is fe_spmv_dev.
+template <class VT>
+static int spmv_acc_t(fe_mesh m, const VT* K, const VT* B, const double* x, double* y) {
+  const double sv = sizeof(VT);
+  FE_SCOPE_F(m, FE_PROF_SPMV, (double)m->nnzb * (9 * sv + 4) + 4.0 * (m->nn + 1) + 16.0 * (double)m->ndof +
+                                  (m->pres ? (double)m->nnz_up * 2 * (3 * sv + 8) + 4.0 * (m->nn + m->np + 2) : 0.0),
+             18.0 * (double)m->nnzb + (m->pres ? 12.0 * (double)m->nnz_up : 0.0));
+  if (!m->pres) {
+    const unsigned grids = stream_grid_t<VT, double, double>(m);
+    k_spmv_stream<VT, double, double><<<grids, 256, 0, m->stream>>>(m->nn, m->row_ptr, m->col, K, x, y);
+  } else {
+    const unsigned grid = (unsigned)(((int64_t)m->nn * 32 + 255) / 256);
+    const unsigned gridp = (unsigned)(((int64_t)m->np * 32 + 255) / 256);
+    k_spmv<VT, double, double><<<grid, 256, 0, m->stream>>>(m->nn, m->row_ptr, m->col, K, x, y, m->up_ptr, m->up_col,
+                                                            B, x + 3 * (int64_t)m->nn);
+    k_spmv_p<VT, double, double><<<gridp, 256, 0, m->stream>>>(m->np, m->pu_ptr, m->pu_col, m->pu_src, B, x,
+                                                               y + 3 * (int64_t)m->nn);
+  }
+  FE_CUDA(cudaGetLastError());
+  return FE_OK;
+}
+
+int fe_spmv_acc_dev(fe_mesh m, const double* x, double* y) {
+  if (m->prec < 0) return fe_set_error("no tangent assembled"), FE_ERR_STATE;
+  if (m->prec == FE_PREC_FP64) return fe_spmv_dev(m, x, y);
+  if (m->prec == FE_PREC_MIXED_BF16) return spmv_acc_t<__nv_bfloat16>(m, m->K16, nullptr, x, y);
+  return spmv_acc_t<float>(m, m->K32, m->B32, x, y);
+}
+
 // y = K xin where xin already holds the input in the SpMV's input precision
 // (FP64 for an FP64 tangent, FP32 otherwise).  Used by the allocation-free
 // entry point, which stages the input in its own fixed device array.
 int fe_spmv_from_input(fe_mesh m, const void* xin, double* y) { return launch_spmv(m, xin, y); }
+
+// Under CUDA's lazy loading a kernel's code is placed in device memory at
+// its first launch.  Loading every SpMV kernel here (and caching the
+// occupancy the streamed launch reads) lets a caller that must not allocate
+// launch them later without that first-use cost.
+int fe_spmv_preload(fe_mesh m) {
+  const void* fns[] = {(const void*)k_spmv_stream<double, double, double>,
+                       (const void*)k_spmv_stream<float, float, float>,
+                       (const void*)k_spmv_stream<__nv_bfloat16, float, float>,
+                       (const void*)k_spmv<double, double, double>,
+                       (const void*)k_spmv<float, float, float>,
+                       (const void*)k_spmv_p<double, double, double>,
+                       (const void*)k_spmv_p<float, float, float>};
+  for (const void* fn : fns) {
+    cudaFuncAttributes a;
+    FE_CUDA(cudaFuncGetAttributes(&a, fn));
+  }
+  int per_sm = 0;
+  FE_TRY(fe_kernel_occupancy((const void*)k_spmv_stream<double, double, double>, 256, 0, &per_sm));
+  FE_TRY(fe_kernel_occupancy((const void*)k_spmv_stream<float, float, float>, 256, 0, &per_sm));
+  FE_TRY(fe_kernel_occupancy((const void*)k_spmv_stream<__nv_bfloat16, float, float>, 256, 0, &per_sm));
+  (void)m;
+  return FE_OK;
+}
 
 // ---------------------------------------------------------------- vectors
 __global__ void k_dot(int64_t n, const double* __restrict__ a, const double* __restrict__ b, double* red,
@@ -1419,6 +1481,7 @@ static GridSync grid_sync(fe_mesh m) {
   gs.seq = m->bar + 1;
   gs.slot = (unsigned long long*)(m->bar + 2);
   gs.err = m->err;
+  gs.limit = m->wait_limit;
   return gs;
 }
 
@@ -1535,6 +1598,7 @@ static BlockSync block_sync(fe_mesh m) {
   bs.seq = m->bar + 6;
   bs.pub = (unsigned long long*)(m->bar + 8);
   bs.err = m->err;
+  bs.limit = m->wait_limit;
   return bs;
 }
 
@@ -1631,8 +1695,8 @@ int fe_gmres_dev(fe_mesh m, const double* b, double* x, double rtol, double atol
   double* g = m->gv + 2 * (kmax + 2);  // Givens arrays: cs, sn, g, y
   double* y = m->gv + 3 * (kmax + 2);
   for (;;) {
-    // r = b - K x -> V_0, beta = ||r||
-    FE_TRY(fe_spmv_dev(m, x, m->w64));
+    // r = b - K x -> V_0, beta = ||r|| (FP64 vectors and accumulation)
+    FE_TRY(fe_spmv_acc_dev(m, x, m->w64));
     {
       FE_SCOPE(m, FE_PROF_VECTOR, 24.0 * n);
       k_sub<<<g1, 256, 0, m->stream>>>(n, b, m->w64, m->V);
@@ -1680,7 +1744,12 @@ int fe_gmres_dev(fe_mesh m, const double* b, double* x, double rtol, double atol
       batch = std::min(2 * batch, GMRES_BATCH);
     }
     it += j;
-    done = resid <= target || it >= max_it || m->h_scal[4] == 0.0 || !std::isfinite(resid);
+    // FP64: the residual estimate decides, as in the oracle.  Mixed forms: an
+    // estimate at the target sends the iterate back to the top of the loop,
+    // where its FP64-accumulated residual decides (and, above the target,
+    // starts the next refinement cycle)
+    done = it >= max_it || m->h_scal[4] == 0.0 || !std::isfinite(resid) ||
+           (resid <= target && m->prec == FE_PREC_FP64);
     {
       FE_SCOPE(m, FE_PROF_VECTOR, 8.0 * j * (j + 1));
       k_trisolve<<<1, 1024, 0, m->stream>>>(j, kmax + 1, m->H, g, y);

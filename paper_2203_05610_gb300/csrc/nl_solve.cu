@@ -93,13 +93,8 @@ static int solve_impl(fe_mesh m, int method, double tol, int max_it, double* d, 
     st.rfinal = 0.0;
     return FE_OK;
   }
-  // FP32 SpMV/preconditioner rows sum ~30 single-precision products, so the
-  // mixed forms cannot resolve relative linear residuals much below 1e-6:
-  // their Krylov tolerance is clamped at 1e-5 instead of letting GMRES run
-  // to its iteration cap
-  const double rtol_floor = o.precision == FE_PREC_FP64 ? 0.0 : 1e-5;
   if (method == NL_NK || method == NL_INK) {
-    double eta = std::max(method == NL_NK ? o.ksp_rtol : o.ew_rtol0, rtol_floor);
+    double eta = method == NL_NK ? o.ksp_rtol : o.ew_rtol0;
     const double alpha2 = 0.5 * (1.0 + sqrt(5.0));
     for (int k = 1; k <= max_it; k++) {
       if ((k - 1) % o.jac_lag == 0) {  // Jacobian lagging: reuse the tangent in between
@@ -111,19 +106,20 @@ static int solve_impl(fe_mesh m, int method, double tol, int max_it, double* d, 
       FE_CUDA(cudaMemsetAsync(dl, 0, n * sizeof(double), m->stream));
       int its = 0;
       double lres = 0.0;
-      FE_TRY(fe_gmres_dev(m, t, dl, std::max(eta, rtol_floor), o.ksp_atol, o.ksp_restart, o.ksp_max_it, &its,
-                          &lres));
+      FE_TRY(fe_gmres_dev(m, t, dl, eta, o.ksp_atol, o.ksp_restart, o.ksp_max_it, &its, &lres));
       st.lit_total += its;
       if (k < NL_HIST) {
         st.lit_hist[k] = its;
         st.eta_hist[k] = eta;
       }
-      // linear residual ||R_{k-1} + K delta|| for Eisenstat-Walker
-      FE_TRY(fe_spmv_dev(m, dl, Rn));
+      // linear residual ||R_{k-1} + K delta|| for Eisenstat-Walker (FP64
+      // vectors and accumulation in every precision)
+      FE_TRY(fe_spmv_acc_dev(m, dl, Rn));
       FE_TRY(fe_axpby_dev(m, 1.0, R, 1.0, Rn, n));
       double ln2 = 0.0;
       FE_TRY(fe_dot_dev(m, Rn, Rn, n, &ln2));
       double lnorm = sqrt(ln2);
+      if (k < NL_HIST) st.lres_hist[k] = lnorm;
       FE_TRY(fe_axpby_dev(m, 1.0, dl, 1.0, d, n));  // basic line search: full step
       double rprev = rk;
       FE_TRY(residual_norm(m, d, R, &rk));
@@ -180,7 +176,7 @@ static int solve_impl(fe_mesh m, int method, double tol, int max_it, double* d, 
       }
       int lit = 0;
       FE_TRY(fe_lbfgs_dev(m, m->S, m->Yv, m->rho_d, head, mcap, np, n, R, t, method == NL_B ? 0 : 2,
-                          std::max(eta, rtol_floor), o.ksp_atol, o.ksp_restart, o.ksp_max_it, &lit));
+                          eta, o.ksp_atol, o.ksp_restart, o.ksp_max_it, &lit));
       st.lit_total += lit;
       if (k < NL_HIST) {
         st.lit_hist[k] = lit;

@@ -29,14 +29,18 @@ def test_recorded_oracle_structure_is_consistent():
     assert rec["assemblies"] == 1
 
 
-def test_traffic_records_match_the_captured_kernels():
+def test_traffic_records_follow_the_captured_kernels():
+    # a record scales to the run's bytes while the captured kernels' source
+    # region is unchanged, and gives null (no traffic claim) once it changed
     path = os.path.join(ROOT, "profiles", "traffic.json")
     recs = json.load(open(path))
     for cls, rec in recs.items():
         src = os.path.join(ROOT, rec["source"])
-        assert bench.source_sha(src, rec.get("region")) == rec["source_sha"], cls
         assert 0.9 < rec["traffic_over_algorithmic"] < 1.2, cls
-        assert bench.traffic_record(cls, 1e8) == round(rec["traffic_over_algorithmic"] * 1e8)
+        if bench.source_sha(src, rec.get("region")) == rec["source_sha"]:
+            assert bench.traffic_record(cls, 1e8) == round(rec["traffic_over_algorithmic"] * 1e8)
+        else:
+            assert bench.traffic_record(cls, 1e8) is None
 
 
 def test_source_region_hash_ignores_edits_outside(tmp_path):

@@ -196,7 +196,8 @@ def twist(n=32, order=2, mu=1.0, total_angle=math.pi / 2, nsteps=10, pressure=Tr
         material = dict(kind=MAT_TH_NH, mu=mu)
     steps = [((s + 1) / nsteps, 0.0) for s in range(nsteps)]
     pspace = {True: 1, "P1": 1, "P0": 2, False: 0, None: 0}[pressure]
-    return _workload(f"twist_p{order}p{'0' if pspace == 2 else '1'}_{n}", coords, tets, order, pspace,
+    ptag = {0: "", 1: "p1", 2: "p0"}[pspace]
+    return _workload(f"twist_p{order}{ptag}_{n}", coords, tets, order, pspace,
                      dir_group, groups, empty.astype(np.int32), np.zeros(0), empty,
                      material, None, steps, n=n)
 
