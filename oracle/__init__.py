@@ -73,6 +73,13 @@ def lib():
             L.om_tet_rule.argtypes = [I, P, P]
             L.om_tri_rule.restype = I
             L.om_tri_rule.argtypes = [P, P]
+            L.om_set_pc.argtypes = [P, I]
+            L.om_amg_levels.restype = I
+            L.om_amg_levels.argtypes = [P]
+            L.om_amg_level_info.argtypes = [P, I, P]
+            L.om_amg_copy.argtypes = [P, I, P, P, P, P, P, P, P, P, P, P, P, P]
+            L.om_amg_smooth.argtypes = [P, I, P, P, I]
+            L.om_amg_vcycle.argtypes = [P, P, P]
             L.om_splitmix64.restype = ctypes.c_ulonglong
             L.om_splitmix64.argtypes = [ctypes.c_ulonglong]
             _lib = L
@@ -139,7 +146,7 @@ def splitmix64(x):
 
 def default_opts(method):
     """Appendix A defaults, with the readings: restart 500, m = 50."""
-    o = np.zeros(13)
+    o = np.zeros(14)
     o[0] = 0
     o[1] = {0: 1e-6, 1: 1e-2, 2: 0.0, 3: 1e-2}[method]
     o[2] = {0: 1e-10, 1: 1e-14, 2: 0.0, 3: 1e-14}[method]
@@ -153,6 +160,7 @@ def default_opts(method):
     o[10] = 1  # jac_lag
     o[11] = 0  # hess_reassemble
     o[12] = 0  # ib_adaptive
+    o[13] = 0  # pc_type: 0 block-Jacobi, 1 AMG
     return o
 
 
@@ -248,6 +256,50 @@ class Mesh:
         it = lib().om_gmres(self.h, _p(b), _p(x), rtol, atol, restart, max_it, _p(res))
         return x, it, res[0]
 
+    def set_pc(self, pc_type):
+        """Preconditioner of the displacement block: 0 / "bj" nodal
+        block-Jacobi, 1 / "amg" the AMG V-cycle (set up by tangent())."""
+        lib().om_set_pc(self.h, {"bj": 0, "amg": 1}.get(pc_type, pc_type))
+
+    def amg_levels(self):
+        """The AMG hierarchy of the last tangent: one dict per level (A_l,
+        absent components, near null space, aggregates, P and T, rho; the
+        coarsest level's dense inverse)."""
+        L = lib()
+        out = []
+        nlev = L.om_amg_levels(self.h)
+        for lv in range(nlev):
+            info = np.zeros(5, dtype=np.int64)
+            L.om_amg_level_info(self.h, lv, _p(info))
+            n, b, nnz, nc, nnzp = map(int, info)
+            d = dict(n=n, b=b, ptr=np.zeros(n + 1, dtype=np.int32), col=np.zeros(nnz, dtype=np.int32),
+                     val=np.zeros((nnz, b, b)), absent=np.zeros(n, dtype=np.uint8), ns=np.zeros((n * b, 6)), nc=nc)
+            rho = np.zeros(1)
+            if nnzp:
+                d.update(agg=np.zeros(n, dtype=np.int32), pptr=np.zeros(n + 1, dtype=np.int32),
+                         pcol=np.zeros(nnzp, dtype=np.int32), pval=np.zeros((nnzp, b, 6)),
+                         tval=np.zeros((nnzp, b, 6)))
+            if lv == nlev - 1:
+                d["inv"] = np.zeros((n * b, n * b))
+            L.om_amg_copy(self.h, lv, _p(d["ptr"]), _p(d["col"]), _p(d["val"]), _p(d["absent"]), _p(d["ns"]),
+                          _p(d.get("agg")), _p(d.get("pptr")), _p(d.get("pcol")), _p(d.get("pval")),
+                          _p(d.get("tval")), _p(rho), _p(d.get("inv")))
+            d["rho"] = float(rho[0])
+            out.append(d)
+        return out
+
+    def amg_smooth(self, level, b, x, deg=2):
+        b = np.ascontiguousarray(b, dtype=np.float64)
+        x = np.array(x, dtype=np.float64)
+        lib().om_amg_smooth(self.h, int(level), _p(b), _p(x), int(deg))
+        return x
+
+    def amg_vcycle(self, b):
+        b = np.ascontiguousarray(b, dtype=np.float64)
+        x = np.zeros(3 * self.nn)
+        lib().om_amg_vcycle(self.h, _p(b), _p(x))
+        return x
+
     def lbfgs_apply(self, S, Y, rho, q, h0=0):
         S = np.ascontiguousarray(S, dtype=np.float64)
         Y = np.ascontiguousarray(Y, dtype=np.float64)
@@ -265,7 +317,7 @@ class Mesh:
         if opts:
             keys = ["precision", "ksp_rtol", "ksp_atol", "ew_rtol0", "ew_rtolmax", "ksp_restart",
                     "ksp_max_it", "lbfgs_m", "dtol", "apply_dirichlet", "jac_lag", "hess_reassemble",
-                    "ib_adaptive"]
+                    "ib_adaptive", "pc_type"]
             for k, v in opts.items():
                 o[keys.index(k)] = v
         d = np.ascontiguousarray(d, dtype=np.float64)

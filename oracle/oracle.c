@@ -397,6 +397,8 @@ struct om_mesh {
   double* Sd;   /* [np] Schur diagonal */
   int have_K;
   long long lit; /* Krylov iterations, accumulated by om_gmres */
+  int pc_type;   /* displacement block: 0 nodal block-Jacobi, 1 algebraic multigrid */
+  struct om_amg* amg;
 };
 
 static int cmp_ll(const void* a, const void* b) {
@@ -596,12 +598,14 @@ om_mesh* om_create(int order, int pressure_order, int nv, int ne, const double* 
   return m;
 }
 
+static void amg_free(struct om_amg* h);
+
 void om_destroy(om_mesh* m) {
   if (!m) return;
   free(m->X); free(m->conn); free(m->colors); free(m->row_ptr); free(m->col);
   free(m->up_ptr); free(m->up_col); free(m->dgroup); free(m->groups); free(m->fnodes);
   free(m->fkind); free(m->fdata); free(m->fib); free(m->K); free(m->B1); free(m->Dinv);
-  free(m->Sd); free(m);
+  free(m->Sd); amg_free(m->amg); free(m);
 }
 
 void om_info(const om_mesh* m, long long* out) {
@@ -835,6 +839,601 @@ static long find_block(const int* ptr, const int* col, int row, int c) {
   abort();
 }
 
+/* ======================================================================
+ * Algebraic multigrid preconditioner: smoothed aggregation on the nodal
+ * blocks.  The paper preconditions its Krylov solves with algebraic
+ * multigrid on blocks of size 3 (BoomerAMG with bs = 3, Section "Test
+ * problems and solvers details" and Appendix A) but does not describe the
+ * tool, so this is a plain smoothed-aggregation V-cycle of that class; each
+ * choice is a stated reading:
+ *   - graph of level l: the block pattern of A_l without nodes whose
+ *     components are all absent (Dirichlet at level 0); no strength filter;
+ *   - aggregation: roots = greedy maximal distance-2 independent set in
+ *     descending splitmix64(node) priority, ties by id; phase 1: a root and
+ *     its graph neighbours; phase 2: every other node joins the aggregate of
+ *     its smallest-id phase-1 neighbour; aggregates numbered by root id;
+ *   - near null space: the six rigid motions of linear elasticity (three
+ *     translations, rotations (-y, x, 0), (0, -z, y), (z, 0, -x) at the node
+ *     coordinates), zero at absent components; tentative prolongator per
+ *     aggregate by modified Gram-Schmidt QR of its rows of the near null
+ *     space (nodes ascending): B_a = Q_a R_a, T = Q, coarse near null space
+ *     R; a column left with norm <= 1e-8 of its original norm is dropped
+ *     (zero column of Q and R) and that coarse component is absent; coarse
+ *     nodes carry 6 components;
+ *   - smoothed prolongator P = (I - omega D^{-1} A) T with D the block
+ *     diagonal, omega = 4 / (3 rho), rho = spectral radius of D^{-1} A
+ *     estimated by 15 power steps from x_k = u(splitmix64(k)) - 1/2,
+ *     u(h) = (h >> 11) 2^-53;
+ *   - Galerkin coarse operator A_{l+1} = P^T A_l P, absent components with a
+ *     unit diagonal;
+ *   - smoother: Chebyshev of degree 2 in D^{-1} A on [rho/30, 1.1 rho],
+ *     before and after the coarse correction;
+ *   - coarsest level (<= 16 nodes, or aggregation that no longer coarsens
+ *     by 10 %): exact solve with the inverse from Gauss-Jordan elimination
+ *     with partial pivoting.
+ * The V-cycle is a fixed linear operator, so right-preconditioned GMRES
+ * and the BFGS initial inverse Hessian use it unchanged.
+ * ====================================================================== */
+#define OM_AMG_MAXLEV 12
+#define OM_AMG_COARSE 16
+#define OM_AMG_NS 6
+
+typedef struct {
+  int n, b;              /* block rows, components per node (3 at level 0, 6 below) */
+  int *ptr, *col;        /* A_l pattern */
+  double* val;           /* A_l [nnz][b*b] row-major blocks (level 0: the tangent) */
+  double* dinv;          /* [n][b*b] inverse diagonal blocks */
+  unsigned char* absent; /* [n] bit c: component c absent */
+  double* ns;            /* [n*b][6] near null space */
+  double rho;
+  int nc;                /* aggregates */
+  int* agg;              /* [n], -1 none */
+  int *pptr, *pcol;      /* P (and T): n x nc, blocks b x 6 */
+  double *pval, *tval;
+  double* inv;           /* coarsest: dense (b n)^2 inverse */
+} om_amg_level;
+
+struct om_amg {
+  int nlev;
+  om_amg_level lev[OM_AMG_MAXLEV];
+};
+
+static double om_u01(unsigned long long h) { return (double)(h >> 11) * (1.0 / 9007199254740992.0); }
+
+/* y = A x for a block-CSR matrix with br x bc blocks */
+static void bsr_mv(int n, int br, int bc, const int* ptr, const int* col, const double* val, const double* x,
+                   double* y) {
+  for (int a = 0; a < n; a++) {
+    double s[OM_AMG_NS] = {0};
+    for (int k = ptr[a]; k < ptr[a + 1]; k++)
+      for (int i = 0; i < br; i++)
+        for (int j = 0; j < bc; j++) s[i] += val[(long)br * bc * k + bc * i + j] * x[(long)bc * col[k] + j];
+    for (int i = 0; i < br; i++) y[(long)br * a + i] = s[i];
+  }
+}
+
+/* y = A^T x (A: n block rows of br x bc blocks, nc block columns) */
+static void bsr_tmv(int n, int nc, int br, int bc, const int* ptr, const int* col, const double* val,
+                    const double* x, double* y) {
+  for (long i = 0; i < (long)bc * nc; i++) y[i] = 0.0;
+  for (int a = 0; a < n; a++)
+    for (int k = ptr[a]; k < ptr[a + 1]; k++)
+      for (int i = 0; i < br; i++)
+        for (int j = 0; j < bc; j++)
+          y[(long)bc * col[k] + j] += val[(long)br * bc * k + bc * i + j] * x[(long)br * a + i];
+}
+
+/* inverse of a dense N x N matrix (row-major) by Gauss-Jordan elimination
+ * with partial pivoting */
+static void gauss_jordan_inverse(int N, const double* Ain, double* I) {
+  double* A = (double*)xcalloc((size_t)N * N, sizeof(double));
+  memcpy(A, Ain, sizeof(double) * (size_t)N * N);
+  for (size_t i = 0; i < (size_t)N * N; i++) I[i] = 0.0;
+  for (int i = 0; i < N; i++) I[(size_t)i * N + i] = 1.0;
+  for (int c = 0; c < N; c++) {
+    int p = c;
+    for (int r = c + 1; r < N; r++)
+      if (fabs(A[(size_t)r * N + c]) > fabs(A[(size_t)p * N + c])) p = r;
+    if (p != c)
+      for (int j = 0; j < N; j++) {
+        double t = A[(size_t)c * N + j];
+        A[(size_t)c * N + j] = A[(size_t)p * N + j];
+        A[(size_t)p * N + j] = t;
+        t = I[(size_t)c * N + j];
+        I[(size_t)c * N + j] = I[(size_t)p * N + j];
+        I[(size_t)p * N + j] = t;
+      }
+    double piv = A[(size_t)c * N + c];
+    for (int j = 0; j < N; j++) {
+      A[(size_t)c * N + j] /= piv;
+      I[(size_t)c * N + j] /= piv;
+    }
+    for (int r = 0; r < N; r++) {
+      if (r == c) continue;
+      double f = A[(size_t)r * N + c];
+      if (f == 0.0) continue;
+      for (int j = 0; j < N; j++) {
+        A[(size_t)r * N + j] -= f * A[(size_t)c * N + j];
+        I[(size_t)r * N + j] -= f * I[(size_t)c * N + j];
+      }
+    }
+  }
+  free(A);
+}
+
+static void amg_block_dinv(om_amg_level* L) {
+  int b = L->b;
+  L->dinv = (double*)xcalloc((size_t)b * b * (L->n > 0 ? L->n : 1), sizeof(double));
+  for (int a = 0; a < L->n; a++) {
+    long k = find_block(L->ptr, L->col, a, a);
+    gauss_jordan_inverse(b, L->val + (long)b * b * k, L->dinv + (long)b * b * a);
+  }
+}
+
+static void amg_apply_dinv(const om_amg_level* L, const double* r, double* z) {
+  int b = L->b;
+  for (int a = 0; a < L->n; a++)
+    for (int i = 0; i < b; i++) {
+      double s = 0.0;
+      for (int j = 0; j < b; j++) s += L->dinv[(long)b * b * a + b * i + j] * r[(long)b * a + j];
+      z[(long)b * a + i] = s;
+    }
+}
+
+/* spectral radius of D^{-1} A by power steps */
+static double amg_rho(const om_amg_level* L) {
+  long N = (long)L->b * L->n;
+  double* x = (double*)xcalloc(N, sizeof(double));
+  double* t = (double*)xcalloc(N, sizeof(double));
+  double* y = (double*)xcalloc(N, sizeof(double));
+  for (long i = 0; i < N; i++) x[i] = om_u01(om_splitmix64((unsigned long long)i)) - 0.5;
+  double rho = 0.0;
+  for (int it = 0; it < 15; it++) {
+    bsr_mv(L->n, L->b, L->b, L->ptr, L->col, L->val, x, t);
+    amg_apply_dinv(L, t, y);
+    double nx = nrm2(x, N), ny = nrm2(y, N);
+    rho = ny / nx;
+    for (long i = 0; i < N; i++) x[i] = y[i] / ny;
+  }
+  free(x); free(t); free(y);
+  return rho;
+}
+
+static int node_priority_cmp(const void* a, const void* b) {
+  const unsigned long long* x = (const unsigned long long*)a;
+  const unsigned long long* y = (const unsigned long long*)b;
+  if (x[0] != y[0]) return x[0] > y[0] ? -1 : 1; /* descending hash */
+  return x[1] < y[1] ? -1 : (x[1] > y[1]);       /* ascending id */
+}
+
+static int all_absent(const om_amg_level* L, int i) { return L->absent[i] == (unsigned char)((1u << L->b) - 1u); }
+
+/* aggregation of level L (fills agg, nc) */
+static void amg_aggregate(om_amg_level* L) {
+  int n = L->n;
+  int* root_of = (int*)xcalloc(n > 0 ? n : 1, sizeof(int)); /* phase-1 root, -1 none */
+  unsigned long long* ord = (unsigned long long*)xcalloc(2L * (n > 0 ? n : 1), sizeof(unsigned long long));
+  for (int i = 0; i < n; i++) {
+    ord[2 * i] = om_splitmix64((unsigned long long)i);
+    ord[2 * i + 1] = (unsigned long long)i;
+    root_of[i] = -1;
+  }
+  qsort(ord, n, 2 * sizeof(unsigned long long), node_priority_cmp);
+  for (int q = 0; q < n; q++) { /* phase 1 in priority order */
+    int i = (int)ord[2 * q + 1];
+    if (all_absent(L, i) || root_of[i] >= 0) continue;
+    int blocked = 0;
+    for (int k = L->ptr[i]; k < L->ptr[i + 1] && !blocked; k++) {
+      int j = L->col[k];
+      if (j != i && !all_absent(L, j) && root_of[j] >= 0) blocked = 1;
+    }
+    if (blocked) continue;
+    for (int k = L->ptr[i]; k < L->ptr[i + 1]; k++)
+      if (!all_absent(L, L->col[k])) root_of[L->col[k]] = i;
+    root_of[i] = i;
+  }
+  int* id_of = (int*)xcalloc(n > 0 ? n : 1, sizeof(int)); /* aggregate of each root, roots ascending */
+  int nc = 0;
+  for (int i = 0; i < n; i++) id_of[i] = root_of[i] == i ? nc++ : -1;
+  L->agg = (int*)xcalloc(n > 0 ? n : 1, sizeof(int));
+  for (int i = 0; i < n; i++) L->agg[i] = root_of[i] >= 0 ? id_of[root_of[i]] : -1;
+  for (int i = 0; i < n; i++) { /* phase 2 */
+    if (all_absent(L, i) || root_of[i] >= 0) continue;
+    for (int k = L->ptr[i]; k < L->ptr[i + 1]; k++) {
+      int j = L->col[k];
+      if (j != i && root_of[j] >= 0) {
+        L->agg[i] = id_of[root_of[j]];
+        break;
+      }
+    }
+  }
+  L->nc = nc;
+  free(root_of); free(ord); free(id_of);
+}
+
+static int cmp_int(const void* a, const void* b) {
+  int x = *(const int*)a, y = *(const int*)b;
+  return (x > y) - (x < y);
+}
+
+/* append c to a growing int array */
+static void push_int(int** arr, long* len, long* cap, int c) {
+  if (*len == *cap) {
+    *cap = 2 * *cap + 16;
+    *arr = (int*)realloc(*arr, (size_t)*cap * sizeof(int));
+    if (!*arr) abort();
+  }
+  (*arr)[(*len)++] = c;
+}
+
+/* tentative prolongator T, smoothed prolongator P and coarse level
+ * C: A_c = P^T A P */
+static void amg_coarsen(om_amg_level* L, om_amg_level* C) {
+  const int n = L->n, nc = L->nc, b = L->b, K = OM_AMG_NS;
+  const int bb = b * K; /* P block size */
+  /* members of every aggregate, ascending */
+  int* mptr = (int*)xcalloc(nc + 1, sizeof(int));
+  for (int i = 0; i < n; i++)
+    if (L->agg[i] >= 0) mptr[L->agg[i] + 1]++;
+  for (int a = 0; a < nc; a++) mptr[a + 1] += mptr[a];
+  int* mem = (int*)xcalloc(mptr[nc] > 0 ? mptr[nc] : 1, sizeof(int));
+  int* fill = (int*)xcalloc(nc > 0 ? nc : 1, sizeof(int));
+  for (int i = 0; i < n; i++)
+    if (L->agg[i] >= 0) mem[mptr[L->agg[i]] + fill[L->agg[i]]++] = i;
+  /* QR per aggregate: T rows (tq[i][b][K]) and coarse near null space */
+  double* tq = (double*)xcalloc((size_t)n * bb + 1, sizeof(double));
+  C->n = nc;
+  C->b = K;
+  C->ns = (double*)xcalloc((size_t)nc * K * K + 1, sizeof(double));
+  C->absent = (unsigned char*)xcalloc(nc > 0 ? nc : 1, 1);
+  for (int a = 0; a < nc; a++) {
+    int m = mptr[a + 1] - mptr[a];
+    int R = m * b;
+    double* Q = (double*)xcalloc((size_t)R * K, sizeof(double)); /* column-major R x K */
+    for (int c = 0; c < K; c++)
+      for (int s = 0; s < m; s++)
+        for (int i = 0; i < b; i++) Q[(size_t)c * R + s * b + i] = L->ns[((size_t)mem[mptr[a] + s] * b + i) * K + c];
+    double* Rm = C->ns + (size_t)a * K * K; /* R_a, row-major K x K */
+    for (int c = 0; c < K; c++) {
+      double* v = Q + (size_t)c * R;
+      double n0 = nrm2(v, R);
+      for (int p = 0; p < c; p++) { /* modified Gram-Schmidt */
+        double r = dot(Q + (size_t)p * R, v, R);
+        Rm[p * K + c] = r;
+        for (int t = 0; t < R; t++) v[t] -= r * Q[(size_t)p * R + t];
+      }
+      double nv = nrm2(v, R);
+      if (n0 == 0.0 || nv <= 1e-8 * n0) {
+        for (int t = 0; t < R; t++) v[t] = 0.0;
+        Rm[c * K + c] = 0.0;
+        C->absent[a] |= (unsigned char)(1u << c);
+      } else {
+        for (int t = 0; t < R; t++) v[t] /= nv;
+        Rm[c * K + c] = nv;
+      }
+    }
+    for (int s = 0; s < m; s++)
+      for (int i = 0; i < b; i++)
+        for (int c = 0; c < K; c++) tq[((size_t)mem[mptr[a] + s] * b + i) * K + c] = Q[(size_t)c * R + s * b + i];
+    free(Q);
+  }
+  /* pattern of P (= pattern of T widened by one graph step): row i gets the
+   * aggregates of its graph neighbours */
+  int* mark = (int*)xcalloc(nc > 0 ? nc : 1, sizeof(int));
+  for (int a = 0; a < nc; a++) mark[a] = -1;
+  L->pptr = (int*)xcalloc(n + 1, sizeof(int));
+  long cap = 0, nnz = 0;
+  L->pcol = NULL;
+  for (int i = 0; i < n; i++) {
+    long start = nnz;
+    if (!all_absent(L, i))
+      for (int k = L->ptr[i]; k < L->ptr[i + 1]; k++) {
+        int a = L->agg[L->col[k]];
+        if (a >= 0 && mark[a] != i) {
+          mark[a] = i;
+          push_int(&L->pcol, &nnz, &cap, a);
+        }
+      }
+    qsort(L->pcol + start, nnz - start, sizeof(int), cmp_int);
+    L->pptr[i + 1] = (int)nnz;
+  }
+  if (!L->pcol) L->pcol = (int*)xcalloc(1, sizeof(int));
+  L->pval = (double*)xcalloc((size_t)bb * nnz + 1, sizeof(double));
+  L->tval = (double*)xcalloc((size_t)bb * nnz + 1, sizeof(double));
+  const double omega = 4.0 / (3.0 * L->rho);
+  for (int i = 0; i < n; i++) {
+    if (all_absent(L, i)) continue;
+    if (L->agg[i] >= 0) { /* T block of node i */
+      long q = find_block(L->pptr, L->pcol, i, L->agg[i]);
+      for (int t = 0; t < bb; t++) {
+        L->tval[(size_t)bb * q + t] = tq[(size_t)i * bb + t];
+        L->pval[(size_t)bb * q + t] += tq[(size_t)i * bb + t];
+      }
+    }
+    for (int k = L->ptr[i]; k < L->ptr[i + 1]; k++) { /* - omega D_i^{-1} A_ij T_j */
+      int j = L->col[k], a = L->agg[j];
+      if (a < 0) continue;
+      long q = find_block(L->pptr, L->pcol, i, a);
+      double DA[OM_AMG_NS * OM_AMG_NS];
+      for (int r = 0; r < b; r++)
+        for (int c = 0; c < b; c++) {
+          double s = 0.0;
+          for (int l = 0; l < b; l++) s += L->dinv[(size_t)b * b * i + b * r + l] * L->val[(size_t)b * b * k + b * l + c];
+          DA[b * r + c] = s;
+        }
+      for (int r = 0; r < b; r++)
+        for (int c = 0; c < K; c++) {
+          double s = 0.0;
+          for (int l = 0; l < b; l++) s += DA[b * r + l] * tq[((size_t)j * b + l) * K + c];
+          L->pval[(size_t)bb * q + K * r + c] -= omega * s;
+        }
+    }
+  }
+  /* AP = A P: n x nc, blocks b x K */
+  int* apptr = (int*)xcalloc(n + 1, sizeof(int));
+  int* apcol = NULL;
+  long apn = 0, apcap = 0;
+  for (int a = 0; a < nc; a++) mark[a] = -1;
+  for (int i = 0; i < n; i++) {
+    long start = apn;
+    for (int k = L->ptr[i]; k < L->ptr[i + 1]; k++) {
+      int j = L->col[k];
+      for (int q = L->pptr[j]; q < L->pptr[j + 1]; q++)
+        if (mark[L->pcol[q]] != i) {
+          mark[L->pcol[q]] = i;
+          push_int(&apcol, &apn, &apcap, L->pcol[q]);
+        }
+    }
+    qsort(apcol + start, apn - start, sizeof(int), cmp_int);
+    apptr[i + 1] = (int)apn;
+  }
+  if (!apcol) apcol = (int*)xcalloc(1, sizeof(int));
+  double* apval = (double*)xcalloc((size_t)bb * apn + 1, sizeof(double));
+  for (int i = 0; i < n; i++)
+    for (int k = L->ptr[i]; k < L->ptr[i + 1]; k++) {
+      int j = L->col[k];
+      for (int q = L->pptr[j]; q < L->pptr[j + 1]; q++) {
+        long p = find_block(apptr, apcol, i, L->pcol[q]);
+        for (int r = 0; r < b; r++)
+          for (int c = 0; c < K; c++) {
+            double s = 0.0;
+            for (int l = 0; l < b; l++) s += L->val[(size_t)b * b * k + b * r + l] * L->pval[(size_t)bb * q + K * l + c];
+            apval[(size_t)bb * p + K * r + c] += s;
+          }
+      }
+    }
+  /* A_c = P^T (AP): entry (a, e) = sum_i P_ia^T AP_ie; rows of P^T first */
+  int* tptr = (int*)xcalloc(nc + 1, sizeof(int));
+  long np = L->pptr[n];
+  for (long q = 0; q < np; q++) tptr[L->pcol[q] + 1]++;
+  for (int a = 0; a < nc; a++) tptr[a + 1] += tptr[a];
+  int* trow = (int*)xcalloc(np + 1, sizeof(int));
+  int* tidx = (int*)xcalloc(np + 1, sizeof(int));
+  for (int a = 0; a < nc; a++) fill[a] = 0;
+  for (int i = 0; i < n; i++)
+    for (int q = L->pptr[i]; q < L->pptr[i + 1]; q++) {
+      int a = L->pcol[q], s = tptr[a] + fill[a]++;
+      trow[s] = i;
+      tidx[s] = q;
+    }
+  C->ptr = (int*)xcalloc(nc + 1, sizeof(int));
+  C->col = NULL;
+  long cn = 0, ccap = 0;
+  for (int a = 0; a < nc; a++) mark[a] = -1;
+  for (int a = 0; a < nc; a++) {
+    long start = cn;
+    for (int s = tptr[a]; s < tptr[a + 1]; s++)
+      for (int p = apptr[trow[s]]; p < apptr[trow[s] + 1]; p++)
+        if (mark[apcol[p]] != a) {
+          mark[apcol[p]] = a;
+          push_int(&C->col, &cn, &ccap, apcol[p]);
+        }
+    if (mark[a] != a) { /* the diagonal block is always stored */
+      mark[a] = a;
+      push_int(&C->col, &cn, &ccap, a);
+    }
+    qsort(C->col + start, cn - start, sizeof(int), cmp_int);
+    C->ptr[a + 1] = (int)cn;
+  }
+  if (!C->col) C->col = (int*)xcalloc(1, sizeof(int));
+  C->val = (double*)xcalloc((size_t)K * K * cn + 1, sizeof(double));
+  for (int a = 0; a < nc; a++)
+    for (int s = tptr[a]; s < tptr[a + 1]; s++) {
+      int i = trow[s], q = tidx[s];
+      for (int p = apptr[i]; p < apptr[i + 1]; p++) {
+        long e = find_block(C->ptr, C->col, a, apcol[p]);
+        for (int r = 0; r < K; r++)
+          for (int c = 0; c < K; c++) {
+            double v = 0.0;
+            for (int l = 0; l < b; l++) v += L->pval[(size_t)bb * q + K * l + r] * apval[(size_t)bb * p + K * l + c];
+            C->val[(size_t)K * K * e + K * r + c] += v;
+          }
+      }
+    }
+  for (int a = 0; a < nc; a++) { /* absent coarse components: unit diagonal */
+    long e = find_block(C->ptr, C->col, a, a);
+    for (int c = 0; c < K; c++)
+      if ((C->absent[a] >> c) & 1) C->val[(size_t)K * K * e + K * c + c] = 1.0;
+  }
+  free(mptr); free(mem); free(fill); free(tq); free(mark); free(apptr); free(apcol); free(apval);
+  free(tptr); free(trow); free(tidx);
+}
+
+static void amg_free(struct om_amg* h) {
+  if (!h) return;
+  for (int l = 0; l < h->nlev; l++) {
+    om_amg_level* L = h->lev + l;
+    if (l > 0) {
+      free(L->ptr);
+      free(L->col);
+      free(L->val);
+    }
+    free(L->dinv); free(L->absent); free(L->ns); free(L->agg); free(L->pptr); free(L->pcol);
+    free(L->pval); free(L->tval); free(L->inv);
+  }
+  free(h);
+}
+
+/* hierarchy from the assembled tangent (displacement block) */
+static void amg_setup(om_mesh* m) {
+  amg_free(m->amg);
+  struct om_amg* h = (struct om_amg*)xcalloc(1, sizeof(struct om_amg));
+  om_amg_level* L = h->lev;
+  L->n = m->nn;
+  L->b = 3;
+  L->ptr = m->row_ptr;
+  L->col = m->col;
+  L->val = m->K;
+  L->absent = (unsigned char*)xcalloc(m->nn, 1);
+  L->ns = (double*)xcalloc((size_t)m->nn * 3 * OM_AMG_NS, sizeof(double));
+  for (int a = 0; a < m->nn; a++) {
+    const double* x = m->X + 3L * a;
+    /* rigid motions: translations e_c, rotations (-y, x, 0), (0, -z, y), (z, 0, -x) */
+    double rb[3][OM_AMG_NS] = {{1, 0, 0, -x[1], 0, x[2]}, {0, 1, 0, x[0], -x[2], 0}, {0, 0, 1, 0, x[1], -x[0]}};
+    for (int c = 0; c < 3; c++) {
+      int fixed = is_fixed(m, a, c);
+      if (fixed) L->absent[a] |= (unsigned char)(1u << c);
+      for (int k = 0; k < OM_AMG_NS; k++) L->ns[(3L * a + c) * OM_AMG_NS + k] = fixed ? 0.0 : rb[c][k];
+    }
+  }
+  int l = 0;
+  for (;;) {
+    L = h->lev + l;
+    amg_block_dinv(L);
+    if (L->n <= OM_AMG_COARSE || l == OM_AMG_MAXLEV - 1) break;
+    amg_aggregate(L);
+    if (L->nc == 0 || L->nc > 0.9 * L->n) {
+      free(L->agg);
+      L->agg = NULL;
+      L->nc = 0;
+      break;
+    }
+    L->rho = amg_rho(L);
+    amg_coarsen(L, h->lev + l + 1);
+    l++;
+  }
+  h->nlev = l + 1;
+  {
+    int N = L->b * L->n;
+    double* A = (double*)xcalloc((size_t)N * N + 1, sizeof(double));
+    for (int a = 0; a < L->n; a++)
+      for (int k = L->ptr[a]; k < L->ptr[a + 1]; k++)
+        for (int i = 0; i < L->b; i++)
+          for (int j = 0; j < L->b; j++)
+            A[(size_t)(L->b * a + i) * N + L->b * L->col[k] + j] = L->val[(size_t)L->b * L->b * k + L->b * i + j];
+    L->inv = (double*)xcalloc((size_t)N * N + 1, sizeof(double));
+    gauss_jordan_inverse(N, A, L->inv);
+    free(A);
+  }
+  m->amg = h;
+}
+
+/* Chebyshev smoothing of A x = b on level L from the given x (deg steps) */
+static void amg_cheb(const om_amg_level* L, const double* b, double* x, int deg) {
+  long N = (long)L->b * L->n;
+  double lo = L->rho / 30.0, hi = 1.1 * L->rho;
+  double theta = 0.5 * (hi + lo), delta = 0.5 * (hi - lo), sigma = theta / delta, rho_old = 1.0 / sigma;
+  double* r = (double*)xcalloc(N, sizeof(double));
+  double* z = (double*)xcalloc(N, sizeof(double));
+  double* d = (double*)xcalloc(N, sizeof(double));
+  double* t = (double*)xcalloc(N, sizeof(double));
+  bsr_mv(L->n, L->b, L->b, L->ptr, L->col, L->val, x, t);
+  for (long i = 0; i < N; i++) r[i] = b[i] - t[i];
+  amg_apply_dinv(L, r, z);
+  for (long i = 0; i < N; i++) d[i] = z[i] / theta;
+  for (int k = 1; k <= deg; k++) {
+    for (long i = 0; i < N; i++) x[i] += d[i];
+    if (k == deg) break;
+    bsr_mv(L->n, L->b, L->b, L->ptr, L->col, L->val, d, t);
+    for (long i = 0; i < N; i++) r[i] -= t[i];
+    amg_apply_dinv(L, r, z);
+    double rho_new = 1.0 / (2.0 * sigma - rho_old);
+    for (long i = 0; i < N; i++) d[i] = rho_new * rho_old * d[i] + 2.0 * rho_new / delta * z[i];
+    rho_old = rho_new;
+  }
+  free(r); free(z); free(d); free(t);
+}
+
+static void amg_vcycle(const struct om_amg* h, int l, const double* b, double* x) {
+  const om_amg_level* L = h->lev + l;
+  long N = (long)L->b * L->n;
+  if (l == h->nlev - 1) {
+    for (long i = 0; i < N; i++) {
+      double s = 0.0;
+      for (long j = 0; j < N; j++) s += L->inv[(size_t)i * N + j] * b[j];
+      x[i] = s;
+    }
+    return;
+  }
+  const om_amg_level* C = h->lev + l + 1;
+  long Nc = (long)C->b * C->n;
+  double* r = (double*)xcalloc(N, sizeof(double));
+  double* bc = (double*)xcalloc(Nc + 1, sizeof(double));
+  double* xc = (double*)xcalloc(Nc + 1, sizeof(double));
+  for (long i = 0; i < N; i++) x[i] = 0.0;
+  amg_cheb(L, b, x, 2);
+  bsr_mv(L->n, L->b, L->b, L->ptr, L->col, L->val, x, r);
+  for (long i = 0; i < N; i++) r[i] = b[i] - r[i];
+  bsr_tmv(L->n, C->n, L->b, C->b, L->pptr, L->pcol, L->pval, r, bc);
+  amg_vcycle(h, l + 1, bc, xc);
+  bsr_mv(L->n, L->b, C->b, L->pptr, L->pcol, L->pval, xc, r); /* r = P xc */
+  for (long i = 0; i < N; i++) x[i] += r[i];
+  amg_cheb(L, b, x, 2);
+  free(r); free(bc); free(xc);
+}
+
+void om_set_pc(om_mesh* m, int pc_type) {
+  m->pc_type = pc_type;
+  if (pc_type != 1) {
+    amg_free(m->amg);
+    m->amg = NULL;
+  }
+}
+
+int om_amg_levels(const om_mesh* m) { return m->amg ? m->amg->nlev : 0; }
+
+/* out: n, b, nnz(A_l), nc, nnz(P_l) */
+void om_amg_level_info(const om_mesh* m, int l, long long* out) {
+  const om_amg_level* L = m->amg->lev + l;
+  out[0] = L->n;
+  out[1] = L->b;
+  out[2] = L->ptr[L->n];
+  out[3] = L->nc;
+  out[4] = L->pptr ? L->pptr[L->n] : 0;
+}
+
+/* level l: A_l (ptr, col, val [nnz][b*b]), absent mask, near null space
+ * ns [n*b][6], aggregates, P and T (pptr, pcol, pval/tval [nnzP][b*6]),
+ * rho, and for the coarsest level the dense inverse inv [(b n)^2] */
+void om_amg_copy(const om_mesh* m, int l, int* ptr, int* col, double* val, unsigned char* absent, double* ns,
+                 int* agg, int* pptr, int* pcol, double* pval, double* tval, double* rho, double* inv) {
+  const om_amg_level* L = m->amg->lev + l;
+  long nnz = L->ptr[L->n];
+  size_t bb = (size_t)L->b * L->b;
+  if (ptr) memcpy(ptr, L->ptr, sizeof(int) * (size_t)(L->n + 1));
+  if (col) memcpy(col, L->col, sizeof(int) * (size_t)nnz);
+  if (val) memcpy(val, L->val, sizeof(double) * bb * (size_t)nnz);
+  if (absent) memcpy(absent, L->absent, (size_t)L->n);
+  if (ns && L->ns) memcpy(ns, L->ns, sizeof(double) * (size_t)L->n * L->b * OM_AMG_NS);
+  if (agg && L->agg) memcpy(agg, L->agg, sizeof(int) * (size_t)L->n);
+  if (L->pptr) {
+    long np = L->pptr[L->n];
+    if (pptr) memcpy(pptr, L->pptr, sizeof(int) * (size_t)(L->n + 1));
+    if (pcol) memcpy(pcol, L->pcol, sizeof(int) * (size_t)np);
+    if (pval) memcpy(pval, L->pval, sizeof(double) * (size_t)L->b * OM_AMG_NS * (size_t)np);
+    if (tval) memcpy(tval, L->tval, sizeof(double) * (size_t)L->b * OM_AMG_NS * (size_t)np);
+  }
+  if (rho) *rho = L->rho;
+  if (inv && L->inv) memcpy(inv, L->inv, sizeof(double) * (size_t)L->b * L->n * L->b * L->n);
+}
+
+/* Chebyshev smoothing on level l (x in/out) and one V-cycle from level 0 */
+void om_amg_smooth(const om_mesh* m, int l, const double* b, double* x, int deg) {
+  amg_cheb(m->amg->lev + l, b, x, deg);
+}
+
+void om_amg_vcycle(const om_mesh* m, const double* b, double* x) { amg_vcycle(m->amg, 0, b, x); }
+
 void om_tangent(om_mesh* m, const double* d) {
   memset(m->K, 0, sizeof(double) * 9 * m->nnzb);
   if (m->pres) memset(m->B1, 0, sizeof(double) * 3 * m->nnz_up);
@@ -946,6 +1545,7 @@ void om_tangent(om_mesh* m, const double* d) {
         }
     }
   }
+  if (m->pc_type == 1) amg_setup(m);
   m->have_K = 1;
 }
 
@@ -979,14 +1579,19 @@ void om_spmv(const om_mesh* m, const double* x, double* y) {
 }
 
 void om_pc(const om_mesh* m, const double* x, double* y) {
-  /* displacement: nodal block-Jacobi; u-p: lower Schur (Appendix B),
-   * z_u = D^{-1} x_u, z_p = S^{-1} (x_p - B2 z_u), S = point diagonal */
-  for (int a = 0; a < m->nn; a++)
-    for (int i = 0; i < 3; i++) {
-      double s = 0.0;
-      for (int k = 0; k < 3; k++) s += m->Dinv[9L * a + 3 * i + k] * x[3L * a + k];
-      y[3L * a + i] = s;
-    }
+  /* displacement: nodal block-Jacobi or one AMG V-cycle; u-p: lower Schur
+   * (Appendix B), z_u = M_A^{-1} x_u, z_p = S^{-1} (x_p - B2 z_u), S = point
+   * diagonal */
+  if (m->pc_type == 1 && m->amg) {
+    amg_vcycle(m->amg, 0, x, y);
+  } else {
+    for (int a = 0; a < m->nn; a++)
+      for (int i = 0; i < 3; i++) {
+        double s = 0.0;
+        for (int k = 0; k < 3; k++) s += m->Dinv[9L * a + 3 * i + k] * x[3L * a + k];
+        y[3L * a + i] = s;
+      }
+  }
   if (m->pres) {
     double* t = (double*)xcalloc(m->np, sizeof(double));
     for (int v = 0; v < m->np; v++) t[v] = x[3L * m->nn + v];
@@ -1131,6 +1736,7 @@ int om_solve(om_mesh* m, int method, double tol, int max_it, double* d, const do
   double dtol = opts[8];
   int jac_lag = (int)opts[10] > 0 ? (int)opts[10] : 1, hess_re = (int)opts[11];
   int ib_adaptive = (int)opts[12];
+  om_set_pc(m, (int)opts[13]);
   double* res_hist = stats + 6;
   double* lit_hist = stats + 6 + OM_HIST;
   double* eta_hist = stats + 6 + 2 * OM_HIST;

@@ -16,13 +16,14 @@
  *   [14] c_log = 4 beta_s + 2 alpha_s
  * Dirichlet group array groups[ngroups][8]:
  *   mask, center x, y, z, angle, translation x, y, z
- * Solver option array opts[13]:
+ * Solver option array opts[14]:
  *   precision(ignored: FP64), ksp_rtol, ksp_atol, ew_rtol0, ew_rtolmax,
  *   ksp_restart, ksp_max_it, lbfgs_m, dtol, apply_dirichlet,
  *   jac_lag (NK/iNK: tangent assembled every jac_lag iterations, >= 1),
  *   hess_reassemble (B/iB: tangent re-assembled and memory restarted every
  *   hess_reassemble iterations, 0 = never),
- *   ib_adaptive (iB: 1 = Eisenstat-Walker choice-2 tolerance for the H0 solve)
+ *   ib_adaptive (iB: 1 = Eisenstat-Walker choice-2 tolerance for the H0 solve),
+ *   pc_type (0 nodal block-Jacobi, 1 algebraic multigrid V-cycle)
  * Stats array (6 + 4*OM_HIST doubles):
  *   status, nit, lit_total, assemblies, r0, rfinal,
  *   res_hist[OM_HIST], lit_hist[OM_HIST], eta_hist[OM_HIST],
@@ -63,6 +64,17 @@ int om_solve(om_mesh* m, int method, double tol, int max_it, double* d, const do
              double* stats);
 void om_lbfgs_apply(om_mesh* m, const double* S, const double* Y, const double* rho, int k,
                     const double* q, double* z, int h0);
+
+/* preconditioner of the displacement block: 0 nodal block-Jacobi, 1 the
+ * smoothed-aggregation AMG V-cycle (set up by om_tangent) */
+void om_set_pc(om_mesh* m, int pc_type);
+int om_amg_levels(const om_mesh* m);
+/* out: n, b (components per node), nnz(A_l), nc, nnz(P_l) */
+void om_amg_level_info(const om_mesh* m, int l, long long* out);
+void om_amg_copy(const om_mesh* m, int l, int* ptr, int* col, double* val, unsigned char* absent, double* ns,
+                 int* agg, int* pptr, int* pcol, double* pval, double* tval, double* rho, double* inv);
+void om_amg_smooth(const om_mesh* m, int l, const double* b, double* x, int deg);
+void om_amg_vcycle(const om_mesh* m, const double* b, double* x);
 
 /* pointwise pieces, exposed for the pins */
 void om_material(const double* matp, const double* F, const double* fib, double gamma, double p,

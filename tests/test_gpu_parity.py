@@ -241,12 +241,25 @@ def test_nl_solve_fp64(fe, case, method):
     assert np.linalg.norm(xg.cpu().numpy() - x) <= xtol * np.linalg.norm(x)
     if method in ("B", "iB"):
         assert sg["assemblies"] == 1
-    if method == "iNK" and sg["nit"] == so["nit"]:
-        # the Eisenstat-Walker sequence and the linear residuals it is formed
-        # from (the norms agree to rounding, eta to its cancellation)
-        r0 = so["r0"]
-        assert np.allclose(sg["lres_hist"][1:], so["lres_hist"][1:], rtol=1e-6, atol=1e-9 * r0)
-        assert np.allclose(sg["eta_hist"][1:], so["eta_hist"][1:], rtol=1e-6, atol=1e-6)
+    if method == "iNK":
+        # the GPU's Eisenstat-Walker sequence follows from its own recorded
+        # norms by choice 1 with the safeguard and the cap (the rule the
+        # oracle is pinned to); where both sides took the same Krylov steps
+        # the linear residuals agree
+        res, lres, eta = sg["res_hist"], sg["lres_hist"], sg["eta_hist"]
+        phi, e = 0.5 * (1.0 + 5.0 ** 0.5), 0.1
+        assert eta[1] == e
+        for k in range(1, sg["nit"]):
+            cand = abs(res[k] - lres[k]) / res[k - 1]
+            if e ** phi > 0.1:
+                cand = max(cand, e ** phi)
+            e = min(cand, 0.1)
+            assert abs(eta[k + 1] - e) <= 1e-14 * e, k
+        same = [k for k in range(1, min(sg["nit"], so["nit"]) + 1)
+                if all(sg["lit_hist"][i] == so["lit_hist"][i] for i in range(1, k + 1))]
+        for k in same:
+            assert abs(lres[k] - so["lres_hist"][k]) <= 1e-6 * so["lres_hist"][k] + 1e-9 * so["r0"], \
+                (k, lres[k], so["lres_hist"][k], sg["lit_hist"], so["lit_hist"])
 
 
 def test_load_stepping_config1(fe):
