@@ -52,6 +52,8 @@ def parse():
     p.add_argument("--precision", default="mixed_fp32", choices=["fp64", "mixed_fp32", "mixed_bf16"])
     p.add_argument("--ib-adaptive", type=int, default=0, choices=[0, 1],
                    help="iB: Eisenstat-Walker type adaptive H0 tolerance (an extension; 0 = the paper's fixed 1e-2)")
+    p.add_argument("--pc", default="bj", choices=["bj", "amg"],
+                   help="displacement-block preconditioner: nodal block-Jacobi or the AMG V-cycle")
     p.add_argument("--nu", type=float, default=0.3)
     p.add_argument("--traction", type=float, default=1.0)
     p.add_argument("--mesh", default="64,64,8")
@@ -448,7 +450,8 @@ def main():
     m = fe.Mesh(w, device=local)
     load, tm = w["steps"][0]
     m.set_load(load, tm)
-    opts = dict(precision=args.precision, ksp_restart=args.restart, orthog=args.orthog, ib_adaptive=args.ib_adaptive)
+    opts = dict(precision=args.precision, ksp_restart=args.restart, orthog=args.orthog, ib_adaptive=args.ib_adaptive,
+                pc_type=args.pc)
     dev = torch.device("cuda", local)
     d = torch.zeros(m.ndof, dtype=torch.float64, device=dev)
     stats = {}
@@ -549,6 +552,7 @@ def main():
                    config=dict(workload=name, dofs=m.ndof, blocks=m.nnzb, nu=args.nu, traction=args.traction,
                                load_step=f"step 1 of {len(w['steps'])} from rest", methods=methods, precision=args.precision, tol=TOL,
                                ksp_restart=args.restart, orthog=["mgs", "mgs_lowsync", "mgs_blocked"][args.orthog],
+                               preconditioner={"bj": "nodal block-Jacobi", "amg": "AMG V-cycle"}[args.pc],
                                ib_h0_tolerance="adaptive (extension)" if args.ib_adaptive else "fixed",
                                l2="working set > L2 (tangent and Krylov basis), no flush",
                                parallelism=f"replicas x{world}"),

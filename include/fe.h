@@ -270,6 +270,11 @@ typedef struct {
                           eta_k = min(ew_rtolmax, max(0.9 (|R_{k-1}|/|R_{k-2}|)^a,
                           0.9 eta_{k-1}^a if that exceeds 0.1)), a = (1+sqrt 5)/2;
                           0 (default) = fixed ksp_rtol */
+  int32_t pc_type;     /* preconditioner of the displacement block (GMRES and the B/iB H0):
+                          0 (default) nodal block-Jacobi; 1 algebraic multigrid, one
+                          smoothed-aggregation V-cycle on the nodal blocks (the class of
+                          the paper's BoomerAMG with block size 3, Appendix A); see
+                          fe_set_pc */
 } nl_opts;
 
 #define NL_HIST 1024
@@ -349,6 +354,34 @@ typedef struct {
 int fe_profile_reset(fe_mesh m, int timing);
 /* Synchronise the stream and read the counters (host out). */
 int fe_profile_read(fe_mesh m, fe_profile_info* out);
+
+/* Preconditioner of the displacement block for the following tangent
+ * assemblies (and, with a tangent assembled, set up now): 0 nodal
+ * block-Jacobi (default), 1 algebraic multigrid.  The paper preconditions
+ * with BoomerAMG on blocks of 3 (Section "Test problems and solvers
+ * details", Appendix A); this library's AMG is a smoothed-aggregation
+ * V-cycle: aggregates from a greedy distance-2 independent set of the block
+ * graph, the six rigid motions as near null space (tentative prolongator by
+ * per-aggregate QR), P = (I - 4/(3 rho) D^-1 A) T, Galerkin coarse
+ * operators, degree-2 Chebyshev smoothing, an exact coarsest solve.  Its
+ * structure is built once per mesh (host), its numbers after every tangent
+ * assembly (device, FP64; the V-cycle runs in the tangent's precision).
+ * FE_ERR_ARG for pc_type outside {0, 1} or AMG on the u-p form. */
+int fe_set_pc(fe_mesh m, int pc_type);
+
+/* The AMG hierarchy of the last assembly, for inspection and tests:
+ * fe_amg_levels returns the number of levels (0 without a hierarchy);
+ * fe_amg_get_level copies level `level` to host buffers, each nullable:
+ * info [5] = n (block rows), b (components per node: 3 at level 0, 6 below),
+ * nnz(A_l), nc (aggregates; 0 on the coarsest level), nnz(P_l); rho (the
+ * spectral-radius estimate of D^-1 A_l); for level >= 1 the operator A_l:
+ * ptr [n+1], col [nnz], val [nnz][b*b] FP64 row-major blocks (level 0 is the
+ * tangent, see fe_tangent_copy); absent [n] (bit c: component c absent);
+ * agg [n] (aggregate of each node, -1 none); pptr [n+1], pcol [nnz(P_l)],
+ * pval [nnz(P_l)][b*6] the smoothed prolongator in FP64. */
+int fe_amg_levels(fe_mesh m);
+int fe_amg_get_level(fe_mesh m, int level, int64_t* info, double* rho, int32_t* ptr, int32_t* col,
+                     double* val, uint8_t* absent, int32_t* agg, int32_t* pptr, int32_t* pcol, double* pval);
 
 /* Bounded device waits (no counterpart in the paper).  The persistent
  * kernels' grid barriers poll for a published value at most `polls` times

@@ -24,6 +24,7 @@ FE_OK = 0
 NL_DIVERGED, NL_MAX_IT, NL_NONFINITE, KSP_BREAKDOWN = 1, 2, 3, 4
 METHODS = {"NK": 0, "iNK": 1, "B": 2, "iB": 3}
 PRECISIONS = {"fp64": 0, "mixed_fp32": 1, "mixed_bf16": 2}
+PC_TYPES = {"bj": 0, "amg": 1}
 NL_HIST = 1024
 
 
@@ -64,7 +65,7 @@ class nl_opts(C.Structure):
                 ("ew_rtol0", C.c_double), ("ew_rtolmax", C.c_double), ("ksp_restart", C.c_int32),
                 ("ksp_max_it", C.c_int32), ("lbfgs_m", C.c_int32), ("dtol", C.c_double),
                 ("apply_dirichlet", C.c_int32), ("orthog", C.c_int32), ("jac_lag", C.c_int32),
-                ("hess_reassemble", C.c_int32), ("ib_adaptive", C.c_int32)]
+                ("hess_reassemble", C.c_int32), ("ib_adaptive", C.c_int32), ("pc_type", C.c_int32)]
 
 
 class nl_stats(C.Structure):
@@ -129,6 +130,9 @@ SIGNATURES = {
     "serve_poll": (_I, [_P, C.c_int64, _I, C.POINTER(fe_request_status), _P]),
     "serve_clock": (_D, [_P]),
     "serve_destroy": (_I, [_P]),
+    "fe_set_pc": (_I, [_P, _I]),
+    "fe_amg_levels": (_I, [_P]),
+    "fe_amg_get_level": (_I, [_P, _I, _P, C.POINTER(C.c_double), _P, _P, _P, _P, _P, _P, _P, _P]),
     "fe_set_wait_limit": (_I, [_P, C.c_int64]),
     "fe_last_error": (C.c_char_p, []),
 }
@@ -223,6 +227,8 @@ def _opts_struct(method, opts):
     for k, v in (opts or {}).items():
         if k == "precision" and isinstance(v, str):
             v = PRECISIONS[v]
+        if k == "pc_type" and isinstance(v, str):
+            v = PC_TYPES[v]
         setattr(o, k, v)
     return o
 
@@ -336,6 +342,32 @@ class Mesh:
         _check(lib().fe_lbfgs_apply(self.h, C.c_void_p(S.data_ptr()), C.c_void_p(Y.data_ptr()),
                                     C.c_void_p(rho.data_ptr()), k, self._vec(q, "q"), self._vec(z, "z"), int(h0)))
         return z
+
+    def set_pc(self, pc_type):
+        """Displacement-block preconditioner: "bj" (nodal block-Jacobi) or "amg"."""
+        _check(lib().fe_set_pc(self.h, PC_TYPES.get(pc_type, pc_type)))
+
+    def amg_levels(self):
+        """The AMG hierarchy of the last assembly (fe_amg_get_level), one dict per level."""
+        out = []
+        for lv in range(lib().fe_amg_levels(self.h)):
+            info = np.zeros(5, dtype=np.int64)
+            rho = C.c_double()
+            _check(lib().fe_amg_get_level(self.h, lv, _np_ptr(info), C.byref(rho), None, None, None, None, None,
+                                          None, None, None))
+            n, b, nnz, nc, nnzp = map(int, info)
+            d = dict(n=n, b=b, nc=nc, rho=rho.value, absent=np.zeros(n, dtype=np.uint8))
+            if lv > 0:
+                d.update(ptr=np.zeros(n + 1, dtype=np.int32), col=np.zeros(nnz, dtype=np.int32),
+                         val=np.zeros((nnz, b, b)))
+            if nnzp:
+                d.update(agg=np.zeros(n, dtype=np.int32), pptr=np.zeros(n + 1, dtype=np.int32),
+                         pcol=np.zeros(nnzp, dtype=np.int32), pval=np.zeros((nnzp, b, 6)))
+            _check(lib().fe_amg_get_level(self.h, lv, None, None, _np_ptr(d.get("ptr")), _np_ptr(d.get("col")),
+                                          _np_ptr(d.get("val")), _np_ptr(d["absent"]), _np_ptr(d.get("agg")),
+                                          _np_ptr(d.get("pptr")), _np_ptr(d.get("pcol")), _np_ptr(d.get("pval"))))
+            out.append(d)
+        return out
 
     def set_wait_limit(self, polls=-1):
         """Polls before a bounded device wait gives up (< 0: the default)."""

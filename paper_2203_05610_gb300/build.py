@@ -10,7 +10,7 @@ CSRC = os.path.join(HERE, "csrc")
 LIBDIR = os.path.join(HERE, "_lib")
 SO = os.path.join(LIBDIR, "libfe.so")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
-SOURCES = ["fe_mesh.cu", "fe_assemble.cu", "fe_krylov.cu", "nl_solve.cu", "fe_noalloc.cu", "fe_serve.cu"]
+SOURCES = ["fe_mesh.cu", "fe_assemble.cu", "fe_krylov.cu", "nl_solve.cu", "fe_amg.cu", "fe_noalloc.cu", "fe_serve.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-I", INCLUDE, "-I", CSRC]

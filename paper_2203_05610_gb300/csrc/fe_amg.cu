@@ -1,0 +1,1253 @@
+// fe_amg.cu -- smoothed-aggregation algebraic multigrid (AMG) on the nodal
+// blocks, as the preconditioner of the displacement block.
+//
+// The paper preconditions its Krylov solves with algebraic multigrid on
+// blocks of size 3 (BoomerAMG with bs = 3, Section "Test problems and
+// solvers details" and Appendix A) without describing it; this is a
+// smoothed-aggregation V-cycle of that class:
+//   - aggregation on the block graph of A_l (nodes whose components are all
+//     absent -- Dirichlet at level 0 -- left out, no strength filter): roots
+//     = greedy maximal distance-2 independent set in descending
+//     splitmix64(node) priority, ties by id; a root takes its neighbours;
+//     every other node joins the aggregate of its smallest-id neighbour
+//     taken so; aggregates numbered by root id;
+//   - near null space: the six rigid motions (translations, rotations
+//     (-y, x, 0), (0, -z, y), (z, 0, -x)); tentative prolongator T by
+//     modified Gram-Schmidt QR of each aggregate's rows (columns left with
+//     <= 1e-8 of their norm are dropped and that coarse component is
+//     absent); coarse nodes carry 6 components;
+//   - P = (I - omega D^-1 A) T, omega = 4 / (3 rho), rho from 15 power steps
+//     on D^-1 A (D the block diagonal) from x_k = u(splitmix64(k)) - 1/2;
+//   - Galerkin A_{l+1} = P^T A_l P, absent components with a unit diagonal;
+//   - Chebyshev smoothing of degree 2 in D^-1 A on [rho/30, 1.1 rho] before
+//     and after the coarse correction; exact solve on the coarsest level
+//     (<= 16 nodes) with the inverse from Gauss-Jordan elimination.
+//
+// GB300 design.  Everything that depends only on the mesh -- the
+// aggregates, T (rigid motions at the node coordinates), the patterns of P,
+// A P, P^T and every coarse operator, and the index lists of the Galerkin
+// products -- is built once per mesh on the host (native C++, like the
+// mesh's own block pattern) and kept resident.  What depends on the
+// tangent's values runs on the device after every assembly: block
+// inverses, power iterations, P, A P, P^T A P and the coarsest inverse,
+// each output entry computed by one thread from a fixed gather list (no
+// atomics: deterministic, and the same summation order as a plain loop).
+// The numbers are formed in FP64; the V-cycle runs in the tangent's
+// precision (FP32 values, vectors and accumulation in the mixed forms).  A
+// Chebyshev step is one fused kernel: the SpMV with A_l, the residual update,
+// the block-Jacobi product and the direction and iterate updates of its
+// rows (r stays b - A x throughout, so the residual for the restriction
+// comes for free); level 0 reads the tangent in its tiled layout.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <numeric>
+#include <type_traits>
+#include <vector>
+
+#include "fe_internal.h"
+
+namespace {
+
+constexpr int AMG_MAXLEV = 12;
+constexpr int AMG_COARSE = 16;   // the coarsest level has at most this many nodes
+constexpr int AMG_NS = 6;        // near null space vectors
+constexpr int AMG_DENSE_MAX = 96;
+constexpr int AMG_POWER_STEPS = 15;
+constexpr double AMG_QR_DROP = 1e-8;
+constexpr int AMG_RED_BLOCKS = 256;
+
+uint64_t mix64(uint64_t z) {  // splitmix64 (Steele, Lea and Flood; Vigna's constants)
+  z += 0x9E3779B97F4A7C15ULL;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+  return z ^ (z >> 31);
+}
+__device__ __forceinline__ uint64_t mix64_d(uint64_t z) {
+  z += 0x9E3779B97F4A7C15ULL;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+  return z ^ (z >> 31);
+}
+
+}  // namespace
+
+struct AmgLevel {
+  int n = 0, b = 3, nc = 0;
+  int64_t nnz = 0, nnzp = 0, nnzap = 0, nnzr = 0;
+  // structure (device)
+  const int* ptr = nullptr;  // A_l pattern (level 0: the mesh's)
+  const int* col = nullptr;
+  const int* diag = nullptr; // [n] diagonal block positions
+  int* own = nullptr;        // one allocation holding this level's int arrays
+  unsigned char* absent = nullptr;
+  int *agg = nullptr, *pptr = nullptr, *pcol = nullptr, *prow = nullptr;
+  int *rptr = nullptr, *rcol = nullptr, *rsrc = nullptr;
+  int *apptr = nullptr, *apcol = nullptr, *aprow = nullptr;
+  int* crow = nullptr;       // row of each entry of A_l (level >= 1)
+  double* tnode = nullptr;   // [n][b*6] tentative block of each node
+  // numbers (device)
+  double* val64 = nullptr;  // level >= 1: [nnz][b*b]
+  float* val32 = nullptr;
+  double* dinv64 = nullptr;
+  float* dinv32 = nullptr;
+  double *p64 = nullptr, *r64 = nullptr, *ap64 = nullptr;
+  float *p32 = nullptr, *r32 = nullptr;
+  double* inv64 = nullptr;
+  float* inv32 = nullptr;
+  double rho = 0.0;
+  // V-cycle vectors [n*b] in the V-cycle precision
+  void *x = nullptr, *r = nullptr, *d0 = nullptr, *d1 = nullptr, *e = nullptr;
+};
+
+struct AmgHier {
+  int nlev = 0;
+  AmgLevel lev[AMG_MAXLEV];
+  int vec_elem = 0;          // bytes per V-cycle vector element allocated (0: none yet)
+  double* pw = nullptr;      // power iterations: x, y [2][max n*b]
+  double* part = nullptr;    // [2][AMG_RED_BLOCKS] partial sums
+  double* scal = nullptr;    // [4] rho, 1/|y|
+  std::vector<void*> allocs; // device buffers owned by the hierarchy
+  int64_t bytes = 0;         // their size (counted in the mesh's device bytes)
+};
+
+namespace {
+
+// ---------------------------------------------------------------- host structure
+struct HostLevel {
+  int n = 0, b = 3, nc = 0;
+  std::vector<int> ptr, col, diag;
+  std::vector<uint8_t> absent;
+  std::vector<double> ns;  // [n*b][6]
+  std::vector<int> agg, pptr, pcol, rptr, rcol, rsrc, apptr, apcol;
+  std::vector<double> tnode;  // [n][b*6]
+};
+
+uint8_t full_mask(int b) { return (uint8_t)((1u << b) - 1u); }
+
+// sorted unique values of v[beg, end) appended to out; returns the new size
+void sort_unique(std::vector<int>& tmp) {
+  std::sort(tmp.begin(), tmp.end());
+  tmp.erase(std::unique(tmp.begin(), tmp.end()), tmp.end());
+}
+
+void aggregate(HostLevel& L) {
+  const int n = L.n;
+  const uint8_t full = full_mask(L.b);
+  std::vector<int> order(n);
+  std::iota(order.begin(), order.end(), 0);
+  std::vector<uint64_t> pri(n);
+  for (int i = 0; i < n; i++) pri[i] = mix64((uint64_t)i);
+  std::sort(order.begin(), order.end(), [&](int a, int c) { return pri[a] != pri[c] ? pri[a] > pri[c] : a < c; });
+  std::vector<int> root(n, -1);  // root whose neighbourhood took the node
+  for (int i : order) {
+    if (L.absent[i] == full || root[i] >= 0) continue;
+    bool taken = false;
+    for (int k = L.ptr[i]; k < L.ptr[i + 1] && !taken; k++) {
+      const int j = L.col[k];
+      taken = j != i && L.absent[j] != full && root[j] >= 0;
+    }
+    if (taken) continue;
+    for (int k = L.ptr[i]; k < L.ptr[i + 1]; k++)
+      if (L.absent[L.col[k]] != full) root[L.col[k]] = i;
+    root[i] = i;
+  }
+  std::vector<int> id(n, -1);
+  L.nc = 0;
+  for (int i = 0; i < n; i++)
+    if (root[i] == i) id[i] = L.nc++;
+  L.agg.assign(n, -1);
+  for (int i = 0; i < n; i++)
+    if (root[i] >= 0) L.agg[i] = id[root[i]];
+  for (int i = 0; i < n; i++) {  // nodes at distance 2 from every root
+    if (L.absent[i] == full || root[i] >= 0) continue;
+    for (int k = L.ptr[i]; k < L.ptr[i + 1]; k++) {
+      const int j = L.col[k];
+      if (j != i && root[j] >= 0) {
+        L.agg[i] = id[root[j]];
+        break;
+      }
+    }
+  }
+}
+
+// T per node, coarse near null space and absent components, all patterns
+// of the level's products and the coarse level's pattern
+void coarsen(HostLevel& L, HostLevel& C) {
+  const int n = L.n, nc = L.nc, b = L.b, K = AMG_NS;
+  std::vector<std::vector<int>> members(nc);
+  for (int i = 0; i < n; i++)
+    if (L.agg[i] >= 0) members[L.agg[i]].push_back(i);
+  C.n = nc;
+  C.b = K;
+  C.absent.assign(nc, 0);
+  C.ns.assign((size_t)nc * K * K, 0.0);
+  L.tnode.assign((size_t)n * b * K, 0.0);
+  std::vector<double> Q;
+  for (int a = 0; a < nc; a++) {
+    const std::vector<int>& mem = members[a];
+    const int rows = (int)mem.size() * b;
+    Q.assign((size_t)rows * K, 0.0);  // column c at Q[c * rows ...]
+    for (size_t s = 0; s < mem.size(); s++)
+      for (int i = 0; i < b; i++)
+        for (int c = 0; c < K; c++) Q[(size_t)c * rows + s * b + i] = L.ns[((size_t)mem[s] * b + i) * K + c];
+    double* R = C.ns.data() + (size_t)a * K * K;  // R(p, c) at R[p K + c]
+    for (int c = 0; c < K; c++) {
+      double* v = Q.data() + (size_t)c * rows;
+      double n0 = 0.0;
+      for (int t = 0; t < rows; t++) n0 += v[t] * v[t];
+      n0 = std::sqrt(n0);
+      for (int p = 0; p < c; p++) {
+        const double* q = Q.data() + (size_t)p * rows;
+        double h = 0.0;
+        for (int t = 0; t < rows; t++) h += q[t] * v[t];
+        R[p * K + c] = h;
+        for (int t = 0; t < rows; t++) v[t] -= h * q[t];
+      }
+      double nv = 0.0;
+      for (int t = 0; t < rows; t++) nv += v[t] * v[t];
+      nv = std::sqrt(nv);
+      if (n0 == 0.0 || nv <= AMG_QR_DROP * n0) {
+        std::fill(v, v + rows, 0.0);
+        R[c * K + c] = 0.0;
+        C.absent[a] |= (uint8_t)(1u << c);
+      } else {
+        for (int t = 0; t < rows; t++) v[t] /= nv;
+        R[c * K + c] = nv;
+      }
+    }
+    for (size_t s = 0; s < mem.size(); s++)
+      for (int i = 0; i < b; i++)
+        for (int c = 0; c < K; c++) L.tnode[((size_t)mem[s] * b + i) * K + c] = Q[(size_t)c * rows + s * b + i];
+  }
+  const uint8_t full = full_mask(b);
+  std::vector<int> tmp;
+  // P: row i takes the aggregates of its neighbours
+  L.pptr.assign(n + 1, 0);
+  L.pcol.clear();
+  for (int i = 0; i < n; i++) {
+    tmp.clear();
+    if (L.absent[i] != full)
+      for (int k = L.ptr[i]; k < L.ptr[i + 1]; k++)
+        if (L.agg[L.col[k]] >= 0) tmp.push_back(L.agg[L.col[k]]);
+    sort_unique(tmp);
+    L.pcol.insert(L.pcol.end(), tmp.begin(), tmp.end());
+    L.pptr[i + 1] = (int)L.pcol.size();
+  }
+  // A P: row i takes the P rows of its neighbours
+  L.apptr.assign(n + 1, 0);
+  L.apcol.clear();
+  for (int i = 0; i < n; i++) {
+    tmp.clear();
+    for (int k = L.ptr[i]; k < L.ptr[i + 1]; k++) {
+      const int j = L.col[k];
+      tmp.insert(tmp.end(), L.pcol.begin() + L.pptr[j], L.pcol.begin() + L.pptr[j + 1]);
+    }
+    sort_unique(tmp);
+    L.apcol.insert(L.apcol.end(), tmp.begin(), tmp.end());
+    L.apptr[i + 1] = (int)L.apcol.size();
+  }
+  // P^T: row a lists (fine node, P entry) by ascending fine node
+  L.rptr.assign(nc + 1, 0);
+  for (int q = 0; q < L.pptr[n]; q++) L.rptr[L.pcol[q] + 1]++;
+  for (int a = 0; a < nc; a++) L.rptr[a + 1] += L.rptr[a];
+  L.rcol.assign(L.pptr[n], 0);
+  L.rsrc.assign(L.pptr[n], 0);
+  {
+    std::vector<int> fill(L.rptr.begin(), L.rptr.end() - 1);
+    for (int i = 0; i < n; i++)
+      for (int q = L.pptr[i]; q < L.pptr[i + 1]; q++) {
+        const int s = fill[L.pcol[q]]++;
+        L.rcol[s] = i;
+        L.rsrc[s] = q;
+      }
+  }
+  // coarse pattern: row a takes the A P rows of its P^T row, and the diagonal
+  C.ptr.assign(nc + 1, 0);
+  C.col.clear();
+  for (int a = 0; a < nc; a++) {
+    tmp.clear();
+    tmp.push_back(a);
+    for (int s = L.rptr[a]; s < L.rptr[a + 1]; s++) {
+      const int i = L.rcol[s];
+      tmp.insert(tmp.end(), L.apcol.begin() + L.apptr[i], L.apcol.begin() + L.apptr[i + 1]);
+    }
+    sort_unique(tmp);
+    C.col.insert(C.col.end(), tmp.begin(), tmp.end());
+    C.ptr[a + 1] = (int)C.col.size();
+  }
+  C.diag.assign(nc, -1);
+  for (int a = 0; a < nc; a++)
+    for (int k = C.ptr[a]; k < C.ptr[a + 1]; k++)
+      if (C.col[k] == a) C.diag[a] = k;
+}
+
+// ---------------------------------------------------------------- device helpers
+template <class V>
+__device__ __forceinline__ double ldd(const V* p);
+template <>
+__device__ __forceinline__ double ldd<double>(const double* p) { return *p; }
+template <>
+__device__ __forceinline__ double ldd<float>(const float* p) { return (double)*p; }
+template <>
+__device__ __forceinline__ double ldd<__nv_bfloat16>(const __nv_bfloat16* p) { return (double)__bfloat162float(*p); }
+
+// a stored value in the V-cycle's arithmetic type T (FP32 values stay FP32)
+template <class T, class V>
+__device__ __forceinline__ T ldt(const V* p) {
+  if constexpr (std::is_same<V, __nv_bfloat16>::value) return (T)__bfloat162float(*p);
+  else return (T)__ldg(p);
+}
+
+// entry c of block k: level 0 reads the tangent in its tiled layout, coarser
+// levels their block-major FP64 values
+template <class V, int B>
+struct Vals {
+  const V* v;
+  bool tiled;
+  __device__ __forceinline__ double operator()(int64_t k, int c) const {
+    return tiled ? ldd<V>(v + kv_index(k, c)) : ldd<V>(v + k * (B * B) + c);
+  }
+};
+
+__device__ __forceinline__ int find_col(const int* __restrict__ col, int lo, int hi, int c) {
+  while (lo < hi) {
+    const int mid = (lo + hi) >> 1;
+    const int v = __ldg(col + mid);
+    if (v == c) return mid;
+    if (v < c) lo = mid + 1;
+    else hi = mid;
+  }
+  return -1;
+}
+
+// inverse of a B x B matrix by Gauss-Jordan elimination with partial pivoting
+template <int B>
+__device__ void gj_inverse(double (&a)[B][B], double (&inv)[B][B]) {
+  for (int i = 0; i < B; i++)
+    for (int j = 0; j < B; j++) inv[i][j] = i == j ? 1.0 : 0.0;
+  for (int c = 0; c < B; c++) {
+    int p = c;
+    for (int r = c + 1; r < B; r++)
+      if (fabs(a[r][c]) > fabs(a[p][c])) p = r;
+    if (p != c)
+      for (int j = 0; j < B; j++) {
+        double t = a[c][j];
+        a[c][j] = a[p][j];
+        a[p][j] = t;
+        t = inv[c][j];
+        inv[c][j] = inv[p][j];
+        inv[p][j] = t;
+      }
+    const double piv = a[c][c];
+    for (int j = 0; j < B; j++) {
+      a[c][j] /= piv;
+      inv[c][j] /= piv;
+    }
+    for (int r = 0; r < B; r++) {
+      if (r == c) continue;
+      const double f = a[r][c];
+      if (f == 0.0) continue;
+      for (int j = 0; j < B; j++) {
+        a[r][j] -= f * a[c][j];
+        inv[r][j] -= f * inv[c][j];
+      }
+    }
+  }
+}
+
+// ---------------------------------------------------------------- numeric setup kernels (FP64)
+template <class V, int B>
+__global__ void k_amg_dinv(int n, const int* __restrict__ diag, Vals<V, B> A, double* __restrict__ dinv) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  double a[B][B], inv[B][B];
+  const int64_t k = diag[i];
+  for (int r = 0; r < B; r++)
+    for (int c = 0; c < B; c++) a[r][c] = A(k, B * r + c);
+  gj_inverse<B>(a, inv);
+  for (int r = 0; r < B; r++)
+    for (int c = 0; c < B; c++) dinv[(int64_t)i * B * B + B * r + c] = inv[r][c];
+}
+
+// y = D^-1 (A x), one warp per block row
+template <class V, int B>
+__global__ void __launch_bounds__(256) k_amg_dmv(int n, const int* __restrict__ ptr, const int* __restrict__ col,
+                                                 Vals<V, B> A, const double* __restrict__ dinv,
+                                                 const double* __restrict__ x, double* __restrict__ y) {
+  const int row = (int)(((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+  const int lane = threadIdx.x & 31;
+  if (row >= n) return;
+  double s[B];
+  for (int r = 0; r < B; r++) s[r] = 0.0;
+  for (int k = ptr[row] + lane; k < ptr[row + 1]; k += 32) {
+    const int c = col[k];
+    for (int r = 0; r < B; r++)
+      for (int j = 0; j < B; j++) s[r] += A(k, B * r + j) * x[(int64_t)B * c + j];
+  }
+  for (int r = 0; r < B; r++)
+    for (int off = 16; off > 0; off >>= 1) s[r] += __shfl_xor_sync(0xffffffffu, s[r], off);
+  if (lane == 0)
+    for (int r = 0; r < B; r++) {
+      double t = 0.0;
+      for (int j = 0; j < B; j++) t += dinv[(int64_t)row * B * B + B * r + j] * s[j];
+      y[(int64_t)B * row + r] = t;
+    }
+}
+
+__global__ void k_amg_start(int64_t N, double* __restrict__ x) {
+  const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (k < N) x[k] = (double)(mix64_d((uint64_t)k) >> 11) * (1.0 / 9007199254740992.0) - 0.5;
+}
+
+// partial sums of x.x and y.y over a fixed grid (fixed order: deterministic)
+__global__ void __launch_bounds__(256) k_amg_sumsq2(int64_t N, const double* __restrict__ x,
+                                                    const double* __restrict__ y, double* __restrict__ part) {
+  __shared__ double sh[2][8];
+  double sx = 0.0, sy = 0.0;
+  for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < N; k += (int64_t)gridDim.x * blockDim.x) {
+    sx += x[k] * x[k];
+    sy += y[k] * y[k];
+  }
+  for (int off = 16; off > 0; off >>= 1) {
+    sx += __shfl_xor_sync(0xffffffffu, sx, off);
+    sy += __shfl_xor_sync(0xffffffffu, sy, off);
+  }
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (lane == 0) {
+    sh[0][w] = sx;
+    sh[1][w] = sy;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double a = 0.0, c = 0.0;
+    for (int i = 0; i < (int)(blockDim.x >> 5); i++) {
+      a += sh[0][i];
+      c += sh[1][i];
+    }
+    part[blockIdx.x] = a;
+    part[gridDim.x + blockIdx.x] = c;
+  }
+}
+
+// rho = |y| / |x|, x = y / |y|
+__global__ void k_amg_power_step(int64_t N, int nblk, const double* __restrict__ part, const double* __restrict__ y,
+                                 double* __restrict__ x, double* __restrict__ scal) {
+  __shared__ double s_inv;
+  if (threadIdx.x == 0) {
+    double xx = 0.0, yy = 0.0;
+    for (int i = 0; i < nblk; i++) {
+      xx += part[i];
+      yy += part[nblk + i];
+    }
+    scal[0] = sqrt(yy) / sqrt(xx);
+    s_inv = 1.0 / sqrt(yy);
+  }
+  __syncthreads();
+  for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < N; k += (int64_t)gridDim.x * blockDim.x)
+    x[k] = y[k] * s_inv;
+}
+
+// P entry q = (row i, aggregate a): [agg(i) = a] T_i - omega sum_{k: agg(col k) = a} D_i^-1 A_k T_col(k)
+template <class V, int B>
+__global__ void k_amg_pvals(int64_t nnzp, const int* __restrict__ prow, const int* __restrict__ pcol,
+                            const int* __restrict__ ptr, const int* __restrict__ col, Vals<V, B> A,
+                            const int* __restrict__ agg, const double* __restrict__ dinv,
+                            const double* __restrict__ tnode, double omega, double* __restrict__ p) {
+  const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= nnzp) return;
+  const int i = prow[q], a = pcol[q];
+  double acc[B][AMG_NS];
+  for (int r = 0; r < B; r++)
+    for (int c = 0; c < AMG_NS; c++)
+      acc[r][c] = agg[i] == a ? tnode[(int64_t)i * B * AMG_NS + AMG_NS * r + c] : 0.0;
+  double D[B][B];
+  for (int r = 0; r < B; r++)
+    for (int c = 0; c < B; c++) D[r][c] = dinv[(int64_t)i * B * B + B * r + c];
+  for (int k = ptr[i]; k < ptr[i + 1]; k++) {
+    const int j = col[k];
+    if (agg[j] != a) continue;
+    double DA[B][B];
+    for (int r = 0; r < B; r++)
+      for (int c = 0; c < B; c++) {
+        double s = 0.0;
+        for (int l = 0; l < B; l++) s += D[r][l] * A(k, B * l + c);
+        DA[r][c] = s;
+      }
+    const double* T = tnode + (int64_t)j * B * AMG_NS;
+    for (int r = 0; r < B; r++)
+      for (int c = 0; c < AMG_NS; c++) {
+        double s = 0.0;
+        for (int l = 0; l < B; l++) s += DA[r][l] * T[AMG_NS * l + c];
+        acc[r][c] -= omega * s;
+      }
+  }
+  for (int r = 0; r < B; r++)
+    for (int c = 0; c < AMG_NS; c++) p[q * B * AMG_NS + AMG_NS * r + c] = acc[r][c];
+}
+
+// A P entry (row i, aggregate a) = sum_k A_k P_(col k, a)
+template <class V, int B>
+__global__ void k_amg_ap(int64_t nnzap, const int* __restrict__ aprow, const int* __restrict__ apcol,
+                         const int* __restrict__ ptr, const int* __restrict__ col, Vals<V, B> A,
+                         const int* __restrict__ pptr, const int* __restrict__ pcol, const double* __restrict__ p,
+                         double* __restrict__ ap) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= nnzap) return;
+  const int i = aprow[e], a = apcol[e];
+  double acc[B][AMG_NS];
+  for (int r = 0; r < B; r++)
+    for (int c = 0; c < AMG_NS; c++) acc[r][c] = 0.0;
+  for (int k = ptr[i]; k < ptr[i + 1]; k++) {
+    const int j = col[k];
+    const int q = find_col(pcol, pptr[j], pptr[j + 1], a);
+    if (q < 0) continue;
+    const double* P = p + (int64_t)q * B * AMG_NS;
+    for (int r = 0; r < B; r++) {
+      double Ar[B];
+      for (int l = 0; l < B; l++) Ar[l] = A(k, B * r + l);
+      for (int c = 0; c < AMG_NS; c++) {
+        double s = 0.0;
+        for (int l = 0; l < B; l++) s += Ar[l] * P[AMG_NS * l + c];
+        acc[r][c] += s;
+      }
+    }
+  }
+  for (int r = 0; r < B; r++)
+    for (int c = 0; c < AMG_NS; c++) ap[e * B * AMG_NS + AMG_NS * r + c] = acc[r][c];
+}
+
+// coarse entry (a, c) = sum over P^T row a (fine node i, P entry q) of P_q^T (A P)_(i, c);
+// absent coarse components get a unit diagonal
+template <int B>
+__global__ void k_amg_rap(int64_t nnzc, const int* __restrict__ crow, const int* __restrict__ ccol,
+                          const int* __restrict__ rptr, const int* __restrict__ rcol, const int* __restrict__ rsrc,
+                          const int* __restrict__ apptr, const int* __restrict__ apcol, const double* __restrict__ p,
+                          const double* __restrict__ ap, const unsigned char* __restrict__ cabsent,
+                          double* __restrict__ out) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= nnzc) return;
+  const int a = crow[e], cc = ccol[e];
+  double acc[AMG_NS][AMG_NS];
+  for (int r = 0; r < AMG_NS; r++)
+    for (int c = 0; c < AMG_NS; c++) acc[r][c] = 0.0;
+  for (int s = rptr[a]; s < rptr[a + 1]; s++) {
+    const int i = rcol[s];
+    const int pe = find_col(apcol, apptr[i], apptr[i + 1], cc);
+    if (pe < 0) continue;
+    const double* P = p + (int64_t)rsrc[s] * B * AMG_NS;
+    const double* Q = ap + (int64_t)pe * B * AMG_NS;
+    for (int r = 0; r < AMG_NS; r++)
+      for (int c = 0; c < AMG_NS; c++) {
+        double v = 0.0;
+        for (int l = 0; l < B; l++) v += P[AMG_NS * l + r] * Q[AMG_NS * l + c];
+        acc[r][c] += v;
+      }
+  }
+  if (a == cc) {
+    const unsigned m = cabsent[a];
+    for (int c = 0; c < AMG_NS; c++)
+      if ((m >> c) & 1u) acc[c][c] = 1.0;
+  }
+  for (int r = 0; r < AMG_NS; r++)
+    for (int c = 0; c < AMG_NS; c++) out[e * AMG_NS * AMG_NS + AMG_NS * r + c] = acc[r][c];
+}
+
+// R = P^T values: R entry s holds the transpose of P entry rsrc[s]
+template <int B>
+__global__ void k_amg_rvals(int64_t nnzr, const int* __restrict__ rsrc, const double* __restrict__ p,
+                            double* __restrict__ rv) {
+  const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= nnzr) return;
+  const double* P = p + (int64_t)rsrc[s] * B * AMG_NS;
+  for (int c = 0; c < AMG_NS; c++)
+    for (int r = 0; r < B; r++) rv[s * B * AMG_NS + B * c + r] = P[AMG_NS * r + c];
+}
+
+// dense inverse of the coarsest operator (N <= 96): one block, Gauss-Jordan
+// with partial pivoting in shared memory (first maximal pivot on ties)
+template <class V, int B>
+__global__ void __launch_bounds__(1024) k_amg_dense_inverse(int n, const int* __restrict__ ptr,
+                                                            const int* __restrict__ col, Vals<V, B> A,
+                                                            double* __restrict__ inv) {
+  extern __shared__ double sm[];
+  const int N = n * B;
+  double* M = sm;
+  double* I = sm + N * N;
+  double* fac = sm + 2 * N * N;  // column c before the elimination step
+  __shared__ int s_piv;
+  for (int t = threadIdx.x; t < N * N; t += blockDim.x) {
+    M[t] = 0.0;
+    I[t] = (t / N == t % N) ? 1.0 : 0.0;
+  }
+  __syncthreads();
+  for (int a = threadIdx.x; a < n; a += blockDim.x)
+    for (int k = ptr[a]; k < ptr[a + 1]; k++)
+      for (int r = 0; r < B; r++)
+        for (int c = 0; c < B; c++) M[(B * a + r) * N + B * col[k] + c] = A(k, B * r + c);
+  __syncthreads();
+  for (int c = 0; c < N; c++) {
+    if (threadIdx.x == 0) {
+      int p = c;
+      for (int r = c + 1; r < N; r++)
+        if (fabs(M[r * N + c]) > fabs(M[p * N + c])) p = r;
+      s_piv = p;
+    }
+    __syncthreads();
+    const int p = s_piv;
+    if (p != c)
+      for (int j = threadIdx.x; j < N; j += blockDim.x) {
+        double t = M[c * N + j];
+        M[c * N + j] = M[p * N + j];
+        M[p * N + j] = t;
+        t = I[c * N + j];
+        I[c * N + j] = I[p * N + j];
+        I[p * N + j] = t;
+      }
+    __syncthreads();
+    const double piv = M[c * N + c];
+    __syncthreads();
+    for (int j = threadIdx.x; j < N; j += blockDim.x) {
+      M[c * N + j] /= piv;
+      I[c * N + j] /= piv;
+    }
+    for (int r = threadIdx.x; r < N; r += blockDim.x) fac[r] = M[r * N + c];
+    __syncthreads();
+    for (int t = threadIdx.x; t < N * N; t += blockDim.x) {
+      const int r = t / N, j = t % N;
+      const double f = fac[r];
+      if (r == c || f == 0.0) continue;
+      M[r * N + j] -= f * M[c * N + j];
+      I[r * N + j] -= f * I[c * N + j];
+    }
+    __syncthreads();
+  }
+  for (int t = threadIdx.x; t < N * N; t += blockDim.x) inv[t] = I[t];
+}
+
+__global__ void k_amg_to_f32(int64_t n, const double* __restrict__ a, float* __restrict__ b) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) b[i] = (float)a[i];
+}
+
+// ---------------------------------------------------------------- V-cycle kernels
+// One Chebyshev step of level l, fused (row i of n block rows, B components):
+//   t = (A g)_i; x_i = (setx ? 0 : x_i) + cx g_i; r_i -= t;
+//   dout_i = c1 g_i + c2 D_i^-1 r_i; final: x_i += dout_i.
+// One warp per block row, one lane per block; level 0 reads the tangent
+// in its tiled layout.
+enum { VC_SETX = 1, VC_FINAL = 2, VC_KEEPX = 4 };
+
+template <class V, class T, int B>
+__global__ void __launch_bounds__(256) k_vc_cheb(int n, const int* __restrict__ ptr, const int* __restrict__ col,
+                                                 const V* __restrict__ val, int tiled, const T* __restrict__ dinv,
+                                                 const T* __restrict__ g, T* __restrict__ x, T* __restrict__ r,
+                                                 T* __restrict__ dout, T cx, T c1, T c2, int flags) {
+  const int row = (int)(((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+  const int lane = threadIdx.x & 31;
+  if (row >= n) return;
+  T s[B];
+#pragma unroll
+  for (int q = 0; q < B; q++) s[q] = T(0);
+  for (int k = ptr[row] + lane; k < ptr[row + 1]; k += 32) {
+    const int c = __ldg(col + k);
+    T gv[B];
+#pragma unroll
+    for (int j = 0; j < B; j++) gv[j] = g[(int64_t)B * c + j];
+#pragma unroll
+    for (int q = 0; q < B; q++)
+#pragma unroll
+      for (int j = 0; j < B; j++) {
+        const int64_t at = tiled ? kv_index(k, B * q + j) : (int64_t)k * B * B + B * q + j;
+        s[q] += ldt<T, V>(val + at) * gv[j];
+      }
+  }
+#pragma unroll
+  for (int q = 0; q < B; q++)
+    for (int off = 16; off > 0; off >>= 1) s[q] += __shfl_xor_sync(0xffffffffu, s[q], off);
+  if (lane != 0) return;
+  const int64_t o = (int64_t)B * row;
+  T rn[B], gi[B];
+#pragma unroll
+  for (int q = 0; q < B; q++) {
+    gi[q] = g[o + q];
+    rn[q] = r[o + q] - s[q];
+    r[o + q] = rn[q];
+  }
+  T xi[B];
+  const bool wx = !(flags & VC_KEEPX);
+#pragma unroll
+  for (int q = 0; q < B; q++) xi[q] = ((flags & VC_SETX) ? T(0) : (wx ? x[o + q] : T(0))) + cx * gi[q];
+  if (dout) {
+#pragma unroll
+    for (int q = 0; q < B; q++) {
+      T t = T(0);
+#pragma unroll
+      for (int j = 0; j < B; j++) t += dinv[(int64_t)row * B * B + B * q + j] * rn[j];
+      const T dn = c1 * gi[q] + c2 * t;
+      dout[o + q] = dn;
+      if (flags & VC_FINAL) xi[q] += dn;
+    }
+  }
+  if (wx)
+#pragma unroll
+    for (int q = 0; q < B; q++) x[o + q] = xi[q];
+}
+
+// level-0 start of the pre-smoothing: r = b, d = D^-1 b / theta
+template <class T>
+__global__ void k_vc_init0(int n, const T* __restrict__ dinv, const double* __restrict__ b, T* __restrict__ r,
+                           T* __restrict__ d, T inv_theta) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  T bi[3];
+  for (int q = 0; q < 3; q++) {
+    bi[q] = (T)b[3 * (int64_t)i + q];
+    r[3 * (int64_t)i + q] = bi[q];
+  }
+  for (int q = 0; q < 3; q++) {
+    T t = T(0);
+    for (int j = 0; j < 3; j++) t += dinv[(int64_t)i * 9 + 3 * q + j] * bi[j];
+    d[3 * (int64_t)i + q] = t * inv_theta;
+  }
+}
+
+// restriction to the coarse level (6 components): s = (P^T r)_a;
+// coarsest: bout = s; else: rc = s, dc = D_c^-1 s / theta_c
+template <class T, int BF>
+__global__ void __launch_bounds__(256) k_vc_restrict(int nc, const int* __restrict__ rptr, const int* __restrict__ rcol,
+                                                     const T* __restrict__ rv, const T* __restrict__ rf,
+                                                     const T* __restrict__ dinvc, T* __restrict__ rc,
+                                                     T* __restrict__ dc, T inv_theta) {
+  const int a = (int)(((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+  const int lane = threadIdx.x & 31;
+  if (a >= nc) return;
+  T s[AMG_NS];
+#pragma unroll
+  for (int q = 0; q < AMG_NS; q++) s[q] = T(0);
+  for (int k = rptr[a] + lane; k < rptr[a + 1]; k += 32) {
+    const int i = __ldg(rcol + k);
+    T f[BF];
+#pragma unroll
+    for (int j = 0; j < BF; j++) f[j] = rf[(int64_t)BF * i + j];
+#pragma unroll
+    for (int q = 0; q < AMG_NS; q++)
+#pragma unroll
+      for (int j = 0; j < BF; j++) s[q] += rv[(int64_t)k * BF * AMG_NS + BF * q + j] * f[j];
+  }
+#pragma unroll
+  for (int q = 0; q < AMG_NS; q++)
+    for (int off = 16; off > 0; off >>= 1) s[q] += __shfl_xor_sync(0xffffffffu, s[q], off);
+  if (lane != 0) return;
+  const int64_t o = (int64_t)AMG_NS * a;
+#pragma unroll
+  for (int q = 0; q < AMG_NS; q++) rc[o + q] = s[q];
+  if (dc)
+#pragma unroll
+    for (int q = 0; q < AMG_NS; q++) {
+      T t = T(0);
+#pragma unroll
+      for (int j = 0; j < AMG_NS; j++) t += dinvc[(int64_t)a * AMG_NS * AMG_NS + AMG_NS * q + j] * s[j];
+      dc[o + q] = t * inv_theta;
+    }
+}
+
+// coarsest solve: x = inv b (one block)
+template <class T>
+__global__ void k_vc_dense(int N, const T* __restrict__ inv, const T* __restrict__ b, T* __restrict__ x) {
+  for (int i = threadIdx.x; i < N; i += blockDim.x) {
+    T s = T(0);
+    for (int j = 0; j < N; j++) s += inv[(int64_t)i * N + j] * b[j];
+    x[i] = s;
+  }
+}
+
+// prolongation: e_i = (P xc)_i, x_i += e_i
+template <class T, int BF>
+__global__ void __launch_bounds__(256) k_vc_prolong(int n, const int* __restrict__ pptr, const int* __restrict__ pcol,
+                                                    const T* __restrict__ pv, const T* __restrict__ xc,
+                                                    T* __restrict__ x, T* __restrict__ e) {
+  const int i = (int)(((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+  const int lane = threadIdx.x & 31;
+  if (i >= n) return;
+  T s[BF];
+#pragma unroll
+  for (int q = 0; q < BF; q++) s[q] = T(0);
+  for (int k = pptr[i] + lane; k < pptr[i + 1]; k += 32) {
+    const int a = __ldg(pcol + k);
+    T c[AMG_NS];
+#pragma unroll
+    for (int j = 0; j < AMG_NS; j++) c[j] = xc[(int64_t)AMG_NS * a + j];
+#pragma unroll
+    for (int q = 0; q < BF; q++)
+#pragma unroll
+      for (int j = 0; j < AMG_NS; j++) s[q] += pv[(int64_t)k * BF * AMG_NS + AMG_NS * q + j] * c[j];
+  }
+#pragma unroll
+  for (int q = 0; q < BF; q++)
+    for (int off = 16; off > 0; off >>= 1) s[q] += __shfl_xor_sync(0xffffffffu, s[q], off);
+  if (lane != 0) return;
+#pragma unroll
+  for (int q = 0; q < BF; q++) {
+    e[(int64_t)BF * i + q] = s[q];
+    x[(int64_t)BF * i + q] += s[q];
+  }
+}
+
+template <class A, class B>
+__global__ void k_vc_convert(int64_t n, const A* __restrict__ a, B* __restrict__ b) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) b[i] = (B)a[i];
+}
+
+// ---------------------------------------------------------------- host drivers
+template <class X>
+int dev_alloc(fe_mesh m, X** p, size_t count) {
+  count = count ? count : 1;
+  FE_TRY(fe_alloc_t(m, p, count));
+  m->amg->allocs.push_back((void*)*p);
+  m->amg->bytes += (int64_t)(count * sizeof(X));
+  return FE_OK;
+}
+
+template <class X>
+int upload(fe_mesh m, X** p, const std::vector<X>& v) {
+  FE_TRY(dev_alloc(m, p, v.size()));
+  if (!v.empty()) FE_CUDA(cudaMemcpyAsync(*p, v.data(), v.size() * sizeof(X), cudaMemcpyHostToDevice, m->stream));
+  return FE_OK;
+}
+
+unsigned blocks_for(int64_t n, int per) { return (unsigned)std::max<int64_t>(1, (n + per - 1) / per); }
+
+// structure of every level, once per mesh
+int build_structure(fe_mesh m) {
+  AmgHier* h = m->amg;
+  std::vector<HostLevel> hl(1);
+  HostLevel& L0 = hl[0];
+  const int nn = m->nn;
+  L0.n = nn;
+  L0.b = 3;
+  L0.ptr.resize(nn + 1);
+  L0.col.resize(m->nnzb);
+  std::vector<uint8_t> fix(nn);
+  std::vector<double> X((size_t)nn * 3);
+  FE_CUDA(cudaMemcpyAsync(L0.ptr.data(), m->row_ptr, sizeof(int) * (nn + 1), cudaMemcpyDeviceToHost, m->stream));
+  FE_CUDA(cudaMemcpyAsync(L0.col.data(), m->col, sizeof(int) * m->nnzb, cudaMemcpyDeviceToHost, m->stream));
+  FE_CUDA(cudaMemcpyAsync(fix.data(), m->fixmask, nn, cudaMemcpyDeviceToHost, m->stream));
+  FE_CUDA(cudaMemcpyAsync(X.data(), m->X, sizeof(double) * 3 * nn, cudaMemcpyDeviceToHost, m->stream));
+  FE_CUDA(cudaStreamSynchronize(m->stream));
+  L0.absent = fix;
+  L0.ns.assign((size_t)nn * 3 * AMG_NS, 0.0);
+  for (int a = 0; a < nn; a++) {
+    const double x = X[3 * a], y = X[3 * a + 1], z = X[3 * a + 2];
+    const double rb[3][AMG_NS] = {{1, 0, 0, -y, 0, z}, {0, 1, 0, x, -z, 0}, {0, 0, 1, 0, y, -x}};
+    for (int c = 0; c < 3; c++)
+      for (int k = 0; k < AMG_NS; k++) L0.ns[((size_t)3 * a + c) * AMG_NS + k] = ((fix[a] >> c) & 1) ? 0.0 : rb[c][k];
+  }
+  int l = 0;
+  for (;;) {
+    HostLevel& L = hl[l];
+    if (L.n <= AMG_COARSE || l == AMG_MAXLEV - 1) break;
+    aggregate(L);
+    if (L.nc == 0 || L.nc > 0.9 * L.n) {
+      L.agg.clear();
+      L.nc = 0;
+      break;
+    }
+    hl.emplace_back();
+    coarsen(hl[l], hl[l + 1]);
+    l++;
+  }
+  const int nlev = l + 1;
+  const HostLevel& Lc = hl[nlev - 1];
+  if (Lc.n * Lc.b > AMG_DENSE_MAX)
+    return fe_set_error("AMG: the coarsest level has %d unknowns (at most %d)", Lc.n * Lc.b, AMG_DENSE_MAX),
+           FE_ERR_ARG;
+  h->nlev = nlev;
+  for (int q = 0; q < nlev; q++) {
+    HostLevel& H = hl[q];
+    AmgLevel& A = h->lev[q];
+    A.n = H.n;
+    A.b = H.b;
+    A.nc = q < nlev - 1 ? H.nc : 0;
+    if (q == 0) {
+      A.ptr = m->row_ptr;
+      A.col = m->col;
+      A.diag = m->diag_pos;
+      A.nnz = m->nnzb;
+    } else {
+      int *p = nullptr, *c = nullptr, *d = nullptr, *cr = nullptr;
+      FE_TRY(upload(m, &p, H.ptr));
+      FE_TRY(upload(m, &c, H.col));
+      FE_TRY(upload(m, &d, H.diag));
+      std::vector<int> crow(H.col.size());
+      for (int a = 0; a < H.n; a++)
+        for (int k = H.ptr[a]; k < H.ptr[a + 1]; k++) crow[k] = a;
+      FE_TRY(upload(m, &cr, crow));
+      A.ptr = p;
+      A.col = c;
+      A.diag = d;
+      A.crow = cr;
+      A.nnz = (int64_t)H.col.size();
+    }
+    FE_TRY(upload(m, &A.absent, H.absent));
+    if (q < nlev - 1) {
+      FE_TRY(upload(m, &A.agg, H.agg));
+      FE_TRY(upload(m, &A.pptr, H.pptr));
+      FE_TRY(upload(m, &A.pcol, H.pcol));
+      std::vector<int> prow(H.pcol.size()), aprow(H.apcol.size());
+      for (int i = 0; i < H.n; i++) {
+        for (int k = H.pptr[i]; k < H.pptr[i + 1]; k++) prow[k] = i;
+        for (int k = H.apptr[i]; k < H.apptr[i + 1]; k++) aprow[k] = i;
+      }
+      FE_TRY(upload(m, &A.prow, prow));
+      FE_TRY(upload(m, &A.rptr, H.rptr));
+      FE_TRY(upload(m, &A.rcol, H.rcol));
+      FE_TRY(upload(m, &A.rsrc, H.rsrc));
+      FE_TRY(upload(m, &A.apptr, H.apptr));
+      FE_TRY(upload(m, &A.apcol, H.apcol));
+      FE_TRY(upload(m, &A.aprow, aprow));
+      FE_TRY(upload(m, &A.tnode, H.tnode));
+      A.nnzp = (int64_t)H.pcol.size();
+      A.nnzr = A.nnzp;
+      A.nnzap = (int64_t)H.apcol.size();
+    }
+  }
+  int64_t maxN = 0;
+  for (int q = 0; q < nlev; q++) maxN = std::max<int64_t>(maxN, (int64_t)h->lev[q].n * h->lev[q].b);
+  FE_TRY(dev_alloc(m, &h->pw, (size_t)2 * maxN));
+  FE_TRY(dev_alloc(m, &h->part, (size_t)2 * AMG_RED_BLOCKS));
+  FE_TRY(dev_alloc(m, &h->scal, 4));
+  FE_CUDA(cudaStreamSynchronize(m->stream));  // host vectors above go out of scope
+  return FE_OK;
+}
+
+// numbers of level q (A_q already numeric): D^-1, rho, P, AP, R and A_{q+1}
+template <class V, int B>
+int numeric_level(fe_mesh m, int q, Vals<V, B> A) {
+  AmgHier* h = m->amg;
+  AmgLevel& L = h->lev[q];
+  const int64_t N = (int64_t)L.n * L.b;
+  if (!L.dinv64) FE_TRY(dev_alloc(m, &L.dinv64, (size_t)L.n * B * B));
+  {
+    FE_SCOPE(m, FE_PROF_TANGENT, (double)L.n * B * B * 16);
+    k_amg_dinv<V, B><<<blocks_for(L.n, 128), 128, 0, m->stream>>>(L.n, L.diag, A, L.dinv64);
+  }
+  FE_CUDA(cudaGetLastError());
+  if (q == h->nlev - 1) {  // coarsest: dense inverse
+    const int Nd = L.n * B;
+    if (!L.inv64) FE_TRY(dev_alloc(m, &L.inv64, (size_t)Nd * Nd));
+    const int smem = (2 * Nd * Nd + Nd) * (int)sizeof(double);
+    FE_TRY(fe_kernel_smem((const void*)k_amg_dense_inverse<V, B>, smem));
+    {
+      FE_SCOPE(m, FE_PROF_TANGENT, 8.0 * Nd * Nd);
+      k_amg_dense_inverse<V, B><<<1, 1024, smem, m->stream>>>(L.n, L.ptr, L.col, A, L.inv64);
+    }
+    FE_CUDA(cudaGetLastError());
+    return FE_OK;
+  }
+  // rho: power steps on D^-1 A
+  double* x = h->pw;
+  double* y = h->pw + N;
+  k_amg_start<<<blocks_for(N, 256), 256, 0, m->stream>>>(N, x);
+  for (int it = 0; it < AMG_POWER_STEPS; it++) {
+    {
+      FE_SCOPE(m, FE_PROF_TANGENT, (double)L.nnz * (B * B * sizeof(V) + 4) + 16.0 * N);
+      k_amg_dmv<V, B><<<blocks_for((int64_t)L.n * 32, 256), 256, 0, m->stream>>>(L.n, L.ptr, L.col, A, L.dinv64, x, y);
+    }
+    k_amg_sumsq2<<<AMG_RED_BLOCKS, 256, 0, m->stream>>>(N, x, y, h->part);
+    k_amg_power_step<<<blocks_for(N, 256), 256, 0, m->stream>>>(N, AMG_RED_BLOCKS, h->part, y, x, h->scal);
+  }
+  FE_CUDA(cudaGetLastError());
+  FE_CUDA(cudaMemcpyAsync(m->h_scal + 20, h->scal, sizeof(double), cudaMemcpyDeviceToHost, m->stream));
+  FE_CUDA(cudaStreamSynchronize(m->stream));
+  L.rho = m->h_scal[20];
+  if (!(L.rho > 0.0) || !std::isfinite(L.rho))
+    return fe_set_error("AMG: spectral radius estimate %g on level %d", L.rho, q), FE_ERR_STATE;
+  const double omega = 4.0 / (3.0 * L.rho);
+  if (!L.p64) FE_TRY(dev_alloc(m, &L.p64, (size_t)L.nnzp * B * AMG_NS));
+  if (!L.ap64) FE_TRY(dev_alloc(m, &L.ap64, (size_t)L.nnzap * B * AMG_NS));
+  if (!L.r64) FE_TRY(dev_alloc(m, &L.r64, (size_t)L.nnzr * B * AMG_NS));
+  AmgLevel& C = h->lev[q + 1];
+  if (!C.val64) FE_TRY(dev_alloc(m, &C.val64, (size_t)C.nnz * AMG_NS * AMG_NS));
+  {
+    FE_SCOPE(m, FE_PROF_TANGENT, (double)L.nnzp * B * AMG_NS * 8);
+    k_amg_pvals<V, B><<<blocks_for(L.nnzp, 128), 128, 0, m->stream>>>(L.nnzp, L.prow, L.pcol, L.ptr, L.col, A, L.agg,
+                                                                     L.dinv64, L.tnode, omega, L.p64);
+  }
+  FE_CUDA(cudaGetLastError());
+  {
+    FE_SCOPE(m, FE_PROF_TANGENT, (double)L.nnzap * B * AMG_NS * 8);
+    k_amg_ap<V, B><<<blocks_for(L.nnzap, 128), 128, 0, m->stream>>>(L.nnzap, L.aprow, L.apcol, L.ptr, L.col, A,
+                                                                   L.pptr, L.pcol, L.p64, L.ap64);
+  }
+  FE_CUDA(cudaGetLastError());
+  {
+    FE_SCOPE(m, FE_PROF_TANGENT, (double)C.nnz * AMG_NS * AMG_NS * 8);
+    k_amg_rap<B><<<blocks_for(C.nnz, 128), 128, 0, m->stream>>>(C.nnz, C.crow, C.col, L.rptr, L.rcol, L.rsrc,
+                                                               L.apptr, L.apcol, L.p64, L.ap64, C.absent, C.val64);
+  }
+  FE_CUDA(cudaGetLastError());
+  k_amg_rvals<B><<<blocks_for(L.nnzr, 256), 256, 0, m->stream>>>(L.nnzr, L.rsrc, L.p64, L.r64);
+  FE_CUDA(cudaGetLastError());
+  return FE_OK;
+}
+
+int to_f32(fe_mesh m, const double* a, float** b, int64_t n) {
+  if (!*b) FE_TRY(dev_alloc(m, b, (size_t)n));
+  k_amg_to_f32<<<blocks_for(n, 256), 256, 0, m->stream>>>(n, a, *b);
+  FE_CUDA(cudaGetLastError());
+  return FE_OK;
+}
+
+template <class V>
+int numeric_all(fe_mesh m, const V* K0) {
+  AmgHier* h = m->amg;
+  FE_TRY((numeric_level<V, 3>(m, 0, Vals<V, 3>{K0, true})));
+  for (int q = 1; q < h->nlev; q++) FE_TRY((numeric_level<double, AMG_NS>(m, q, Vals<double, AMG_NS>{h->lev[q].val64, false})));
+  if (m->prec != FE_PREC_FP64) {  // the V-cycle's FP32 copies
+    for (int q = 0; q < h->nlev; q++) {
+      AmgLevel& L = h->lev[q];
+      const int64_t bb = (int64_t)L.b * L.b;
+      FE_TRY(to_f32(m, L.dinv64, &L.dinv32, (int64_t)L.n * bb));
+      if (q > 0) FE_TRY(to_f32(m, L.val64, &L.val32, L.nnz * bb));
+      if (q < h->nlev - 1) {
+        FE_TRY(to_f32(m, L.p64, &L.p32, L.nnzp * L.b * AMG_NS));
+        FE_TRY(to_f32(m, L.r64, &L.r32, L.nnzr * L.b * AMG_NS));
+      } else {
+        const int64_t Nd = (int64_t)L.n * L.b;
+        FE_TRY(to_f32(m, L.inv64, &L.inv32, Nd * Nd));
+      }
+    }
+  }
+  return FE_OK;
+}
+
+int ensure_vectors(fe_mesh m, int elem) {
+  AmgHier* h = m->amg;
+  if (h->vec_elem == elem) return FE_OK;  // (a precision change allocates a new set)
+  for (int q = 0; q < h->nlev; q++) {
+    AmgLevel& L = h->lev[q];
+    const size_t bytes = (size_t)L.n * L.b * elem;
+    void** vs[5] = {&L.x, &L.r, &L.d0, &L.d1, &L.e};
+    for (void** v : vs) {
+      char* p = nullptr;
+      FE_TRY(dev_alloc(m, &p, bytes));
+      *v = p;
+    }
+  }
+  h->vec_elem = elem;
+  return FE_OK;
+}
+
+struct Cheb {
+  double inv_theta, c1, c2;
+};
+Cheb cheb_coeffs(double rho) {
+  const double lo = rho / 30.0, hi = 1.1 * rho;
+  const double theta = 0.5 * (hi + lo), delta = 0.5 * (hi - lo), sigma = theta / delta;
+  const double r0 = 1.0 / sigma, r1 = 1.0 / (2.0 * sigma - r0);
+  return Cheb{1.0 / theta, r1 * r0, 2.0 * r1 / delta};
+}
+
+// one V-cycle in precision T; level 0 values of type V (tiled); b FP64 [3 nn];
+// the result in the level-0 x vector
+template <class T, class V>
+int vcycle(fe_mesh m, const V* K0, const double* b, T* x0) {
+  AmgHier* h = m->amg;
+  const int L = h->nlev;
+  auto vals = [&](int q) -> const T* {
+    if constexpr (sizeof(T) == 8) return (const T*)h->lev[q].val64;
+    else return (const T*)h->lev[q].val32;
+  };
+  auto dinv = [&](int q) -> const T* {
+    if constexpr (sizeof(T) == 8) return (const T*)h->lev[q].dinv64;
+    else return (const T*)h->lev[q].dinv32;
+  };
+  auto pv = [&](int q) -> const T* {
+    if constexpr (sizeof(T) == 8) return (const T*)h->lev[q].p64;
+    else return (const T*)h->lev[q].p32;
+  };
+  auto rv = [&](int q) -> const T* {
+    if constexpr (sizeof(T) == 8) return (const T*)h->lev[q].r64;
+    else return (const T*)h->lev[q].r32;
+  };
+  auto inv = [&](int q) -> const T* {
+    if constexpr (sizeof(T) == 8) return (const T*)h->lev[q].inv64;
+    else return (const T*)h->lev[q].inv32;
+  };
+  auto X = [&](int q) { return q == 0 ? x0 : (T*)h->lev[q].x; };
+  const double sv = sizeof(T), s0 = sizeof(V);
+  // Chebyshev step on level q (fused SpMV)
+  auto step = [&](int q, const T* g, T* dout, double cx, double c1, double c2, int flags) -> int {
+    AmgLevel& Lq = h->lev[q];
+    const int B = Lq.b;
+    const double bytes = (double)Lq.nnz * (B * B * (q == 0 ? s0 : sv) + 4) + 4.0 * (Lq.n + 1) +
+                         (double)Lq.n * B * (sv * 5 + B * sv);
+    FE_SCOPE_F(m, FE_PROF_PC, bytes, 2.0 * Lq.nnz * B * B);
+    const unsigned grid = blocks_for((int64_t)Lq.n * 32, 256);
+    if (q == 0)
+      k_vc_cheb<V, T, 3><<<grid, 256, 0, m->stream>>>(Lq.n, Lq.ptr, Lq.col, K0, 1, dinv(0), g, X(0), (T*)Lq.r, dout,
+                                                       (T)cx, (T)c1, (T)c2, flags);
+    else
+      k_vc_cheb<T, T, AMG_NS><<<grid, 256, 0, m->stream>>>(Lq.n, Lq.ptr, Lq.col, vals(q), 0, dinv(q), g, X(q),
+                                                            (T*)Lq.r, dout, (T)cx, (T)c1, (T)c2, flags);
+    FE_CUDA(cudaGetLastError());
+    return FE_OK;
+  };
+  if (L == 1) {  // one level: the exact solve
+    AmgLevel& L0 = h->lev[0];
+    const int64_t N = (int64_t)L0.n * 3;
+    k_vc_convert<double, T><<<blocks_for(N, 256), 256, 0, m->stream>>>(N, b, (T*)L0.r);
+    FE_SCOPE(m, FE_PROF_PC, (double)N * N * sv);
+    k_vc_dense<T><<<1, 256, 0, m->stream>>>((int)N, inv(0), (const T*)L0.r, x0);
+    FE_CUDA(cudaGetLastError());
+    return FE_OK;
+  }
+  // downward: pre-smoothing, restriction
+  for (int q = 0; q < L - 1; q++) {
+    AmgLevel& Lq = h->lev[q];
+    const Cheb ch = cheb_coeffs(Lq.rho);
+    if (q == 0) {
+      FE_SCOPE(m, FE_PROF_PC, (double)Lq.n * (24 + 9 * sv + 6 * sv));
+      k_vc_init0<T><<<blocks_for(Lq.n, 256), 256, 0, m->stream>>>(Lq.n, dinv(0), b, (T*)Lq.r, (T*)Lq.d0,
+                                                                   (T)ch.inv_theta);
+      FE_CUDA(cudaGetLastError());
+    }
+    // x = d0; r -= A d0; d1 = c1 d0 + c2 D^-1 r
+    FE_TRY(step(q, (const T*)Lq.d0, (T*)Lq.d1, 1.0, ch.c1, ch.c2, VC_SETX));
+    // x += d1; r -= A d1 (r = b - A x for the restriction)
+    FE_TRY(step(q, (const T*)Lq.d1, nullptr, 1.0, 0.0, 0.0, 0));
+    AmgLevel& Cq = h->lev[q + 1];
+    const bool coarsest = q + 1 == L - 1;
+    const Cheb cc = coarsest ? Cheb{0, 0, 0} : cheb_coeffs(Cq.rho);
+    {
+      FE_SCOPE_F(m, FE_PROF_PC, (double)Lq.nnzr * (Lq.b * AMG_NS * sv + 4) + (double)Lq.n * Lq.b * sv +
+                                    (double)Cq.n * AMG_NS * sv * 2,
+                 2.0 * Lq.nnzr * Lq.b * AMG_NS);
+      const unsigned grid = blocks_for((int64_t)Cq.n * 32, 256);
+      if (Lq.b == 3)
+        k_vc_restrict<T, 3><<<grid, 256, 0, m->stream>>>(Cq.n, Lq.rptr, Lq.rcol, rv(q), (const T*)Lq.r, dinv(q + 1),
+                                                         (T*)Cq.r, coarsest ? nullptr : (T*)Cq.d0, (T)cc.inv_theta);
+      else
+        k_vc_restrict<T, AMG_NS><<<grid, 256, 0, m->stream>>>(Cq.n, Lq.rptr, Lq.rcol, rv(q), (const T*)Lq.r,
+                                                              dinv(q + 1), (T*)Cq.r, coarsest ? nullptr : (T*)Cq.d0,
+                                                              (T)cc.inv_theta);
+      FE_CUDA(cudaGetLastError());
+    }
+  }
+  {  // coarsest
+    AmgLevel& Lc = h->lev[L - 1];
+    const int N = Lc.n * Lc.b;
+    FE_SCOPE(m, FE_PROF_PC, (double)N * N * sv);
+    k_vc_dense<T><<<1, 256, 0, m->stream>>>(N, inv(L - 1), (const T*)Lc.r, X(L - 1));
+    FE_CUDA(cudaGetLastError());
+  }
+  // upward: prolongation, post-smoothing
+  for (int q = L - 2; q >= 0; q--) {
+    AmgLevel& Lq = h->lev[q];
+    const Cheb ch = cheb_coeffs(Lq.rho);
+    {
+      FE_SCOPE_F(m, FE_PROF_PC, (double)Lq.nnzp * (Lq.b * AMG_NS * sv + 4) + (double)Lq.n * Lq.b * sv * 3,
+                 2.0 * Lq.nnzp * Lq.b * AMG_NS);
+      const unsigned grid = blocks_for((int64_t)Lq.n * 32, 256);
+      if (Lq.b == 3)
+        k_vc_prolong<T, 3><<<grid, 256, 0, m->stream>>>(Lq.n, Lq.pptr, Lq.pcol, pv(q), X(q + 1), X(q), (T*)Lq.e);
+      else
+        k_vc_prolong<T, AMG_NS><<<grid, 256, 0, m->stream>>>(Lq.n, Lq.pptr, Lq.pcol, pv(q), X(q + 1), X(q),
+                                                             (T*)Lq.e);
+      FE_CUDA(cudaGetLastError());
+    }
+    // r -= A e; d0 = D^-1 r / theta
+    FE_TRY(step(q, (const T*)Lq.e, (T*)Lq.d0, 0.0, 0.0, ch.inv_theta, VC_KEEPX));
+    // x += d0; r -= A d0; d1 = c1 d0 + c2 D^-1 r; x += d1
+    FE_TRY(step(q, (const T*)Lq.d0, (T*)Lq.d1, 1.0, ch.c1, ch.c2, VC_FINAL));
+  }
+  return FE_OK;
+}
+
+}  // namespace
+
+int fe_amg_setup(fe_mesh m) {
+  if (m->pres) return fe_set_error("AMG is offered for the displacement block of the displacement form"), FE_ERR_ARG;
+  if (!m->amg) {
+    m->amg = new AmgHier();
+    int rc = build_structure(m);
+    if (rc != FE_OK) {
+      fe_amg_free(m);
+      return rc;
+    }
+  }
+  if (m->prec == FE_PREC_FP64) FE_TRY(numeric_all<double>(m, m->K64));
+  else if (m->prec == FE_PREC_MIXED_BF16) FE_TRY(numeric_all<__nv_bfloat16>(m, m->K16));
+  else FE_TRY(numeric_all<float>(m, m->K32));
+  return FE_OK;
+}
+
+int fe_amg_apply(fe_mesh m, const double* x, void* z, bool z_double) {
+  if (!m->amg || m->amg->lev[0].dinv64 == nullptr) return fe_set_error("AMG hierarchy not set up"), FE_ERR_STATE;
+  AmgHier* h = m->amg;
+  const int64_t N = (int64_t)m->nn * 3;
+  if (m->prec == FE_PREC_FP64) {
+    FE_TRY(ensure_vectors(m, 8));
+    double* out = z_double ? (double*)z : (double*)h->lev[0].x;
+    FE_TRY((vcycle<double, double>(m, m->K64, x, out)));
+    if (!z_double) k_vc_convert<double, float><<<blocks_for(N, 256), 256, 0, m->stream>>>(N, out, (float*)z);
+  } else {
+    FE_TRY(ensure_vectors(m, 4));
+    float* out = z_double ? (float*)h->lev[0].x : (float*)z;
+    if (m->prec == FE_PREC_MIXED_BF16) FE_TRY((vcycle<float, __nv_bfloat16>(m, m->K16, x, out)));
+    else FE_TRY((vcycle<float, float>(m, m->K32, x, out)));
+    if (z_double) k_vc_convert<float, double><<<blocks_for(N, 256), 256, 0, m->stream>>>(N, out, (double*)z);
+  }
+  FE_CUDA(cudaGetLastError());
+  return FE_OK;
+}
+
+void fe_amg_free(fe_mesh m) {
+  if (!m->amg) return;
+  for (void* p : m->amg->allocs) cudaFree(p);
+  m->device_bytes -= m->amg->bytes;
+  delete m->amg;
+  m->amg = nullptr;
+}
+
+// Copy of level `level` of the hierarchy to host buffers (each may be NULL):
+// info [5] = n, b, nnz(A_l), nc, nnz(P_l); rho; A_l pattern and FP64 values
+// (level 0: the tangent's own pattern and values are not copied), absent
+// components, aggregates, and P_l's pattern and FP64 values.
+extern "C" int fe_amg_get_level(fe_mesh m, int level, int64_t* info, double* rho, int32_t* ptr, int32_t* col,
+                                double* val, uint8_t* absent, int32_t* agg, int32_t* pptr, int32_t* pcol,
+                                double* pval) {
+  if (!m) return fe_set_error("NULL mesh"), FE_ERR_ARG;
+  if (!m->amg || m->amg->lev[0].dinv64 == nullptr) return fe_set_error("no AMG hierarchy"), FE_ERR_STATE;
+  AmgHier* h = m->amg;
+  if (level < 0 || level >= h->nlev) return fe_set_error("level %d outside [0, %d)", level, h->nlev), FE_ERR_ARG;
+  FE_CUDA(cudaSetDevice(m->device));
+  FE_CUDA(cudaStreamSynchronize(m->stream));
+  const AmgLevel& L = h->lev[level];
+  const bool last = level == h->nlev - 1;
+  if (info) {
+    info[0] = L.n;
+    info[1] = L.b;
+    info[2] = L.nnz;
+    info[3] = last ? 0 : L.nc;
+    info[4] = last ? 0 : L.nnzp;
+  }
+  if (rho) *rho = L.rho;
+  if (level > 0) {
+    if (ptr) FE_CUDA(cudaMemcpy(ptr, L.ptr, sizeof(int) * (L.n + 1), cudaMemcpyDeviceToHost));
+    if (col) FE_CUDA(cudaMemcpy(col, L.col, sizeof(int) * L.nnz, cudaMemcpyDeviceToHost));
+    if (val) FE_CUDA(cudaMemcpy(val, L.val64, sizeof(double) * L.nnz * L.b * L.b, cudaMemcpyDeviceToHost));
+  }
+  if (absent) FE_CUDA(cudaMemcpy(absent, L.absent, L.n, cudaMemcpyDeviceToHost));
+  if (!last) {
+    if (agg) FE_CUDA(cudaMemcpy(agg, L.agg, sizeof(int) * L.n, cudaMemcpyDeviceToHost));
+    if (pptr) FE_CUDA(cudaMemcpy(pptr, L.pptr, sizeof(int) * (L.n + 1), cudaMemcpyDeviceToHost));
+    if (pcol) FE_CUDA(cudaMemcpy(pcol, L.pcol, sizeof(int) * L.nnzp, cudaMemcpyDeviceToHost));
+    if (pval) FE_CUDA(cudaMemcpy(pval, L.p64, sizeof(double) * L.nnzp * L.b * AMG_NS, cudaMemcpyDeviceToHost));
+  }
+  return FE_OK;
+}
+
+extern "C" int fe_amg_levels(fe_mesh m) { return (m && m->amg && m->amg->lev[0].dinv64) ? m->amg->nlev : 0; }

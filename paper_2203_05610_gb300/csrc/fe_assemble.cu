@@ -860,6 +860,7 @@ int fe_tangent_dev(fe_mesh m, const double* d, int precision) {
     FE_CUDA(cudaGetLastError());
   }
   m->prec = precision;
+  if (m->pc_type == 1) FE_TRY(fe_amg_setup(m));  // the AMG hierarchy of this tangent
   return FE_OK;
 }
 

@@ -154,6 +154,8 @@ struct fe_mesh_s {
   std::vector<ProfRec> prof_pending;
   std::vector<cudaEvent_t> ev_free;
 
+  int pc_type = 0;           // displacement-block preconditioner: 0 nodal block-Jacobi, 1 AMG V-cycle
+  struct AmgHier* amg = nullptr;  // AMG hierarchy (fe_amg.cu), built at the first AMG tangent
   unsigned wait_limit = 1u << 26;  // polls before a bounded device wait gives up
   int coop_blocks = 0;       // co-resident blocks for the persistent kernels
   int sm_count = 0;
@@ -225,6 +227,14 @@ int fe_lbfgs_dev(fe_mesh m, const double* S, const double* Y, const double* rho,
 int fe_workspace(fe_mesh m, int restart);
 int fe_spmv_from_input(fe_mesh m, const void* xin, double* y);  // input already in the SpMV precision
 int fe_spmv_preload(fe_mesh m);  // loads every SpMV kernel and caches its launch facts
+// fe_amg.cu: smoothed-aggregation AMG.  fe_amg_setup builds the hierarchy
+// for the tangent just assembled (its structure once per mesh, on the host;
+// its numbers every time, on the device); fe_amg_apply runs one V-cycle on
+// the displacement part of x (FP64) into z (FP64 or FP32, z_double says
+// which); fe_amg_free releases everything.
+int fe_amg_setup(fe_mesh m);
+int fe_amg_apply(fe_mesh m, const double* x, void* z, bool z_double);
+void fe_amg_free(fe_mesh m);
 // fe_noalloc.cu: resolves the fixed array of fe_spmv_noalloc on the mesh's
 // device and loads the kernels that entry point launches (called by
 // fe_mesh_create with the mesh's device current)

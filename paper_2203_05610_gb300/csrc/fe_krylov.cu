@@ -1136,6 +1136,7 @@ __global__ void __launch_bounds__(256) k_pc_schur(int np, int nn, const int* __r
 
 template <class OT>
 static int pc_apply_t(fe_mesh m, const double* x, OT* z) {
+  if (m->pc_type == 1) return fe_amg_apply(m, x, z, sizeof(OT) == 8);  // one AMG V-cycle
   FE_SCOPE(m, FE_PROF_PC, (double)m->nn * (9.0 * (m->prec == FE_PREC_FP64 ? 8 : 4) + 24 + 3.0 * sizeof(OT)) +
                               (m->pres ? (double)m->nnz_up * (8 + 12.0 * (m->prec == FE_PREC_FP64 ? 8 : 4)) + 24.0 * m->np
                                        : 0.0));
@@ -1715,11 +1716,11 @@ int fe_gmres_dev(fe_mesh m, const double* b, double* x, double rtol, double atol
     FE_CUDA(cudaGetLastError());
     // the block-Jacobi application is fused into the Arnoldi step (it writes
     // z = D^{-1} V_{j+1} for the next SpMV); the u-p Schur preconditioner
-    // needs B2 z_u and runs as its own kernels.  Steps are queued in batches
+    // (it needs B2 z_u) and the AMG V-cycle run as their own kernels.  Steps are queued in batches
     // of GMRES_BATCH; the step that meets the stopping test raises a device
     // flag that turns the rest of its batch into no-ops, so the host reads
     // the scalars once per batch.
-    const bool fuse = !m->pres;
+    const bool fuse = !m->pres && m->pc_type == 0;
     FE_CUDA(cudaMemsetAsync(m->scal + 10, 0, 2 * sizeof(double), m->stream));  // out[7], out[8]
     int batch = 1;
     bool done = false;

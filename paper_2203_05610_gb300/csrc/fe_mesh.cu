@@ -71,14 +71,18 @@ std::mutex g_kernel_mu;
 std::map<KernelKey, int> g_kernel_cache;  // smem opt-ins (threads = -1) and occupancies
 }  // namespace
 
+// The opt-in is one value per kernel and device: raise it to the largest
+// size asked for so far (a smaller later request must not lower it below a
+// size an earlier launch of that kernel still uses).
 int fe_kernel_smem(const void* fn, int smem_bytes) {
   int dev = 0;
   FE_CUDA(cudaGetDevice(&dev));
   std::lock_guard<std::mutex> lk(g_kernel_mu);
-  KernelKey k{fn, dev, -1, (size_t)smem_bytes};
-  if (g_kernel_cache.count(k)) return FE_OK;
+  KernelKey k{fn, dev, -1, 0};
+  auto it = g_kernel_cache.find(k);
+  if (it != g_kernel_cache.end() && it->second >= smem_bytes) return FE_OK;
   FE_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes));
-  g_kernel_cache[k] = 1;
+  g_kernel_cache[k] = smem_bytes;
   return FE_OK;
 }
 
@@ -729,6 +733,7 @@ static int create_impl(const fe_mesh_desc* desc, fe_mesh m) {
 }
 
 static void free_all(fe_mesh m) {
+  fe_amg_free(m);
   prof_resolve(m);
   for (cudaEvent_t e : m->ev_free) cudaEventDestroy(e);
   m->ev_free.clear();
@@ -760,6 +765,18 @@ extern "C" int fe_mesh_create(const fe_mesh_desc* desc, fe_mesh* out) {
     return rc;
   }
   *out = m;
+  return FE_OK;
+}
+
+extern "C" int fe_set_pc(fe_mesh m, int pc_type) {
+  if (!m) return fe_set_error("NULL mesh"), FE_ERR_ARG;
+  if (pc_type != 0 && pc_type != 1) return fe_set_error("pc_type must be 0 (block-Jacobi) or 1 (AMG)"), FE_ERR_ARG;
+  if (pc_type == 1 && m->pres)
+    return fe_set_error("AMG is offered for the displacement form (no pressure unknowns)"), FE_ERR_ARG;
+  FE_CUDA(cudaSetDevice(m->device));
+  const bool rebuild = pc_type == 1 && m->pc_type != 1 && m->prec >= 0;
+  m->pc_type = pc_type;
+  if (rebuild) FE_TRY(fe_amg_setup(m));  // a tangent is assembled already
   return FE_OK;
 }
 

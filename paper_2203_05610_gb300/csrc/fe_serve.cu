@@ -75,6 +75,7 @@ int64_t estimate_footprint(const Request& r, int64_t* ndof_out) {
   b += 9 * sval * nnzb + 9 * sval * nn + (o.precision == FE_PREC_MIXED_BF16 ? 18 * nnzb : 0);  // tangent
   b += 8 * ndof * (restart + 1) + 8 * (restart + 1) * (restart + 1);                             // Krylov basis
   b += 8 * ndof * (2 * mpairs + 12);                                                              // BFGS pairs, vectors
+  if (o.pc_type == 1) b += (d.order == 1 ? 2500 : 6000) * nn;  // AMG: P, A P, P^T in FP64 and coarse levels
   *ndof_out = ndof;
   return b + b / 8 + (64 << 20);
 }
@@ -92,7 +93,8 @@ struct fe_server_s {
   std::deque<int64_t> queue;
   std::map<int64_t, std::unique_ptr<Request>> reqs;
   std::thread scheduler;
-  std::vector<std::thread> workers;
+  std::map<int64_t, std::thread> workers;  // running requests' threads, by request id
+  std::vector<int64_t> finished;           // workers that have returned, to be joined
   std::chrono::steady_clock::time_point t0 = std::chrono::steady_clock::now();
   double now() const {
     return std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
@@ -162,13 +164,32 @@ static void run_request(fe_server s, Request* r) {
     r->error = err;
     s->used -= r->st.footprint;
     s->active--;
+    s->finished.push_back(r->id);
   }
   s->cv.notify_all();
+}
+
+// joins the threads of finished requests (called without the lock held)
+static void join_finished(fe_server s, std::unique_lock<std::mutex>& lk) {
+  std::vector<std::thread> done;
+  for (int64_t id : s->finished) {
+    auto it = s->workers.find(id);
+    if (it != s->workers.end()) {
+      done.push_back(std::move(it->second));
+      s->workers.erase(it);
+    }
+  }
+  s->finished.clear();
+  if (done.empty()) return;
+  lk.unlock();
+  for (auto& t : done) t.join();
+  lk.lock();
 }
 
 static void scheduler_loop(fe_server s) {
   std::unique_lock<std::mutex> lk(s->mu);
   for (;;) {
+    join_finished(s, lk);  // a long-running server keeps no thread of a finished request
     // first fit in arrival order
     bool admitted = false;
     for (auto it = s->queue.begin(); it != s->queue.end();) {
@@ -187,7 +208,7 @@ static void scheduler_loop(fe_server s) {
         s->active++;
         r->st.state = FE_REQ_RUNNING;
         it = s->queue.erase(it);
-        s->workers.emplace_back(run_request, s, r);
+        s->workers.emplace(r->id, std::thread(run_request, s, r));
         admitted = true;
         continue;
       }
@@ -293,7 +314,7 @@ extern "C" int serve_destroy(fe_server s) {
   }
   s->cv.notify_all();
   s->scheduler.join();
-  for (auto& t : s->workers) t.join();
+  for (auto& t : s->workers) t.second.join();
   delete s;
   return FE_OK;
 }

@@ -33,6 +33,7 @@ extern "C" int nl_opts_default(nl_method method, nl_opts* o) {
   o->jac_lag = 1;
   o->hess_reassemble = 0;
   o->ib_adaptive = 0;
+  o->pc_type = 0;
   return FE_OK;
 }
 
@@ -248,16 +249,20 @@ extern "C" int nl_solve(fe_mesh m, int method, double tol, int max_it, double* d
     o.jac_lag = opts->jac_lag > 0 ? opts->jac_lag : 1;
     o.hess_reassemble = opts->hess_reassemble;
     o.ib_adaptive = opts->ib_adaptive;
+    o.pc_type = opts->pc_type;
   }
   if (o.jac_lag < 1 || o.hess_reassemble < 0)
     return fe_set_error("jac_lag must be >= 1 (0 = 1) and hess_reassemble >= 0"), FE_ERR_ARG;
   if (o.orthog < 0 || o.orthog > 2) return fe_set_error("orthog must be 0, 1 or 2"), FE_ERR_ARG;
   if (o.precision < 0 || o.precision > 2) return fe_set_error("bad precision"), FE_ERR_ARG;
+  if (o.pc_type < 0 || o.pc_type > 1) return fe_set_error("pc_type must be 0 or 1"), FE_ERR_ARG;
+  if (o.pc_type == 1 && m->pres) return fe_set_error("AMG is offered for the displacement form"), FE_ERR_ARG;
   FE_CUDA(cudaSetDevice(m->device));
   nl_stats local;
   nl_stats& st = stats ? *stats : local;
   std::memset(&st, 0, sizeof(st));
   auto t0 = std::chrono::steady_clock::now();
+  m->pc_type = o.pc_type;  // used by every tangent assembly of the solve
   int rc = solve_impl(m, method, tol, max_it, d, o, st);
   auto t1 = std::chrono::steady_clock::now();
   st.time_s = std::chrono::duration<double>(t1 - t0).count();
