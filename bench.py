@@ -52,7 +52,7 @@ def parse():
     p.add_argument("--precision", default="mixed_fp32", choices=["fp64", "mixed_fp32", "mixed_bf16"])
     p.add_argument("--ib-adaptive", type=int, default=0, choices=[0, 1],
                    help="iB: Eisenstat-Walker type adaptive H0 tolerance (an extension; 0 = the paper's fixed 1e-2)")
-    p.add_argument("--pc", default="bj", choices=["bj", "amg"],
+    p.add_argument("--pc", default="amg", choices=["bj", "amg"],
                    help="displacement-block preconditioner: nodal block-Jacobi or the AMG V-cycle")
     p.add_argument("--nu", type=float, default=0.3)
     p.add_argument("--traction", type=float, default=1.0)
@@ -65,8 +65,9 @@ def parse():
     p.add_argument("--twist-pressure", default="P1", choices=["P1", "P0"],
                    help="twist pressure space: P1 (Taylor-Hood) or P0 (the paper's P2-P0 pair)")
     p.add_argument("--no-cpu-baseline", action="store_true")
-    p.add_argument("--cpu-sample-iters", type=int, default=0,
-                   help="GMRES iterations of the oracle's timed sample (0 = one full restart cycle)")
+    p.add_argument("--oracle-sample", action="store_true", help=argparse.SUPPRESS)
+    p.add_argument("--no-matrix", action="store_true",
+                   help="skip the methods x precisions matrix measured after the timed region")
     p.add_argument("--serve", type=int, default=0,
                    help="serving mix: number of requests of the seeded Poisson stream (0 = off)")
     p.add_argument("--serve-max-dofs", type=float, default=5e4)
@@ -75,10 +76,7 @@ def parse():
                    help="offered load: arrival rate as a multiple of the measured one-at-a-time capacity "
                         "(above 1 the queue fills and the served rate is the server's capacity)")
     p.add_argument("--serve-precision", default="mixed_fp32", choices=["fp64", "mixed_fp32"])
-    a = p.parse_args()
-    if a.cpu_sample_iters <= 0:
-        a.cpu_sample_iters = a.restart
-    return a
+    return p.parse_args()
 
 
 def workload(args):
@@ -218,121 +216,151 @@ def source_sha(path, region=None):
 
 
 ORACLE_WORK = os.path.join(ROOT, "tests", "golden", "oracle_solve_work.json")
+ORACLE_SOLUTION = os.path.join(ROOT, "tests", "golden", "cook_p2_64x64x8_step1.npz")
+SAMPLE_ITS = 2  # nonlinear iterations of the oracle's timed sample
 
 
-def oracle_work(name, method, restart):
-    """Iteration structure of the oracle's own full solve of this workload
-    (written by tests/golden/oracle_solve_work.py, which calls only the
-    oracle), or None when not recorded for this workload/method/restart."""
+def oracle_work(name, method, restart, pc):
+    """The oracle's own full solve of this workload (written by
+    tests/golden/oracle_solve_work.py, which calls only the oracle): its
+    iteration structure, per-iteration times and wall time, or None when not
+    recorded for this workload, method, restart and preconditioner."""
     try:
         rec = json.load(open(ORACLE_WORK))
     except (OSError, ValueError):
         return None
-    if rec.get("workload") != name or rec.get("method") != method or rec.get("ksp_restart") != restart \
-            or rec.get("status") != 0:
+    if (rec.get("workload") != name or rec.get("method") != method or rec.get("ksp_restart") != restart
+            or rec.get("pc") != pc or rec.get("status") != 0):
         return None
     return rec
 
 
-def oracle_part_times(w, its):
-    """Time the oracle's parts on the workload: one residual, one tangent,
-    GMRES runs of its//4 and its iterations (Arnoldi cost a + b*j per step)."""
+def scaled_solve_s(time_hist, lit_hist, lit_total):
+    """Full-solve time from the timed first two iterations of the same
+    solve: the first iteration (which also assembles the tangent and sets up
+    the preconditioner) plus the second iteration's cost per Krylov
+    iteration times the Krylov iterations of all later iterations (the cost
+    of an iteration follows its Krylov iterations; lit_hist and lit_total
+    from the oracle's own full solve)."""
+    t1, t2 = float(time_hist[1]), float(time_hist[2])
+    return t1 + (t2 - t1) * (lit_total - lit_hist[1]) / max(lit_hist[2], 1)
+
+
+def oracle_sample(w, method, restart, pc):
+    """The oracle's solve of the workload, stopped after its first
+    SAMPLE_ITS nonlinear iterations: per-iteration times (time_hist)."""
     import numpy as np
     import oracle as O
     m = O.Mesh(w)
     load, tm = w["steps"][0]
     m.set_load(load, tm)
-    d = np.zeros(m.ndof)
-    m.apply_dirichlet(d)
     t0 = time.perf_counter()
-    r, _ = m.residual(d)
-    t_res = time.perf_counter() - t0
-    t0 = time.perf_counter()
-    m.tangent(d)
-    t_tan = time.perf_counter() - t0
-    n1, n2 = max(its // 4, 1), its
-    t0 = time.perf_counter()
-    m.gmres(-r, rtol=0.0, atol=0.0, restart=500, max_it=n1)
-    t1 = time.perf_counter() - t0
-    t0 = time.perf_counter()
-    m.gmres(-r, rtol=0.0, atol=0.0, restart=500, max_it=n2)
-    t2 = time.perf_counter() - t0
-    # t(n) = a*n + b*n(n-1)/2 through both samples: a = SpMV + preconditioner +
-    # vector work per step, b = one MGS inner product and update
-    A = np.array([[n1, n1 * (n1 - 1) / 2], [n2, n2 * (n2 - 1) / 2]])
-    a_, b_ = np.linalg.solve(A, np.array([t1, t2]))
-    return dict(res=t_res, tan=t_tan, a=max(a_, 0.0), b=max(b_, 0.0), n1=n1, n2=n2, t1=t1, t2=t2)
+    _, st = m.solve(method, np.zeros(m.ndof), tol=TOL, max_it=SAMPLE_ITS,
+                    opts=dict(ksp_restart=restart, pc_type={"bj": 0, "amg": 1}[pc]))
+    return dict(time_hist=[float(x) for x in st["time_hist"]], lit=int(st["lit_total"]), nit=int(st["nit"]),
+                wall_s=time.perf_counter() - t0)
 
 
-def modelled_solve_s(pt, work, restart):
-    """Oracle time of one solve with the given iteration structure."""
-    t = (work["nit"] + 1) * pt["res"] + work["assemblies"] * pt["tan"]
-    for L in work["lit_hist"][1:work["nit"] + 1]:
-        L = int(L)
-        while L > 0:  # restart cycles
-            c = min(L, restart)
-            t += pt["a"] * c + pt["b"] * c * (c - 1) / 2
-            L -= c
-    return t
+def cpu_baseline_from(sample, rec, name, method, pc):
+    """cpu_baseline of the JSON line: the timed sample scaled to solves/s
+    with the oracle's own iteration count, and its measured full solve."""
+    nit = rec["nit"]
+    t_full = scaled_solve_s(sample["time_hist"], rec["lit_hist"], rec["lit_total"])
+    th = sample["time_hist"]
+    return dict(value=round(1.0 / t_full, 6), unit="solves/s", cores=1, kind="oracle",
+                sample=(f"oracle (plain FP64 C, 1 thread) {method} with the {pc.upper()} preconditioner on {name}, "
+                        f"stopped after its first {SAMPLE_ITS} nonlinear iterations ({th[1]:.1f} s and "
+                        f"{th[2]:.1f} s from the start; the first includes the tangent and the preconditioner "
+                        f"setup), scaled to a full solve by Krylov work (the oracle's own full solve: {nit} "
+                        f"nonlinear, {rec['lit_total']} Krylov iterations): {t_full:.1f} s per solve"),
+                scaled_solve_s=round(t_full, 1),
+                measured_full_solve=dict(wall_s=rec["wall_s"], nit=nit, lit=rec["lit_total"], host=rec.get("host"),
+                                         note="the oracle's full solve recorded by tests/golden/oracle_solve_work.py"))
 
 
-def cpu_baseline_sample(w, name, args, gpu_stats, method_list):
-    """The oracle on a bounded sample of the same workload, in solves/s: the
-    timed per-part costs combined with the iteration structure of the
-    oracle's own full solve when recorded, else with the GPU run's (same
-    algorithm; says which)."""
-    pt = oracle_part_times(w, args.cpu_sample_iters)
-    total, src = 0.0, []
-    for meth in method_list:
-        rec = oracle_work(name, meth, args.restart)
-        work = rec if rec else gpu_stats[meth]
-        src.append(f"{meth}: {'oracle full solve' if rec else 'GPU run'} iteration structure")
-        total += modelled_solve_s(pt, work, args.restart)
-    sample = (f"oracle (1 thread) on the same workload: 1 residual ({pt['res']:.2f} s), 1 tangent "
-              f"({pt['tan']:.2f} s), GMRES runs of {pt['n1']} and {pt['n2']} iterations ({pt['t1']:.2f} s, "
-              f"{pt['t2']:.2f} s); solves/s from these per-part times and the {'; '.join(src)}")
-    return dict(value=len(method_list) / total, unit="solves/s", cores=1, kind="oracle", sample=sample,
-                modelled_solve_s=round(total / len(method_list), 1))
+def run_oracle_sample(args):
+    """--oracle-sample: print the oracle's timed sample as one JSON line."""
+    w, name = workload(args)
+    method = [m.strip() for m in args.methods.split(",") if m.strip()][0]
+    print(json.dumps(dict(name=name, method=method, **oracle_sample(w, method, args.restart, args.pc))), flush=True)
+
+
+def start_oracle_sample(args):
+    """The CPU baseline runs beside the GPU work in a process of its own
+    (started before the first CUDA call)."""
+    cmd = [sys.executable, os.path.abspath(__file__), "--oracle-sample", "--methods", args.methods, "--restart",
+           str(args.restart), "--pc", args.pc, "--mesh", args.mesh, "--nu", str(args.nu), "--traction",
+           str(args.traction), "--workload", args.workload]
+    return subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+
+
+REF_KRYLOV_ITS = 10  # Krylov iterations timed per reference step
 
 
 def run_reference(args):
-    """The oracle as the reference arm: every step times a bounded sample of
-    the same workload (one residual, one tangent, two short GMRES runs) and
-    the step's solve time is the oracle's full-solve time modelled from those
-    per-part times and the iteration structure of the oracle's own full
-    solve (tests/golden/oracle_solve_work.json)."""
+    """The oracle as the reference arm.  Its full solve of this workload
+    takes minutes (single-threaded FP64), so every step times a bounded
+    sample of it -- one residual evaluation and REF_KRYLOV_ITS iterations of
+    the preconditioned GMRES on the tangent of d_0 -- and the step's solve
+    time is these per-part times combined with the iteration structure of
+    the oracle's own full solve (nonlinear iterations, Krylov iterations),
+    plus the tangent assembly and preconditioner setup timed once before the
+    steps.  Warm-up steps run the small Cook P1 8x8x2 solve (CPU code needs
+    no warming)."""
     world, rank, local = dist_env()
     if rank != 0:
         return
+    import numpy as np
+    import oracle as O
+    import workloads as W
     w, name = workload(args)
-    methods = [m.strip() for m in args.methods.split(",") if m.strip()]
-    works = {m: oracle_work(name, m, args.restart) for m in methods}
-    missing = [m for m, r in works.items() if r is None]
-    if missing:
-        print(json.dumps(dict(impl="reference", unavailable=f"no recorded oracle solve structure for {name} "
-                                                            f"{missing} restart {args.restart}")), flush=True)
+    method = [m.strip() for m in args.methods.split(",") if m.strip()][0]
+    rec = oracle_work(name, method, args.restart, args.pc)
+    if rec is None:
+        print(json.dumps(dict(impl="reference", unavailable=f"no recorded oracle solve of {name} {method} "
+                                                            f"restart {args.restart} pc {args.pc}")), flush=True)
         return
     for _ in range(args.warmup):
-        oracle_part_times(w, args.cpu_sample_iters)
+        wc = W.cook(8, 8, 2, order=1, nu=args.nu)
+        mc = O.Mesh(wc)
+        mc.set_load(wc["steps"][0][0])
+        mc.solve(method, np.zeros(mc.ndof), opts=dict(pc_type={"bj": 0, "amg": 1}[args.pc]))
+    m = O.Mesh(w)
+    load, tm = w["steps"][0]
+    m.set_load(load, tm)
+    d = m.apply_dirichlet(np.zeros(m.ndof))
+    r, _ = m.residual(d)
+    m.set_pc(args.pc)
+    t0 = time.perf_counter()
+    m.tangent(d)
+    t_setup = time.perf_counter() - t0
     t_model, t_wall = 0.0, 0.0
     for _ in range(args.steps):
         t0 = time.perf_counter()
-        pt = oracle_part_times(w, args.cpu_sample_iters)
-        t_wall += time.perf_counter() - t0
-        t_model += sum(modelled_solve_s(pt, works[m], args.restart) for m in methods)
-    value = args.steps * len(methods) / t_model
-    sample = (f"each step: oracle (1 thread) residual, tangent and GMRES runs of {max(args.cpu_sample_iters // 4, 1)} "
-              f"and {args.cpu_sample_iters} iterations on {name} ({t_wall / args.steps:.1f} s of CPU per step); "
-              f"solve time modelled from these and the oracle's own full-solve iteration structure "
-              f"({', '.join(f'{m}: nit {works[m]['nit']}, Krylov {works[m]['lit_total']}' for m in methods)})")
-    out = dict(impl="reference", metric=METRIC, value=value, unit="solves/s", n_gpus=args.gpus,
-               steps=args.steps, warmup=args.warmup, ms_per_step=1e3 * t_model / args.steps,
+        m.residual(d)
+        t_res = time.perf_counter() - t0
+        t0 = time.perf_counter()
+        m.gmres(-r, rtol=0.0, atol=0.0, restart=args.restart, max_it=REF_KRYLOV_ITS)
+        t_kry = (time.perf_counter() - t0) / REF_KRYLOV_ITS
+        t_wall += t_res + t_kry * REF_KRYLOV_ITS
+        t_model += rec["assemblies"] * t_setup + (rec["nit"] + 1) * t_res + rec["lit_total"] * t_kry
+    value = args.steps / t_model
+    sample = (f"each step: oracle (plain FP64 C, 1 thread) residual and {REF_KRYLOV_ITS} {args.pc.upper()}-"
+              f"preconditioned GMRES iterations on {name}; solve time = tangent + preconditioner setup "
+              f"({t_setup:.1f} s, timed once) + {rec['nit'] + 1} residuals + {rec['lit_total']} Krylov iterations "
+              f"(the oracle's own full {method} solve), scaled from these per-part times; the oracle's measured "
+              f"full solve took {rec['wall_s']} s on {rec.get('host', {}).get('machine', '?')}")
+    out = dict(impl="reference", metric=METRIC, value=round(value, 6), unit="solves/s", n_gpus=args.gpus,
+               steps=args.steps, warmup=args.warmup, ms_per_step=round(1e3 * t_model / args.steps, 1),
                higher_is_better=True, scaling="weak", vs_baseline=None, dtype="f64", data="synthetic",
                config=dict(workload=name, nu=args.nu, traction=args.traction,
-                           load_step=f"step 1 of {len(w['steps'])} from rest", methods=methods,
-                           ksp_restart=args.restart, tol=TOL),
-               cpu_baseline=dict(kind="oracle", cores=1, value=value, sample=sample),
-               e2e=dict(value=value, unit="solves/s", h2d_bytes_per_step=0, d2h_bytes_per_step=0))
+                           load_step=f"step 1 of {len(w['steps'])} from rest", methods=[method],
+                           preconditioner={"bj": "nodal block-Jacobi", "amg": "AMG V-cycle"}[args.pc],
+                           ksp_restart=args.restart, tol=TOL, sample_wall_s_per_step=round(t_wall / args.steps, 1)),
+               cpu_baseline=dict(kind="oracle", cores=1, value=round(value, 6), unit="solves/s", sample=sample,
+                                 scaled_solve_s=round(t_model / args.steps, 1),
+                                 measured_full_solve=dict(wall_s=rec["wall_s"], host=rec.get("host"))),
+               e2e=dict(value=round(value, 6), unit="solves/s", h2d_bytes_per_step=0, d2h_bytes_per_step=0))
     print(json.dumps(out), flush=True)
 
 
@@ -428,16 +456,62 @@ def run_serving(args):
     print(json.dumps(out), flush=True)
 
 
+def oracle_solution(name):
+    """The oracle's converged solution of the benchmark workload (written by
+    tests/golden/oracle_reference_solution.py), or None."""
+    if name != "cook_p2_64x64x8":
+        return None
+    try:
+        import numpy as np
+        return np.load(ORACLE_SOLUTION)["d"]
+    except (OSError, KeyError, ValueError):
+        return None
+
+
+def method_matrix(m, dev, opts_base, ref, methods=("NK", "iNK", "B", "iB"), precisions=("mixed_fp32", "fp64")):
+    """Each method in each precision (with the run's preconditioner), solved
+    once after a warm-up solve, outside the timed region: status, nonlinear
+    and Krylov iterations, time to tolerance and the relative error against
+    the FP64 oracle's solution."""
+    import numpy as np
+    import torch
+    out = {}
+    d = torch.zeros(m.ndof, dtype=torch.float64, device=dev)
+    for prec in precisions:
+        for meth in methods:
+            o = dict(opts_base, precision=prec)
+            rec = None
+            for rep in range(2):
+                d.zero_()
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                _, st = m.solve(meth, d, tol=TOL, opts=o)
+                torch.cuda.synchronize()
+                rec = dict(status=st["status"], nit=st["nit"], lit=st["lit_total"], assemblies=st["assemblies"],
+                           time_to_tol_s=round(time.perf_counter() - t0, 4), rrel=st["rfinal"] / st["r0"])
+            if ref is not None and rec["status"] == 0:
+                x = d.cpu().numpy()
+                rec["err_vs_oracle"] = float(np.linalg.norm(x - ref) / np.linalg.norm(ref))
+            out[f"{meth}/{prec}"] = rec
+    return out
+
+
 def main():
     args = parse()
+    if args.oracle_sample:
+        run_oracle_sample(args)
+        return
     if args.impl == "reference":
         run_reference(args)
         return
     if args.serve:
         run_serving(args)
         return
-    import torch
     world, rank, local = dist_env()
+    cpu_proc = None
+    if world == 1 and not args.no_cpu_baseline:
+        cpu_proc = start_oracle_sample(args)  # a process of its own, before any CUDA call
+    import torch
     if world > 1:
         import torch.distributed as dist
         torch.cuda.set_device(local)
@@ -486,6 +560,7 @@ def main():
     solves, ms, value = job_throughput(converged, ev0.elapsed_time(ev1), dist, dev)
     if dist:
         dist.barrier()
+    m.profile_reset(timing=False)
 
     # end to end through the C ABI with host buffers: pinned initial guess in,
     # solution out, every step
@@ -502,46 +577,60 @@ def main():
     e2e_s = world_reduce(time.perf_counter() - t0, dist, dev, "max")
 
     if rank == 0:
+        import numpy as np
+        ref = oracle_solution(name)
+        err_headline = None
+        if ref is not None:
+            err_headline = float(np.linalg.norm(h_out.numpy() - ref) / np.linalg.norm(ref))
+        matrix = None
+        if not args.no_matrix and args.workload == "cook":
+            base = dict(ksp_restart=args.restart, orthog=args.orthog, pc_type=args.pc)
+            matrix = method_matrix(m, dev, base, ref)
+            if args.pc == "amg":  # the benchmark spec's nodal block-Jacobi, for comparison
+                matrix.update({k + "/block_jacobi": v for k, v in
+                               method_matrix(m, dev, dict(base, pc_type="bj"), ref, methods=("iB",),
+                                             precisions=("mixed_fp32",)).items()})
         pk, src = peaks()
         timed = {k: v for k, v in prof.items() if v["timed"] > 0}
         dom = max(timed, key=lambda k: timed[k]["ms"])
         tot_ms = sum(v["ms"] for v in timed.values())
 
-        def hbm_line(name):
-            v = timed[name]
+        def hbm_line(cls):
+            v = timed[cls]
             achieved = v["bytes"] / (v["ms"] / 1e3) / 1e9
-            tr = traffic_record(name, v["bytes"] / v["timed"])
-            return dict(kernel=name, bound="hbm", achieved=round(achieved, 1), peak=pk["hbm_gbs"], unit="GB/s",
+            tr = traffic_record(cls, v["bytes"] / v["timed"])
+            return dict(kernel=cls, bound="hbm", achieved=round(achieved, 1), peak=pk["hbm_gbs"], unit="GB/s",
                         frac=round(achieved / pk["hbm_gbs"], 4), traffic=tr,
                         peak_source=f"{src} STREAM-style copy (MEASURED_PEAKS.json)",
                         avg_launch_us=round(1e3 * v["ms"] / v["timed"], 2),
                         share_of_kernel_time=round(v["ms"] / tot_ms, 3),
                         algorithmic_bytes_per_launch=round(v["bytes"] / v["timed"]))
 
-        if dom in ("arnoldi", "twoloop"):
+        def alu_line(cls):
             # FP64 dot/axpy sweeps: bound by the FP64 FMA rate (2 FMA per entry
             # per inner product), not by HBM; peak: GB300 FP64 1.25 TFLOP/s
-            v = timed[dom]
+            v = timed[cls]
             achieved = v["flops"] / (v["ms"] / 1e3) / 1e12
-            line = hbm_line(dom)
-            roof = dict(kernel=dom, bound="alu", achieved=round(achieved, 4), peak=FP64_PEAK_TFLOPS, unit="TFLOP/s",
+            line = hbm_line(cls)
+            return dict(kernel=cls, bound="alu", achieved=round(achieved, 4), peak=FP64_PEAK_TFLOPS, unit="TFLOP/s",
                         frac=round(achieved / FP64_PEAK_TFLOPS, 4), traffic=line["traffic"],
                         peak_source="FP64 FMA: nominal GB300 1.25 TFLOP/s (an FMA-chain probe measured 1.19)",
                         avg_launch_us=line["avg_launch_us"], share_of_kernel_time=line["share_of_kernel_time"],
                         algorithmic_bytes_per_launch=line["algorithmic_bytes_per_launch"],
                         algorithmic_flops_per_launch=round(v["flops"] / v["timed"]),
                         hbm_view=dict(achieved=line["achieved"], peak=line["peak"], unit="GB/s", frac=line["frac"]))
-        else:
-            roof = hbm_line(dom)
-        roof_spmv = hbm_line("spmv") if "spmv" in timed else None
+
+        roof = alu_line(dom) if dom in ("arnoldi", "twoloop") else hbm_line(dom)
         per_method = {}
         for meth in methods:
             sts = stats[meth]
             per_method[meth] = dict(status=sts[-1]["status"], converged=sum(1 for x in sts if x["status"] == 0),
                                     nit=sts[-1]["nit"], lit=sts[-1]["lit_total"],
                                     assemblies=sts[-1]["assemblies"],
-                                    time_to_tol_s=sorted(s["time_s"] for s in sts)[len(sts) // 2],
+                                    time_to_tol_s=sorted(s_["time_s"] for s_ in sts)[len(sts) // 2],
                                     rrel=sts[-1]["rfinal"] / sts[-1]["r0"])
+            if err_headline is not None and meth == methods[-1]:
+                per_method[meth]["err_vs_oracle"] = err_headline
         launches = sum(v["launches"] for v in prof.values())
         out = dict(metric=METRIC, value=round(value, 4), unit="solves/s", n_gpus=world, steps=args.steps,
                    warmup=args.warmup, ms_per_step=round(ms / args.steps, 3), higher_is_better=True,
@@ -550,22 +639,39 @@ def main():
                                                                  else "bf16+f32+f64"),
                    data="synthetic",
                    config=dict(workload=name, dofs=m.ndof, blocks=m.nnzb, nu=args.nu, traction=args.traction,
-                               load_step=f"step 1 of {len(w['steps'])} from rest", methods=methods, precision=args.precision, tol=TOL,
-                               ksp_restart=args.restart, orthog=["mgs", "mgs_lowsync", "mgs_blocked"][args.orthog],
+                               load_step=f"step 1 of {len(w['steps'])} from rest", methods=methods,
+                               precision=args.precision, tol=TOL, ksp_restart=args.restart,
+                               orthog=["mgs", "mgs_lowsync", "mgs_blocked"][args.orthog],
                                preconditioner={"bj": "nodal block-Jacobi", "amg": "AMG V-cycle"}[args.pc],
                                ib_h0_tolerance="adaptive (extension)" if args.ib_adaptive else "fixed",
                                l2="working set > L2 (tangent and Krylov basis), no flush",
                                parallelism=f"replicas x{world}"),
-                   methods=per_method, roofline=roof, roofline_spmv=roof_spmv,
+                   methods=per_method, roofline=roof,
+                   roofline_spmv=hbm_line("spmv") if "spmv" in timed else None,
+                   roofline_arnoldi=alu_line("arnoldi") if "arnoldi" in timed else None,
                    kernels={k: dict(launches=v["launches"], ms=round(v["ms"], 3),
                                     gbs=round(v["bytes"] / max(v["ms"], 1e-9) / 1e6, 1)) for k, v in prof.items()},
                    gpu_launches=launches, clocks=clocks,
                    e2e=dict(value=round(solves / e2e_s, 4) if converged else 0.0, unit="solves/s",
                             h2d_bytes_per_step=8 * m.ndof * len(methods),
                             d2h_bytes_per_step=8 * m.ndof * len(methods)))
-        if world == 1 and not args.no_cpu_baseline:
-            out["cpu_baseline"] = cpu_baseline_sample(w, name, args, {k: v[-1] for k, v in stats.items()}, methods)
+        if matrix is not None:
+            out["method_matrix"] = dict(note="each method in each precision solved once after a warm-up solve, "
+                                             "outside the timed region; err_vs_oracle against the FP64 oracle's "
+                                             "solution (tests/golden/cook_p2_64x64x8_step1.npz)", results=matrix)
+        if cpu_proc is not None:
+            try:
+                line = cpu_proc.communicate(timeout=900)[0].strip().splitlines()[-1]
+                smp = json.loads(line)
+                rec = oracle_work(name, smp["method"], args.restart, args.pc)
+                if rec is not None:
+                    out["cpu_baseline"] = cpu_baseline_from(smp, rec, name, smp["method"], args.pc)
+            except (subprocess.TimeoutExpired, IndexError, ValueError) as e:
+                cpu_proc.kill()
+                out["cpu_baseline"] = dict(unavailable=f"oracle sample did not finish: {type(e).__name__}")
         print(json.dumps(out), flush=True)
+    elif cpu_proc is not None:
+        cpu_proc.kill()
     if dist:
         dist.destroy_process_group()
 

@@ -337,11 +337,11 @@ enum {
   FE_PROF_RESIDUAL = 0, /* element residual + node gather */
   FE_PROF_TANGENT = 1,  /* coloured tangent assembly, springs, diagonal inverse */
   FE_PROF_SPMV = 2,     /* block-CSR SpMV */
-  FE_PROF_PC = 3,       /* block-Jacobi / Schur preconditioner */
+  FE_PROF_PC = 3,       /* block-Jacobi / Schur preconditioner, AMG V-cycle (one launch of its graph) */
   FE_PROF_ARNOLDI = 4,  /* persistent MGS Arnoldi step */
   FE_PROF_TWOLOOP = 5,  /* L-BFGS two-loop recursion */
   FE_PROF_VECTOR = 6,   /* dots, axpys, copies, GMRES update */
-  FE_PROF_OTHER = 7
+  FE_PROF_OTHER = 7     /* mesh set-up and the AMG hierarchy's numbers after each assembly */
 };
 typedef struct {
   int64_t launches[FE_PROF_CLASSES]; /* kernel launches since the last reset */

@@ -321,12 +321,13 @@ class Mesh:
             for k, v in opts.items():
                 o[keys.index(k)] = v
         d = np.ascontiguousarray(d, dtype=np.float64)
-        st = np.zeros(6 + 4 * HIST)
+        st = np.zeros(6 + 5 * HIST)
         status = lib().om_solve(self.h, mth, tol, max_it, _p(d), _p(o), _p(st))
         nit = int(st[1])
         stats = dict(status=status, nit=nit, lit_total=int(st[2]), assemblies=int(st[3]),
                      r0=st[4], rfinal=st[5], res_hist=st[6:6 + nit + 1].copy(),
                      lit_hist=st[6 + HIST:6 + HIST + nit + 1].astype(int),
                      eta_hist=st[6 + 2 * HIST:6 + 2 * HIST + nit + 1].copy(),
-                     lres_hist=st[6 + 3 * HIST:6 + 3 * HIST + nit + 1].copy())
+                     lres_hist=st[6 + 3 * HIST:6 + 3 * HIST + nit + 1].copy(),
+                     time_hist=st[6 + 4 * HIST:6 + 4 * HIST + nit + 1].copy())
         return d, stats

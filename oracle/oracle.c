@@ -22,6 +22,7 @@
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
+#include <time.h>
 
 /* ======================================================================
  * small helpers
@@ -1728,6 +1729,13 @@ void om_lbfgs_apply(om_mesh* m, const double* S, const double* Y, const double* 
 /* ======================================================================
  * nonlinear solvers (Section "Numerical solvers", Appendix A)
  * ====================================================================== */
+/* seconds since t0 (instrumentation: the per-iteration times of a solve) */
+static double om_elapsed(const struct timespec* t0) {
+  struct timespec t;
+  clock_gettime(CLOCK_MONOTONIC, &t);
+  return (double)(t.tv_sec - t0->tv_sec) + 1e-9 * (double)(t.tv_nsec - t0->tv_nsec);
+}
+
 int om_solve(om_mesh* m, int method, double tol, int max_it, double* d, const double* opts,
              double* stats) {
   long n = m->ndof;
@@ -1741,7 +1749,10 @@ int om_solve(om_mesh* m, int method, double tol, int max_it, double* d, const do
   double* lit_hist = stats + 6 + OM_HIST;
   double* eta_hist = stats + 6 + 2 * OM_HIST;
   double* lres_hist = stats + 6 + 3 * OM_HIST;
-  for (int i = 0; i < 6 + 4 * OM_HIST; i++) stats[i] = 0.0;
+  double* time_hist = stats + 6 + 4 * OM_HIST;
+  for (int i = 0; i < 6 + 5 * OM_HIST; i++) stats[i] = 0.0;
+  struct timespec ts0;
+  clock_gettime(CLOCK_MONOTONIC, &ts0);
   if ((int)opts[9]) om_apply_dirichlet(m, d);
   double* R = (double*)xcalloc(n, sizeof(double));
   double* Rn = (double*)xcalloc(n, sizeof(double));
@@ -1751,6 +1762,7 @@ int om_solve(om_mesh* m, int method, double tol, int max_it, double* d, const do
   int assemblies = 0, status = 2, nit = 0;
   double r0 = om_residual(m, d, R), rk = r0;
   res_hist[0] = r0;
+  time_hist[0] = om_elapsed(&ts0);
   if (!isfinite(r0)) {
     status = 3;
     goto out;
@@ -1788,7 +1800,10 @@ int om_solve(om_mesh* m, int method, double tol, int max_it, double* d, const do
       double rprev = rk;
       rk = om_residual(m, d, R);
       nit = k;
-      if (k < OM_HIST) res_hist[k] = rk;
+      if (k < OM_HIST) {
+        res_hist[k] = rk;
+        time_hist[k] = om_elapsed(&ts0);
+      }
       if (!isfinite(rk)) { status = 3; goto out; }
       if (rk <= tol * r0) { status = 0; goto out; }
       if (rk > dtol * r0) { status = 1; goto out; }
@@ -1846,7 +1861,10 @@ int om_solve(om_mesh* m, int method, double tol, int max_it, double* d, const do
       }
       rk = om_residual(m, d, Rn);
       nit = k;
-      if (k < OM_HIST) res_hist[k] = rk;
+      if (k < OM_HIST) {
+        res_hist[k] = rk;
+        time_hist[k] = om_elapsed(&ts0);
+      }
       /* secant pair s = delta, y = R_{k+1} - R_k, rho = 1/(y.s), skipped when y.s <= 0 */
       for (long i = 0; i < n; i++) t[i] = Rn[i] - R[i];
       double ys = dot(t, dl, n);

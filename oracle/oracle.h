@@ -24,11 +24,13 @@
  *   hess_reassemble iterations, 0 = never),
  *   ib_adaptive (iB: 1 = Eisenstat-Walker choice-2 tolerance for the H0 solve),
  *   pc_type (0 nodal block-Jacobi, 1 algebraic multigrid V-cycle)
- * Stats array (6 + 4*OM_HIST doubles):
+ * Stats array (6 + 5*OM_HIST doubles):
  *   status, nit, lit_total, assemblies, r0, rfinal,
  *   res_hist[OM_HIST], lit_hist[OM_HIST], eta_hist[OM_HIST],
  *   lres_hist[OM_HIST] (NK/iNK: linear residual ||R_{k-1} + K_{k-1} delta_k||
- *   of iteration k, the second norm of the Eisenstat-Walker forcing term)
+ *   of iteration k, the second norm of the Eisenstat-Walker forcing term),
+ *   time_hist[OM_HIST] (seconds from the start of the solve to the end of
+ *   iteration k; instrumentation for the timed CPU baseline)
  */
 #ifndef ORACLE_H
 #define ORACLE_H

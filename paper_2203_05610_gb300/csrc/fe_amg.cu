@@ -39,6 +39,7 @@
 // rows (r stays b - A x throughout, so the residual for the restriction
 // comes for free); level 0 reads the tangent in its tiled layout.
 #include <algorithm>
+#include <climits>
 #include <cmath>
 #include <cstring>
 #include <numeric>
@@ -96,6 +97,10 @@ struct AmgLevel {
   double* inv64 = nullptr;
   float* inv32 = nullptr;
   double rho = 0.0;
+  double *vt64 = nullptr, *pt64 = nullptr;  // tiled V-cycle copies of A_l (l >= 1) and P_l
+  float *vt32 = nullptr, *pt32 = nullptr;
+  double* coef64 = nullptr;  // Chebyshev coefficients {1/theta, c1, c2} in device memory, so
+  float* coef32 = nullptr;   // a captured V-cycle stays valid when a new tangent changes them
   // V-cycle vectors [n*b] in the V-cycle precision
   void *x = nullptr, *r = nullptr, *d0 = nullptr, *d1 = nullptr, *e = nullptr;
 };
@@ -109,6 +114,13 @@ struct AmgHier {
   double* scal = nullptr;    // [4] rho, 1/|y|
   std::vector<void*> allocs; // device buffers owned by the hierarchy
   int64_t bytes = 0;         // their size (counted in the mesh's device bytes)
+  // the V-cycle captured as a CUDA graph: input vin (FP64), output lev[0].x
+  double* vin = nullptr;
+  cudaStream_t cap = nullptr;       // capture stream (the mesh's may be the legacy stream)
+  cudaGraphExec_t exec = nullptr;
+  int exec_prec = -1;               // tangent precision the graph was captured for
+  double vc_bytes = 0, vc_flops = 0; // algorithmic bytes and flops of one V-cycle
+  unsigned grid0 = 0;               // one wave of the streamed level-0 kernel
 };
 
 namespace {
@@ -283,6 +295,15 @@ void coarsen(HostLevel& L, HostLevel& C) {
 }
 
 // ---------------------------------------------------------------- device helpers
+// V-cycle copies of the operators are tiled like the tangent: tiles of 32
+// consecutive blocks, component-major inside a tile, so the lanes of a warp
+// reading one component of consecutive blocks read one 128-byte run
+template <int NV>
+__host__ __device__ __forceinline__ int64_t tix(int64_t k, int c) {
+  return (k >> 5) * (NV * 32) + 32 * c + (k & 31);
+}
+inline int64_t tiled_count(int64_t nblocks, int nv) { return (nblocks + 31) / 32 * 32 * nv; }
+
 template <class V>
 __device__ __forceinline__ double ldd(const V* p);
 template <>
@@ -630,19 +651,179 @@ __global__ void k_amg_to_f32(int64_t n, const double* __restrict__ a, float* __r
   if (i < n) b[i] = (float)a[i];
 }
 
+// block-major FP64 blocks of nv values -> the tiled layout in type T
+template <int NV, class T>
+__global__ void k_amg_tile(int64_t nblocks, const double* __restrict__ src, T* __restrict__ dst) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nblocks * NV) return;
+  const int64_t k = i / NV;
+  const int c = (int)(i % NV);
+  dst[tix<NV>(k, c)] = (T)src[i];
+}
+
 // ---------------------------------------------------------------- V-cycle kernels
 // One Chebyshev step of level l, fused (row i of n block rows, B components):
 //   t = (A g)_i; x_i = (setx ? 0 : x_i) + cx g_i; r_i -= t;
 //   dout_i = c1 g_i + c2 D_i^-1 r_i; final: x_i += dout_i.
 // One warp per block row, one lane per block; level 0 reads the tangent
 // in its tiled layout.
-enum { VC_SETX = 1, VC_FINAL = 2, VC_KEEPX = 4 };
+enum { VC_SETX = 1, VC_FINAL = 2, VC_KEEPX = 4, VC_START = 8 };
 
-template <class V, class T, int B>
+
+// Chebyshev epilogue of block row `row` with row sum s = (A g)_row
+template <class T, int B>
+__device__ __forceinline__ void cheb_rows(int64_t row, const T (&s)[B], const T* __restrict__ dinv,
+                                          const T* __restrict__ g, T* __restrict__ x, T* __restrict__ r,
+                                          T* __restrict__ dout, T cx, const T* __restrict__ coef, int flags) {
+  const int64_t o = (int64_t)B * row;
+  T rn[B], gi[B], xi[B];
+#pragma unroll
+  for (int q = 0; q < B; q++) {
+    gi[q] = g[o + q];
+    rn[q] = r[o + q] - s[q];
+    r[o + q] = rn[q];
+  }
+  const bool wx = !(flags & VC_KEEPX);
+#pragma unroll
+  for (int q = 0; q < B; q++) xi[q] = ((flags & VC_SETX) ? T(0) : (wx ? x[o + q] : T(0))) + cx * gi[q];
+  if (dout) {
+    const T c1 = (flags & VC_START) ? T(0) : coef[1];
+    const T c2 = (flags & VC_START) ? coef[0] : coef[2];
+#pragma unroll
+    for (int q = 0; q < B; q++) {
+      T t = T(0);
+#pragma unroll
+      for (int j = 0; j < B; j++) t += dinv[row * B * B + B * q + j] * rn[j];
+      const T dn = c1 * gi[q] + c2 * t;
+      dout[o + q] = dn;
+      if (flags & VC_FINAL) xi[q] += dn;
+    }
+  }
+  if (wx)
+#pragma unroll
+    for (int q = 0; q < B; q++) x[o + q] = xi[q];
+}
+
+// Level-0 Chebyshev step, streamed like the SpMV: a warp takes groups of 16
+// consecutive block rows and walks their (contiguous) blocks in chunks of 32,
+// one block per lane, forming the row sums by a segmented scan across the
+// lanes and carrying a row's partial sum into the next chunk; values, column
+// indices and the gather of g run two chunks ahead.  The lane holding a
+// row's last block applies that row's Chebyshev update (cheb_rows), so the
+// updates of a chunk's rows run in parallel.  Every row of A holds its
+// diagonal block, so no row is empty.
+constexpr int VC_RPW = 16;
+
+template <class V, class T>
+__device__ __forceinline__ void vc_load_chunk(const int* __restrict__ col, const V* __restrict__ val, int64_t k,
+                                              int64_t kend, int& c, T (&v)[9]) {
+  if (k < kend) {
+    c = __ldg(col + k);
+#pragma unroll
+    for (int t = 0; t < 9; t++) v[t] = ldt<T, V>(val + tix<9>(k, t));
+  } else {
+    c = -1;
+#pragma unroll
+    for (int t = 0; t < 9; t++) v[t] = T(0);
+  }
+}
+
+template <class T>
+__device__ __forceinline__ void vc_load_g(const T* __restrict__ g, int c, T (&x)[3]) {
+#pragma unroll
+  for (int j = 0; j < 3; j++) x[j] = c >= 0 ? g[3 * (int64_t)c + j] : T(0);
+}
+
+template <class V, class T>
+__global__ void __launch_bounds__(256) k_vc_cheb0(int n, const int* __restrict__ row_ptr, const int* __restrict__ col,
+                                                  const V* __restrict__ val, const T* __restrict__ dinv,
+                                                  const T* __restrict__ g, T* __restrict__ x, T* __restrict__ r,
+                                                  T* __restrict__ dout, T cx, const T* __restrict__ coef,
+                                                  int flags) {
+  const int lane = threadIdx.x & 31;
+  const int ngroups = (n + VC_RPW - 1) / VC_RPW;
+  const int nwarps = (int)(((int64_t)gridDim.x * blockDim.x) >> 5);
+  for (int grp = (int)((((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5)); grp < ngroups; grp += nwarps) {
+    const int r0 = grp * VC_RPW;
+    const int nr = min(VC_RPW, n - r0);
+    const int rpl = lane < nr ? __ldg(row_ptr + r0 + lane) : INT_MAX;  // start of row r0 + lane
+    const int kstart = __shfl_sync(0xffffffffu, rpl, 0);
+    const int kend = __ldg(row_ptr + r0 + nr);
+    int c0, c1;
+    T v0[9], v1[9];
+    vc_load_chunk<V, T>(col, val, (int64_t)kstart + lane, kend, c0, v0);
+    vc_load_chunk<V, T>(col, val, (int64_t)kstart + 32 + lane, kend, c1, v1);
+    T xa[3];
+    vc_load_g<T>(g, c0, xa);
+    T carry[3] = {T(0), T(0), T(0)};
+    int rowbase = r0 - 1;
+    for (int kc = kstart; kc < kend; kc += 32) {
+      int c2;
+      T v2[9];
+      vc_load_chunk<V, T>(col, val, (int64_t)kc + 64 + lane, kend, c2, v2);
+      T xb[3];
+      vc_load_g<T>(g, c1, xb);
+      T p[3] = {T(0), T(0), T(0)};
+      if (c0 >= 0)
+#pragma unroll
+        for (int q = 0; q < 3; q++) p[q] = v0[3 * q] * xa[0] + v0[3 * q + 1] * xa[1] + v0[3 * q + 2] * xa[2];
+      const unsigned bit = (rpl >= kc && rpl - kc < 32) ? (1u << (rpl - kc)) : 0u;
+      const unsigned heads = __reduce_or_sync(0xffffffffu, bit);
+      const unsigned below = heads & (0xffffffffu >> (31 - lane));
+      const int sstart = below ? 31 - __clz(below) : -1;
+#pragma unroll
+      for (int off = 1; off < 32; off <<= 1) {
+        T t[3];
+#pragma unroll
+        for (int q = 0; q < 3; q++) t[q] = __shfl_up_sync(0xffffffffu, p[q], off);
+        if (lane >= off && lane - off >= sstart)
+#pragma unroll
+          for (int q = 0; q < 3; q++) p[q] += t[q];
+      }
+      const int nvalid = min(32, kend - kc);
+      const bool cont = nvalid == 32 && kc + 32 < kend && !__any_sync(0xffffffffu, rpl == kc + 32);
+      const bool tail = lane < nvalid && ((lane < 31 && ((heads >> (lane + 1)) & 1u)) || (lane == nvalid - 1 && !cont));
+      if (tail) {
+        const int row = rowbase + __popc(below);
+        const bool add = sstart < 0;
+        T sum[3];
+#pragma unroll
+        for (int q = 0; q < 3; q++) sum[q] = p[q] + (add ? carry[q] : T(0));
+        cheb_rows<T, 3>(row, sum, dinv, g, x, r, dout, cx, coef, flags);
+      }
+      T l[3];
+#pragma unroll
+      for (int q = 0; q < 3; q++) l[q] = __shfl_sync(0xffffffffu, p[q], 31);
+      if (cont) {
+        const bool whole = heads == 0u;  // lane 31's segment started before this chunk
+#pragma unroll
+        for (int q = 0; q < 3; q++) carry[q] = l[q] + (whole ? carry[q] : T(0));
+      } else {
+#pragma unroll
+        for (int q = 0; q < 3; q++) carry[q] = T(0);
+      }
+      rowbase += __popc(heads);
+      c0 = c1;
+      c1 = c2;
+#pragma unroll
+      for (int t = 0; t < 9; t++) {
+        v0[t] = v1[t];
+        v1[t] = v2[t];
+      }
+#pragma unroll
+      for (int j = 0; j < 3; j++) xa[j] = xb[j];
+    }
+  }
+}
+
+// Chebyshev step of a coarse level: one warp per block row (coarse rows
+// are few and long), one lane per block, values tiled
+template <class T, int B>
 __global__ void __launch_bounds__(256) k_vc_cheb(int n, const int* __restrict__ ptr, const int* __restrict__ col,
-                                                 const V* __restrict__ val, int tiled, const T* __restrict__ dinv,
+                                                 const T* __restrict__ val, const T* __restrict__ dinv,
                                                  const T* __restrict__ g, T* __restrict__ x, T* __restrict__ r,
-                                                 T* __restrict__ dout, T cx, T c1, T c2, int flags) {
+                                                 T* __restrict__ dout, T cx, const T* __restrict__ coef,
+                                                 int flags) {
   const int row = (int)(((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
   const int lane = threadIdx.x & 31;
   if (row >= n) return;
@@ -657,49 +838,21 @@ __global__ void __launch_bounds__(256) k_vc_cheb(int n, const int* __restrict__ 
 #pragma unroll
     for (int q = 0; q < B; q++)
 #pragma unroll
-      for (int j = 0; j < B; j++) {
-        const int64_t at = tiled ? kv_index(k, B * q + j) : (int64_t)k * B * B + B * q + j;
-        s[q] += ldt<T, V>(val + at) * gv[j];
-      }
+      for (int j = 0; j < B; j++) s[q] += __ldg(val + tix<B * B>(k, B * q + j)) * gv[j];
   }
 #pragma unroll
   for (int q = 0; q < B; q++)
     for (int off = 16; off > 0; off >>= 1) s[q] += __shfl_xor_sync(0xffffffffu, s[q], off);
-  if (lane != 0) return;
-  const int64_t o = (int64_t)B * row;
-  T rn[B], gi[B];
-#pragma unroll
-  for (int q = 0; q < B; q++) {
-    gi[q] = g[o + q];
-    rn[q] = r[o + q] - s[q];
-    r[o + q] = rn[q];
-  }
-  T xi[B];
-  const bool wx = !(flags & VC_KEEPX);
-#pragma unroll
-  for (int q = 0; q < B; q++) xi[q] = ((flags & VC_SETX) ? T(0) : (wx ? x[o + q] : T(0))) + cx * gi[q];
-  if (dout) {
-#pragma unroll
-    for (int q = 0; q < B; q++) {
-      T t = T(0);
-#pragma unroll
-      for (int j = 0; j < B; j++) t += dinv[(int64_t)row * B * B + B * q + j] * rn[j];
-      const T dn = c1 * gi[q] + c2 * t;
-      dout[o + q] = dn;
-      if (flags & VC_FINAL) xi[q] += dn;
-    }
-  }
-  if (wx)
-#pragma unroll
-    for (int q = 0; q < B; q++) x[o + q] = xi[q];
+  if (lane == 0) cheb_rows<T, B>(row, s, dinv, g, x, r, dout, cx, coef, flags);
 }
 
 // level-0 start of the pre-smoothing: r = b, d = D^-1 b / theta
 template <class T>
 __global__ void k_vc_init0(int n, const T* __restrict__ dinv, const double* __restrict__ b, T* __restrict__ r,
-                           T* __restrict__ d, T inv_theta) {
+                           T* __restrict__ d, const T* __restrict__ coef) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
+  const T inv_theta = coef[0];
   T bi[3];
   for (int q = 0; q < 3; q++) {
     bi[q] = (T)b[3 * (int64_t)i + q];
@@ -713,19 +866,23 @@ __global__ void k_vc_init0(int n, const T* __restrict__ dinv, const double* __re
 }
 
 // restriction to the coarse level (6 components): s = (P^T r)_a;
-// coarsest: bout = s; else: rc = s, dc = D_c^-1 s / theta_c
+// coarsest: bout = s; else: rc = s, dc = D_c^-1 s / theta_c.  A block of 128
+// threads per coarse row: P^T rows are long (an aggregate's nodes and their
+// neighbours, hundreds of blocks at level 0), so a warp per row would leave
+// too few warps in flight; the block's partial sums are reduced in a fixed
+// order (deterministic).
 template <class T, int BF>
-__global__ void __launch_bounds__(256) k_vc_restrict(int nc, const int* __restrict__ rptr, const int* __restrict__ rcol,
+__global__ void __launch_bounds__(128) k_vc_restrict(int nc, const int* __restrict__ rptr, const int* __restrict__ rcol,
                                                      const T* __restrict__ rv, const T* __restrict__ rf,
                                                      const T* __restrict__ dinvc, T* __restrict__ rc,
-                                                     T* __restrict__ dc, T inv_theta) {
-  const int a = (int)(((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
-  const int lane = threadIdx.x & 31;
-  if (a >= nc) return;
+                                                     T* __restrict__ dc, const T* __restrict__ coefc) {
+  __shared__ T sh[4][AMG_NS];
+  const int a = blockIdx.x;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   T s[AMG_NS];
 #pragma unroll
   for (int q = 0; q < AMG_NS; q++) s[q] = T(0);
-  for (int k = rptr[a] + lane; k < rptr[a + 1]; k += 32) {
+  for (int k = rptr[a] + threadIdx.x; k < rptr[a + 1]; k += blockDim.x) {
     const int i = __ldg(rcol + k);
     T f[BF];
 #pragma unroll
@@ -736,13 +893,19 @@ __global__ void __launch_bounds__(256) k_vc_restrict(int nc, const int* __restri
       for (int j = 0; j < BF; j++) s[q] += rv[(int64_t)k * BF * AMG_NS + BF * q + j] * f[j];
   }
 #pragma unroll
-  for (int q = 0; q < AMG_NS; q++)
+  for (int q = 0; q < AMG_NS; q++) {
     for (int off = 16; off > 0; off >>= 1) s[q] += __shfl_xor_sync(0xffffffffu, s[q], off);
-  if (lane != 0) return;
+    if (lane == 0) sh[w][q] = s[q];
+  }
+  __syncthreads();
+  if (threadIdx.x != 0) return;
+#pragma unroll
+  for (int q = 0; q < AMG_NS; q++) s[q] = (sh[0][q] + sh[1][q]) + (sh[2][q] + sh[3][q]);
   const int64_t o = (int64_t)AMG_NS * a;
 #pragma unroll
   for (int q = 0; q < AMG_NS; q++) rc[o + q] = s[q];
-  if (dc)
+  if (dc) {
+    const T inv_theta = coefc[0];
 #pragma unroll
     for (int q = 0; q < AMG_NS; q++) {
       T t = T(0);
@@ -750,6 +913,7 @@ __global__ void __launch_bounds__(256) k_vc_restrict(int nc, const int* __restri
       for (int j = 0; j < AMG_NS; j++) t += dinvc[(int64_t)a * AMG_NS * AMG_NS + AMG_NS * q + j] * s[j];
       dc[o + q] = t * inv_theta;
     }
+  }
 }
 
 // coarsest solve: x = inv b (one block)
@@ -762,31 +926,38 @@ __global__ void k_vc_dense(int N, const T* __restrict__ inv, const T* __restrict
   }
 }
 
-// prolongation: e_i = (P xc)_i, x_i += e_i
-template <class T, int BF>
+// prolongation: e_i = (P xc)_i, x_i += e_i.  LPR lanes per fine row: a P row
+// holds the few aggregates around the node (about 7 at level 0), so a whole
+// warp per row would idle most lanes (4 lanes: two blocks each, in flight
+// together); P is tiled, so the lanes of a warp
+// (consecutive rows, consecutive blocks) read each component in one run.
+// Rows of wholly absent nodes have no blocks: their e stays zero.
+template <class T, int BF, int LPR>
 __global__ void __launch_bounds__(256) k_vc_prolong(int n, const int* __restrict__ pptr, const int* __restrict__ pcol,
                                                     const T* __restrict__ pv, const T* __restrict__ xc,
                                                     T* __restrict__ x, T* __restrict__ e) {
-  const int i = (int)(((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
-  const int lane = threadIdx.x & 31;
-  if (i >= n) return;
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int i = (int)(t / LPR);
+  const int l = (int)(t % LPR);
+  const bool active = i < n;
   T s[BF];
 #pragma unroll
   for (int q = 0; q < BF; q++) s[q] = T(0);
-  for (int k = pptr[i] + lane; k < pptr[i + 1]; k += 32) {
-    const int a = __ldg(pcol + k);
-    T c[AMG_NS];
+  if (active)
+    for (int k = pptr[i] + l; k < pptr[i + 1]; k += LPR) {
+      const int a = __ldg(pcol + k);
+      T c[AMG_NS];
 #pragma unroll
-    for (int j = 0; j < AMG_NS; j++) c[j] = xc[(int64_t)AMG_NS * a + j];
+      for (int j = 0; j < AMG_NS; j++) c[j] = xc[(int64_t)AMG_NS * a + j];
 #pragma unroll
-    for (int q = 0; q < BF; q++)
+      for (int q = 0; q < BF; q++)
 #pragma unroll
-      for (int j = 0; j < AMG_NS; j++) s[q] += pv[(int64_t)k * BF * AMG_NS + AMG_NS * q + j] * c[j];
-  }
+        for (int j = 0; j < AMG_NS; j++) s[q] += __ldg(pv + tix<BF * AMG_NS>(k, AMG_NS * q + j)) * c[j];
+    }
 #pragma unroll
   for (int q = 0; q < BF; q++)
-    for (int off = 16; off > 0; off >>= 1) s[q] += __shfl_xor_sync(0xffffffffu, s[q], off);
-  if (lane != 0) return;
+    for (int off = LPR / 2; off > 0; off >>= 1) s[q] += __shfl_xor_sync(0xffffffffu, s[q], off, LPR);
+  if (!active || l != 0) return;
 #pragma unroll
   for (int q = 0; q < BF; q++) {
     e[(int64_t)BF * i + q] = s[q];
@@ -930,7 +1101,7 @@ int numeric_level(fe_mesh m, int q, Vals<V, B> A) {
   const int64_t N = (int64_t)L.n * L.b;
   if (!L.dinv64) FE_TRY(dev_alloc(m, &L.dinv64, (size_t)L.n * B * B));
   {
-    FE_SCOPE(m, FE_PROF_TANGENT, (double)L.n * B * B * 16);
+    FE_SCOPE(m, FE_PROF_OTHER, (double)L.n * B * B * 16);
     k_amg_dinv<V, B><<<blocks_for(L.n, 128), 128, 0, m->stream>>>(L.n, L.diag, A, L.dinv64);
   }
   FE_CUDA(cudaGetLastError());
@@ -940,7 +1111,7 @@ int numeric_level(fe_mesh m, int q, Vals<V, B> A) {
     const int smem = (2 * Nd * Nd + Nd) * (int)sizeof(double);
     FE_TRY(fe_kernel_smem((const void*)k_amg_dense_inverse<V, B>, smem));
     {
-      FE_SCOPE(m, FE_PROF_TANGENT, 8.0 * Nd * Nd);
+      FE_SCOPE(m, FE_PROF_OTHER, 8.0 * Nd * Nd);
       k_amg_dense_inverse<V, B><<<1, 1024, smem, m->stream>>>(L.n, L.ptr, L.col, A, L.inv64);
     }
     FE_CUDA(cudaGetLastError());
@@ -952,7 +1123,7 @@ int numeric_level(fe_mesh m, int q, Vals<V, B> A) {
   k_amg_start<<<blocks_for(N, 256), 256, 0, m->stream>>>(N, x);
   for (int it = 0; it < AMG_POWER_STEPS; it++) {
     {
-      FE_SCOPE(m, FE_PROF_TANGENT, (double)L.nnz * (B * B * sizeof(V) + 4) + 16.0 * N);
+      FE_SCOPE(m, FE_PROF_OTHER, (double)L.nnz * (B * B * sizeof(V) + 4) + 16.0 * N);
       k_amg_dmv<V, B><<<blocks_for((int64_t)L.n * 32, 256), 256, 0, m->stream>>>(L.n, L.ptr, L.col, A, L.dinv64, x, y);
     }
     k_amg_sumsq2<<<AMG_RED_BLOCKS, 256, 0, m->stream>>>(N, x, y, h->part);
@@ -971,19 +1142,19 @@ int numeric_level(fe_mesh m, int q, Vals<V, B> A) {
   AmgLevel& C = h->lev[q + 1];
   if (!C.val64) FE_TRY(dev_alloc(m, &C.val64, (size_t)C.nnz * AMG_NS * AMG_NS));
   {
-    FE_SCOPE(m, FE_PROF_TANGENT, (double)L.nnzp * B * AMG_NS * 8);
+    FE_SCOPE(m, FE_PROF_OTHER, (double)L.nnzp * B * AMG_NS * 8);
     k_amg_pvals<V, B><<<blocks_for(L.nnzp, 128), 128, 0, m->stream>>>(L.nnzp, L.prow, L.pcol, L.ptr, L.col, A, L.agg,
                                                                      L.dinv64, L.tnode, omega, L.p64);
   }
   FE_CUDA(cudaGetLastError());
   {
-    FE_SCOPE(m, FE_PROF_TANGENT, (double)L.nnzap * B * AMG_NS * 8);
+    FE_SCOPE(m, FE_PROF_OTHER, (double)L.nnzap * B * AMG_NS * 8);
     k_amg_ap<V, B><<<blocks_for(L.nnzap, 128), 128, 0, m->stream>>>(L.nnzap, L.aprow, L.apcol, L.ptr, L.col, A,
                                                                    L.pptr, L.pcol, L.p64, L.ap64);
   }
   FE_CUDA(cudaGetLastError());
   {
-    FE_SCOPE(m, FE_PROF_TANGENT, (double)C.nnz * AMG_NS * AMG_NS * 8);
+    FE_SCOPE(m, FE_PROF_OTHER, (double)C.nnz * AMG_NS * AMG_NS * 8);
     k_amg_rap<B><<<blocks_for(C.nnz, 128), 128, 0, m->stream>>>(C.nnz, C.crow, C.col, L.rptr, L.rcol, L.rsrc,
                                                                L.apptr, L.apcol, L.p64, L.ap64, C.absent, C.val64);
   }
@@ -1000,11 +1171,47 @@ int to_f32(fe_mesh m, const double* a, float** b, int64_t n) {
   return FE_OK;
 }
 
+int store_coeffs(fe_mesh m);
+
+template <int NV, class T>
+int tile_one(fe_mesh m, const double* src, T** dst, int64_t nblocks) {
+  if (!*dst) FE_TRY(dev_alloc(m, dst, (size_t)tiled_count(nblocks, NV)));
+  k_amg_tile<NV, T><<<blocks_for(nblocks * NV, 256), 256, 0, m->stream>>>(nblocks, src, *dst);
+  FE_CUDA(cudaGetLastError());
+  return FE_OK;
+}
+
+// tiled V-cycle copies of the coarse operators and the prolongators, in the
+// V-cycle's precision
+int tile_copies(fe_mesh m) {
+  AmgHier* h = m->amg;
+  const bool d64 = m->prec == FE_PREC_FP64;
+  for (int q = 0; q < h->nlev; q++) {
+    AmgLevel& L = h->lev[q];
+    if (q > 0) {
+      if (d64) FE_TRY((tile_one<AMG_NS * AMG_NS, double>(m, L.val64, &L.vt64, L.nnz)));
+      else FE_TRY((tile_one<AMG_NS * AMG_NS, float>(m, L.val64, &L.vt32, L.nnz)));
+    }
+    if (q < h->nlev - 1) {
+      if (L.b == 3) {
+        if (d64) FE_TRY((tile_one<3 * AMG_NS, double>(m, L.p64, &L.pt64, L.nnzp)));
+        else FE_TRY((tile_one<3 * AMG_NS, float>(m, L.p64, &L.pt32, L.nnzp)));
+      } else {
+        if (d64) FE_TRY((tile_one<AMG_NS * AMG_NS, double>(m, L.p64, &L.pt64, L.nnzp)));
+        else FE_TRY((tile_one<AMG_NS * AMG_NS, float>(m, L.p64, &L.pt32, L.nnzp)));
+      }
+    }
+  }
+  return FE_OK;
+}
+
 template <class V>
 int numeric_all(fe_mesh m, const V* K0) {
   AmgHier* h = m->amg;
   FE_TRY((numeric_level<V, 3>(m, 0, Vals<V, 3>{K0, true})));
   for (int q = 1; q < h->nlev; q++) FE_TRY((numeric_level<double, AMG_NS>(m, q, Vals<double, AMG_NS>{h->lev[q].val64, false})));
+  FE_TRY(store_coeffs(m));
+  FE_TRY(tile_copies(m));
   if (m->prec != FE_PREC_FP64) {  // the V-cycle's FP32 copies
     for (int q = 0; q < h->nlev; q++) {
       AmgLevel& L = h->lev[q];
@@ -1050,119 +1257,156 @@ Cheb cheb_coeffs(double rho) {
   return Cheb{1.0 / theta, r1 * r0, 2.0 * r1 / delta};
 }
 
-// one V-cycle in precision T; level 0 values of type V (tiled); b FP64 [3 nn];
-// the result in the level-0 x vector
+// Chebyshev coefficients of every smoothed level into device memory
+int store_coeffs(fe_mesh m) {
+  AmgHier* h = m->amg;
+  for (int q = 0; q < h->nlev - 1; q++) {
+    AmgLevel& L = h->lev[q];
+    if (!L.coef64) FE_TRY(dev_alloc(m, &L.coef64, 4));
+    if (!L.coef32) FE_TRY(dev_alloc(m, &L.coef32, 4));
+    const Cheb c = cheb_coeffs(L.rho);
+    double* hd = m->h_scal + 24;  // pinned staging, consumed before the next sync
+    float* hf = (float*)(m->h_scal + 28);
+    hd[0] = c.inv_theta;
+    hd[1] = c.c1;
+    hd[2] = c.c2;
+    hf[0] = (float)c.inv_theta;
+    hf[1] = (float)c.c1;
+    hf[2] = (float)c.c2;
+    FE_CUDA(cudaMemcpyAsync(L.coef64, hd, 3 * sizeof(double), cudaMemcpyHostToDevice, m->stream));
+    FE_CUDA(cudaMemcpyAsync(L.coef32, hf, 3 * sizeof(float), cudaMemcpyHostToDevice, m->stream));
+    FE_CUDA(cudaStreamSynchronize(m->stream));
+  }
+  return FE_OK;
+}
+
+// The kernels of one V-cycle in precision T, level-0 values of type V
+// (tiled), on stream st: input b (FP64 [3 nn]), result in lev[0].x.  Adds
+// the algorithmic bytes and flops of its kernels to *bytes, *flops.
 template <class T, class V>
-int vcycle(fe_mesh m, const V* K0, const double* b, T* x0) {
+int vcycle_launches(fe_mesh m, cudaStream_t st, const V* K0, const double* b, double* bytes, double* flops) {
   AmgHier* h = m->amg;
   const int L = h->nlev;
-  auto vals = [&](int q) -> const T* {
-    if constexpr (sizeof(T) == 8) return (const T*)h->lev[q].val64;
-    else return (const T*)h->lev[q].val32;
-  };
-  auto dinv = [&](int q) -> const T* {
-    if constexpr (sizeof(T) == 8) return (const T*)h->lev[q].dinv64;
-    else return (const T*)h->lev[q].dinv32;
-  };
-  auto pv = [&](int q) -> const T* {
-    if constexpr (sizeof(T) == 8) return (const T*)h->lev[q].p64;
-    else return (const T*)h->lev[q].p32;
-  };
-  auto rv = [&](int q) -> const T* {
-    if constexpr (sizeof(T) == 8) return (const T*)h->lev[q].r64;
-    else return (const T*)h->lev[q].r32;
-  };
-  auto inv = [&](int q) -> const T* {
-    if constexpr (sizeof(T) == 8) return (const T*)h->lev[q].inv64;
-    else return (const T*)h->lev[q].inv32;
-  };
-  auto X = [&](int q) { return q == 0 ? x0 : (T*)h->lev[q].x; };
+  constexpr bool D = sizeof(T) == 8;
+  auto vals = [&](int q) -> const T* { return D ? (const T*)h->lev[q].vt64 : (const T*)h->lev[q].vt32; };
+  auto dinv = [&](int q) -> const T* { return D ? (const T*)h->lev[q].dinv64 : (const T*)h->lev[q].dinv32; };
+  auto pv = [&](int q) -> const T* { return D ? (const T*)h->lev[q].pt64 : (const T*)h->lev[q].pt32; };
+  auto rv = [&](int q) -> const T* { return D ? (const T*)h->lev[q].r64 : (const T*)h->lev[q].r32; };
+  auto inv = [&](int q) -> const T* { return D ? (const T*)h->lev[q].inv64 : (const T*)h->lev[q].inv32; };
+  auto coef = [&](int q) -> const T* { return D ? (const T*)h->lev[q].coef64 : (const T*)h->lev[q].coef32; };
+  auto X = [&](int q) { return (T*)h->lev[q].x; };
   const double sv = sizeof(T), s0 = sizeof(V);
   // Chebyshev step on level q (fused SpMV)
-  auto step = [&](int q, const T* g, T* dout, double cx, double c1, double c2, int flags) -> int {
+  auto step = [&](int q, const T* g, T* dout, double cx, int flags) -> int {
     AmgLevel& Lq = h->lev[q];
     const int B = Lq.b;
-    const double bytes = (double)Lq.nnz * (B * B * (q == 0 ? s0 : sv) + 4) + 4.0 * (Lq.n + 1) +
-                         (double)Lq.n * B * (sv * 5 + B * sv);
-    FE_SCOPE_F(m, FE_PROF_PC, bytes, 2.0 * Lq.nnz * B * B);
-    const unsigned grid = blocks_for((int64_t)Lq.n * 32, 256);
+    *bytes += (double)Lq.nnz * (B * B * (q == 0 ? s0 : sv) + 4) + 4.0 * (Lq.n + 1) + (double)Lq.n * B * (sv * 5 + B * sv);
+    *flops += 2.0 * Lq.nnz * B * B;
     if (q == 0)
-      k_vc_cheb<V, T, 3><<<grid, 256, 0, m->stream>>>(Lq.n, Lq.ptr, Lq.col, K0, 1, dinv(0), g, X(0), (T*)Lq.r, dout,
-                                                       (T)cx, (T)c1, (T)c2, flags);
+      k_vc_cheb0<V, T><<<h->grid0, 256, 0, st>>>(Lq.n, Lq.ptr, Lq.col, K0, dinv(0), g, X(0), (T*)Lq.r, dout, (T)cx,
+                                                 coef(0), flags);
     else
-      k_vc_cheb<T, T, AMG_NS><<<grid, 256, 0, m->stream>>>(Lq.n, Lq.ptr, Lq.col, vals(q), 0, dinv(q), g, X(q),
-                                                            (T*)Lq.r, dout, (T)cx, (T)c1, (T)c2, flags);
+      k_vc_cheb<T, AMG_NS><<<blocks_for((int64_t)Lq.n * 32, 256), 256, 0, st>>>(
+          Lq.n, Lq.ptr, Lq.col, vals(q), dinv(q), g, X(q), (T*)Lq.r, dout, (T)cx, coef(q), flags);
     FE_CUDA(cudaGetLastError());
     return FE_OK;
   };
   if (L == 1) {  // one level: the exact solve
     AmgLevel& L0 = h->lev[0];
     const int64_t N = (int64_t)L0.n * 3;
-    k_vc_convert<double, T><<<blocks_for(N, 256), 256, 0, m->stream>>>(N, b, (T*)L0.r);
-    FE_SCOPE(m, FE_PROF_PC, (double)N * N * sv);
-    k_vc_dense<T><<<1, 256, 0, m->stream>>>((int)N, inv(0), (const T*)L0.r, x0);
+    k_vc_convert<double, T><<<blocks_for(N, 256), 256, 0, st>>>(N, b, (T*)L0.r);
+    k_vc_dense<T><<<1, 256, 0, st>>>((int)N, inv(0), (const T*)L0.r, X(0));
     FE_CUDA(cudaGetLastError());
+    *bytes += (double)N * N * sv + 8.0 * N;
+    *flops += 2.0 * N * N;
     return FE_OK;
   }
   // downward: pre-smoothing, restriction
   for (int q = 0; q < L - 1; q++) {
     AmgLevel& Lq = h->lev[q];
-    const Cheb ch = cheb_coeffs(Lq.rho);
     if (q == 0) {
-      FE_SCOPE(m, FE_PROF_PC, (double)Lq.n * (24 + 9 * sv + 6 * sv));
-      k_vc_init0<T><<<blocks_for(Lq.n, 256), 256, 0, m->stream>>>(Lq.n, dinv(0), b, (T*)Lq.r, (T*)Lq.d0,
-                                                                   (T)ch.inv_theta);
+      k_vc_init0<T><<<blocks_for(Lq.n, 256), 256, 0, st>>>(Lq.n, dinv(0), b, (T*)Lq.r, (T*)Lq.d0, coef(0));
       FE_CUDA(cudaGetLastError());
+      *bytes += (double)Lq.n * (24 + 9 * sv + 6 * sv);
     }
     // x = d0; r -= A d0; d1 = c1 d0 + c2 D^-1 r
-    FE_TRY(step(q, (const T*)Lq.d0, (T*)Lq.d1, 1.0, ch.c1, ch.c2, VC_SETX));
+    FE_TRY(step(q, (const T*)Lq.d0, (T*)Lq.d1, 1.0, VC_SETX));
     // x += d1; r -= A d1 (r = b - A x for the restriction)
-    FE_TRY(step(q, (const T*)Lq.d1, nullptr, 1.0, 0.0, 0.0, 0));
+    FE_TRY(step(q, (const T*)Lq.d1, nullptr, 1.0, 0));
     AmgLevel& Cq = h->lev[q + 1];
     const bool coarsest = q + 1 == L - 1;
-    const Cheb cc = coarsest ? Cheb{0, 0, 0} : cheb_coeffs(Cq.rho);
-    {
-      FE_SCOPE_F(m, FE_PROF_PC, (double)Lq.nnzr * (Lq.b * AMG_NS * sv + 4) + (double)Lq.n * Lq.b * sv +
-                                    (double)Cq.n * AMG_NS * sv * 2,
-                 2.0 * Lq.nnzr * Lq.b * AMG_NS);
-      const unsigned grid = blocks_for((int64_t)Cq.n * 32, 256);
-      if (Lq.b == 3)
-        k_vc_restrict<T, 3><<<grid, 256, 0, m->stream>>>(Cq.n, Lq.rptr, Lq.rcol, rv(q), (const T*)Lq.r, dinv(q + 1),
-                                                         (T*)Cq.r, coarsest ? nullptr : (T*)Cq.d0, (T)cc.inv_theta);
-      else
-        k_vc_restrict<T, AMG_NS><<<grid, 256, 0, m->stream>>>(Cq.n, Lq.rptr, Lq.rcol, rv(q), (const T*)Lq.r,
-                                                              dinv(q + 1), (T*)Cq.r, coarsest ? nullptr : (T*)Cq.d0,
-                                                              (T)cc.inv_theta);
-      FE_CUDA(cudaGetLastError());
-    }
+    *bytes += (double)Lq.nnzr * (Lq.b * AMG_NS * sv + 4) + (double)Lq.n * Lq.b * sv + (double)Cq.n * AMG_NS * sv * 2;
+    *flops += 2.0 * Lq.nnzr * Lq.b * AMG_NS;
+    if (Lq.b == 3)
+      k_vc_restrict<T, 3><<<Cq.n, 128, 0, st>>>(Cq.n, Lq.rptr, Lq.rcol, rv(q), (const T*)Lq.r, dinv(q + 1), (T*)Cq.r,
+                                                coarsest ? nullptr : (T*)Cq.d0, coef(q + 1));
+    else
+      k_vc_restrict<T, AMG_NS><<<Cq.n, 128, 0, st>>>(Cq.n, Lq.rptr, Lq.rcol, rv(q), (const T*)Lq.r, dinv(q + 1),
+                                                     (T*)Cq.r, coarsest ? nullptr : (T*)Cq.d0, coef(q + 1));
+    FE_CUDA(cudaGetLastError());
   }
   {  // coarsest
     AmgLevel& Lc = h->lev[L - 1];
     const int N = Lc.n * Lc.b;
-    FE_SCOPE(m, FE_PROF_PC, (double)N * N * sv);
-    k_vc_dense<T><<<1, 256, 0, m->stream>>>(N, inv(L - 1), (const T*)Lc.r, X(L - 1));
+    k_vc_dense<T><<<1, 256, 0, st>>>(N, inv(L - 1), (const T*)Lc.r, X(L - 1));
     FE_CUDA(cudaGetLastError());
+    *bytes += (double)N * N * sv;
+    *flops += 2.0 * N * N;
   }
   // upward: prolongation, post-smoothing
   for (int q = L - 2; q >= 0; q--) {
     AmgLevel& Lq = h->lev[q];
-    const Cheb ch = cheb_coeffs(Lq.rho);
-    {
-      FE_SCOPE_F(m, FE_PROF_PC, (double)Lq.nnzp * (Lq.b * AMG_NS * sv + 4) + (double)Lq.n * Lq.b * sv * 3,
-                 2.0 * Lq.nnzp * Lq.b * AMG_NS);
-      const unsigned grid = blocks_for((int64_t)Lq.n * 32, 256);
-      if (Lq.b == 3)
-        k_vc_prolong<T, 3><<<grid, 256, 0, m->stream>>>(Lq.n, Lq.pptr, Lq.pcol, pv(q), X(q + 1), X(q), (T*)Lq.e);
-      else
-        k_vc_prolong<T, AMG_NS><<<grid, 256, 0, m->stream>>>(Lq.n, Lq.pptr, Lq.pcol, pv(q), X(q + 1), X(q),
-                                                             (T*)Lq.e);
-      FE_CUDA(cudaGetLastError());
-    }
+    *bytes += (double)Lq.nnzp * (Lq.b * AMG_NS * sv + 4) + (double)Lq.n * Lq.b * sv * 3;
+    *flops += 2.0 * Lq.nnzp * Lq.b * AMG_NS;
+    const unsigned grid = blocks_for((int64_t)Lq.n * 4, 256);
+    if (Lq.b == 3)
+      k_vc_prolong<T, 3, 4><<<grid, 256, 0, st>>>(Lq.n, Lq.pptr, Lq.pcol, pv(q), X(q + 1), X(q), (T*)Lq.e);
+    else
+      k_vc_prolong<T, AMG_NS, 4><<<grid, 256, 0, st>>>(Lq.n, Lq.pptr, Lq.pcol, pv(q), X(q + 1), X(q), (T*)Lq.e);
+    FE_CUDA(cudaGetLastError());
     // r -= A e; d0 = D^-1 r / theta
-    FE_TRY(step(q, (const T*)Lq.e, (T*)Lq.d0, 0.0, 0.0, ch.inv_theta, VC_KEEPX));
+    FE_TRY(step(q, (const T*)Lq.e, (T*)Lq.d0, 0.0, VC_KEEPX | VC_START));
     // x += d0; r -= A d0; d1 = c1 d0 + c2 D^-1 r; x += d1
-    FE_TRY(step(q, (const T*)Lq.d0, (T*)Lq.d1, 1.0, ch.c1, ch.c2, VC_FINAL));
+    FE_TRY(step(q, (const T*)Lq.d0, (T*)Lq.d1, 1.0, VC_FINAL));
   }
+  return FE_OK;
+}
+
+// capture the V-cycle of the current precision into a CUDA graph
+template <class T, class V>
+int capture(fe_mesh m, const V* K0) {
+  AmgHier* h = m->amg;
+  if (h->exec) {
+    cudaGraphExecDestroy(h->exec);
+    h->exec = nullptr;
+  }
+  if (!h->cap) FE_CUDA(cudaStreamCreateWithFlags(&h->cap, cudaStreamNonBlocking));
+  FE_CUDA(cudaStreamSynchronize(m->stream));
+  {  // one wave of resident blocks, no more warps than 16-row groups
+    int per_sm = 0;
+    FE_TRY(fe_kernel_occupancy((const void*)k_vc_cheb0<V, T>, 256, 0, &per_sm));
+    const int64_t groups = ((int64_t)m->nn + VC_RPW - 1) / VC_RPW;
+    h->grid0 = (unsigned)std::max<int64_t>(1, std::min<int64_t>((groups + 7) / 8, (int64_t)std::max(per_sm, 1) * m->sm_count));
+  }
+  double bytes = 0.0, flops = 0.0;
+  m->prof_suspend++;
+  cudaGraph_t g = nullptr;
+  cudaError_t e0 = cudaStreamBeginCapture(h->cap, cudaStreamCaptureModeThreadLocal);
+  int rc = e0 == cudaSuccess ? vcycle_launches<T, V>(m, h->cap, K0, h->vin, &bytes, &flops) : FE_ERR_CUDA;
+  cudaError_t e1 = e0 == cudaSuccess ? cudaStreamEndCapture(h->cap, &g) : e0;
+  m->prof_suspend--;
+  if (rc != FE_OK) {
+    if (g) cudaGraphDestroy(g);
+    return rc;
+  }
+  if (e1 != cudaSuccess)
+    return fe_set_error("capturing the V-cycle failed: %s", cudaGetErrorString(e1)), FE_ERR_CUDA;
+  cudaError_t e2 = cudaGraphInstantiate(&h->exec, g, 0);
+  cudaGraphDestroy(g);
+  if (e2 != cudaSuccess) return fe_set_error("instantiating the V-cycle graph failed: %s", cudaGetErrorString(e2)), FE_ERR_CUDA;
+  h->exec_prec = m->prec;
+  h->vc_bytes = bytes;
+  h->vc_flops = flops;
   return FE_OK;
 }
 
@@ -1188,17 +1432,26 @@ int fe_amg_apply(fe_mesh m, const double* x, void* z, bool z_double) {
   if (!m->amg || m->amg->lev[0].dinv64 == nullptr) return fe_set_error("AMG hierarchy not set up"), FE_ERR_STATE;
   AmgHier* h = m->amg;
   const int64_t N = (int64_t)m->nn * 3;
-  if (m->prec == FE_PREC_FP64) {
-    FE_TRY(ensure_vectors(m, 8));
-    double* out = z_double ? (double*)z : (double*)h->lev[0].x;
-    FE_TRY((vcycle<double, double>(m, m->K64, x, out)));
-    if (!z_double) k_vc_convert<double, float><<<blocks_for(N, 256), 256, 0, m->stream>>>(N, out, (float*)z);
+  const bool d64 = m->prec == FE_PREC_FP64;
+  FE_TRY(ensure_vectors(m, d64 ? 8 : 4));
+  if (!h->vin) FE_TRY(dev_alloc(m, &h->vin, (size_t)N));
+  if (!h->exec || h->exec_prec != m->prec) {
+    if (d64) FE_TRY((capture<double, double>(m, m->K64)));
+    else if (m->prec == FE_PREC_MIXED_BF16) FE_TRY((capture<float, __nv_bfloat16>(m, m->K16)));
+    else FE_TRY((capture<float, float>(m, m->K32)));
+  }
+  FE_CUDA(cudaMemcpyAsync(h->vin, x, N * sizeof(double), cudaMemcpyDeviceToDevice, m->stream));
+  {
+    FE_SCOPE_F(m, FE_PROF_PC, h->vc_bytes, h->vc_flops);
+    FE_CUDA(cudaGraphLaunch(h->exec, m->stream));
+  }
+  const unsigned g = blocks_for(N, 256);
+  if (d64) {
+    if (z_double) FE_CUDA(cudaMemcpyAsync(z, h->lev[0].x, N * sizeof(double), cudaMemcpyDeviceToDevice, m->stream));
+    else k_vc_convert<double, float><<<g, 256, 0, m->stream>>>(N, (const double*)h->lev[0].x, (float*)z);
   } else {
-    FE_TRY(ensure_vectors(m, 4));
-    float* out = z_double ? (float*)h->lev[0].x : (float*)z;
-    if (m->prec == FE_PREC_MIXED_BF16) FE_TRY((vcycle<float, __nv_bfloat16>(m, m->K16, x, out)));
-    else FE_TRY((vcycle<float, float>(m, m->K32, x, out)));
-    if (z_double) k_vc_convert<float, double><<<blocks_for(N, 256), 256, 0, m->stream>>>(N, out, (double*)z);
+    if (z_double) k_vc_convert<float, double><<<g, 256, 0, m->stream>>>(N, (const float*)h->lev[0].x, (double*)z);
+    else FE_CUDA(cudaMemcpyAsync(z, h->lev[0].x, N * sizeof(float), cudaMemcpyDeviceToDevice, m->stream));
   }
   FE_CUDA(cudaGetLastError());
   return FE_OK;
@@ -1206,6 +1459,8 @@ int fe_amg_apply(fe_mesh m, const double* x, void* z, bool z_double) {
 
 void fe_amg_free(fe_mesh m) {
   if (!m->amg) return;
+  if (m->amg->exec) cudaGraphExecDestroy(m->amg->exec);
+  if (m->amg->cap) cudaStreamDestroy(m->amg->cap);
   for (void* p : m->amg->allocs) cudaFree(p);
   m->device_bytes -= m->amg->bytes;
   delete m->amg;

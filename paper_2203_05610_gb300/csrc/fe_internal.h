@@ -141,6 +141,7 @@ struct fe_mesh_s {
 
   // instrumentation
   int prof_timing = 0;
+  int prof_suspend = 0;      // > 0 while kernels are captured into a CUDA graph
   int64_t prof_launches[FE_PROF_CLASSES] = {};
   int64_t prof_timed[FE_PROF_CLASSES] = {};
   double prof_ms[FE_PROF_CLASSES] = {};

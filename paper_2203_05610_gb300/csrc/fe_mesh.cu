@@ -149,6 +149,7 @@ static void prof_resolve(fe_mesh m) {
 
 LaunchScope::LaunchScope(fe_mesh m_, int cls_, double bytes_, double flops_)
     : m(m_), cls(cls_), bytes(bytes_), flops(flops_) {
+  if (m->prof_suspend) return;  // launches captured into a graph are counted at its launch
   m->prof_launches[cls]++;
   if (m->prof_timing) {
     a = ev_get(m);

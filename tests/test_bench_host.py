@@ -12,21 +12,21 @@ import bench
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 
-def test_modelled_solve_time_counts_cycles_and_parts():
-    # t(n) = a n + b n (n-1)/2 per restart cycle, plus residuals and assemblies
-    pt = dict(res=0.5, tan=3.0, a=0.1, b=0.01)
-    work = dict(nit=2, assemblies=1, lit_hist=[0, 120, 30])
-    t = bench.modelled_solve_s(pt, work, restart=50)
-    cycles = [50, 50, 20, 30]
-    expect = 3 * 0.5 + 3.0 + sum(0.1 * c + 0.01 * c * (c - 1) / 2 for c in cycles)
-    assert abs(t - expect) < 1e-12
+def test_scaled_solve_time_from_the_first_iterations():
+    # the first iteration (tangent, preconditioner setup, first step) plus the
+    # second iteration's cost per Krylov iteration for all later ones
+    assert bench.scaled_solve_s([0.1, 30.0, 42.5], [0, 33, 10], 133) == 30.0 + 12.5 * 10
 
 
 def test_recorded_oracle_structure_is_consistent():
-    rec = bench.oracle_work("cook_p2_64x64x8", "iB", 50)
+    rec = bench.oracle_work("cook_p2_64x64x8", "iB", 50, "amg")
     assert rec is not None and rec["status"] == 0
     assert sum(rec["lit_hist"][1:rec["nit"] + 1]) == rec["lit_total"]
     assert rec["assemblies"] == 1
+    th = rec["time_hist"]
+    # the scaled estimate from the recorded first iterations against the recorded full solve
+    est = bench.scaled_solve_s(th, rec["lit_hist"], rec["lit_total"])
+    assert abs(est - th[rec["nit"]]) <= 0.1 * th[rec["nit"]], (est, th[rec["nit"]])
 
 
 def test_traffic_records_follow_the_captured_kernels():
