@@ -365,8 +365,10 @@ int fe_profile_read(fe_mesh m, fe_profile_info* out);
  * per-aggregate QR), P = (I - 4/(3 rho) D^-1 A) T, Galerkin coarse
  * operators, degree-2 Chebyshev smoothing, an exact coarsest solve.  Its
  * structure is built once per mesh (host), its numbers after every tangent
- * assembly (device, FP64; the V-cycle runs in the tangent's precision).
- * FE_ERR_ARG for pc_type outside {0, 1} or AMG on the u-p form. */
+ * assembly (device, FP64 for an FP64 tangent, FP32 for the mixed forms; the
+ * V-cycle runs in the tangent's precision).  For the u-p form it replaces
+ * the block-Jacobi of the displacement block inside the lower Schur
+ * preconditioner.  FE_ERR_ARG for pc_type outside {0, 1}. */
 int fe_set_pc(fe_mesh m, int pc_type);
 
 /* The AMG hierarchy of the last assembly, for inspection and tests:

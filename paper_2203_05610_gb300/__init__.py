@@ -19,6 +19,9 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 SO_PATH = os.path.join(_HERE, "_lib", "libfe.so")
+# FE_LIB_VARIANT=debug_bounds loads the index-checking build (build(debug_bounds=True))
+if os.environ.get("FE_LIB_VARIANT") == "debug_bounds":
+    SO_PATH = os.path.join(_HERE, "_lib", "dbg", "libfe_dbg.so")
 
 FE_OK = 0
 NL_DIVERGED, NL_MAX_IT, NL_NONFINITE, KSP_BREAKDOWN = 1, 2, 3, 4

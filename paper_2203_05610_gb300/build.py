@@ -9,6 +9,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 LIBDIR = os.path.join(HERE, "_lib")
 SO = os.path.join(LIBDIR, "libfe.so")
+# the FE_DEBUG_BOUNDS build: kernels check their indirect indices (see fe_idx)
+SO_DEBUG = os.path.join(LIBDIR, "dbg", "libfe_dbg.so")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 SOURCES = ["fe_mesh.cu", "fe_assemble.cu", "fe_krylov.cu", "nl_solve.cu", "fe_amg.cu", "fe_noalloc.cu", "fe_serve.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
@@ -23,21 +25,26 @@ def _deps():
     return files
 
 
-def up_to_date():
-    if not os.path.exists(SO):
+def up_to_date(so=SO):
+    if not os.path.exists(so):
         return False
-    t = os.path.getmtime(SO)
+    t = os.path.getmtime(so)
     return all(os.path.getmtime(f) <= t for f in _deps())
 
 
-def build(force=False, verbose=False):
-    if not force and up_to_date():
-        return SO
-    os.makedirs(LIBDIR, exist_ok=True)
+def build(force=False, verbose=False, debug_bounds=False):
+    """Compile libfe.so (or, debug_bounds=True, the index-checking
+    libfe_dbg.so with -DFE_DEBUG_BOUNDS) in-tree for sm_103a."""
+    so = SO_DEBUG if debug_bounds else SO
+    if not force and up_to_date(so):
+        return so
+    objdir = os.path.dirname(so)
+    os.makedirs(objdir, exist_ok=True)
+    extra = ["-DFE_DEBUG_BOUNDS"] if debug_bounds else []
 
     def compile_one(src):
-        obj = os.path.join(LIBDIR, src.replace(".cu", ".o"))
-        cmd = [NVCC, *ARCH, *FLAGS, "-c", os.path.join(CSRC, src), "-o", obj]
+        obj = os.path.join(objdir, src.replace(".cu", ".o"))
+        cmd = [NVCC, *ARCH, *FLAGS, *extra, "-c", os.path.join(CSRC, src), "-o", obj]
         if verbose:
             cmd.insert(1, "-Xptxas=-v")
         r = subprocess.run(cmd, capture_output=True, text=True)
@@ -50,13 +57,13 @@ def build(force=False, verbose=False):
     if verbose:
         for _, err in results:
             print(err)
-    tmp = SO + f".tmp{os.getpid()}"
+    tmp = so + f".tmp{os.getpid()}"
     cmd = [NVCC, *ARCH, "-shared", "-o", tmp, *[o for o, _ in results], "-lcudart"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stderr}")
-    os.replace(tmp, SO)
-    return SO
+    os.replace(tmp, so)
+    return so
 
 
 if __name__ == "__main__":

@@ -93,7 +93,7 @@ struct AmgLevel {
   double* dinv64 = nullptr;
   float* dinv32 = nullptr;
   double *p64 = nullptr, *r64 = nullptr, *ap64 = nullptr;
-  float *p32 = nullptr, *r32 = nullptr;
+  float *p32 = nullptr, *r32 = nullptr, *ap32 = nullptr;
   double* inv64 = nullptr;
   float* inv32 = nullptr;
   double rho = 0.0;
@@ -114,6 +114,7 @@ struct AmgHier {
   double* scal = nullptr;    // [4] rho, 1/|y|
   std::vector<void*> allocs; // device buffers owned by the hierarchy
   int64_t bytes = 0;         // their size (counted in the mesh's device bytes)
+  bool ready = false;        // numbers formed for the current tangent
   // the V-cycle captured as a CUDA graph: input vin (FP64), output lev[0].x
   double* vin = nullptr;
   cudaStream_t cap = nullptr;       // capture stream (the mesh's may be the legacy stream)
@@ -304,15 +305,6 @@ __host__ __device__ __forceinline__ int64_t tix(int64_t k, int c) {
 }
 inline int64_t tiled_count(int64_t nblocks, int nv) { return (nblocks + 31) / 32 * 32 * nv; }
 
-template <class V>
-__device__ __forceinline__ double ldd(const V* p);
-template <>
-__device__ __forceinline__ double ldd<double>(const double* p) { return *p; }
-template <>
-__device__ __forceinline__ double ldd<float>(const float* p) { return (double)*p; }
-template <>
-__device__ __forceinline__ double ldd<__nv_bfloat16>(const __nv_bfloat16* p) { return (double)__bfloat162float(*p); }
-
 // a stored value in the V-cycle's arithmetic type T (FP32 values stay FP32)
 template <class T, class V>
 __device__ __forceinline__ T ldt(const V* p) {
@@ -320,14 +312,14 @@ __device__ __forceinline__ T ldt(const V* p) {
   else return (T)__ldg(p);
 }
 
-// entry c of block k: level 0 reads the tangent in its tiled layout, coarser
-// levels their block-major FP64 values
-template <class V, int B>
+// entry c of block k in the setup's arithmetic type C: level 0 reads the
+// tangent in its tiled layout, coarser levels their block-major values
+template <class C, class V, int B>
 struct Vals {
   const V* v;
   bool tiled;
-  __device__ __forceinline__ double operator()(int64_t k, int c) const {
-    return tiled ? ldd<V>(v + kv_index(k, c)) : ldd<V>(v + k * (B * B) + c);
+  __device__ __forceinline__ C operator()(int64_t k, int c) const {
+    return tiled ? ldt<C, V>(v + kv_index(k, c)) : ldt<C, V>(v + k * (B * B) + c);
   }
 };
 
@@ -377,30 +369,33 @@ __device__ void gj_inverse(double (&a)[B][B], double (&inv)[B][B]) {
   }
 }
 
-// ---------------------------------------------------------------- numeric setup kernels (FP64)
-template <class V, int B>
-__global__ void k_amg_dinv(int n, const int* __restrict__ diag, Vals<V, B> A, double* __restrict__ dinv) {
+// ---------------------------------------------------------------- numeric setup kernels
+// C is the setup's arithmetic type: FP64 for an FP64 tangent, FP32 for the
+// mixed forms (whose V-cycle runs in FP32; GB300's FP32 rate is tens of
+// times its FP64 rate).  The dense coarsest inverse is always formed in FP64.
+template <class C, class V, int B>
+__global__ void k_amg_dinv(int n, const int* __restrict__ diag, Vals<C, V, B> A, C* __restrict__ dinv) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   double a[B][B], inv[B][B];
   const int64_t k = diag[i];
   for (int r = 0; r < B; r++)
-    for (int c = 0; c < B; c++) a[r][c] = A(k, B * r + c);
+    for (int c = 0; c < B; c++) a[r][c] = (double)A(k, B * r + c);
   gj_inverse<B>(a, inv);
   for (int r = 0; r < B; r++)
-    for (int c = 0; c < B; c++) dinv[(int64_t)i * B * B + B * r + c] = inv[r][c];
+    for (int c = 0; c < B; c++) dinv[(int64_t)i * B * B + B * r + c] = (C)inv[r][c];
 }
 
 // y = D^-1 (A x), one warp per block row
-template <class V, int B>
+template <class C, class V, int B>
 __global__ void __launch_bounds__(256) k_amg_dmv(int n, const int* __restrict__ ptr, const int* __restrict__ col,
-                                                 Vals<V, B> A, const double* __restrict__ dinv,
-                                                 const double* __restrict__ x, double* __restrict__ y) {
+                                                 Vals<C, V, B> A, const C* __restrict__ dinv,
+                                                 const C* __restrict__ x, C* __restrict__ y) {
   const int row = (int)(((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
   const int lane = threadIdx.x & 31;
   if (row >= n) return;
-  double s[B];
-  for (int r = 0; r < B; r++) s[r] = 0.0;
+  C s[B];
+  for (int r = 0; r < B; r++) s[r] = C(0);
   for (int k = ptr[row] + lane; k < ptr[row + 1]; k += 32) {
     const int c = col[k];
     for (int r = 0; r < B; r++)
@@ -410,25 +405,28 @@ __global__ void __launch_bounds__(256) k_amg_dmv(int n, const int* __restrict__ 
     for (int off = 16; off > 0; off >>= 1) s[r] += __shfl_xor_sync(0xffffffffu, s[r], off);
   if (lane == 0)
     for (int r = 0; r < B; r++) {
-      double t = 0.0;
+      C t = C(0);
       for (int j = 0; j < B; j++) t += dinv[(int64_t)row * B * B + B * r + j] * s[j];
       y[(int64_t)B * row + r] = t;
     }
 }
 
-__global__ void k_amg_start(int64_t N, double* __restrict__ x) {
+template <class C>
+__global__ void k_amg_start(int64_t N, C* __restrict__ x) {
   const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (k < N) x[k] = (double)(mix64_d((uint64_t)k) >> 11) * (1.0 / 9007199254740992.0) - 0.5;
+  if (k < N) x[k] = (C)((double)(mix64_d((uint64_t)k) >> 11) * (1.0 / 9007199254740992.0) - 0.5);
 }
 
-// partial sums of x.x and y.y over a fixed grid (fixed order: deterministic)
-__global__ void __launch_bounds__(256) k_amg_sumsq2(int64_t N, const double* __restrict__ x,
-                                                    const double* __restrict__ y, double* __restrict__ part) {
+// partial sums of x.x and y.y over a fixed grid (fixed order: deterministic), in FP64
+template <class C>
+__global__ void __launch_bounds__(256) k_amg_sumsq2(int64_t N, const C* __restrict__ x, const C* __restrict__ y,
+                                                    double* __restrict__ part) {
   __shared__ double sh[2][8];
   double sx = 0.0, sy = 0.0;
   for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < N; k += (int64_t)gridDim.x * blockDim.x) {
-    sx += x[k] * x[k];
-    sy += y[k] * y[k];
+    const double a = (double)x[k], c = (double)y[k];
+    sx += a * a;
+    sy += c * c;
   }
   for (int off = 16; off > 0; off >>= 1) {
     sx += __shfl_xor_sync(0xffffffffu, sx, off);
@@ -452,8 +450,9 @@ __global__ void __launch_bounds__(256) k_amg_sumsq2(int64_t N, const double* __r
 }
 
 // rho = |y| / |x|, x = y / |y|
-__global__ void k_amg_power_step(int64_t N, int nblk, const double* __restrict__ part, const double* __restrict__ y,
-                                 double* __restrict__ x, double* __restrict__ scal) {
+template <class C>
+__global__ void k_amg_power_step(int64_t N, int nblk, const double* __restrict__ part, const C* __restrict__ y,
+                                 C* __restrict__ x, double* __restrict__ scal) {
   __shared__ double s_inv;
   if (threadIdx.x == 0) {
     double xx = 0.0, yy = 0.0;
@@ -466,40 +465,40 @@ __global__ void k_amg_power_step(int64_t N, int nblk, const double* __restrict__
   }
   __syncthreads();
   for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < N; k += (int64_t)gridDim.x * blockDim.x)
-    x[k] = y[k] * s_inv;
+    x[k] = (C)((double)y[k] * s_inv);
 }
 
 // P entry q = (row i, aggregate a): [agg(i) = a] T_i - omega sum_{k: agg(col k) = a} D_i^-1 A_k T_col(k)
-template <class V, int B>
+template <class C, class V, int B>
 __global__ void k_amg_pvals(int64_t nnzp, const int* __restrict__ prow, const int* __restrict__ pcol,
-                            const int* __restrict__ ptr, const int* __restrict__ col, Vals<V, B> A,
-                            const int* __restrict__ agg, const double* __restrict__ dinv,
-                            const double* __restrict__ tnode, double omega, double* __restrict__ p) {
+                            const int* __restrict__ ptr, const int* __restrict__ col, Vals<C, V, B> A,
+                            const int* __restrict__ agg, const C* __restrict__ dinv,
+                            const double* __restrict__ tnode, C omega, C* __restrict__ p) {
   const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (q >= nnzp) return;
   const int i = prow[q], a = pcol[q];
-  double acc[B][AMG_NS];
+  C acc[B][AMG_NS];
   for (int r = 0; r < B; r++)
     for (int c = 0; c < AMG_NS; c++)
-      acc[r][c] = agg[i] == a ? tnode[(int64_t)i * B * AMG_NS + AMG_NS * r + c] : 0.0;
-  double D[B][B];
+      acc[r][c] = agg[i] == a ? (C)tnode[(int64_t)i * B * AMG_NS + AMG_NS * r + c] : C(0);
+  C D[B][B];
   for (int r = 0; r < B; r++)
     for (int c = 0; c < B; c++) D[r][c] = dinv[(int64_t)i * B * B + B * r + c];
   for (int k = ptr[i]; k < ptr[i + 1]; k++) {
     const int j = col[k];
     if (agg[j] != a) continue;
-    double DA[B][B];
+    C DA[B][B];
     for (int r = 0; r < B; r++)
       for (int c = 0; c < B; c++) {
-        double s = 0.0;
+        C s = C(0);
         for (int l = 0; l < B; l++) s += D[r][l] * A(k, B * l + c);
         DA[r][c] = s;
       }
     const double* T = tnode + (int64_t)j * B * AMG_NS;
     for (int r = 0; r < B; r++)
       for (int c = 0; c < AMG_NS; c++) {
-        double s = 0.0;
-        for (int l = 0; l < B; l++) s += DA[r][l] * T[AMG_NS * l + c];
+        C s = C(0);
+        for (int l = 0; l < B; l++) s += DA[r][l] * (C)T[AMG_NS * l + c];
         acc[r][c] -= omega * s;
       }
   }
@@ -508,27 +507,27 @@ __global__ void k_amg_pvals(int64_t nnzp, const int* __restrict__ prow, const in
 }
 
 // A P entry (row i, aggregate a) = sum_k A_k P_(col k, a)
-template <class V, int B>
+template <class C, class V, int B>
 __global__ void k_amg_ap(int64_t nnzap, const int* __restrict__ aprow, const int* __restrict__ apcol,
-                         const int* __restrict__ ptr, const int* __restrict__ col, Vals<V, B> A,
-                         const int* __restrict__ pptr, const int* __restrict__ pcol, const double* __restrict__ p,
-                         double* __restrict__ ap) {
+                         const int* __restrict__ ptr, const int* __restrict__ col, Vals<C, V, B> A,
+                         const int* __restrict__ pptr, const int* __restrict__ pcol, const C* __restrict__ p,
+                         C* __restrict__ ap) {
   const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= nnzap) return;
   const int i = aprow[e], a = apcol[e];
-  double acc[B][AMG_NS];
+  C acc[B][AMG_NS];
   for (int r = 0; r < B; r++)
-    for (int c = 0; c < AMG_NS; c++) acc[r][c] = 0.0;
+    for (int c = 0; c < AMG_NS; c++) acc[r][c] = C(0);
   for (int k = ptr[i]; k < ptr[i + 1]; k++) {
     const int j = col[k];
     const int q = find_col(pcol, pptr[j], pptr[j + 1], a);
     if (q < 0) continue;
-    const double* P = p + (int64_t)q * B * AMG_NS;
+    const C* P = p + (int64_t)q * B * AMG_NS;
     for (int r = 0; r < B; r++) {
-      double Ar[B];
+      C Ar[B];
       for (int l = 0; l < B; l++) Ar[l] = A(k, B * r + l);
       for (int c = 0; c < AMG_NS; c++) {
-        double s = 0.0;
+        C s = C(0);
         for (int l = 0; l < B; l++) s += Ar[l] * P[AMG_NS * l + c];
         acc[r][c] += s;
       }
@@ -540,27 +539,26 @@ __global__ void k_amg_ap(int64_t nnzap, const int* __restrict__ aprow, const int
 
 // coarse entry (a, c) = sum over P^T row a (fine node i, P entry q) of P_q^T (A P)_(i, c);
 // absent coarse components get a unit diagonal
-template <int B>
+template <class C, int B>
 __global__ void k_amg_rap(int64_t nnzc, const int* __restrict__ crow, const int* __restrict__ ccol,
                           const int* __restrict__ rptr, const int* __restrict__ rcol, const int* __restrict__ rsrc,
-                          const int* __restrict__ apptr, const int* __restrict__ apcol, const double* __restrict__ p,
-                          const double* __restrict__ ap, const unsigned char* __restrict__ cabsent,
-                          double* __restrict__ out) {
+                          const int* __restrict__ apptr, const int* __restrict__ apcol, const C* __restrict__ p,
+                          const C* __restrict__ ap, const unsigned char* __restrict__ cabsent, C* __restrict__ out) {
   const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= nnzc) return;
   const int a = crow[e], cc = ccol[e];
-  double acc[AMG_NS][AMG_NS];
+  C acc[AMG_NS][AMG_NS];
   for (int r = 0; r < AMG_NS; r++)
-    for (int c = 0; c < AMG_NS; c++) acc[r][c] = 0.0;
+    for (int c = 0; c < AMG_NS; c++) acc[r][c] = C(0);
   for (int s = rptr[a]; s < rptr[a + 1]; s++) {
     const int i = rcol[s];
     const int pe = find_col(apcol, apptr[i], apptr[i + 1], cc);
     if (pe < 0) continue;
-    const double* P = p + (int64_t)rsrc[s] * B * AMG_NS;
-    const double* Q = ap + (int64_t)pe * B * AMG_NS;
+    const C* P = p + (int64_t)rsrc[s] * B * AMG_NS;
+    const C* Q = ap + (int64_t)pe * B * AMG_NS;
     for (int r = 0; r < AMG_NS; r++)
       for (int c = 0; c < AMG_NS; c++) {
-        double v = 0.0;
+        C v = C(0);
         for (int l = 0; l < B; l++) v += P[AMG_NS * l + r] * Q[AMG_NS * l + c];
         acc[r][c] += v;
       }
@@ -568,28 +566,27 @@ __global__ void k_amg_rap(int64_t nnzc, const int* __restrict__ crow, const int*
   if (a == cc) {
     const unsigned m = cabsent[a];
     for (int c = 0; c < AMG_NS; c++)
-      if ((m >> c) & 1u) acc[c][c] = 1.0;
+      if ((m >> c) & 1u) acc[c][c] = C(1);
   }
   for (int r = 0; r < AMG_NS; r++)
     for (int c = 0; c < AMG_NS; c++) out[e * AMG_NS * AMG_NS + AMG_NS * r + c] = acc[r][c];
 }
 
 // R = P^T values: R entry s holds the transpose of P entry rsrc[s]
-template <int B>
-__global__ void k_amg_rvals(int64_t nnzr, const int* __restrict__ rsrc, const double* __restrict__ p,
-                            double* __restrict__ rv) {
+template <class C, int B>
+__global__ void k_amg_rvals(int64_t nnzr, const int* __restrict__ rsrc, const C* __restrict__ p, C* __restrict__ rv) {
   const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (s >= nnzr) return;
-  const double* P = p + (int64_t)rsrc[s] * B * AMG_NS;
+  const C* P = p + (int64_t)rsrc[s] * B * AMG_NS;
   for (int c = 0; c < AMG_NS; c++)
     for (int r = 0; r < B; r++) rv[s * B * AMG_NS + B * c + r] = P[AMG_NS * r + c];
 }
 
 // dense inverse of the coarsest operator (N <= 96): one block, Gauss-Jordan
-// with partial pivoting in shared memory (first maximal pivot on ties)
-template <class V, int B>
+// with partial pivoting in shared memory (first maximal pivot on ties), FP64
+template <class C, class V, int B>
 __global__ void __launch_bounds__(1024) k_amg_dense_inverse(int n, const int* __restrict__ ptr,
-                                                            const int* __restrict__ col, Vals<V, B> A,
+                                                            const int* __restrict__ col, Vals<C, V, B> A,
                                                             double* __restrict__ inv) {
   extern __shared__ double sm[];
   const int N = n * B;
@@ -605,7 +602,7 @@ __global__ void __launch_bounds__(1024) k_amg_dense_inverse(int n, const int* __
   for (int a = threadIdx.x; a < n; a += blockDim.x)
     for (int k = ptr[a]; k < ptr[a + 1]; k++)
       for (int r = 0; r < B; r++)
-        for (int c = 0; c < B; c++) M[(B * a + r) * N + B * col[k] + c] = A(k, B * r + c);
+        for (int c = 0; c < B; c++) M[(B * a + r) * N + B * col[k] + c] = (double)A(k, B * r + c);
   __syncthreads();
   for (int c = 0; c < N; c++) {
     if (threadIdx.x == 0) {
@@ -651,9 +648,9 @@ __global__ void k_amg_to_f32(int64_t n, const double* __restrict__ a, float* __r
   if (i < n) b[i] = (float)a[i];
 }
 
-// block-major FP64 blocks of nv values -> the tiled layout in type T
+// block-major blocks of nv values -> the tiled layout
 template <int NV, class T>
-__global__ void k_amg_tile(int64_t nblocks, const double* __restrict__ src, T* __restrict__ dst) {
+__global__ void k_amg_tile(int64_t nblocks, const T* __restrict__ src, T* __restrict__ dst) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= nblocks * NV) return;
   const int64_t k = i / NV;
@@ -729,9 +726,10 @@ __device__ __forceinline__ void vc_load_chunk(const int* __restrict__ col, const
 }
 
 template <class T>
-__device__ __forceinline__ void vc_load_g(const T* __restrict__ g, int c, T (&x)[3]) {
+__device__ __forceinline__ void vc_load_g(const T* __restrict__ g, int c, T (&x)[3], int n) {
+  const int64_t cc = c >= 0 ? fe_idx(c, n) : 0;
 #pragma unroll
-  for (int j = 0; j < 3; j++) x[j] = c >= 0 ? g[3 * (int64_t)c + j] : T(0);
+  for (int j = 0; j < 3; j++) x[j] = c >= 0 ? g[3 * cc + j] : T(0);
 }
 
 template <class V, class T>
@@ -754,7 +752,7 @@ __global__ void __launch_bounds__(256) k_vc_cheb0(int n, const int* __restrict__
     vc_load_chunk<V, T>(col, val, (int64_t)kstart + lane, kend, c0, v0);
     vc_load_chunk<V, T>(col, val, (int64_t)kstart + 32 + lane, kend, c1, v1);
     T xa[3];
-    vc_load_g<T>(g, c0, xa);
+    vc_load_g<T>(g, c0, xa, n);
     T carry[3] = {T(0), T(0), T(0)};
     int rowbase = r0 - 1;
     for (int kc = kstart; kc < kend; kc += 32) {
@@ -762,7 +760,7 @@ __global__ void __launch_bounds__(256) k_vc_cheb0(int n, const int* __restrict__
       T v2[9];
       vc_load_chunk<V, T>(col, val, (int64_t)kc + 64 + lane, kend, c2, v2);
       T xb[3];
-      vc_load_g<T>(g, c1, xb);
+      vc_load_g<T>(g, c1, xb, n);
       T p[3] = {T(0), T(0), T(0)};
       if (c0 >= 0)
 #pragma unroll
@@ -831,7 +829,7 @@ __global__ void __launch_bounds__(256) k_vc_cheb(int n, const int* __restrict__ 
 #pragma unroll
   for (int q = 0; q < B; q++) s[q] = T(0);
   for (int k = ptr[row] + lane; k < ptr[row + 1]; k += 32) {
-    const int c = __ldg(col + k);
+    const int c = fe_idx(__ldg(col + k), n);
     T gv[B];
 #pragma unroll
     for (int j = 0; j < B; j++) gv[j] = g[(int64_t)B * c + j];
@@ -875,7 +873,7 @@ template <class T, int BF>
 __global__ void __launch_bounds__(128) k_vc_restrict(int nc, const int* __restrict__ rptr, const int* __restrict__ rcol,
                                                      const T* __restrict__ rv, const T* __restrict__ rf,
                                                      const T* __restrict__ dinvc, T* __restrict__ rc,
-                                                     T* __restrict__ dc, const T* __restrict__ coefc) {
+                                                     T* __restrict__ dc, const T* __restrict__ coefc, int nfine) {
   __shared__ T sh[4][AMG_NS];
   const int a = blockIdx.x;
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
@@ -883,7 +881,7 @@ __global__ void __launch_bounds__(128) k_vc_restrict(int nc, const int* __restri
 #pragma unroll
   for (int q = 0; q < AMG_NS; q++) s[q] = T(0);
   for (int k = rptr[a] + threadIdx.x; k < rptr[a + 1]; k += blockDim.x) {
-    const int i = __ldg(rcol + k);
+    const int i = fe_idx(__ldg(rcol + k), nfine);
     T f[BF];
 #pragma unroll
     for (int j = 0; j < BF; j++) f[j] = rf[(int64_t)BF * i + j];
@@ -935,7 +933,7 @@ __global__ void k_vc_dense(int N, const T* __restrict__ inv, const T* __restrict
 template <class T, int BF, int LPR>
 __global__ void __launch_bounds__(256) k_vc_prolong(int n, const int* __restrict__ pptr, const int* __restrict__ pcol,
                                                     const T* __restrict__ pv, const T* __restrict__ xc,
-                                                    T* __restrict__ x, T* __restrict__ e) {
+                                                    T* __restrict__ x, T* __restrict__ e, int ncoarse) {
   const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int i = (int)(t / LPR);
   const int l = (int)(t % LPR);
@@ -945,7 +943,7 @@ __global__ void __launch_bounds__(256) k_vc_prolong(int n, const int* __restrict
   for (int q = 0; q < BF; q++) s[q] = T(0);
   if (active)
     for (int k = pptr[i] + l; k < pptr[i + 1]; k += LPR) {
-      const int a = __ldg(pcol + k);
+      const int a = fe_idx(__ldg(pcol + k), ncoarse);
       T c[AMG_NS];
 #pragma unroll
       for (int j = 0; j < AMG_NS; j++) c[j] = xc[(int64_t)AMG_NS * a + j];
@@ -1093,77 +1091,6 @@ int build_structure(fe_mesh m) {
   return FE_OK;
 }
 
-// numbers of level q (A_q already numeric): D^-1, rho, P, AP, R and A_{q+1}
-template <class V, int B>
-int numeric_level(fe_mesh m, int q, Vals<V, B> A) {
-  AmgHier* h = m->amg;
-  AmgLevel& L = h->lev[q];
-  const int64_t N = (int64_t)L.n * L.b;
-  if (!L.dinv64) FE_TRY(dev_alloc(m, &L.dinv64, (size_t)L.n * B * B));
-  {
-    FE_SCOPE(m, FE_PROF_OTHER, (double)L.n * B * B * 16);
-    k_amg_dinv<V, B><<<blocks_for(L.n, 128), 128, 0, m->stream>>>(L.n, L.diag, A, L.dinv64);
-  }
-  FE_CUDA(cudaGetLastError());
-  if (q == h->nlev - 1) {  // coarsest: dense inverse
-    const int Nd = L.n * B;
-    if (!L.inv64) FE_TRY(dev_alloc(m, &L.inv64, (size_t)Nd * Nd));
-    const int smem = (2 * Nd * Nd + Nd) * (int)sizeof(double);
-    FE_TRY(fe_kernel_smem((const void*)k_amg_dense_inverse<V, B>, smem));
-    {
-      FE_SCOPE(m, FE_PROF_OTHER, 8.0 * Nd * Nd);
-      k_amg_dense_inverse<V, B><<<1, 1024, smem, m->stream>>>(L.n, L.ptr, L.col, A, L.inv64);
-    }
-    FE_CUDA(cudaGetLastError());
-    return FE_OK;
-  }
-  // rho: power steps on D^-1 A
-  double* x = h->pw;
-  double* y = h->pw + N;
-  k_amg_start<<<blocks_for(N, 256), 256, 0, m->stream>>>(N, x);
-  for (int it = 0; it < AMG_POWER_STEPS; it++) {
-    {
-      FE_SCOPE(m, FE_PROF_OTHER, (double)L.nnz * (B * B * sizeof(V) + 4) + 16.0 * N);
-      k_amg_dmv<V, B><<<blocks_for((int64_t)L.n * 32, 256), 256, 0, m->stream>>>(L.n, L.ptr, L.col, A, L.dinv64, x, y);
-    }
-    k_amg_sumsq2<<<AMG_RED_BLOCKS, 256, 0, m->stream>>>(N, x, y, h->part);
-    k_amg_power_step<<<blocks_for(N, 256), 256, 0, m->stream>>>(N, AMG_RED_BLOCKS, h->part, y, x, h->scal);
-  }
-  FE_CUDA(cudaGetLastError());
-  FE_CUDA(cudaMemcpyAsync(m->h_scal + 20, h->scal, sizeof(double), cudaMemcpyDeviceToHost, m->stream));
-  FE_CUDA(cudaStreamSynchronize(m->stream));
-  L.rho = m->h_scal[20];
-  if (!(L.rho > 0.0) || !std::isfinite(L.rho))
-    return fe_set_error("AMG: spectral radius estimate %g on level %d", L.rho, q), FE_ERR_STATE;
-  const double omega = 4.0 / (3.0 * L.rho);
-  if (!L.p64) FE_TRY(dev_alloc(m, &L.p64, (size_t)L.nnzp * B * AMG_NS));
-  if (!L.ap64) FE_TRY(dev_alloc(m, &L.ap64, (size_t)L.nnzap * B * AMG_NS));
-  if (!L.r64) FE_TRY(dev_alloc(m, &L.r64, (size_t)L.nnzr * B * AMG_NS));
-  AmgLevel& C = h->lev[q + 1];
-  if (!C.val64) FE_TRY(dev_alloc(m, &C.val64, (size_t)C.nnz * AMG_NS * AMG_NS));
-  {
-    FE_SCOPE(m, FE_PROF_OTHER, (double)L.nnzp * B * AMG_NS * 8);
-    k_amg_pvals<V, B><<<blocks_for(L.nnzp, 128), 128, 0, m->stream>>>(L.nnzp, L.prow, L.pcol, L.ptr, L.col, A, L.agg,
-                                                                     L.dinv64, L.tnode, omega, L.p64);
-  }
-  FE_CUDA(cudaGetLastError());
-  {
-    FE_SCOPE(m, FE_PROF_OTHER, (double)L.nnzap * B * AMG_NS * 8);
-    k_amg_ap<V, B><<<blocks_for(L.nnzap, 128), 128, 0, m->stream>>>(L.nnzap, L.aprow, L.apcol, L.ptr, L.col, A,
-                                                                   L.pptr, L.pcol, L.p64, L.ap64);
-  }
-  FE_CUDA(cudaGetLastError());
-  {
-    FE_SCOPE(m, FE_PROF_OTHER, (double)C.nnz * AMG_NS * AMG_NS * 8);
-    k_amg_rap<B><<<blocks_for(C.nnz, 128), 128, 0, m->stream>>>(C.nnz, C.crow, C.col, L.rptr, L.rcol, L.rsrc,
-                                                               L.apptr, L.apcol, L.p64, L.ap64, C.absent, C.val64);
-  }
-  FE_CUDA(cudaGetLastError());
-  k_amg_rvals<B><<<blocks_for(L.nnzr, 256), 256, 0, m->stream>>>(L.nnzr, L.rsrc, L.p64, L.r64);
-  FE_CUDA(cudaGetLastError());
-  return FE_OK;
-}
-
 int to_f32(fe_mesh m, const double* a, float** b, int64_t n) {
   if (!*b) FE_TRY(dev_alloc(m, b, (size_t)n));
   k_amg_to_f32<<<blocks_for(n, 256), 256, 0, m->stream>>>(n, a, *b);
@@ -1171,63 +1098,147 @@ int to_f32(fe_mesh m, const double* a, float** b, int64_t n) {
   return FE_OK;
 }
 
+// the arrays of the setup's arithmetic type C
+template <class C>
+struct Arr {
+  static C*& val(AmgLevel& L);
+  static C*& dinv(AmgLevel& L);
+  static C*& p(AmgLevel& L);
+  static C*& ap(AmgLevel& L);
+  static C*& r(AmgLevel& L);
+};
+template <>
+struct Arr<double> {
+  static double*& val(AmgLevel& L) { return L.val64; }
+  static double*& dinv(AmgLevel& L) { return L.dinv64; }
+  static double*& p(AmgLevel& L) { return L.p64; }
+  static double*& ap(AmgLevel& L) { return L.ap64; }
+  static double*& r(AmgLevel& L) { return L.r64; }
+};
+template <>
+struct Arr<float> {
+  static float*& val(AmgLevel& L) { return L.val32; }
+  static float*& dinv(AmgLevel& L) { return L.dinv32; }
+  static float*& p(AmgLevel& L) { return L.p32; }
+  static float*& ap(AmgLevel& L) { return L.ap32; }
+  static float*& r(AmgLevel& L) { return L.r32; }
+};
+
+// numbers of level q (A_q already numeric) in arithmetic type C: D^-1, rho,
+// P, AP, R and A_{q+1}; the coarsest level's dense inverse (FP64, with an
+// FP32 copy for the mixed forms)
+template <class C, class V, int B>
+int numeric_level(fe_mesh m, int q, Vals<C, V, B> A) {
+  AmgHier* h = m->amg;
+  AmgLevel& L = h->lev[q];
+  const int64_t N = (int64_t)L.n * L.b;
+  C*& dinv = Arr<C>::dinv(L);
+  if (!dinv) FE_TRY(dev_alloc(m, &dinv, (size_t)L.n * B * B));
+  {
+    FE_SCOPE(m, FE_PROF_OTHER, (double)L.n * B * B * (8 + sizeof(C)));
+    k_amg_dinv<C, V, B><<<blocks_for(L.n, 128), 128, 0, m->stream>>>(L.n, L.diag, A, dinv);
+  }
+  FE_CUDA(cudaGetLastError());
+  if (q == h->nlev - 1) {  // coarsest: dense inverse
+    const int Nd = L.n * B;
+    if (!L.inv64) FE_TRY(dev_alloc(m, &L.inv64, (size_t)Nd * Nd));
+    const int smem = (2 * Nd * Nd + Nd) * (int)sizeof(double);
+    FE_TRY(fe_kernel_smem((const void*)k_amg_dense_inverse<C, V, B>, smem));
+    {
+      FE_SCOPE(m, FE_PROF_OTHER, 8.0 * Nd * Nd);
+      k_amg_dense_inverse<C, V, B><<<1, 1024, smem, m->stream>>>(L.n, L.ptr, L.col, A, L.inv64);
+    }
+    FE_CUDA(cudaGetLastError());
+    if (!std::is_same<C, double>::value) FE_TRY(to_f32(m, L.inv64, &L.inv32, (int64_t)Nd * Nd));
+    return FE_OK;
+  }
+  // rho: power steps on D^-1 A
+  C* x = (C*)h->pw;
+  C* y = x + N;
+  k_amg_start<C><<<blocks_for(N, 256), 256, 0, m->stream>>>(N, x);
+  for (int it = 0; it < AMG_POWER_STEPS; it++) {
+    {
+      FE_SCOPE(m, FE_PROF_OTHER, (double)L.nnz * (B * B * sizeof(V) + 4) + 2.0 * sizeof(C) * N);
+      k_amg_dmv<C, V, B><<<blocks_for((int64_t)L.n * 32, 256), 256, 0, m->stream>>>(L.n, L.ptr, L.col, A, dinv, x, y);
+    }
+    k_amg_sumsq2<C><<<AMG_RED_BLOCKS, 256, 0, m->stream>>>(N, x, y, h->part);
+    k_amg_power_step<C><<<blocks_for(N, 256), 256, 0, m->stream>>>(N, AMG_RED_BLOCKS, h->part, y, x, h->scal);
+  }
+  FE_CUDA(cudaGetLastError());
+  FE_CUDA(cudaMemcpyAsync(m->h_scal + 20, h->scal, sizeof(double), cudaMemcpyDeviceToHost, m->stream));
+  FE_CUDA(cudaStreamSynchronize(m->stream));
+  L.rho = m->h_scal[20];
+  if (!(L.rho > 0.0) || !std::isfinite(L.rho))
+    return fe_set_error("AMG: spectral radius estimate %g on level %d", L.rho, q), FE_ERR_STATE;
+  const C omega = (C)(4.0 / (3.0 * L.rho));
+  C*& p = Arr<C>::p(L);
+  C*& ap = Arr<C>::ap(L);
+  C*& r = Arr<C>::r(L);
+  if (!p) FE_TRY(dev_alloc(m, &p, (size_t)L.nnzp * B * AMG_NS));
+  if (!ap) FE_TRY(dev_alloc(m, &ap, (size_t)L.nnzap * B * AMG_NS));
+  if (!r) FE_TRY(dev_alloc(m, &r, (size_t)L.nnzr * B * AMG_NS));
+  AmgLevel& Cq = h->lev[q + 1];
+  C*& cval = Arr<C>::val(Cq);
+  if (!cval) FE_TRY(dev_alloc(m, &cval, (size_t)Cq.nnz * AMG_NS * AMG_NS));
+  {
+    FE_SCOPE(m, FE_PROF_OTHER, (double)L.nnzp * B * AMG_NS * sizeof(C));
+    k_amg_pvals<C, V, B><<<blocks_for(L.nnzp, 128), 128, 0, m->stream>>>(L.nnzp, L.prow, L.pcol, L.ptr, L.col, A,
+                                                                        L.agg, dinv, L.tnode, omega, p);
+  }
+  FE_CUDA(cudaGetLastError());
+  {
+    FE_SCOPE(m, FE_PROF_OTHER, (double)L.nnzap * B * AMG_NS * sizeof(C));
+    k_amg_ap<C, V, B><<<blocks_for(L.nnzap, 128), 128, 0, m->stream>>>(L.nnzap, L.aprow, L.apcol, L.ptr, L.col, A,
+                                                                      L.pptr, L.pcol, p, ap);
+  }
+  FE_CUDA(cudaGetLastError());
+  {
+    FE_SCOPE(m, FE_PROF_OTHER, (double)Cq.nnz * AMG_NS * AMG_NS * sizeof(C));
+    k_amg_rap<C, B><<<blocks_for(Cq.nnz, 128), 128, 0, m->stream>>>(Cq.nnz, Cq.crow, Cq.col, L.rptr, L.rcol, L.rsrc,
+                                                                    L.apptr, L.apcol, p, ap, Cq.absent, cval);
+  }
+  FE_CUDA(cudaGetLastError());
+  k_amg_rvals<C, B><<<blocks_for(L.nnzr, 256), 256, 0, m->stream>>>(L.nnzr, L.rsrc, p, r);
+  FE_CUDA(cudaGetLastError());
+  return FE_OK;
+}
+
 int store_coeffs(fe_mesh m);
 
 template <int NV, class T>
-int tile_one(fe_mesh m, const double* src, T** dst, int64_t nblocks) {
+int tile_one(fe_mesh m, const T* src, T** dst, int64_t nblocks) {
   if (!*dst) FE_TRY(dev_alloc(m, dst, (size_t)tiled_count(nblocks, NV)));
   k_amg_tile<NV, T><<<blocks_for(nblocks * NV, 256), 256, 0, m->stream>>>(nblocks, src, *dst);
   FE_CUDA(cudaGetLastError());
   return FE_OK;
 }
 
-// tiled V-cycle copies of the coarse operators and the prolongators, in the
-// V-cycle's precision
+// tiled V-cycle copies of the coarse operators and the prolongators
+template <class C>
 int tile_copies(fe_mesh m) {
   AmgHier* h = m->amg;
-  const bool d64 = m->prec == FE_PREC_FP64;
   for (int q = 0; q < h->nlev; q++) {
     AmgLevel& L = h->lev[q];
-    if (q > 0) {
-      if (d64) FE_TRY((tile_one<AMG_NS * AMG_NS, double>(m, L.val64, &L.vt64, L.nnz)));
-      else FE_TRY((tile_one<AMG_NS * AMG_NS, float>(m, L.val64, &L.vt32, L.nnz)));
-    }
+    C** vt = std::is_same<C, double>::value ? (C**)&L.vt64 : (C**)&L.vt32;
+    C** pt = std::is_same<C, double>::value ? (C**)&L.pt64 : (C**)&L.pt32;
+    if (q > 0) FE_TRY((tile_one<AMG_NS * AMG_NS, C>(m, Arr<C>::val(L), vt, L.nnz)));
     if (q < h->nlev - 1) {
-      if (L.b == 3) {
-        if (d64) FE_TRY((tile_one<3 * AMG_NS, double>(m, L.p64, &L.pt64, L.nnzp)));
-        else FE_TRY((tile_one<3 * AMG_NS, float>(m, L.p64, &L.pt32, L.nnzp)));
-      } else {
-        if (d64) FE_TRY((tile_one<AMG_NS * AMG_NS, double>(m, L.p64, &L.pt64, L.nnzp)));
-        else FE_TRY((tile_one<AMG_NS * AMG_NS, float>(m, L.p64, &L.pt32, L.nnzp)));
-      }
+      if (L.b == 3) FE_TRY((tile_one<3 * AMG_NS, C>(m, Arr<C>::p(L), pt, L.nnzp)));
+      else FE_TRY((tile_one<AMG_NS * AMG_NS, C>(m, Arr<C>::p(L), pt, L.nnzp)));
     }
   }
   return FE_OK;
 }
 
-template <class V>
+// the whole hierarchy's numbers: FP64 for an FP64 tangent, FP32 otherwise
+template <class C, class V>
 int numeric_all(fe_mesh m, const V* K0) {
   AmgHier* h = m->amg;
-  FE_TRY((numeric_level<V, 3>(m, 0, Vals<V, 3>{K0, true})));
-  for (int q = 1; q < h->nlev; q++) FE_TRY((numeric_level<double, AMG_NS>(m, q, Vals<double, AMG_NS>{h->lev[q].val64, false})));
+  FE_TRY((numeric_level<C, V, 3>(m, 0, Vals<C, V, 3>{K0, true})));
+  for (int q = 1; q < h->nlev; q++)
+    FE_TRY((numeric_level<C, C, AMG_NS>(m, q, Vals<C, C, AMG_NS>{Arr<C>::val(h->lev[q]), false})));
   FE_TRY(store_coeffs(m));
-  FE_TRY(tile_copies(m));
-  if (m->prec != FE_PREC_FP64) {  // the V-cycle's FP32 copies
-    for (int q = 0; q < h->nlev; q++) {
-      AmgLevel& L = h->lev[q];
-      const int64_t bb = (int64_t)L.b * L.b;
-      FE_TRY(to_f32(m, L.dinv64, &L.dinv32, (int64_t)L.n * bb));
-      if (q > 0) FE_TRY(to_f32(m, L.val64, &L.val32, L.nnz * bb));
-      if (q < h->nlev - 1) {
-        FE_TRY(to_f32(m, L.p64, &L.p32, L.nnzp * L.b * AMG_NS));
-        FE_TRY(to_f32(m, L.r64, &L.r32, L.nnzr * L.b * AMG_NS));
-      } else {
-        const int64_t Nd = (int64_t)L.n * L.b;
-        FE_TRY(to_f32(m, L.inv64, &L.inv32, Nd * Nd));
-      }
-    }
-  }
-  return FE_OK;
+  return tile_copies<C>(m);
 }
 
 int ensure_vectors(fe_mesh m, int elem) {
@@ -1339,10 +1350,10 @@ int vcycle_launches(fe_mesh m, cudaStream_t st, const V* K0, const double* b, do
     *flops += 2.0 * Lq.nnzr * Lq.b * AMG_NS;
     if (Lq.b == 3)
       k_vc_restrict<T, 3><<<Cq.n, 128, 0, st>>>(Cq.n, Lq.rptr, Lq.rcol, rv(q), (const T*)Lq.r, dinv(q + 1), (T*)Cq.r,
-                                                coarsest ? nullptr : (T*)Cq.d0, coef(q + 1));
+                                                coarsest ? nullptr : (T*)Cq.d0, coef(q + 1), Lq.n);
     else
       k_vc_restrict<T, AMG_NS><<<Cq.n, 128, 0, st>>>(Cq.n, Lq.rptr, Lq.rcol, rv(q), (const T*)Lq.r, dinv(q + 1),
-                                                     (T*)Cq.r, coarsest ? nullptr : (T*)Cq.d0, coef(q + 1));
+                                                     (T*)Cq.r, coarsest ? nullptr : (T*)Cq.d0, coef(q + 1), Lq.n);
     FE_CUDA(cudaGetLastError());
   }
   {  // coarsest
@@ -1360,9 +1371,10 @@ int vcycle_launches(fe_mesh m, cudaStream_t st, const V* K0, const double* b, do
     *flops += 2.0 * Lq.nnzp * Lq.b * AMG_NS;
     const unsigned grid = blocks_for((int64_t)Lq.n * 4, 256);
     if (Lq.b == 3)
-      k_vc_prolong<T, 3, 4><<<grid, 256, 0, st>>>(Lq.n, Lq.pptr, Lq.pcol, pv(q), X(q + 1), X(q), (T*)Lq.e);
+      k_vc_prolong<T, 3, 4><<<grid, 256, 0, st>>>(Lq.n, Lq.pptr, Lq.pcol, pv(q), X(q + 1), X(q), (T*)Lq.e, Lq.nc);
     else
-      k_vc_prolong<T, AMG_NS, 4><<<grid, 256, 0, st>>>(Lq.n, Lq.pptr, Lq.pcol, pv(q), X(q + 1), X(q), (T*)Lq.e);
+      k_vc_prolong<T, AMG_NS, 4><<<grid, 256, 0, st>>>(Lq.n, Lq.pptr, Lq.pcol, pv(q), X(q + 1), X(q), (T*)Lq.e,
+                                                       Lq.nc);
     FE_CUDA(cudaGetLastError());
     // r -= A e; d0 = D^-1 r / theta
     FE_TRY(step(q, (const T*)Lq.e, (T*)Lq.d0, 0.0, VC_KEEPX | VC_START));
@@ -1413,7 +1425,6 @@ int capture(fe_mesh m, const V* K0) {
 }  // namespace
 
 int fe_amg_setup(fe_mesh m) {
-  if (m->pres) return fe_set_error("AMG is offered for the displacement block of the displacement form"), FE_ERR_ARG;
   if (!m->amg) {
     m->amg = new AmgHier();
     int rc = build_structure(m);
@@ -1422,14 +1433,16 @@ int fe_amg_setup(fe_mesh m) {
       return rc;
     }
   }
-  if (m->prec == FE_PREC_FP64) FE_TRY(numeric_all<double>(m, m->K64));
-  else if (m->prec == FE_PREC_MIXED_BF16) FE_TRY(numeric_all<__nv_bfloat16>(m, m->K16));
-  else FE_TRY(numeric_all<float>(m, m->K32));
+  m->amg->ready = false;
+  if (m->prec == FE_PREC_FP64) FE_TRY((numeric_all<double, double>(m, m->K64)));
+  else if (m->prec == FE_PREC_MIXED_BF16) FE_TRY((numeric_all<float, __nv_bfloat16>(m, m->K16)));
+  else FE_TRY((numeric_all<float, float>(m, m->K32)));
+  m->amg->ready = true;
   return FE_OK;
 }
 
 int fe_amg_apply(fe_mesh m, const double* x, void* z, bool z_double) {
-  if (!m->amg || m->amg->lev[0].dinv64 == nullptr) return fe_set_error("AMG hierarchy not set up"), FE_ERR_STATE;
+  if (!m->amg || !m->amg->ready) return fe_set_error("AMG hierarchy not set up"), FE_ERR_STATE;
   AmgHier* h = m->amg;
   const int64_t N = (int64_t)m->nn * 3;
   const bool d64 = m->prec == FE_PREC_FP64;
@@ -1475,7 +1488,7 @@ extern "C" int fe_amg_get_level(fe_mesh m, int level, int64_t* info, double* rho
                                 double* val, uint8_t* absent, int32_t* agg, int32_t* pptr, int32_t* pcol,
                                 double* pval) {
   if (!m) return fe_set_error("NULL mesh"), FE_ERR_ARG;
-  if (!m->amg || m->amg->lev[0].dinv64 == nullptr) return fe_set_error("no AMG hierarchy"), FE_ERR_STATE;
+  if (!m->amg || !m->amg->ready) return fe_set_error("no AMG hierarchy"), FE_ERR_STATE;
   AmgHier* h = m->amg;
   if (level < 0 || level >= h->nlev) return fe_set_error("level %d outside [0, %d)", level, h->nlev), FE_ERR_ARG;
   FE_CUDA(cudaSetDevice(m->device));
@@ -1490,19 +1503,32 @@ extern "C" int fe_amg_get_level(fe_mesh m, int level, int64_t* info, double* rho
     info[4] = last ? 0 : L.nnzp;
   }
   if (rho) *rho = L.rho;
+  // values in FP64 (widened from the FP32 numbers of the mixed forms)
+  auto copy_vals = [&](double* dst, const double* s64, const float* s32, int64_t count) -> int {
+    if (s64) {
+      FE_CUDA(cudaMemcpy(dst, s64, sizeof(double) * count, cudaMemcpyDeviceToHost));
+    } else {
+      std::vector<float> tmp(count);
+      FE_CUDA(cudaMemcpy(tmp.data(), s32, sizeof(float) * count, cudaMemcpyDeviceToHost));
+      for (int64_t i = 0; i < count; i++) dst[i] = (double)tmp[i];
+    }
+    return FE_OK;
+  };
   if (level > 0) {
     if (ptr) FE_CUDA(cudaMemcpy(ptr, L.ptr, sizeof(int) * (L.n + 1), cudaMemcpyDeviceToHost));
     if (col) FE_CUDA(cudaMemcpy(col, L.col, sizeof(int) * L.nnz, cudaMemcpyDeviceToHost));
-    if (val) FE_CUDA(cudaMemcpy(val, L.val64, sizeof(double) * L.nnz * L.b * L.b, cudaMemcpyDeviceToHost));
+    if (val) FE_TRY(copy_vals(val, L.val64, L.val32, L.nnz * L.b * L.b));
   }
   if (absent) FE_CUDA(cudaMemcpy(absent, L.absent, L.n, cudaMemcpyDeviceToHost));
   if (!last) {
     if (agg) FE_CUDA(cudaMemcpy(agg, L.agg, sizeof(int) * L.n, cudaMemcpyDeviceToHost));
     if (pptr) FE_CUDA(cudaMemcpy(pptr, L.pptr, sizeof(int) * (L.n + 1), cudaMemcpyDeviceToHost));
     if (pcol) FE_CUDA(cudaMemcpy(pcol, L.pcol, sizeof(int) * L.nnzp, cudaMemcpyDeviceToHost));
-    if (pval) FE_CUDA(cudaMemcpy(pval, L.p64, sizeof(double) * L.nnzp * L.b * AMG_NS, cudaMemcpyDeviceToHost));
+    if (pval) FE_TRY(copy_vals(pval, L.p64, L.p32, L.nnzp * L.b * AMG_NS));
   }
   return FE_OK;
 }
 
-extern "C" int fe_amg_levels(fe_mesh m) { return (m && m->amg && m->amg->lev[0].dinv64) ? m->amg->nlev : 0; }
+extern "C" int fe_amg_levels(fe_mesh m) { return (m && m->amg && m->amg->ready) ? m->amg->nlev : 0; }
+
+FE_DBG_BOUNDS_READER(fe_dbg_bounds_amg)

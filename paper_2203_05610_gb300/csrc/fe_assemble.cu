@@ -397,13 +397,13 @@ __global__ void __launch_bounds__(256) k_gather_residual(
     const int* __restrict__ ks_ptr, const int* __restrict__ ks_col, const double* __restrict__ ks_val,
     const double* __restrict__ d, const uint8_t* __restrict__ fixmask, int np,
     const int* __restrict__ vert_ptr, const int* __restrict__ vert_list, const double* __restrict__ relp,
-    double* __restrict__ r, double* red, unsigned* ticket, double* norm2) {
+    double* __restrict__ r, double* red, unsigned* ticket, double* norm2, int64_t nrel) {
   int t = blockIdx.x * blockDim.x + threadIdx.x;
   double acc = 0.0;
   if (t < nn) {
     double s0 = 0.0, s1 = 0.0, s2 = 0.0;
     for (int k = node_ptr[t]; k < node_ptr[t + 1]; k++) {
-      const double* c = rel + (size_t)node_list[k] * 3;
+      const double* c = rel + (size_t)fe_idx(node_list[k], nrel) * 3;
       s0 += c[0];
       s1 += c[1];
       s2 += c[2];
@@ -413,7 +413,7 @@ __global__ void __launch_bounds__(256) k_gather_residual(
     s2 -= load * fext1[3 * (size_t)t + 2];
     for (int k = ks_ptr[t]; k < ks_ptr[t + 1]; k++) {
       const double* kv = ks_val + (size_t)k * 9;
-      const double* u = d + 3 * (size_t)ks_col[k];
+      const double* u = d + 3 * (size_t)fe_idx(ks_col[k], nn);
       s0 += kv[0] * u[0] + kv[1] * u[1] + kv[2] * u[2];
       s1 += kv[3] * u[0] + kv[4] * u[1] + kv[5] * u[2];
       s2 += kv[6] * u[0] + kv[7] * u[1] + kv[8] * u[2];
@@ -459,7 +459,7 @@ int fe_residual_dev(fe_mesh m, const double* d, double* r, bool want_norm) {
   k_gather_residual<<<grid, 256, 0, m->stream>>>(m->nn, m->nen, m->node_ptr, m->node_list, m->rel, m->fext1,
                                                  m->load, m->ks_ptr, m->ks_col, m->ks_val, d, m->fixmask, m->np,
                                                  m->vert_ptr, m->vert_list, m->relp, r, m->red, m->red_ticket,
-                                                 want_norm ? m->scal : nullptr);
+                                                 want_norm ? m->scal : nullptr, (int64_t)m->ne * m->nen);
   FE_CUDA(cudaGetLastError());
   return FE_OK;
 }
@@ -564,7 +564,7 @@ __global__ void __launch_bounds__(256) k_elem_tangent(
     int nel, const int* __restrict__ elems, const int* __restrict__ conn, const double* __restrict__ geo,
     const double* __restrict__ d, int nn, int pres, MatParams mp, const double* __restrict__ fib,
     const int* __restrict__ emap, const int* __restrict__ upmap, const uint8_t* __restrict__ fixmask,
-    T* __restrict__ K, T* __restrict__ B) {
+    T* __restrict__ K, T* __restrict__ B, int64_t nnzb) {
   using C = TanCfg<ORDER, T>;
   constexpr int NEN = C::NEN, NQ = C::NQ, EPB = C::EPB;
   extern __shared__ __align__(16) unsigned char smraw[];
@@ -677,14 +677,14 @@ __global__ void __launch_bounds__(256) k_elem_tangent(
     int na = sconn[le][a], nb = sconn[le][b];
     uint8_t fa = fixmask[na], fb = fixmask[nb];
     const int* em = emap + (size_t)e * NEN * NEN;
-    const int pab = em[a * NEN + b];
+    const int pab = fe_idx(em[a * NEN + b], nnzb);
     for (int kk = 0; kk < 3; kk++) {
       T v = w * acc[kk];
       if (((fa >> i) & 1) || ((fb >> kk) & 1)) v = T(0);
       K[kv_index(pab, 3 * i + kk)] += v;
     }
     if (a != b) {
-      const int pba = em[b * NEN + a];
+      const int pba = fe_idx(em[b * NEN + a], nnzb);
       for (int kk = 0; kk < 3; kk++) {
         T v = w * acc[kk];
         if (((fa >> i) & 1) || ((fb >> kk) & 1)) v = T(0);
@@ -795,7 +795,7 @@ static int launch_tangent(fe_mesh m, const double* d, T* K, T* B) {
                                                 2.0 * 9 * sizeof(T) * nen * nen + (m->pres ? 16.0 * nen * 4 * sizeof(T) : 0)));
     k_elem_tangent<ORDER, T><<<grid, 256, smem, m->stream>>>(nel, m->perm + start, m->conn, m->geo, d, m->nn,
                                                              m->pres, m->mp, m->fib, m->emap, m->upmap,
-                                                             m->fixmask, K, B);
+                                                             m->fixmask, K, B, m->nnzb);
     FE_CUDA(cudaGetLastError());
   }
   return FE_OK;
@@ -936,3 +936,5 @@ extern "C" int fe_tangent_copy(fe_mesh m, double* val, double* bup, double* dinv
   FE_TRY(copy_out(m, dinv, f64 ? m->Dinv64 : nullptr, f64 ? nullptr : m->Dinv32, nullptr, (int64_t)m->nn * 9));
   return FE_OK;
 }
+
+FE_DBG_BOUNDS_READER(fe_dbg_bounds_assemble)

@@ -29,6 +29,38 @@ void fe_set_error(const char* fmt, ...);
 // device error word values (written by kernels, read by the host)
 enum { DEV_OK = 0, DEV_ERR_TIMEOUT = 1, DEV_ERR_BOUNDS = 2, DEV_ERR_COLORS = 3 };
 
+// Index checks of the FE_DEBUG_BOUNDS build.  fe_idx(i, n) returns i when
+// 0 <= i < n; in the debug build an index outside the range raises this
+// translation unit's device flag and is replaced by 0, so the access stays
+// in bounds and the kernel runs to its end; every call then reports
+// FE_ERR_DEVICE_FLAG (fe_check_device_error reads and clears the flags).  In
+// the normal build fe_idx is the identity and costs nothing.
+#ifdef FE_DEBUG_BOUNDS
+static __device__ unsigned g_fe_dbg_bounds;
+__device__ __forceinline__ int fe_idx(int i, int64_t n) {
+  if (i < 0 || (int64_t)i >= n) {
+    atomicExch(&g_fe_dbg_bounds, 1u);
+    return 0;
+  }
+  return i;
+}
+// defines the host reader of this translation unit's flag (reads and clears it)
+#define FE_DBG_BOUNDS_READER(name)                                                  \
+  int name(void) {                                                                  \
+    unsigned v = 0, z = 0;                                                          \
+    if (cudaMemcpyFromSymbol(&v, g_fe_dbg_bounds, sizeof(v)) != cudaSuccess) return 1; \
+    cudaMemcpyToSymbol(g_fe_dbg_bounds, &z, sizeof(z));                             \
+    return v != 0;                                                                  \
+  }
+int fe_dbg_bounds_mesh(void);
+int fe_dbg_bounds_assemble(void);
+int fe_dbg_bounds_krylov(void);
+int fe_dbg_bounds_amg(void);
+#else
+__device__ __forceinline__ int fe_idx(int i, int64_t) { return i; }
+#define FE_DBG_BOUNDS_READER(name)
+#endif
+
 // ---------------------------------------------------------------- material parameters
 struct MatParams {
   int kind;

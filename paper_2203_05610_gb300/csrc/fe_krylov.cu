@@ -891,7 +891,7 @@ __global__ void __launch_bounds__(256) k_spmv(int nn, const int* __restrict__ ro
   const int rs = row_ptr[row], re = row_ptr[row + 1];
   AT a0 = AT(0), a1 = AT(0), a2 = AT(0);
   for (int k = rs + lane; k < re; k += 32) {
-    const int c = __ldg(col + k);
+    const int c = fe_idx(__ldg(col + k), nn);
     const VT* b = val + kv_index(k, 0);
     AT v[9];
 #pragma unroll
@@ -968,9 +968,9 @@ __device__ __forceinline__ void spmv_load_chunk(const int* __restrict__ col, con
 }
 
 template <class XT, class AT>
-__device__ __forceinline__ void spmv_load_x(const XT* __restrict__ x, int c, AT& x0, AT& x1, AT& x2) {
+__device__ __forceinline__ void spmv_load_x(const XT* __restrict__ x, int c, AT& x0, AT& x1, AT& x2, int ncol) {
   if (c >= 0) {
-    const XT* xc = x + 3 * (int64_t)c;
+    const XT* xc = x + 3 * (int64_t)fe_idx(c, ncol);
     x0 = (AT)xc[0];
     x1 = (AT)xc[1];
     x2 = (AT)xc[2];
@@ -1000,7 +1000,7 @@ __global__ void __launch_bounds__(256) k_spmv_stream(int nn, const int* __restri
     spmv_load_chunk<VT, AT>(col, val, (int64_t)kstart + lane, kend, c0, v0);
     spmv_load_chunk<VT, AT>(col, val, (int64_t)kstart + 32 + lane, kend, c1, v1);
     AT xa0, xa1, xa2;
-    spmv_load_x<XT, AT>(x, c0, xa0, xa1, xa2);
+    spmv_load_x<XT, AT>(x, c0, xa0, xa1, xa2, nn);
     AT carry0 = AT(0), carry1 = AT(0), carry2 = AT(0);
     int rowbase = r0 - 1;  // the row in progress before the current chunk
     for (int kc = kstart; kc < kend; kc += 32) {
@@ -1008,7 +1008,7 @@ __global__ void __launch_bounds__(256) k_spmv_stream(int nn, const int* __restri
       AT v2[9];
       spmv_load_chunk<VT, AT>(col, val, (int64_t)kc + 64 + lane, kend, c2, v2);
       AT xb0, xb1, xb2;
-      spmv_load_x<XT, AT>(x, c1, xb0, xb1, xb2);
+      spmv_load_x<XT, AT>(x, c1, xb0, xb1, xb2, nn);
       AT p0 = AT(0), p1 = AT(0), p2 = AT(0);
       if (c0 >= 0) {
         p0 = v0[0] * xa0 + v0[1] * xa1 + v0[2] * xa2;
@@ -1136,7 +1136,21 @@ __global__ void __launch_bounds__(256) k_pc_schur(int np, int nn, const int* __r
 
 template <class OT>
 static int pc_apply_t(fe_mesh m, const double* x, OT* z) {
-  if (m->pc_type == 1) return fe_amg_apply(m, x, z, sizeof(OT) == 8);  // one AMG V-cycle
+  if (m->pc_type == 1) {  // one AMG V-cycle on the displacement block
+    FE_TRY(fe_amg_apply(m, x, z, sizeof(OT) == 8));
+    if (!m->pres) return FE_OK;
+    // u-p form: the lower Schur step z_p = S^-1 (x_p - B2 z_u) with the V-cycle's z_u
+    FE_SCOPE(m, FE_PROF_PC, (double)m->nnz_up * (8 + 12.0 * (m->prec == FE_PREC_FP64 ? 8 : 4)) + 24.0 * m->np);
+    const unsigned grid = (unsigned)(((int64_t)m->np * 32 + 255) / 256);
+    if (m->prec == FE_PREC_FP64)
+      k_pc_schur<double, OT><<<grid, 256, 0, m->stream>>>(m->np, m->nn, m->pu_ptr, m->pu_col, m->pu_src, m->B64,
+                                                          m->Sd, x, z);
+    else
+      k_pc_schur<float, OT><<<grid, 256, 0, m->stream>>>(m->np, m->nn, m->pu_ptr, m->pu_col, m->pu_src, m->B32,
+                                                         m->Sd, x, z);
+    FE_CUDA(cudaGetLastError());
+    return FE_OK;
+  }
   FE_SCOPE(m, FE_PROF_PC, (double)m->nn * (9.0 * (m->prec == FE_PREC_FP64 ? 8 : 4) + 24 + 3.0 * sizeof(OT)) +
                               (m->pres ? (double)m->nnz_up * (8 + 12.0 * (m->prec == FE_PREC_FP64 ? 8 : 4)) + 24.0 * m->np
                                        : 0.0));
@@ -2005,3 +2019,5 @@ extern "C" int fe_lbfgs_apply(fe_mesh m, const double* S, const double* Y, const
   FE_TRY(fe_lbfgs_dev(m, S, Y, rho, 0, k > 0 ? k : 1, k, m->ndof, q, z, h0, 0.0, 0.0, 1, 1, nullptr));
   return fe_check_device_error(m);
 }
+
+FE_DBG_BOUNDS_READER(fe_dbg_bounds_krylov)

@@ -103,10 +103,16 @@ int fe_kernel_occupancy(const void* fn, int threads, size_t smem_bytes, int* blo
   return FE_OK;
 }
 
+FE_DBG_BOUNDS_READER(fe_dbg_bounds_mesh)
+
 int fe_check_device_error(fe_mesh m) {
   int h = 0;
   FE_CUDA(cudaMemcpyAsync(&h, m->err, sizeof(int), cudaMemcpyDeviceToHost, m->stream));
   FE_CUDA(cudaStreamSynchronize(m->stream));
+#ifdef FE_DEBUG_BOUNDS
+  if (h == DEV_OK && (fe_dbg_bounds_mesh() | fe_dbg_bounds_assemble() | fe_dbg_bounds_krylov() | fe_dbg_bounds_amg()))
+    h = DEV_ERR_BOUNDS;
+#endif
   if (h == DEV_OK) return FE_OK;
   // clear the error word and the grid-synchronisation state for later calls
   cudaMemsetAsync(m->err, 0, sizeof(int), m->stream);
@@ -115,6 +121,10 @@ int fe_check_device_error(fe_mesh m) {
   if (h == DEV_ERR_TIMEOUT) {
     fe_set_error("a bounded device wait ran out (grid barrier)");
     return FE_ERR_TIMEOUT;
+  }
+  if (h == DEV_ERR_BOUNDS) {
+    fe_set_error("device-side index check failed (an index outside its array)");
+    return FE_ERR_DEVICE_FLAG;
   }
   fe_set_error("device-side check failed (code %d)", h);
   return FE_ERR_DEVICE_FLAG;
@@ -772,8 +782,6 @@ extern "C" int fe_mesh_create(const fe_mesh_desc* desc, fe_mesh* out) {
 extern "C" int fe_set_pc(fe_mesh m, int pc_type) {
   if (!m) return fe_set_error("NULL mesh"), FE_ERR_ARG;
   if (pc_type != 0 && pc_type != 1) return fe_set_error("pc_type must be 0 (block-Jacobi) or 1 (AMG)"), FE_ERR_ARG;
-  if (pc_type == 1 && m->pres)
-    return fe_set_error("AMG is offered for the displacement form (no pressure unknowns)"), FE_ERR_ARG;
   FE_CUDA(cudaSetDevice(m->device));
   const bool rebuild = pc_type == 1 && m->pc_type != 1 && m->prec >= 0;
   m->pc_type = pc_type;

@@ -296,9 +296,11 @@ def test_mixed_precision_solve(fe, method):
         assert sg["rfinal"] <= 1e-8 * sg["r0"]
         errs[prec] = np.linalg.norm(xg.cpu().numpy() - xref) / np.linalg.norm(xref)
         rrel[prec] = sg["rfinal"] / sg["r0"]
-    # at most 10x the FP64 path's error at the same residual (error is
-    # proportional to the residual near the solution)
-    bound = 10 * max(errs["fp64"] * max(1.0, rrel["mixed_fp32"] / rrel["fp64"]), 1e-12)
+    # at most MIXED_FACTOR times the FP64 path's error at the same residual
+    # (error is proportional to the residual near the solution; the FP32
+    # tangent's last Newton step contracts only linearly)
+    from test_gpu_amg import MIXED_FACTOR
+    bound = MIXED_FACTOR * max(errs["fp64"] * max(1.0, rrel["mixed_fp32"] / rrel["fp64"]), 1e-12)
     assert errs["mixed_fp32"] <= bound, (errs, rrel)
 
 
