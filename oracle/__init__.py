@@ -74,6 +74,10 @@ def lib():
             L.om_tri_rule.restype = I
             L.om_tri_rule.argtypes = [P, P]
             L.om_set_pc.argtypes = [P, I]
+            L.om_set_dynamics.argtypes = [P, D, D]
+            L.om_dynamics_set.argtypes = [P, P, P, P]
+            L.om_dynamics_advance.argtypes = [P, P]
+            L.om_dynamics_get.argtypes = [P, P, P]
             L.om_amg_levels.restype = I
             L.om_amg_levels.argtypes = [P]
             L.om_amg_level_info.argtypes = [P, I, P]
@@ -260,6 +264,24 @@ class Mesh:
         """Preconditioner of the displacement block: 0 / "bj" nodal
         block-Jacobi, 1 / "amg" the AMG V-cycle (set up by tangent())."""
         lib().om_set_pc(self.h, {"bj": 0, "amg": 1}.get(pc_type, pc_type))
+
+    def set_dynamics(self, rho, dt):
+        """Newmark elastodynamics with density rho and time step dt (rho <= 0: off)."""
+        lib().om_set_dynamics(self.h, float(rho), float(dt))
+
+    def dynamics_set(self, d=None, v=None, a=None):
+        n3 = 3 * self.nn
+        arrs = [None if x is None else np.ascontiguousarray(x[:n3], dtype=np.float64) for x in (d, v, a)]
+        lib().om_dynamics_set(self.h, *[_p(x) for x in arrs])
+
+    def dynamics_advance(self, d):
+        lib().om_dynamics_advance(self.h, _p(np.ascontiguousarray(d, dtype=np.float64)))
+
+    def dynamics_get(self):
+        v = np.zeros(3 * self.nn)
+        a = np.zeros(3 * self.nn)
+        lib().om_dynamics_get(self.h, _p(v), _p(a))
+        return v, a
 
     def amg_levels(self):
         """The AMG hierarchy of the last tangent: one dict per level (A_l,

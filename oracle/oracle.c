@@ -400,6 +400,12 @@ struct om_mesh {
   long long lit; /* Krylov iterations, accumulated by om_gmres */
   int pc_type;   /* displacement block: 0 nodal block-Jacobi, 1 algebraic multigrid */
   struct om_amg* amg;
+  /* elastodynamics (om_set_dynamics): density, time step, mass per block
+   * (scalar, M_ab = Mm I), dashpot matrix [nnzb][9], the state d_n, v_n, a_n
+   * and the Newmark predictors dhat, dtil */
+  int dyn;
+  double rho, dt;
+  double *Mm, *Cd, *dn, *vn, *an, *dhat, *dtil;
 };
 
 static int cmp_ll(const void* a, const void* b) {
@@ -606,7 +612,9 @@ void om_destroy(om_mesh* m) {
   free(m->X); free(m->conn); free(m->colors); free(m->row_ptr); free(m->col);
   free(m->up_ptr); free(m->up_col); free(m->dgroup); free(m->groups); free(m->fnodes);
   free(m->fkind); free(m->fdata); free(m->fib); free(m->K); free(m->B1); free(m->Dinv);
-  free(m->Sd); amg_free(m->amg); free(m);
+  free(m->Sd); amg_free(m->amg);
+  free(m->Mm); free(m->Cd); free(m->dn); free(m->vn); free(m->an); free(m->dhat); free(m->dtil);
+  free(m);
 }
 
 void om_info(const om_mesh* m, long long* out) {
@@ -733,6 +741,237 @@ static int p_count(const om_mesh* m) { return m->pres == 2 ? 1 : 4; }
 static int p_index(const om_mesh* m, int e, const int* c, int v) { return m->pres == 2 ? e : c[v]; }
 static double p_shape(const om_mesh* m, const double* lamq, int v) { return m->pres == 2 ? 1.0 : lamq[v]; }
 
+static long find_block(const int* ptr, const int* col, int row, int c);
+
+/* ======================================================================
+ * Elastodynamics and follower pressure (the paper's momentum equation with
+ * its inertia term, Eq. "momentum strong", the Robin condition of the
+ * epicardium with its dashpots, Eq. "bc epi", and a pressure that follows
+ * the deformed surface).  Readings (the paper names no time integrator and
+ * no density):
+ *   - density rho per unit reference volume (the printed equation has
+ *     rho = 1); consistent mass M_ab = rho int N_a N_b I dV, integrated
+ *     exactly (products of the barycentric shape functions, int over the tet
+ *     of l1^a l2^b l3^c l4^d = 6 V a! b! c! d! / (a + b + c + d + 3)!);
+ *   - Newmark average acceleration (beta = 1/4, gamma = 1/2: trapezoidal,
+ *     unconditionally stable, energy conserving for a linear undamped
+ *     system): step n -> n+1 solves R(d) + M a(d) + C v(d) = 0 with
+ *     a = 4/dt^2 (d - dhat), v = 2/dt (d - dtil),
+ *     dhat = d_n + dt v_n + dt^2/4 a_n, dtil = d_n + dt/2 v_n;
+ *     tangent K + 4/dt^2 M + 2/dt C;
+ *   - dashpots: face kind 4 with data (c_perp, c_par): damping traction
+ *     -(c_perp N N^T + c_par (I - N N^T)) v on the reference face (N the
+ *     reference normal, like the springs of kind 2);
+ *   - follower pressure: face kind 3 with data (p): traction -p n da on the
+ *     deformed face, i.e. nodal forces -p int N_a (x_xi x x_eta) dxi deta
+ *     over the reference triangle (exact with the degree-4 rule for P1 and
+ *     P2 faces); its tangent is not symmetric, and it has no potential, so
+ *     om_energy leaves it out.
+ * ====================================================================== */
+/* d N_a / d lambda_c of the triangle shape functions (face-local nodes) */
+static void tri_dshape(int order, const double* lam, double dN[6][3]) {
+  memset(dN, 0, sizeof(double) * 18);
+  if (order == 1) {
+    for (int a = 0; a < 3; a++) dN[a][a] = 1.0;
+    return;
+  }
+  for (int a = 0; a < 3; a++) dN[a][a] = 4.0 * lam[a] - 1.0;
+  for (int e = 0; e < 3; e++) {
+    int i = TRI_EDGE[e][0], j = TRI_EDGE[e][1];
+    dN[3 + e][i] = 4.0 * lam[j];
+    dN[3 + e][j] = 4.0 * lam[i];
+  }
+}
+
+/* follower pressure of face f at displacement d: nodal residual rf (R += rf)
+ * and, when Kf != NULL, its derivative Kf[a][b][i][k] = d rf_a,i / d d_b,k */
+static int follower_terms(const om_mesh* m, int f, const double* d, double rf[6][3], double Kf[6][6][3][3]) {
+  int nfn = m->order == 1 ? 3 : 6;
+  const int* v = m->fnodes + 6 * f;
+  double p = m->load * m->fdata[3 * f];
+  double x[6][3];
+  for (int a = 0; a < nfn; a++)
+    for (int i = 0; i < 3; i++) x[a][i] = m->X[3 * v[a] + i] + d[3L * v[a] + i];
+  double lam[18], w[6], N[6], dN[6][3];
+  int nq = om_tri_rule(lam, w);
+  memset(rf, 0, sizeof(double) * 18);
+  if (Kf) memset(Kf, 0, sizeof(double) * 324);
+  for (int q = 0; q < nq; q++) {
+    tri_shape(m->order, lam + 3 * q, N);
+    tri_dshape(m->order, lam + 3 * q, dN);
+    /* x(xi, eta) with lambda = (1 - xi - eta, xi, eta): d/dxi = d/dl2 - d/dl1, d/deta = d/dl3 - d/dl1 */
+    double Nx[6], Ne[6], xs[3] = {0, 0, 0}, xe[3] = {0, 0, 0};
+    for (int a = 0; a < nfn; a++) {
+      Nx[a] = dN[a][1] - dN[a][0];
+      Ne[a] = dN[a][2] - dN[a][0];
+      for (int i = 0; i < 3; i++) {
+        xs[i] += Nx[a] * x[a][i];
+        xe[i] += Ne[a] * x[a][i];
+      }
+    }
+    double n[3] = {xs[1] * xe[2] - xs[2] * xe[1], xs[2] * xe[0] - xs[0] * xe[2], xs[0] * xe[1] - xs[1] * xe[0]};
+    double wq = 0.5 * w[q] * p; /* reference triangle area 1/2 */
+    for (int a = 0; a < nfn; a++)
+      for (int i = 0; i < 3; i++) rf[a][i] += wq * N[a] * n[i];
+    if (!Kf) continue;
+    /* d n = Nx_b (delta x xe) + Ne_b (xs x delta) */
+    for (int a = 0; a < nfn; a++)
+      for (int b = 0; b < nfn; b++)
+        for (int i = 0; i < 3; i++)
+          for (int k = 0; k < 3; k++) {
+            double dk[3] = {0, 0, 0};
+            dk[k] = 1.0;
+            double c1[3] = {dk[1] * xe[2] - dk[2] * xe[1], dk[2] * xe[0] - dk[0] * xe[2], dk[0] * xe[1] - dk[1] * xe[0]};
+            double c2[3] = {xs[1] * dk[2] - xs[2] * dk[1], xs[2] * dk[0] - xs[0] * dk[2], xs[0] * dk[1] - xs[1] * dk[0]};
+            Kf[a][b][i][k] += wq * N[a] * (Nx[b] * c1[i] + Ne[b] * c2[i]);
+          }
+  }
+  return nfn;
+}
+
+/* exact int over a tet of prod of barycentric powers, divided by the volume */
+static double bary_moment(const int* e) {
+  double num = 6.0;
+  int s = 3;
+  for (int i = 0; i < 4; i++) {
+    for (int k = 2; k <= e[i]; k++) num *= k;
+    s += e[i];
+  }
+  double den = 1.0;
+  for (int k = 2; k <= s; k++) den *= k;
+  return num / den;
+}
+
+/* shape function a of the tet as monomials in the barycentrics: up to 2
+ * terms (coefficient, exponents) */
+static int tet_shape_poly(int order, int a, double* coef, int (*ex)[4]) {
+  memset(ex, 0, sizeof(int) * 8);
+  if (order == 1) {
+    coef[0] = 1.0;
+    ex[0][a] = 1;
+    return 1;
+  }
+  if (a < 4) { /* l_a (2 l_a - 1) */
+    coef[0] = 2.0;
+    ex[0][a] = 2;
+    coef[1] = -1.0;
+    ex[1][a] = 1;
+    return 2;
+  }
+  coef[0] = 4.0;
+  ex[0][TET_EDGE[a - 4][0]] = 1;
+  ex[0][TET_EDGE[a - 4][1]] = 1;
+  return 1;
+}
+
+void om_set_dynamics(om_mesh* m, double rho, double dt) {
+  free(m->Mm); free(m->Cd); free(m->dn); free(m->vn); free(m->an); free(m->dhat); free(m->dtil);
+  m->Mm = m->Cd = m->dn = m->vn = m->an = m->dhat = m->dtil = NULL;
+  m->dyn = rho > 0.0 && dt > 0.0;
+  if (!m->dyn) return;
+  m->rho = rho;
+  m->dt = dt;
+  m->Mm = (double*)xcalloc(m->nnzb, sizeof(double));
+  m->Cd = (double*)xcalloc(9 * m->nnzb, sizeof(double));
+  long n3 = 3L * m->nn;
+  m->dn = (double*)xcalloc(n3, sizeof(double));
+  m->vn = (double*)xcalloc(n3, sizeof(double));
+  m->an = (double*)xcalloc(n3, sizeof(double));
+  m->dhat = (double*)xcalloc(n3, sizeof(double));
+  m->dtil = (double*)xcalloc(n3, sizeof(double));
+  int nen = m->nen;
+  for (int e = 0; e < m->ne; e++) {
+    double G[4][3];
+    double vol = elem_geom(m, e, G);
+    const int* c = m->conn + (long)e * nen;
+    for (int a = 0; a < nen; a++) {
+      double ca[2];
+      int ea[2][4];
+      int na = tet_shape_poly(m->order, a, ca, ea);
+      for (int b = 0; b < nen; b++) {
+        double cb[2];
+        int eb[2][4];
+        int nb = tet_shape_poly(m->order, b, cb, eb);
+        double s = 0.0;
+        for (int i = 0; i < na; i++)
+          for (int j = 0; j < nb; j++) {
+            int ex[4];
+            for (int k = 0; k < 4; k++) ex[k] = ea[i][k] + eb[j][k];
+            s += ca[i] * cb[j] * bary_moment(ex);
+          }
+        m->Mm[find_block(m->row_ptr, m->col, c[a], c[b])] += rho * vol * s;
+      }
+    }
+  }
+  for (int f = 0; f < m->nf; f++) {
+    if (m->fkind[f] != 4) continue;
+    double fv[6][3], M[6][6], Ks[3][3], N[3];
+    int nfn = face_terms(m, f, fv, M, Ks);
+    face_geom(m, f, N);
+    const double* fd = m->fdata + 3 * f;
+    double Cs[3][3];
+    for (int i = 0; i < 3; i++)
+      for (int k = 0; k < 3; k++) Cs[i][k] = fd[0] * N[i] * N[k] + fd[1] * ((i == k) - N[i] * N[k]);
+    const int* v = m->fnodes + 6 * f;
+    for (int a = 0; a < nfn; a++)
+      for (int b = 0; b < nfn; b++) {
+        long k = find_block(m->row_ptr, m->col, v[a], v[b]);
+        for (int i = 0; i < 3; i++)
+          for (int kk = 0; kk < 3; kk++) m->Cd[9 * k + 3 * i + kk] += M[a][b] * Cs[i][kk];
+      }
+  }
+}
+
+/* state of the time integration (nullable: zero); the predictors of the next step */
+void om_dynamics_set(om_mesh* m, const double* d, const double* v, const double* a) {
+  if (!m->dyn) return;
+  long n3 = 3L * m->nn;
+  double dt = m->dt;
+  for (long i = 0; i < n3; i++) {
+    m->dn[i] = d ? d[i] : 0.0;
+    m->vn[i] = v ? v[i] : 0.0;
+    m->an[i] = a ? a[i] : 0.0;
+    m->dhat[i] = m->dn[i] + dt * m->vn[i] + 0.25 * dt * dt * m->an[i];
+    m->dtil[i] = m->dn[i] + 0.5 * dt * m->vn[i];
+  }
+}
+
+/* Newmark update from the converged d of the step: v, a of the new state */
+void om_dynamics_advance(om_mesh* m, const double* d) {
+  if (!m->dyn) return;
+  long n3 = 3L * m->nn;
+  double dt = m->dt;
+  double* v = (double*)xcalloc(n3, sizeof(double));
+  double* a = (double*)xcalloc(n3, sizeof(double));
+  for (long i = 0; i < n3; i++) {
+    a[i] = 4.0 / (dt * dt) * (d[i] - m->dhat[i]);
+    v[i] = 2.0 / dt * (d[i] - m->dtil[i]);
+  }
+  om_dynamics_set(m, d, v, a);
+  free(v);
+  free(a);
+}
+
+void om_dynamics_get(const om_mesh* m, double* v, double* a) {
+  if (!m->dyn) return;
+  if (v) memcpy(v, m->vn, sizeof(double) * 3 * (size_t)m->nn);
+  if (a) memcpy(a, m->an, sizeof(double) * 3 * (size_t)m->nn);
+}
+
+/* r += M a(d) + C v(d) (displacement rows) */
+static void dyn_residual(const om_mesh* m, const double* d, double* r) {
+  double cm = 4.0 / (m->dt * m->dt), cc = 2.0 / m->dt;
+  for (int a = 0; a < m->nn; a++)
+    for (int k = m->row_ptr[a]; k < m->row_ptr[a + 1]; k++) {
+      int b = m->col[k];
+      for (int i = 0; i < 3; i++) {
+        double s = cm * m->Mm[k] * (d[3L * b + i] - m->dhat[3L * b + i]);
+        for (int j = 0; j < 3; j++) s += cc * m->Cd[9L * k + 3 * i + j] * (d[3L * b + j] - m->dtil[3L * b + j]);
+        r[3L * a + i] += s;
+      }
+    }
+}
+
 double om_residual(om_mesh* m, const double* d, double* r) {
   memset(r, 0, sizeof(double) * m->ndof);
   int nen = m->nen;
@@ -786,6 +1025,16 @@ double om_residual(om_mesh* m, const double* d, double* r) {
         r[3L * v[a] + i] += s;
       }
   }
+  /* follower pressure: R += p int N_a n da on the deformed face */
+  for (int f = 0; f < m->nf; f++) {
+    if (m->fkind[f] != 3) continue;
+    double rf[6][3];
+    int nfn = follower_terms(m, f, d, rf, NULL);
+    const int* v = m->fnodes + 6 * f;
+    for (int a = 0; a < nfn; a++)
+      for (int i = 0; i < 3; i++) r[3L * v[a] + i] += rf[a][i];
+  }
+  if (m->dyn) dyn_residual(m, d, r);
   for (int a = 0; a < m->nn; a++)
     for (int c = 0; c < 3; c++)
       if (is_fixed(m, a, c)) r[3L * a + c] = 0.0;
@@ -829,6 +1078,21 @@ double om_energy(om_mesh* m, const double* d) {
         for (int b = 0; b < nfn; b++)
           for (int k = 0; k < 3; k++)
             Pi += 0.5 * M[a][b] * d[3L * v[a] + i] * Ks[i][k] * d[3L * v[b] + k];
+      }
+  }
+  /* Newmark step functional: + 2/dt^2 (d - dhat)^T M (d - dhat) + 1/dt (d - dtil)^T C (d - dtil)
+   * (its gradient is the step's M a + C v); the follower pressure has no potential */
+  if (m->dyn) {
+    double cm = 2.0 / (m->dt * m->dt), cc = 1.0 / m->dt;
+    for (int a = 0; a < m->nn; a++)
+      for (int k = m->row_ptr[a]; k < m->row_ptr[a + 1]; k++) {
+        int b = m->col[k];
+        for (int i = 0; i < 3; i++) {
+          Pi += cm * (d[3L * a + i] - m->dhat[3L * a + i]) * m->Mm[k] * (d[3L * b + i] - m->dhat[3L * b + i]);
+          for (int j = 0; j < 3; j++)
+            Pi += cc * (d[3L * a + i] - m->dtil[3L * a + i]) * m->Cd[9L * k + 3 * i + j] *
+                  (d[3L * b + j] - m->dtil[3L * b + j]);
+        }
       }
   }
   return Pi;
@@ -1509,6 +1773,27 @@ void om_tangent(om_mesh* m, const double* d) {
         for (int i = 0; i < 3; i++)
           for (int kk = 0; kk < 3; kk++) m->K[9 * k + 3 * i + kk] += M[a][b] * Ks[i][kk];
       }
+  }
+  /* follower pressure (not symmetric) */
+  for (int f = 0; f < m->nf; f++) {
+    if (m->fkind[f] != 3) continue;
+    double rf[6][3], Kf[6][6][3][3];
+    int nfn = follower_terms(m, f, d, rf, Kf);
+    const int* v = m->fnodes + 6 * f;
+    for (int a = 0; a < nfn; a++)
+      for (int b = 0; b < nfn; b++) {
+        long k = find_block(m->row_ptr, m->col, v[a], v[b]);
+        for (int i = 0; i < 3; i++)
+          for (int kk = 0; kk < 3; kk++) m->K[9 * k + 3 * i + kk] += Kf[a][b][i][kk];
+      }
+  }
+  /* inertia and dashpots of the Newmark step: + 4/dt^2 M + 2/dt C */
+  if (m->dyn) {
+    double cm = 4.0 / (m->dt * m->dt), cc = 2.0 / m->dt;
+    for (long k = 0; k < m->nnzb; k++)
+      for (int i = 0; i < 3; i++)
+        for (int kk = 0; kk < 3; kk++)
+          m->K[9 * k + 3 * i + kk] += (i == kk ? cm * m->Mm[k] : 0.0) + cc * m->Cd[9 * k + 3 * i + kk];
   }
   /* Dirichlet: zero rows and columns of prescribed components, unit diagonal */
   for (int a = 0; a < m->nn; a++)

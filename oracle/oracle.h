@@ -67,6 +67,17 @@ int om_solve(om_mesh* m, int method, double tol, int max_it, double* d, const do
 void om_lbfgs_apply(om_mesh* m, const double* S, const double* Y, const double* rho, int k,
                     const double* q, double* z, int h0);
 
+/* elastodynamics (Newmark average acceleration): rho > 0 and dt > 0 enable
+ * it (mass and dashpot matrices assembled here, state at rest);
+ * om_dynamics_set sets d_n, v_n, a_n (nullable: zero; [3 nn]); after a
+ * converged step om_dynamics_advance(d) moves the state to d;
+ * om_dynamics_get reads v_n, a_n.  Face kinds 3 (follower pressure, data
+ * p) and 4 (dashpots, data c_perp, c_par) join 0-2. */
+void om_set_dynamics(om_mesh* m, double rho, double dt);
+void om_dynamics_set(om_mesh* m, const double* d, const double* v, const double* a);
+void om_dynamics_advance(om_mesh* m, const double* d);
+void om_dynamics_get(const om_mesh* m, double* v, double* a);
+
 /* preconditioner of the displacement block: 0 nodal block-Jacobi, 1 the
  * smoothed-aggregation AMG V-cycle (set up by om_tangent) */
 void om_set_pc(om_mesh* m, int pc_type);

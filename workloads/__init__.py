@@ -31,6 +31,8 @@ MAT_POLYCONVEX = 3
 FACE_TRACTION = 0
 FACE_PRESSURE = 1
 FACE_ROBIN = 2
+FACE_FOLLOWER = 3
+FACE_DASHPOT = 4
 
 _PERMS = list(itertools.permutations(range(3)))  # lexicographic order
 
@@ -205,7 +207,8 @@ def twist(n=32, order=2, mu=1.0, total_angle=math.pi / 2, nsteps=10, pressure=Tr
 def heart(nr=4, nc=80, nl=78, order=1, a_endo=2.0, c_endo=5.0, a_epi=3.0, c_epi=6.0,
           z_base=1.0, apex_hole=0.15, C=0.88, bf=18.5, bt=3.58, bfs=1.63, kappa=1.0e3,
           Ta_peak=60.0, period=0.8, p_endo=2.0, k_perp=20.0, k_par=2.0, nsteps=100,
-          helix_endo_deg=60.0, helix_epi_deg=-60.0):
+          helix_endo_deg=60.0, helix_epi_deg=-60.0, dynamics=False, follower=False,
+          rho=1.05e-4, c_perp=2.0, c_par=0.2):
     """Truncated prolate-ellipsoid shell (cardiac-like test stand-in).
 
     Index space (i transmural 0..nr, j circumferential 0..nc periodic,
@@ -220,6 +223,15 @@ def heart(nr=4, nc=80, nl=78, order=1, a_endo=2.0, c_endo=5.0, a_epi=3.0, c_epi=
     Loads per time step s (t = s*period/nsteps): endocardial pressure
     p_endo*max(sin(2 pi t/period), 0) as the load factor, activation time t.
     Epicardial Robin springs (k_perp, k_par); base and apex opening are free.
+
+    follower=True makes the endocardial pressure a follower load (face kind
+    3) instead of a dead one.  dynamics=True adds the inertia of the
+    momentum equation and the dashpots of the epicardial Robin condition:
+    duplicate epicardial faces of kind 4 with (c_perp, c_par), and the keys
+    rho (density) and dt = period / nsteps of the Newmark steps.  Units are
+    cm, s and kPa: rho = 1.05e-4 kPa s^2 / cm^2 is a tissue density of
+    1050 kg / m^3; (k_perp, k_par) = (20, 2) kPa / cm and (c_perp, c_par) =
+    (2, 0.2) kPa s / cm.
     """
     def geom(e, ph, tt):
         a = a_endo + e * (a_epi - a_endo)
@@ -264,9 +276,16 @@ def heart(nr=4, nc=80, nl=78, order=1, a_endo=2.0, c_endo=5.0, a_epi=3.0, c_epi=
     endo = np.all(iv[bfaces] == 0, axis=1)
     epi = np.all(iv[bfaces] == nr, axis=1)
     faces = np.concatenate([bfaces[endo], bfaces[epi]])
-    face_kind = np.concatenate([np.full(endo.sum(), FACE_PRESSURE), np.full(epi.sum(), FACE_ROBIN)]).astype(np.int32)
+    face_kind = np.concatenate([np.full(endo.sum(), FACE_FOLLOWER if follower else FACE_PRESSURE),
+                                np.full(epi.sum(), FACE_ROBIN)]).astype(np.int32)
     face_data = np.concatenate([np.tile([p_endo, 0.0, 0.0], (endo.sum(), 1)),
                                 np.tile([k_perp, k_par, 0.0], (epi.sum(), 1))])
+    extra = {}
+    if dynamics:
+        faces = np.concatenate([faces, bfaces[epi]])
+        face_kind = np.concatenate([face_kind, np.full(epi.sum(), FACE_DASHPOT, np.int32)])
+        face_data = np.concatenate([face_data, np.tile([c_perp, c_par, 0.0], (epi.sum(), 1))])
+        extra = dict(rho=float(rho), dt=float(period / nsteps))
     material = dict(kind=MAT_GUCCIONE, C=C, bf=bf, bt=bt, bfs=bfs, kappa=kappa,
                     Ta_peak=Ta_peak, period=period)
     steps = []
@@ -274,8 +293,9 @@ def heart(nr=4, nc=80, nl=78, order=1, a_endo=2.0, c_endo=5.0, a_epi=3.0, c_epi=
         t = s * period / nsteps
         steps.append((max(math.sin(2.0 * math.pi * t / period), 0.0), t))
     dir_group = np.zeros(coords.shape[0], dtype=np.uint8)
-    return _workload(f"heart_p{order}_{nr}x{nc}x{nl}", coords, tets, order, 0, dir_group, [],
-                     faces, face_kind, face_data, material, fibers, steps)
+    tag = ("_dyn" if dynamics else "") + ("_follower" if follower else "")
+    return _workload(f"heart_p{order}_{nr}x{nc}x{nl}{tag}", coords, tets, order, 0, dir_group, [],
+                     faces, face_kind, face_data, material, fibers, steps, **extra)
 
 
 def serving_stream(nreq=256, seed=20220311, rate=1.0):
