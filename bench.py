@@ -496,6 +496,45 @@ def method_matrix(m, dev, opts_base, ref, methods=("NK", "iNK", "B", "iB"), prec
     return out
 
 
+def dynamic_cardiac(dev, opts_base, nsteps=10, methods=("iB", "NK")):
+    """The cardiac configuration (4 x 80 x 78 hexes, 149,760 P1 tets) as an
+    elastodynamic heartbeat: inertia, epicardial dashpots and the follower
+    endocardial pressure, nsteps Newmark steps from rest, each step
+    warm-started from the last; per method the median step time, the
+    nonlinear and Krylov iterations, and the final relative residuals.
+    Outside the timed region of the headline line."""
+    import torch
+    import paper_2203_05610_gb300 as fe
+    import workloads as W
+    w = W.heart(dynamics=True, follower=True)
+    m = fe.Mesh(w, device=dev.index or 0)
+    out = dict(workload=w["name"], dofs=m.ndof, rho=w["rho"], dt=w["dt"], steps=nsteps)
+    for meth in methods:
+        m.set_dynamics(w["rho"], w["dt"])
+        d = torch.zeros(m.ndof, dtype=torch.float64, device=dev)
+        times, nits, lits, worst = [], [], [], 0.0
+        ok = True
+        for s in range(nsteps):
+            load, tm = w["steps"][s]
+            m.set_load(load, tm)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            _, st = m.solve(meth, d, tol=TOL, opts=opts_base)
+            m.dynamics_advance(d)
+            torch.cuda.synchronize()
+            times.append(time.perf_counter() - t0)
+            nits.append(st["nit"])
+            lits.append(st["lit_total"])
+            ok = ok and st["status"] == 0
+            if st["r0"] > 0:
+                worst = max(worst, st["rfinal"] / st["r0"])
+        srt = sorted(times)
+        out[meth] = dict(converged_all=ok, step_s_median=round(srt[len(srt) // 2], 4),
+                         steps_per_s=round(nsteps / sum(times), 3), nit=nits, lit=lits, worst_rrel=worst)
+    m.close()
+    return out
+
+
 def main():
     args = parse()
     if args.oracle_sample:
@@ -590,6 +629,10 @@ def main():
                 matrix.update({k + "/block_jacobi": v for k, v in
                                method_matrix(m, dev, dict(base, pc_type="bj"), ref, methods=("iB",),
                                              precisions=("mixed_fp32",)).items()})
+        dyn = None
+        if not args.no_matrix and args.workload == "cook":
+            dyn = dynamic_cardiac(dev, dict(ksp_restart=args.restart, orthog=args.orthog, pc_type=args.pc,
+                                            precision=args.precision))
         pk, src = peaks()
         timed = {k: v for k, v in prof.items() if v["timed"] > 0}
         dom = max(timed, key=lambda k: timed[k]["ms"])
@@ -659,6 +702,8 @@ def main():
             out["method_matrix"] = dict(note="each method in each precision solved once after a warm-up solve, "
                                              "outside the timed region; err_vs_oracle against the FP64 oracle's "
                                              "solution (tests/golden/cook_p2_64x64x8_step1.npz)", results=matrix)
+        if dyn is not None:
+            out["dynamic_cardiac"] = dyn
         if cpu_proc is not None:
             try:
                 line = cpu_proc.communicate(timeout=900)[0].strip().splitlines()[-1]

@@ -95,8 +95,19 @@ typedef enum {
 typedef enum {
   FE_FACE_TRACTION = 0, /* dead traction t = load * data[0..2] per unit reference area */
   FE_FACE_PRESSURE = 1, /* dead pressure: t = -load * data[0] * N (reference outward normal) */
-  FE_FACE_ROBIN = 2     /* springs: t = -(kperp N x N + kpar (I - N x N)) d,
+  FE_FACE_ROBIN = 2,    /* springs: t = -(kperp N x N + kpar (I - N x N)) d,
                            data = {kperp, kpar, 0}; not scaled by load */
+  FE_FACE_FOLLOWER = 3, /* follower pressure: t da = -load * data[0] * n da on the
+                           DEFORMED face (n its outward normal), i.e. nodal forces
+                           load * data[0] * int N_a (x_xi x x_eta) dxi deta over the
+                           reference triangle; its tangent is not symmetric and it
+                           has no potential (fe_energy leaves it out).  The
+                           pressure on the moving endocardium of the paper's
+                           heartbeat test. */
+  FE_FACE_DASHPOT = 4   /* dashpots of the epicardial Robin condition (Eq. "bc epi",
+                           the C terms): t = -(cperp N x N + cpar (I - N x N)) v,
+                           v the velocity of the Newmark step, data = {cperp, cpar, 0};
+                           inactive until fe_set_dynamics turns inertia on */
 } fe_face_kind;
 
 /* ---- mesh description (host data, copied by fe_mesh_create) ------------ */
@@ -176,6 +187,37 @@ int fe_mesh_get_topology(fe_mesh m, int32_t* conn, int32_t* colors,
  * quasi-static problem with time-dependent data; load stepping of the
  * tests. */
 int fe_set_load(fe_mesh m, double load, double time);
+
+/* ---- elastodynamics: Newmark average acceleration ------------------------
+ * The momentum equation with its inertia term (Section "Problem
+ * formulation", Eq. "momentum strong"; the paper keeps unit density and
+ * names no time integrator).  Readings: density rho per unit reference
+ * volume, consistent mass M = rho int N_a N_b I dV, Newmark's average
+ * acceleration rule (beta = 1/4, gamma = 1/2).  With the state d_n, v_n,
+ * a_n, a time step is one nl_solve of
+ *   R(d) + M a(d) + C v(d) = 0,  a(d) = 4/dt^2 (d - dhat),  v(d) = 2/dt (d - dtil),
+ *   dhat = d_n + dt v_n + dt^2/4 a_n,  dtil = d_n + dt/2 v_n,
+ * C the dashpots of the FE_FACE_DASHPOT faces.  The tangent gains
+ * 4/dt^2 M + 2/dt C, fe_energy the step functional
+ * 2/dt^2 (d - dhat)^T M (d - dhat) + 1/dt (d - dtil)^T C (d - dtil).
+ * Prescribed components keep R = 0 as in the static problem.
+ *
+ * fe_set_dynamics: rho > 0 and dt > 0 turn inertia on with the state at
+ *   rest (d_n = v_n = a_n = 0); rho <= 0 or dt <= 0 turns it off.
+ *   FE_ERR_ARG for non-finite values.  The first call allocates 6 vectors
+ *   of 3 nn doubles on the mesh's device (kept until fe_mesh_destroy).
+ * fe_dynamics_set: d_n, v_n, a_n from device arrays of 3 nn doubles (node
+ *   major, the displacement part of a solution vector); NULL = zero.
+ * fe_dynamics_advance: after a converged step with solution d (device,
+ *   [ndof], its displacement part read) moves the state to a_{n+1} = a(d),
+ *   v_{n+1} = v(d), d_{n+1} = d.
+ * fe_dynamics_get: copies v_n and a_n into device arrays of 3 nn doubles
+ *   (NULL skips one).
+ * The last three return FE_ERR_STATE while dynamics is off. */
+int fe_set_dynamics(fe_mesh m, double rho, double dt);
+int fe_dynamics_set(fe_mesh m, const double* d, const double* v, const double* a);
+int fe_dynamics_advance(fe_mesh m, const double* d);
+int fe_dynamics_get(fe_mesh m, double* v, double* a);
 
 /* Write the prescribed Dirichlet values of the current load into d
  * (device, [ndof]); other entries are left unchanged. */

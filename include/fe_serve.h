@@ -6,10 +6,14 @@
  * thread admits queued requests in arrival order as soon as a slot is free
  * and their estimated device footprint fits the HBM budget, and runs every
  * admitted request on its own CUDA stream, so the work of all admitted
- * requests overlaps on the device.  Results are the same as a solve of the
+ * requests overlaps on the device.  Small requests (fe_batch.h) are instead
+ * handed to batcher threads that solve all such requests waiting at that
+ * moment in one launch (one CTA per request), so requests that arrive while
+ * a batch runs form the next one.  Results are the same as a solve of the
  * same request alone (same kernels, same launch shapes, deterministic
- * reductions).  Each request is one call of nl_solve (include/fe.h), i.e.
- * one load step of the paper's quasi-static problem (arxiv 2203.05610,
+ * reductions; a batched request's result does not depend on its batch).
+ * Each request is one call of nl_solve (include/fe.h) or its batched form,
+ * i.e. one load step of the paper's quasi-static problem (arxiv 2203.05610,
  * Section "Numerical solvers"); the serving loop itself has no counterpart
  * in the paper.
  *
@@ -30,7 +34,22 @@ typedef struct {
   int32_t device;      /* CUDA device ordinal */
   int64_t hbm_budget;  /* bytes admitted requests may hold together; 0 = 80% of free memory */
   int32_t max_active;  /* requests solved concurrently (slots); <= 0 means 8 */
+  int64_t batch_max_dofs; /* requests up to this many unknowns that fe_batch_supported
+                             accepts are solved in shared launches (fe_batch.h);
+                             0 = 60000, < 0 = never */
 } fe_server_opts;
+
+/* One entry of the launch-shape autotuner of the batched path: per size
+ * class (order, precision, floor(log2 ndof)) the first batches try 128 and
+ * 256 threads per CTA, each timed per unit of work (sum over the batch's
+ * requests of ndof x (nonlinear + Krylov iterations)); later batches of the
+ * class use the cheaper shape. */
+typedef struct {
+  int32_t order, precision, size_class; /* the class */
+  int32_t threads;                      /* chosen threads per CTA (0: still trying) */
+  int32_t batches[2];                   /* batches timed with 128 and 256 threads */
+  double cost[2];                       /* best seconds per unit of work, 128 and 256 threads (0: none) */
+} fe_tuning_entry;
 
 typedef struct {
   const fe_mesh_desc* mesh; /* copied by serve_submit (device/stream fields ignored) */
@@ -64,6 +83,10 @@ int serve_submit(fe_server s, const fe_request* req, int64_t* id_out);
 /* Status of a request; wait = 1 blocks until it is DONE or FAILED.  d_out
  * (host [ndof], nullable) receives the solution once DONE. */
 int serve_poll(fe_server s, int64_t id, int wait, fe_request_status* status, double* d_out);
+
+/* The autotuner's table: up to cap entries into out (host); returns the
+ * number of classes seen (may exceed cap). */
+int serve_tuning(fe_server s, fe_tuning_entry* out, int cap);
 
 /* Seconds on the server's steady clock (the clock of t_submit etc.). */
 double serve_clock(fe_server s);

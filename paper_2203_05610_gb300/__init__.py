@@ -78,6 +78,16 @@ class nl_stats(C.Structure):
                 ("eta_hist", C.c_double * NL_HIST), ("lres_hist", C.c_double * NL_HIST)]
 
 
+BATCH_HIST = 64  # FE_BATCH_HIST of include/fe_batch.h
+
+
+class fe_batch_out(C.Structure):
+    _fields_ = [("status", C.c_int32), ("nit", C.c_int32), ("assemblies", C.c_int32), ("hist_len", C.c_int32),
+                ("lit_total", C.c_int64), ("r0", C.c_double), ("rfinal", C.c_double),
+                ("res_hist", C.c_double * BATCH_HIST), ("lit_hist", C.c_int32 * BATCH_HIST),
+                ("eta_hist", C.c_double * BATCH_HIST)]
+
+
 PROF_CLASSES = ["residual", "tangent", "spmv", "pc", "arnoldi", "twoloop", "vector", "other"]
 
 
@@ -87,7 +97,13 @@ class fe_profile_info(C.Structure):
 
 
 class fe_server_opts(C.Structure):
-    _fields_ = [("device", C.c_int32), ("hbm_budget", C.c_int64), ("max_active", C.c_int32)]
+    _fields_ = [("device", C.c_int32), ("hbm_budget", C.c_int64), ("max_active", C.c_int32),
+                ("batch_max_dofs", C.c_int64)]
+
+
+class fe_tuning_entry(C.Structure):
+    _fields_ = [("order", C.c_int32), ("precision", C.c_int32), ("size_class", C.c_int32), ("threads", C.c_int32),
+                ("batches", C.c_int32 * 2), ("cost", C.c_double * 2)]
 
 
 class fe_request(C.Structure):
@@ -132,11 +148,18 @@ SIGNATURES = {
     "serve_submit": (_I, [_P, C.POINTER(fe_request), C.POINTER(C.c_int64)]),
     "serve_poll": (_I, [_P, C.c_int64, _I, C.POINTER(fe_request_status), _P]),
     "serve_clock": (_D, [_P]),
+    "serve_tuning": (_I, [_P, _P, _I]),
     "serve_destroy": (_I, [_P]),
     "fe_set_pc": (_I, [_P, _I]),
     "fe_amg_levels": (_I, [_P]),
     "fe_amg_get_level": (_I, [_P, _I, _P, C.POINTER(C.c_double), _P, _P, _P, _P, _P, _P, _P, _P]),
     "fe_set_wait_limit": (_I, [_P, C.c_int64]),
+    "fe_batch_supported": (_I, [_P, _I, C.POINTER(nl_opts)]),
+    "fe_batch_solve": (_I, [_I, _P, _P, _P, _P, _P, _P, _I, _P]),
+    "fe_set_dynamics": (_I, [_P, _D, _D]),
+    "fe_dynamics_set": (_I, [_P, _P, _P, _P]),
+    "fe_dynamics_advance": (_I, [_P, _P]),
+    "fe_dynamics_get": (_I, [_P, _P, _P]),
     "fe_last_error": (C.c_char_p, []),
 }
 
@@ -372,6 +395,28 @@ class Mesh:
             out.append(d)
         return out
 
+    def set_dynamics(self, rho, dt):
+        """Newmark elastodynamics with density rho and step dt, state at rest
+        (rho <= 0: static again)."""
+        _check(lib().fe_set_dynamics(self.h, float(rho), float(dt)))
+
+    def dynamics_set(self, d=None, v=None, a=None):
+        """State d_n, v_n, a_n: CUDA float64 tensors of 3 nn entries (None: zero)."""
+        ptrs = [None if t is None else _dev_ptr(t, 3 * self.nn, nm) for t, nm in ((d, "d"), (v, "v"), (a, "a"))]
+        _check(lib().fe_dynamics_set(self.h, *ptrs))
+
+    def dynamics_advance(self, d):
+        """Move the state to the converged step solution d ([ndof])."""
+        _check(lib().fe_dynamics_advance(self.h, self._vec(d, "d")))
+
+    def dynamics_get(self):
+        """(v_n, a_n) as CUDA float64 tensors of 3 nn entries."""
+        import torch
+        v = torch.zeros(3 * self.nn, dtype=torch.float64, device=self.device)
+        a = torch.zeros_like(v)
+        _check(lib().fe_dynamics_get(self.h, _dev_ptr(v, 3 * self.nn, "v"), _dev_ptr(a, 3 * self.nn, "a")))
+        return v, a
+
     def set_wait_limit(self, polls=-1):
         """Polls before a bounded device wait gives up (< 0: the default)."""
         _check(lib().fe_set_wait_limit(self.h, int(polls)))
@@ -401,6 +446,40 @@ class Mesh:
         return d, stats
 
 
+def batch_supported(mesh, method, opts):
+    """True when the request can run in fe_batch_solve."""
+    mth = METHODS[method] if isinstance(method, str) else int(method)
+    o = _opts_struct(mth, opts)
+    return bool(lib().fe_batch_supported(mesh.h, mth, C.byref(o)))
+
+
+def batch_solve(meshes, methods, ds, tols, max_its=None, opts=None, threads=256):
+    """Solve len(meshes) requests in one launch (include/fe_batch.h), one
+    CTA per request.  ds: CUDA float64 tensors [ndof], overwritten by the
+    solutions.  opts: one dict (all requests) or a list of dicts.  Returns
+    one stats dict per request."""
+    n = len(meshes)
+    mths = [METHODS[x] if isinstance(x, str) else int(x) for x in methods]
+    if max_its is None:
+        max_its = [50 if x < 2 else 1000 for x in mths]
+    olist = opts if isinstance(opts, (list, tuple)) else [opts] * n
+    O = (nl_opts * n)(*[_opts_struct(mths[i], olist[i]) for i in range(n)])
+    H = (C.c_void_p * n)(*[m.h.value if isinstance(m.h, C.c_void_p) else m.h for m in meshes])
+    D = (C.c_void_p * n)(*[_dev_ptr(ds[i], meshes[i].ndof, "d").value for i in range(n)])
+    M = (C.c_int * n)(*mths)
+    T = (C.c_double * n)(*[float(t) for t in tols])
+    I = (C.c_int * n)(*[int(x) for x in max_its])
+    out = (fe_batch_out * n)()
+    _check(lib().fe_batch_solve(n, H, M, T, I, O, D, int(threads), out))
+    res = []
+    for st in out:
+        k = st.hist_len
+        res.append(dict(status=st.status, nit=st.nit, lit_total=int(st.lit_total), assemblies=st.assemblies,
+                        r0=st.r0, rfinal=st.rfinal, res_hist=np.array(st.res_hist[:k]),
+                        lit_hist=np.array(st.lit_hist[:k]), eta_hist=np.array(st.eta_hist[:k])))
+    return res
+
+
 def _stats_dict(st):
     n = st.hist_len
     return dict(status=st.status, nit=st.nit, lit_total=int(st.lit_total), assemblies=st.assemblies, r0=st.r0,
@@ -412,14 +491,23 @@ def _stats_dict(st):
 class Server:
     """Continuous-batching request loop on one GPU (include/fe_serve.h)."""
 
-    def __init__(self, device=0, hbm_budget=0, max_active=8):
+    def __init__(self, device=0, hbm_budget=0, max_active=8, batch_max_dofs=0):
         import torch
         torch.cuda.init()
-        o = fe_server_opts(device=int(device), hbm_budget=int(hbm_budget), max_active=int(max_active))
+        o = fe_server_opts(device=int(device), hbm_budget=int(hbm_budget), max_active=int(max_active),
+                           batch_max_dofs=int(batch_max_dofs))
         h = C.c_void_p()
         _check(lib().serve_create(C.byref(o), C.byref(h)))
         self.h = h
         self._ndof = {}
+
+    def tuning(self):
+        """The batched path's autotuner table (fe_tuning_entry), one dict per size class."""
+        n = lib().serve_tuning(self.h, None, 0)
+        arr = (fe_tuning_entry * max(n, 1))()
+        n = _check(lib().serve_tuning(self.h, arr, n))
+        return [dict(order=e.order, precision=e.precision, size_class=e.size_class, threads=e.threads,
+                     batches=list(e.batches), cost=list(e.cost)) for e in arr[:n]]
 
     def submit(self, w, method, tol=1e-8, max_it=None, opts=None, load=1.0, time=0.0, d0=None):
         mth = METHODS[method] if isinstance(method, str) else int(method)

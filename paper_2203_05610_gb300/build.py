@@ -12,7 +12,8 @@ SO = os.path.join(LIBDIR, "libfe.so")
 # the FE_DEBUG_BOUNDS build: kernels check their indirect indices (see fe_idx)
 SO_DEBUG = os.path.join(LIBDIR, "dbg", "libfe_dbg.so")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
-SOURCES = ["fe_mesh.cu", "fe_assemble.cu", "fe_krylov.cu", "nl_solve.cu", "fe_amg.cu", "fe_noalloc.cu", "fe_serve.cu"]
+SOURCES = ["fe_mesh.cu", "fe_assemble.cu", "fe_krylov.cu", "nl_solve.cu", "fe_amg.cu", "fe_noalloc.cu", "fe_serve.cu",
+           "fe_batch.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-I", INCLUDE, "-I", CSRC]

@@ -32,8 +32,10 @@
 // inverses, power iterations, P, A P, P^T A P and the coarsest inverse,
 // each output entry computed by one thread from a fixed gather list (no
 // atomics: deterministic, and the same summation order as a plain loop).
-// The numbers are formed in FP64; the V-cycle runs in the tangent's
-// precision (FP32 values, vectors and accumulation in the mixed forms).  A
+// The numbers are formed in FP64 for an FP64 tangent and in FP32 for the
+// mixed forms (GB300's FP32 rate is tens of times its FP64 rate); the
+// V-cycle runs in the tangent's precision (FP32 values, vectors and
+// accumulation in the mixed forms), the coarsest inverse is formed in FP64.  A
 // Chebyshev step is one fused kernel: the SpMV with A_l, the residual update,
 // the block-Jacobi product and the direction and iterate updates of its
 // rows (r stays b - A x throughout, so the residual for the restriction

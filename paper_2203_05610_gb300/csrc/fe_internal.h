@@ -56,6 +56,7 @@ int fe_dbg_bounds_mesh(void);
 int fe_dbg_bounds_assemble(void);
 int fe_dbg_bounds_krylov(void);
 int fe_dbg_bounds_amg(void);
+int fe_dbg_bounds_batch(void);
 #else
 __device__ __forceinline__ int fe_idx(int i, int64_t) { return i; }
 #define FE_DBG_BOUNDS_READER(name)
@@ -125,6 +126,28 @@ struct fe_mesh_s {
   int* ks_col = nullptr;
   double* ks_val = nullptr;  // [nnz_ks][9]
   int* ks_kpos = nullptr;    // [nnz_ks] block index in the tangent pattern
+  // The face pattern (ks_*) covers the node pairs of every face of kind 2
+  // (springs), 3 (follower pressure) and 4 (dashpots).  ks_val holds the
+  // springs, plus 2/dt times the dashpots while dynamics is on; the host
+  // keeps both parts to rebuild it when dt changes.
+  std::vector<double> h_ks_spring, h_ks_dashpot;  // [nnz_ks][9] each
+  bool has_dashpots = false;
+  double* kc_val = nullptr;  // [nnz_ks][9] the dashpots alone (device, while dynamics is on)
+  // follower pressure faces (kind 3), evaluated on the deformed surface
+  int nff = 0;
+  int* ff_nodes = nullptr;   // [nff][6] face nodes (vertices, then P2 edge nodes (0,1), (1,2), (2,0))
+  double* ff_p = nullptr;    // [nff] pressure at load factor 1
+  int* fn_ptr = nullptr;     // [nn+1] node -> its (follower face, local node) slots
+  int* fn_list = nullptr;    // face * 8 + local node
+  int* fk_ptr = nullptr;     // [nnz_ks+1] face-pattern entry -> its follower blocks
+  int* fk_list = nullptr;    // face * 64 + a * 8 + b (block (a, b) of that face)
+
+  // Newmark average-acceleration state (fe_set_dynamics); dyn == nullptr: static
+  double dyn_rho = 0.0, dyn_dt = 0.0;
+  double mass_c = 0.0;       // 4 rho / dt^2: the inertia weight of the step
+  double dyn_const = 0.0;    // constant of the step functional (energy only)
+  double* dyn = nullptr;     // [6][3 nn]: d_n, v_n, a_n, dhat, dtil, fdyn = 4/dt^2 M dhat + 2/dt C dtil
+  double* dyn_keep = nullptr;  // the state storage, kept while dynamics is off
 
   // tangent and preconditioner
   int prec = -1;             // precision of the assembled tangent (-1 none)
@@ -210,6 +233,31 @@ constexpr int BAR_WORDS = 64;    // u32 words of the grid reduction state
 __host__ __device__ __forceinline__ int64_t kv_index(int64_t p, int c) { return (p >> 5) * 288 + 32 * c + (p & 31); }
 inline size_t kv_count(int64_t nnzb) { return (size_t)((nnzb + 31) / 32) * 288; }
 
+// Consistent mass of one tet: int_T N_a N_b dV = V * mass_hat(order, a, b)
+// (local nodes: vertices 0..3, then the P2 edge nodes (0,1), (0,2), (0,3),
+// (1,2), (1,3), (2,3)).  Closed forms from int_T l1^i l2^j l3^k l4^l dV =
+// 6 V i! j! k! l! / (i + j + k + l + 3)!: P1 (1 + delta_ab) / 20; P2 over
+// 420: vertex-vertex 6 (a = b) or 1, vertex-edge -4 (the vertex is an end
+// of the edge) or -6, edge-edge 32 (a = b), 16 (one shared vertex) or 8.
+__host__ __device__ __forceinline__ double mass_hat(int order, int a, int b) {
+  if (order == 1) return a == b ? 0.1 : 0.05;
+  // end vertices of edge k, packed one per nibble: (0,1) (0,2) (0,3) (1,2) (1,3) (2,3)
+  auto e0 = [](int k) { return (0x211000 >> (4 * k)) & 15; };
+  auto e1 = [](int k) { return (0x332321 >> (4 * k)) & 15; };
+  double c;
+  if (a < 4 && b < 4) {
+    c = a == b ? 6.0 : 1.0;
+  } else if (a >= 4 && b >= 4) {
+    int p = a - 4, q = b - 4;
+    int shared = (e0(p) == e0(q)) + (e0(p) == e1(q)) + (e1(p) == e0(q)) + (e1(p) == e1(q));
+    c = p == q ? 32.0 : (shared ? 16.0 : 8.0);
+  } else {
+    int v = a < 4 ? a : b, ed = (a < 4 ? b : a) - 4;
+    c = (e0(ed) == v || e1(ed) == v) ? -4.0 : -6.0;
+  }
+  return c / 420.0;
+}
+
 // Counts one kernel launch of class `cls` and, with timing on, brackets it
 // with events on the mesh stream: open the scope, launch, close the scope.
 struct LaunchScope {
@@ -268,6 +316,9 @@ int fe_spmv_preload(fe_mesh m);  // loads every SpMV kernel and caches its launc
 int fe_amg_setup(fe_mesh m);
 int fe_amg_apply(fe_mesh m, const double* x, void* z, bool z_double);
 void fe_amg_free(fe_mesh m);
+// fe_assemble.cu: uploads the face-pattern values (springs plus 2/dt times
+// the dashpots while dynamics is on)
+int fe_upload_face_values(fe_mesh m);
 // fe_noalloc.cu: resolves the fixed array of fe_spmv_noalloc on the mesh's
 // device and loads the kernels that entry point launches (called by
 // fe_mesh_create with the mesh's device current)

@@ -110,7 +110,8 @@ int fe_check_device_error(fe_mesh m) {
   FE_CUDA(cudaMemcpyAsync(&h, m->err, sizeof(int), cudaMemcpyDeviceToHost, m->stream));
   FE_CUDA(cudaStreamSynchronize(m->stream));
 #ifdef FE_DEBUG_BOUNDS
-  if (h == DEV_OK && (fe_dbg_bounds_mesh() | fe_dbg_bounds_assemble() | fe_dbg_bounds_krylov() | fe_dbg_bounds_amg()))
+  if (h == DEV_OK && (fe_dbg_bounds_mesh() | fe_dbg_bounds_assemble() | fe_dbg_bounds_krylov() | fe_dbg_bounds_amg() |
+                        fe_dbg_bounds_batch()))
     h = DEV_ERR_BOUNDS;
 #endif
   if (h == DEV_OK) return FE_OK;
@@ -414,7 +415,9 @@ static int validate(const fe_mesh_desc* d) {
   for (int64_t i = 0; i < 3LL * d->nf; i++)
     if (d->faces[i] < 0 || d->faces[i] >= d->nv) return fe_set_error("face vertex id out of range"), FE_ERR_ARG;
   for (int i = 0; i < d->nf; i++)
-    if (d->face_kind[i] < 0 || d->face_kind[i] > 2) return fe_set_error("bad face kind"), FE_ERR_ARG;
+    if (d->face_kind[i] < 0 || d->face_kind[i] > 4) return fe_set_error("bad face kind"), FE_ERR_ARG;
+  for (int64_t i = 0; i < 3LL * d->nf; i++)
+    if (!std::isfinite(d->face_data[i])) return fe_set_error("face data must be finite"), FE_ERR_ARG;
   if (d->dir_group)
     for (int i = 0; i < d->nv; i++)
       if (d->dir_group[i] > d->ngroups) return fe_set_error("dir_group id beyond ngroups"), FE_ERR_ARG;
@@ -466,6 +469,7 @@ static int create_impl(const fe_mesh_desc* desc, fe_mesh m) {
   auto edge_id = [&](int a, int b) -> int {
     uint64_t key = ((uint64_t)std::min(a, b) << 32) | (uint64_t)std::max(a, b);
     auto it = std::lower_bound(ekeys.begin(), ekeys.end(), key);
+    if (it == ekeys.end() || *it != key) return -1;  // not an edge of the mesh
     return nv + (int)(it - ekeys.begin());
   };
   const int nn = nv + (int)ekeys.size();
@@ -560,8 +564,16 @@ static int create_impl(const fe_mesh_desc* desc, fe_mesh m) {
   //   int phi_edge = A/3, M = A/180 [6 on vertex diagonal, -1 vertex-vertex,
   //   -4 vertex-opposite edge, 0 vertex-adjacent edge, 32 edge diagonal,
   //   16 edge-edge]
+  // Face pattern: node pairs of the faces of kinds 2 (springs), 3 (follower
+  // pressure) and 4 (dashpots); springs and dashpots keep separate values.
+  struct FaceBlock {
+    std::array<double, 9> spring{}, dashpot{};
+    std::vector<int> follower;  // face * 64 + a * 8 + b
+  };
   std::vector<double> fext((size_t)nn * 3, 0.0);
-  std::map<std::pair<int, int>, std::array<double, 9>> springs;
+  std::map<std::pair<int, int>, FaceBlock> fpat;
+  std::vector<int> ff_nodes, fn_count(nn, 0);
+  std::vector<double> ff_p;
   for (int f = 0; f < desc->nf; f++) {
     const int* v = desc->faces + 3 * f;
     const double* x0 = desc->coords + 3 * (size_t)v[0];
@@ -571,13 +583,17 @@ static int create_impl(const fe_mesh_desc* desc, fe_mesh m) {
     double b[3] = {x2[0] - x0[0], x2[1] - x0[1], x2[2] - x0[2]};
     double n[3] = {a[1] * b[2] - a[2] * b[1], a[2] * b[0] - a[0] * b[2], a[0] * b[1] - a[1] * b[0]};
     double ln = sqrt(n[0] * n[0] + n[1] * n[1] + n[2] * n[2]);
+    if (!(ln > 0.0)) return fe_set_error("face %d is degenerate", f), FE_ERR_ARG;
     double A = 0.5 * ln;
     double N[3] = {n[0] / ln, n[1] / ln, n[2] / ln};
     int nodes[6];
     int nfn = m->order == 1 ? 3 : 6;
     for (int k = 0; k < 3; k++) nodes[k] = v[k];
     if (m->order == 2)
-      for (int k = 0; k < 3; k++) nodes[3 + k] = edge_id(v[k], v[(k + 1) % 3]);
+      for (int k = 0; k < 3; k++) {
+        nodes[3 + k] = edge_id(v[k], v[(k + 1) % 3]);
+        if (nodes[3 + k] < 0) return fe_set_error("face %d is not a face of the mesh", f), FE_ERR_ARG;
+      }
     double intphi[6], M[6][6];
     for (int p = 0; p < nfn; p++)
       for (int q = 0; q < nfn; q++) {
@@ -602,34 +618,60 @@ static int create_impl(const fe_mesh_desc* desc, fe_mesh m) {
       for (int i = 0; i < 3; i++) t[i] = kind == FE_FACE_TRACTION ? fd[i] : -fd[0] * N[i];
       for (int p = 0; p < nfn; p++)
         for (int i = 0; i < 3; i++) fext[3 * (size_t)nodes[p] + i] += t[i] * intphi[p];
-    } else {
+    } else if (kind == FE_FACE_FOLLOWER) {
+      int ff = (int)ff_p.size();
+      ff_p.push_back(fd[0]);
+      for (int p = 0; p < 6; p++) ff_nodes.push_back(p < nfn ? nodes[p] : nodes[0]);
+      for (int p = 0; p < nfn; p++) {
+        fn_count[nodes[p]]++;
+        for (int q = 0; q < nfn; q++) fpat[{nodes[p], nodes[q]}].follower.push_back(ff * 64 + p * 8 + q);
+      }
+    } else {  // springs or dashpots: (c_perp N x N + c_par (I - N x N)) times the face mass
       double Ks[9];
       for (int i = 0; i < 3; i++)
         for (int k = 0; k < 3; k++) Ks[3 * i + k] = fd[0] * N[i] * N[k] + fd[1] * ((i == k) - N[i] * N[k]);
       for (int p = 0; p < nfn; p++)
         for (int q = 0; q < nfn; q++) {
-          auto& blk = springs[{nodes[p], nodes[q]}];
+          FaceBlock& fb = fpat[{nodes[p], nodes[q]}];
+          auto& blk = kind == FE_FACE_ROBIN ? fb.spring : fb.dashpot;
           for (int k = 0; k < 9; k++) blk[k] += M[p][q] * Ks[k];
         }
+      if (kind == FE_FACE_DASHPOT) m->has_dashpots = true;
     }
   }
-  std::vector<int> ks_ptr(nn + 1, 0), ks_col, ks_kpos;
-  std::vector<double> ks_val;
-  for (auto& kv : springs) {
+  std::vector<int> ks_ptr(nn + 1, 0), ks_col, ks_kpos, fk_ptr(1, 0), fk_list;
+  for (auto& kv : fpat) {
     ks_ptr[kv.first.first + 1]++;
     ks_col.push_back(kv.first.second);
-    ks_val.insert(ks_val.end(), kv.second.begin(), kv.second.end());
+    m->h_ks_spring.insert(m->h_ks_spring.end(), kv.second.spring.begin(), kv.second.spring.end());
+    m->h_ks_dashpot.insert(m->h_ks_dashpot.end(), kv.second.dashpot.begin(), kv.second.dashpot.end());
+    fk_list.insert(fk_list.end(), kv.second.follower.begin(), kv.second.follower.end());
+    fk_ptr.push_back((int)fk_list.size());
     int a = kv.first.first, b = kv.first.second;
     ks_kpos.push_back((int)(std::lower_bound(col.begin() + row_ptr[a], col.begin() + row_ptr[a + 1], b) - col.begin()));
   }
   for (int a = 0; a < nn; a++) ks_ptr[a + 1] += ks_ptr[a];
   m->nnz_ks = (int64_t)ks_col.size();
+  m->nff = (int)ff_p.size();
+  std::vector<int> fn_ptr(nn + 1, 0), fn_list;
+  if (m->nff) {  // node -> (follower face, local node), faces in order
+    for (int a = 0; a < nn; a++) fn_ptr[a + 1] = fn_ptr[a] + fn_count[a];
+    fn_list.resize(fn_ptr[nn]);
+    std::vector<int> fill(fn_ptr.begin(), fn_ptr.end() - 1);
+    int nfn = m->order == 1 ? 3 : 6;
+    for (int ff = 0; ff < m->nff; ff++)
+      for (int p = 0; p < nfn; p++) fn_list[fill[ff_nodes[6 * ff + p]]++] = ff * 8 + p;
+  }
 
   // ---- uploads
   FE_TRY(upload(m, &m->X, X));
   FE_TRY(upload(m, &m->conn, conn));
   FE_TRY(upload(m, &m->row_ptr, row_ptr));
-  FE_TRY(upload(m, &m->col, col));
+  {  // column indices padded to whole 32-block tiles: the SpMV copies them tile by tile
+    std::vector<int> colp(col);
+    colp.resize((col.size() + 31) / 32 * 32, 0);
+    FE_TRY(upload(m, &m->col, colp));
+  }
   FE_TRY(upload(m, &m->diag_pos, diag));
   FE_TRY(upload(m, &m->dgroup, dgroup));
   FE_TRY(upload(m, &m->fixmask, fixmask));
@@ -639,8 +681,16 @@ static int create_impl(const fe_mesh_desc* desc, fe_mesh m) {
   FE_TRY(upload(m, &m->fext1, fext));
   FE_TRY(upload(m, &m->ks_ptr, ks_ptr));
   FE_TRY(upload(m, &m->ks_col, ks_col));
-  FE_TRY(upload(m, &m->ks_val, ks_val));
+  FE_TRY(fe_upload_face_values(m));
   FE_TRY(upload(m, &m->ks_kpos, ks_kpos));
+  if (m->nff) {
+    FE_TRY(upload(m, &m->ff_nodes, ff_nodes));
+    FE_TRY(upload(m, &m->ff_p, ff_p));
+    FE_TRY(upload(m, &m->fn_ptr, fn_ptr));
+    FE_TRY(upload(m, &m->fn_list, fn_list));
+    FE_TRY(upload(m, &m->fk_ptr, fk_ptr));
+    FE_TRY(upload(m, &m->fk_list, fk_list));
+  }
   if (m->pres) {
     FE_TRY(upload(m, &m->up_ptr, up_ptr));
     FE_TRY(upload(m, &m->up_col, up_col));

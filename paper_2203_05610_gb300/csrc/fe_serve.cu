@@ -7,6 +7,13 @@
 // tangent, Krylov and BFGS workspace, so admitted requests overlap on the
 // device.  A finished request frees its memory and its slot at once, and the
 // scheduler admits the next queued requests that now fit.
+//
+// Small requests that the batched solver supports (fe_batch.h) are handed
+// by their worker, once the mesh is built, to batcher threads: a batcher
+// takes every waiting request of one (order, precision) and solves them in
+// one launch, one CTA each; requests that arrive meanwhile wait for the next
+// launch (continuous batching at launch granularity).  Its launch shape
+// (threads per CTA) comes from a small autotuner per size class.
 #include <algorithm>
 #include <chrono>
 #include <condition_variable>
@@ -19,6 +26,7 @@
 #include <thread>
 #include <vector>
 
+#include "../../include/fe_batch.h"
 #include "../../include/fe_serve.h"
 #include "fe_internal.h"
 
@@ -80,6 +88,31 @@ int64_t estimate_footprint(const Request& r, int64_t* ndof_out) {
   return b + b / 8 + (64 << 20);
 }
 
+// a request waiting for (or in) a batched launch
+struct BatchItem {
+  Request* r = nullptr;
+  fe_mesh m = nullptr;
+  double* d = nullptr;
+  int64_t ndof = 0;
+  bool done = false;
+  int rc = FE_OK;
+  std::string error;
+  fe_batch_out out{};
+};
+
+struct TuneEntry {
+  int batches[2] = {0, 0};
+  double cost[2] = {0.0, 0.0};  // best seconds per unit of work, 128 / 256 threads
+  int chosen = 0;
+};
+
+// size class of the autotuner: (order, precision, floor(log2 ndof))
+int64_t tune_key(int order, int prec, int64_t ndof) {
+  int cls = 0;
+  while ((int64_t(2) << cls) <= ndof) cls++;
+  return ((int64_t)order << 40) | ((int64_t)prec << 32) | cls;
+}
+
 }  // namespace
 
 struct fe_server_s {
@@ -95,6 +128,13 @@ struct fe_server_s {
   std::thread scheduler;
   std::map<int64_t, std::thread> workers;  // running requests' threads, by request id
   std::vector<int64_t> finished;           // workers that have returned, to be joined
+  // batched path
+  int64_t batch_max_dofs = 60000;
+  std::deque<BatchItem*> bq;               // requests waiting for a batched launch
+  std::condition_variable bcv;             // batchers wait here; items are signalled on cv
+  std::vector<std::thread> batchers;
+  std::map<int64_t, TuneEntry> tune;
+  bool stop_batch = false;
   std::chrono::steady_clock::time_point t0 = std::chrono::steady_clock::now();
   double now() const {
     return std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
@@ -140,7 +180,47 @@ static void run_request(fe_server s, Request* r) {
       r->st.t_start = s->now();
       r->st.ndof = ndof;
     }
-    rc = nl_solve(m, r->method, r->tol, r->max_it, d, r->has_opts ? &r->opts : nullptr, &stats);
+    const bool batched = r->has_opts && s->batch_max_dofs > 0 && ndof <= s->batch_max_dofs &&
+                         fe_batch_supported(m, r->method, &r->opts);
+    if (batched) {
+      BatchItem item;
+      item.r = r;
+      item.m = m;
+      item.d = d;
+      item.ndof = ndof;
+      if (cudaStreamSynchronize(stream) != cudaSuccess) {  // the initial guess is in place
+        rc = FE_ERR_CUDA;
+        fe_set_error("initial guess copy failed");
+      } else {
+        std::unique_lock<std::mutex> lk(s->mu);
+        s->bq.push_back(&item);
+        s->bcv.notify_one();
+        s->cv.wait(lk, [&] { return item.done; });
+        rc = item.rc;
+        if (rc < 0) fe_set_error("%s", item.error.c_str());
+      }
+      if (rc >= 0) {  // the batched solver's record in nl_solve's form
+        const fe_batch_out& o = item.out;
+        stats.status = o.status;
+        stats.nit = o.nit;
+        stats.lit_total = o.lit_total;
+        stats.assemblies = o.assemblies;
+        stats.r0 = o.r0;
+        stats.rfinal = o.rfinal;
+        stats.hist_len = std::min(o.hist_len, (int32_t)FE_BATCH_HIST);
+        for (int k = 0; k < stats.hist_len; k++) {
+          stats.res_hist[k] = o.res_hist[k];
+          stats.lit_hist[k] = o.lit_hist[k];
+          stats.eta_hist[k] = o.eta_hist[k];
+        }
+        {
+          std::lock_guard<std::mutex> lk(s->mu);
+          stats.time_s = s->now() - r->st.t_start;
+        }
+      }
+    } else {
+      rc = nl_solve(m, r->method, r->tol, r->max_it, d, r->has_opts ? &r->opts : nullptr, &stats);
+    }
     if (rc >= 0) {
       out.resize(ndof);
       if (cudaMemcpyAsync(out.data(), d, ndof * sizeof(double), cudaMemcpyDeviceToHost, stream) != cudaSuccess ||
@@ -186,6 +266,74 @@ static void join_finished(fe_server s, std::unique_lock<std::mutex>& lk) {
   lk.lock();
 }
 
+// Batcher thread: takes every waiting request of the first waiting
+// request's (order, precision), solves them in one launch with the
+// autotuner's shape, and signals their workers.
+static void batcher_loop(fe_server s) {
+  cudaSetDevice(s->device);
+  std::unique_lock<std::mutex> lk(s->mu);
+  for (;;) {
+    s->bcv.wait(lk, [s] { return s->stop_batch || !s->bq.empty(); });
+    if (s->bq.empty()) break;  // stopping and nothing left
+    const int order = s->bq.front()->m->order;
+    const int prec = s->bq.front()->r->opts.precision;
+    std::vector<BatchItem*> take;
+    for (auto it = s->bq.begin(); it != s->bq.end();) {
+      if ((*it)->m->order == order && (*it)->r->opts.precision == prec) {
+        take.push_back(*it);
+        it = s->bq.erase(it);
+      } else {
+        ++it;
+      }
+    }
+    // launch shape: the class of the largest request decides
+    int64_t nmax = 0;
+    for (BatchItem* b : take) nmax = std::max(nmax, b->ndof);
+    const int64_t key = tune_key(order, prec, nmax);
+    TuneEntry& te = s->tune[key];
+    int slot = te.chosen ? (te.chosen == 128 ? 0 : 1) : (te.batches[0] <= te.batches[1] ? 0 : 1);
+    const int threads = slot == 0 ? 128 : 256;
+    lk.unlock();
+    const size_t n = take.size();
+    std::vector<fe_mesh> meshes(n);
+    std::vector<int> methods(n), max_its(n);
+    std::vector<double> tols(n);
+    std::vector<nl_opts> opts(n);
+    std::vector<double*> ds(n);
+    std::vector<fe_batch_out> outs(n);
+    for (size_t i = 0; i < n; i++) {
+      meshes[i] = take[i]->m;
+      methods[i] = take[i]->r->method;
+      max_its[i] = take[i]->r->max_it;
+      tols[i] = take[i]->r->tol;
+      opts[i] = take[i]->r->opts;
+      ds[i] = take[i]->d;
+    }
+    const auto t0 = std::chrono::steady_clock::now();
+    const int rc = fe_batch_solve((int)n, meshes.data(), methods.data(), tols.data(), max_its.data(), opts.data(),
+                                  ds.data(), threads, outs.data());
+    const double dt = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    const std::string err = rc < 0 ? std::string(fe_last_error()) : std::string();
+    lk.lock();
+    if (rc == FE_OK) {  // cost per unit of work: ndof x (nonlinear + Krylov iterations)
+      double work = 0.0;
+      for (size_t i = 0; i < n; i++) work += (double)take[i]->ndof * (double)(outs[i].nit + outs[i].lit_total + 1);
+      const double c = dt / std::max(work, 1.0);
+      TuneEntry& t2 = s->tune[key];
+      t2.batches[slot]++;
+      if (t2.cost[slot] == 0.0 || c < t2.cost[slot]) t2.cost[slot] = c;
+      if (!t2.chosen && t2.batches[0] > 0 && t2.batches[1] > 0) t2.chosen = t2.cost[0] <= t2.cost[1] ? 128 : 256;
+    }
+    for (size_t i = 0; i < n; i++) {
+      take[i]->rc = rc < 0 ? rc : outs[i].status;
+      take[i]->out = outs[i];
+      take[i]->error = err;
+      take[i]->done = true;
+    }
+    s->cv.notify_all();
+  }
+}
+
 static void scheduler_loop(fe_server s) {
   std::unique_lock<std::mutex> lk(s->mu);
   for (;;) {
@@ -229,7 +377,9 @@ extern "C" int serve_create(const fe_server_opts* opts, fe_server* out) {
   s->device = opts->device;
   s->budget = opts->hbm_budget > 0 ? opts->hbm_budget : (int64_t)(0.8 * (double)free_b);
   s->max_active = opts->max_active > 0 ? opts->max_active : 8;
+  s->batch_max_dofs = opts->batch_max_dofs == 0 ? 60000 : opts->batch_max_dofs;
   s->scheduler = std::thread(scheduler_loop, s);
+  for (int i = 0; i < 2; i++) s->batchers.emplace_back(batcher_loop, s);
   *out = s;
   return FE_OK;
 }
@@ -304,6 +454,27 @@ extern "C" int serve_poll(fe_server s, int64_t id, int wait, fe_request_status* 
   return FE_OK;
 }
 
+extern "C" int serve_tuning(fe_server s, fe_tuning_entry* out, int cap) {
+  if (!s) return fe_set_error("NULL server"), FE_ERR_ARG;
+  std::lock_guard<std::mutex> lk(s->mu);
+  int i = 0;
+  for (const auto& kv : s->tune) {
+    if (out && i < cap) {
+      fe_tuning_entry& e = out[i];
+      e.order = (int32_t)(kv.first >> 40);
+      e.precision = (int32_t)((kv.first >> 32) & 0xff);
+      e.size_class = (int32_t)(kv.first & 0xffffffff);
+      e.threads = kv.second.chosen;
+      e.batches[0] = kv.second.batches[0];
+      e.batches[1] = kv.second.batches[1];
+      e.cost[0] = kv.second.cost[0];
+      e.cost[1] = kv.second.cost[1];
+    }
+    i++;
+  }
+  return i;
+}
+
 extern "C" double serve_clock(fe_server s) { return s ? s->now() : 0.0; }
 
 extern "C" int serve_destroy(fe_server s) {
@@ -315,6 +486,12 @@ extern "C" int serve_destroy(fe_server s) {
   s->cv.notify_all();
   s->scheduler.join();
   for (auto& t : s->workers) t.second.join();
+  {
+    std::lock_guard<std::mutex> lk(s->mu);
+    s->stop_batch = true;
+  }
+  s->bcv.notify_all();
+  for (auto& t : s->batchers) t.join();
   delete s;
   return FE_OK;
 }

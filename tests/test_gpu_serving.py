@@ -73,3 +73,48 @@ def test_admission_rejects_requests_beyond_the_budget(fe):
     r = srv.poll(rid, wait=True)
     srv.close()
     assert r["state"] == "failed" and r["result"] == -2 and "budget" in r["error"]
+
+
+def _small_requests():
+    o64 = dict(precision="fp64", ksp_atol=0.0, ksp_restart=30)
+    o32 = dict(precision="mixed_fp32", ksp_restart=30)
+    return [
+        (W.cook(4, 4, 2, order=1, nu=0.3), "NK", o64, (0.4, 0.0)),
+        (W.cook(3, 3, 1, order=2, nu=0.3), "iB", o32, (0.4, 0.0)),
+        (W.heart(nr=2, nc=8, nl=6), "iNK", o32, (0.2, 0.01)),
+        (W.cook(8, 8, 2, order=1, nu=0.49), "iNK", o32, (0.2, 0.0)),
+        (W.cook(6, 6, 2, order=2, nu=0.3), "NK", o32, (0.2, 0.0)),
+        (W.twist(2, order=2), "iNK", dict(precision="fp64", ksp_restart=30), (0.3, 0.0)),  # u-p: stream path
+    ]
+
+
+def test_small_requests_are_batched_and_match_alone(fe):
+    """Small requests go through shared launches (fe_batch.h); each result is
+    bit-identical to the same request solved alone by the batched solver
+    (whatever launch shape the autotuner gave its batch), and the u-p
+    request, which the batched solver does not take, to its solve alone."""
+    reqs = _small_requests() * 3
+    alone = []
+    for w, meth, opts, (load, tm) in reqs:
+        m = fe.Mesh(w)
+        m.set_load(load, tm)
+        d = m.zeros()
+        if fe.batch_supported(m, meth, opts):
+            st = fe.batch_solve([m], [meth], [d], [1e-8], opts=opts)[0]
+        else:
+            _, st = m.solve(meth, d, tol=1e-8, opts=opts)
+        assert st["status"] == 0, (meth, st["res_hist"][-3:])
+        alone.append(d.cpu().numpy())
+        m.close()
+    srv = fe.Server(max_active=32)
+    ids = [srv.submit(w, meth, tol=1e-8, opts=opts, load=load, time=tm) for w, meth, opts, (load, tm) in reqs]
+    res = [srv.poll(i, wait=True) for i in ids]
+    tune = srv.tuning()
+    srv.close()
+    for r, a, (w, meth, _, _) in zip(res, alone, reqs):
+        assert r["state"] == "done" and r["result"] == 0, (meth, r)
+        if w["pressure_order"] == 0:
+            assert np.array_equal(r["d"], a), (w["name"], meth)
+        else:
+            assert np.abs(r["d"] - a).max() <= 1e-12 * np.abs(a).max()
+    assert tune and sum(sum(e["batches"]) for e in tune) >= 2
