@@ -783,12 +783,19 @@ static void tri_dshape(int order, const double* lam, double dN[6][3]) {
   }
 }
 
-/* follower pressure of face f at displacement d: nodal residual rf (R += rf)
- * and, when Kf != NULL, its derivative Kf[a][b][i][k] = d rf_a,i / d d_b,k */
+/* follower loads of face f at displacement d: nodal residual rf (R += rf)
+ * and, when Kf != NULL, its derivative Kf[a][b][i][k] = d rf_a,i / d d_b,k.
+ * Kind 3, follower pressure: rf_a = p int N_a n with n = x_xi x x_eta.
+ * Kind 5, traction per unit deformed area (the Cook load "in the deformed
+ * configuration"): rf_a = -int N_a t |n|, whose derivative along the
+ * displacement of node b is -int N_a t (x) g_b with g_b = d|n|/d x_b =
+ * Nx_b (x_eta x n/|n|) + Ne_b (n/|n| x x_xi). */
 static int follower_terms(const om_mesh* m, int f, const double* d, double rf[6][3], double Kf[6][6][3][3]) {
   int nfn = m->order == 1 ? 3 : 6;
   const int* v = m->fnodes + 6 * f;
+  const int kind = m->fkind[f];
   double p = m->load * m->fdata[3 * f];
+  double tr[3] = {m->load * m->fdata[3 * f], m->load * m->fdata[3 * f + 1], m->load * m->fdata[3 * f + 2]};
   double x[6][3];
   for (int a = 0; a < nfn; a++)
     for (int i = 0; i < 3; i++) x[a][i] = m->X[3 * v[a] + i] + d[3L * v[a] + i];
@@ -810,6 +817,22 @@ static int follower_terms(const om_mesh* m, int f, const double* d, double rf[6]
       }
     }
     double n[3] = {xs[1] * xe[2] - xs[2] * xe[1], xs[2] * xe[0] - xs[0] * xe[2], xs[0] * xe[1] - xs[1] * xe[0]};
+    if (kind == 5) {
+      double nl = sqrt(n[0] * n[0] + n[1] * n[1] + n[2] * n[2]);
+      double nh[3] = {n[0] / nl, n[1] / nl, n[2] / nl};
+      double wt = 0.5 * w[q]; /* reference triangle area 1/2 */
+      for (int a = 0; a < nfn; a++)
+        for (int i = 0; i < 3; i++) rf[a][i] -= wt * N[a] * tr[i] * nl;
+      if (!Kf) continue;
+      /* x_eta x nh and nh x x_xi */
+      double u1[3] = {xe[1] * nh[2] - xe[2] * nh[1], xe[2] * nh[0] - xe[0] * nh[2], xe[0] * nh[1] - xe[1] * nh[0]};
+      double u2[3] = {nh[1] * xs[2] - nh[2] * xs[1], nh[2] * xs[0] - nh[0] * xs[2], nh[0] * xs[1] - nh[1] * xs[0]};
+      for (int a = 0; a < nfn; a++)
+        for (int b = 0; b < nfn; b++)
+          for (int i = 0; i < 3; i++)
+            for (int k = 0; k < 3; k++) Kf[a][b][i][k] -= wt * N[a] * tr[i] * (Nx[b] * u1[k] + Ne[b] * u2[k]);
+      continue;
+    }
     double wq = 0.5 * w[q] * p; /* reference triangle area 1/2 */
     for (int a = 0; a < nfn; a++)
       for (int i = 0; i < 3; i++) rf[a][i] += wq * N[a] * n[i];
@@ -1025,9 +1048,9 @@ double om_residual(om_mesh* m, const double* d, double* r) {
         r[3L * v[a] + i] += s;
       }
   }
-  /* follower pressure: R += p int N_a n da on the deformed face */
+  /* follower loads: R += p int N_a n da, or R -= int N_a t |n|, on the deformed face */
   for (int f = 0; f < m->nf; f++) {
-    if (m->fkind[f] != 3) continue;
+    if (m->fkind[f] != 3 && m->fkind[f] != 5) continue;
     double rf[6][3];
     int nfn = follower_terms(m, f, d, rf, NULL);
     const int* v = m->fnodes + 6 * f;
@@ -1774,9 +1797,9 @@ void om_tangent(om_mesh* m, const double* d) {
           for (int kk = 0; kk < 3; kk++) m->K[9 * k + 3 * i + kk] += M[a][b] * Ks[i][kk];
       }
   }
-  /* follower pressure (not symmetric) */
+  /* follower loads (not symmetric) */
   for (int f = 0; f < m->nf; f++) {
-    if (m->fkind[f] != 3) continue;
+    if (m->fkind[f] != 3 && m->fkind[f] != 5) continue;
     double rf[6][3], Kf[6][6][3][3];
     int nfn = follower_terms(m, f, d, rf, Kf);
     const int* v = m->fnodes + 6 * f;

@@ -72,7 +72,8 @@ void om_lbfgs_apply(om_mesh* m, const double* S, const double* Y, const double* 
  * om_dynamics_set sets d_n, v_n, a_n (nullable: zero; [3 nn]); after a
  * converged step om_dynamics_advance(d) moves the state to d;
  * om_dynamics_get reads v_n, a_n.  Face kinds 3 (follower pressure, data
- * p) and 4 (dashpots, data c_perp, c_par) join 0-2. */
+ * p), 4 (dashpots, data c_perp, c_par) and 5 (traction t per unit deformed
+ * area, data t) join 0-2. */
 void om_set_dynamics(om_mesh* m, double rho, double dt);
 void om_dynamics_set(om_mesh* m, const double* d, const double* v, const double* a);
 void om_dynamics_advance(om_mesh* m, const double* d);

@@ -428,3 +428,52 @@ def test_newmark_energy_balance_with_dashpots():
     for k in range(len(drops)):
         assert E[k] - E[k + 1] == pytest.approx(drops[k], rel=1e-4)
     assert sum(drops) > 1e-3 * E[0]  # the dashpots really dissipate
+
+
+# ---------------------------------------------------------------- traction per unit deformed area
+def _one_face_box(order, kind, t):
+    """The box with a traction on its x = max face only."""
+    w = box(2, order)
+    bf = W.boundary_faces(w["coords"], w["tets"])
+    c = w["coords"]
+    Xref = c[:, 0] - 0.1 * (c[:, 1] - 0.05 * c[:, 2])  # the unit-cube coordinate before the shear
+    right = bf[np.all(np.isclose(Xref[bf], 1.0), axis=1)]
+    assert len(right) == 8
+    return dict(w, faces=right, face_kind=np.full(len(right), kind, np.int32),
+                face_data=np.tile(np.array(t, float), (len(right), 1)))
+
+
+@pytest.mark.parametrize("order", [1, 2])
+def test_deformed_area_traction(order):
+    """Face kind 5 (traction per unit deformed area): equal to the dead
+    traction at d = 0; under an affine map x = F X its total force is t
+    times the deformed area A |cof(F) N| (Nanson); its tangent matches
+    central differences of the residual and is not symmetric."""
+    t = (0.3, -0.2, 0.5)
+    w5, w0 = _one_face_box(order, 5, t), _one_face_box(order, W.FACE_TRACTION, t)
+    wn = dict(w5, faces=w5["faces"][:0], face_kind=w5["face_kind"][:0], face_data=w5["face_data"][:0])
+    m5, m0, mn = O.Mesh(w5), O.Mesh(w0), O.Mesh(wn)
+    for mm in (m5, m0, mn):
+        mm.set_load(1.0)
+    z = np.zeros(m5.ndof)
+    np.testing.assert_allclose(m5.residual(z)[0], m0.residual(z)[0], rtol=1e-12, atol=1e-15)
+    X = m5.topology()["X"]
+    F = np.array([[1.2, 0.1, 0.05], [-0.1, 0.9, 0.2], [0.0, 0.15, 1.1]])
+    d = ((X @ F.T) - X).ravel()
+    f = (m5.residual(d)[0] - mn.residual(d)[0]).reshape(-1, 3)
+    x = w5["coords"][w5["faces"][0]]
+    nrm = np.cross(x[1] - x[0], x[2] - x[0])
+    N = nrm / np.linalg.norm(nrm)
+    A = sum(0.5 * np.linalg.norm(np.cross(*(w5["coords"][fc][1:] - w5["coords"][fc][0]))) for fc in w5["faces"])
+    cof = np.linalg.det(F) * np.linalg.inv(F).T
+    area = A * np.linalg.norm(cof @ N)
+    np.testing.assert_allclose(f.sum(axis=0), -np.array(t) * area, rtol=1e-12)
+    # tangent of the traction part against central differences
+    d = random_field(m5, w5, 0.05, 9)
+    m5.tangent(d)
+    mn.tangent(d)
+    Kt = oracle_dense_K(m5, w5) - oracle_dense_K(mn, wn)
+    Kfd = fd_jacobian(m5, d) - fd_jacobian(mn, d)
+    assert np.abs(Kt).max() > 1e-3
+    assert np.abs(Kt - Kfd).max() < 1e-7 * np.abs(Kt).max()
+    assert np.abs(Kt - Kt.T).max() > 1e-3 * np.abs(Kt).max()
