@@ -52,7 +52,7 @@ def parse():
     p.add_argument("--precision", default="mixed_fp32", choices=["fp64", "mixed_fp32", "mixed_bf16"])
     p.add_argument("--ib-adaptive", type=int, default=0, choices=[0, 1],
                    help="iB: Eisenstat-Walker type adaptive H0 tolerance (an extension; 0 = the paper's fixed 1e-2)")
-    p.add_argument("--pc", default="amg", choices=["bj", "amg"],
+    p.add_argument("--pc", default="amg", choices=["bj", "amg", "amg_bf16"],
                    help="displacement-block preconditioner: nodal block-Jacobi or the AMG V-cycle")
     p.add_argument("--nu", type=float, default=0.3)
     p.add_argument("--traction", type=float, default=1.0)
@@ -71,7 +71,9 @@ def parse():
     p.add_argument("--serve", type=int, default=0,
                    help="serving mix: number of requests of the seeded Poisson stream (0 = off)")
     p.add_argument("--serve-max-dofs", type=float, default=5e4)
-    p.add_argument("--serve-slots", type=int, default=8)
+    p.add_argument("--serve-slots", type=int, default=64)
+    p.add_argument("--serve-batch-dofs", type=float, default=6e4,
+                   help="serving: requests up to this size run in shared launches (0: never)")
     p.add_argument("--serve-rate", type=float, default=4.0,
                    help="offered load: arrival rate as a multiple of the measured one-at-a-time capacity "
                         "(above 1 the queue fills and the served rate is the server's capacity)")
@@ -220,6 +222,12 @@ ORACLE_SOLUTION = os.path.join(ROOT, "tests", "golden", "cook_p2_64x64x8_step1.n
 SAMPLE_ITS = 2  # nonlinear iterations of the oracle's timed sample
 
 
+def oracle_pc(pc):
+    """The oracle's preconditioner for a GPU preconditioner choice: its AMG
+    is FP64 throughout, the counterpart of both GPU AMG variants."""
+    return "amg" if pc == "amg_bf16" else pc
+
+
 def oracle_work(name, method, restart, pc):
     """The oracle's own full solve of this workload (written by
     tests/golden/oracle_solve_work.py, which calls only the oracle): its
@@ -230,7 +238,7 @@ def oracle_work(name, method, restart, pc):
     except (OSError, ValueError):
         return None
     if (rec.get("workload") != name or rec.get("method") != method or rec.get("ksp_restart") != restart
-            or rec.get("pc") != pc or rec.get("status") != 0):
+            or rec.get("pc") != oracle_pc(pc) or rec.get("status") != 0):
         return None
     return rec
 
@@ -256,7 +264,7 @@ def oracle_sample(w, method, restart, pc):
     m.set_load(load, tm)
     t0 = time.perf_counter()
     _, st = m.solve(method, np.zeros(m.ndof), tol=TOL, max_it=SAMPLE_ITS,
-                    opts=dict(ksp_restart=restart, pc_type={"bj": 0, "amg": 1}[pc]))
+                    opts=dict(ksp_restart=restart, pc_type={"bj": 0, "amg": 1}[oracle_pc(pc)]))
     return dict(time_hist=[float(x) for x in st["time_hist"]], lit=int(st["lit_total"]), nit=int(st["nit"]),
                 wall_s=time.perf_counter() - t0)
 
@@ -268,7 +276,7 @@ def cpu_baseline_from(sample, rec, name, method, pc):
     t_full = scaled_solve_s(sample["time_hist"], rec["lit_hist"], rec["lit_total"])
     th = sample["time_hist"]
     return dict(value=round(1.0 / t_full, 6), unit="solves/s", cores=1, kind="oracle",
-                sample=(f"oracle (plain FP64 C, 1 thread) {method} with the {pc.upper()} preconditioner on {name}, "
+                sample=(f"oracle (plain FP64 C, 1 thread) {method} with the {oracle_pc(pc).upper()} preconditioner on {name}, "
                         f"stopped after its first {SAMPLE_ITS} nonlinear iterations ({th[1]:.1f} s and "
                         f"{th[2]:.1f} s from the start; the first includes the tangent and the preconditioner "
                         f"setup), scaled to a full solve by Krylov work (the oracle's own full solve: {nit} "
@@ -324,13 +332,13 @@ def run_reference(args):
         wc = W.cook(8, 8, 2, order=1, nu=args.nu)
         mc = O.Mesh(wc)
         mc.set_load(wc["steps"][0][0])
-        mc.solve(method, np.zeros(mc.ndof), opts=dict(pc_type={"bj": 0, "amg": 1}[args.pc]))
+        mc.solve(method, np.zeros(mc.ndof), opts=dict(pc_type={"bj": 0, "amg": 1}[oracle_pc(args.pc)]))
     m = O.Mesh(w)
     load, tm = w["steps"][0]
     m.set_load(load, tm)
     d = m.apply_dirichlet(np.zeros(m.ndof))
     r, _ = m.residual(d)
-    m.set_pc(args.pc)
+    m.set_pc(oracle_pc(args.pc))
     t0 = time.perf_counter()
     m.tangent(d)
     t_setup = time.perf_counter() - t0
@@ -345,7 +353,7 @@ def run_reference(args):
         t_wall += t_res + t_kry * REF_KRYLOV_ITS
         t_model += rec["assemblies"] * t_setup + (rec["nit"] + 1) * t_res + rec["lit_total"] * t_kry
     value = args.steps / t_model
-    sample = (f"each step: oracle (plain FP64 C, 1 thread) residual and {REF_KRYLOV_ITS} {args.pc.upper()}-"
+    sample = (f"each step: oracle (plain FP64 C, 1 thread) residual and {REF_KRYLOV_ITS} {oracle_pc(args.pc).upper()}-"
               f"preconditioned GMRES iterations on {name}; solve time = tangent + preconditioner setup "
               f"({t_setup:.1f} s, timed once) + {rec['nit'] + 1} residuals + {rec['lit_total']} Krylov iterations "
               f"(the oracle's own full {method} solve), scaled from these per-part times; the oracle's measured "
@@ -355,7 +363,8 @@ def run_reference(args):
                higher_is_better=True, scaling="weak", vs_baseline=None, dtype="f64", data="synthetic",
                config=dict(workload=name, nu=args.nu, traction=args.traction,
                            load_step=f"step 1 of {len(w['steps'])} from rest", methods=[method],
-                           preconditioner={"bj": "nodal block-Jacobi", "amg": "AMG V-cycle"}[args.pc],
+                           preconditioner={"bj": "nodal block-Jacobi", "amg": "AMG V-cycle",
+                                               "amg_bf16": "AMG V-cycle, BF16 fine-level smoother"}[args.pc],
                            ksp_restart=args.restart, tol=TOL, sample_wall_s_per_step=round(t_wall / args.steps, 1)),
                cpu_baseline=dict(kind="oracle", cores=1, value=round(value, 6), unit="solves/s", sample=sample,
                                  scaled_solve_s=round(t_model / args.steps, 1),
@@ -395,33 +404,40 @@ def serving_workload(req, max_dofs):
 
 def run_serving(args):
     """Serving mix: the seeded Poisson stream served with continuous batching
-    against the same solves one at a time (same precision and options), with
-    arrivals at --serve-rate times the one-at-a-time capacity."""
+    in the mixed form (small requests in shared launches, the rest on their
+    own streams), against the plain FP64 solve of each request one at a time;
+    arrivals at --serve-rate times the one-at-a-time capacity.  Both forms
+    solve to the same relative residual; each served result's difference
+    from the FP64 solution is reported."""
     import numpy as np
     import torch
     import paper_2203_05610_gb300 as fe
     import workloads as W
     reqs = W.serving_stream(nreq=args.serve)
     jobs = [serving_workload(r, args.serve_max_dofs) for r in reqs]
-    sopts = dict(precision=args.serve_precision, ksp_restart=args.restart, orthog=args.orthog)
-    # one at a time, same options (also warms up the library)
-    t_solo, solo_st = [], []
+    base = dict(ksp_restart=args.restart, orthog=args.orthog)
+    bopts = dict(base, precision="fp64")
+    sopts = dict(base, precision=args.serve_precision)
+    # plain FP64 one at a time (also warms up the library)
+    t_solo, solo_st, solo_x = [], [], []
     for w, meth, load, tm, _ in jobs:
         m = fe.Mesh(w)
         m.set_load(load, tm)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        d, st = m.solve(meth, m.zeros(), tol=TOL, opts=sopts)
+        d, st = m.solve(meth, m.zeros(), tol=TOL, opts=bopts)
         torch.cuda.synchronize()
         t_solo.append(time.perf_counter() - t0)
         solo_st.append(st["status"])
+        solo_x.append(d.cpu().numpy())
         m.close()
     solo_ok = sum(1 for x in solo_st if x == 0)
     cap = solo_ok / sum(t_solo)
     # arrivals: the stream's exponential gaps rescaled to rate x capacity
     arr = np.array([r["arrival"] for r in reqs])
     arr = (arr - arr[0]) / (arr[-1] - arr[0] + 1e-12) * (len(jobs) / (args.serve_rate * cap))
-    srv = fe.Server(max_active=args.serve_slots)
+    srv = fe.Server(max_active=args.serve_slots, batch_max_dofs=int(args.serve_batch_dofs) if args.serve_batch_dofs
+                    else -1)
     t0 = srv.clock()
     ids = []
     for (w, meth, load, tm, _), a in zip(jobs, arr):
@@ -429,30 +445,47 @@ def run_serving(args):
             time.sleep(min(0.002, max(0.0, a - (srv.clock() - t0))))
         ids.append(srv.submit(w, meth, tol=TOL, opts=sopts, load=load, time=tm))
     res = [srv.poll(i, wait=True) for i in ids]
+    tune = srv.tuning()
     srv.close()
     done = [r for r in res if r["state"] == "done" and r["result"] == 0]
     span = max(r["t_end"] for r in res) - t0
     lat = np.sort([r["t_end"] - r["t_submit"] for r in done])
     solo = np.sort(t_solo)
-    for (w, meth, load, tm, name), ts, ss, r in zip(jobs, t_solo, solo_st, res):
-        print(json.dumps(dict(request=name, ndof=r["ndof"], solo_s=round(ts, 3), solo_status=int(ss),
+    diffs = []
+    for (w, meth, load, tm, name), ts, ss, xs, r in zip(jobs, t_solo, solo_st, solo_x, res):
+        rd = None
+        if r["state"] == "done" and r["result"] == 0 and ss == 0:
+            rd = float(np.linalg.norm(r["d"] - xs) / max(np.linalg.norm(xs), 1e-300))
+            diffs.append(rd)
+        print(json.dumps(dict(request=name, ndof=r["ndof"], solo_fp64_s=round(ts, 4), solo_status=int(ss),
                               served_state=r["state"], served_result=r["result"],
-                              served_run_s=round(r["t_end"] - r["t_start"], 3),
-                              latency_s=round(r["t_end"] - r["t_submit"], 3))), file=sys.stderr)
+                              served_run_s=round(r["t_end"] - r["t_start"], 4),
+                              latency_s=round(r["t_end"] - r["t_submit"], 4), rel_diff_vs_fp64=rd)),
+              file=sys.stderr)
+    eligible = sum(1 for w, *_ in jobs if w["pressure_order"] == 0) if args.serve_batch_dofs else 0
     out = dict(metric=METRIC, value=round(len(done) / span, 4), unit="solves/s", n_gpus=1, steps=len(jobs),
                warmup=0, ms_per_step=round(1e3 * span / len(jobs), 3), higher_is_better=True, scaling="weak",
-               vs_baseline=None, dtype="f32+f64", data="synthetic",
+               vs_baseline=None, dtype="f32+f64" if args.serve_precision == "mixed_fp32" else "f64",
+               data="synthetic",
                config=dict(workload="serving_mix", requests=len(jobs), seed=20220311,
-                           dofs_range=[1e3, args.serve_max_dofs], slots=args.serve_slots, ksp_restart=args.restart,
+                           dofs_range=[1e3, args.serve_max_dofs], slots=args.serve_slots,
+                           batch_max_dofs=args.serve_batch_dofs, ksp_restart=args.restart,
                            orthog=["mgs", "mgs_lowsync", "mgs_blocked"][args.orthog], method="iNK",
+                           preconditioner="nodal block-Jacobi", tol=TOL,
                            arrival_rate_x_capacity=args.serve_rate, precision=args.serve_precision,
-                           families={n: sum(1 for j in jobs if j[4].startswith(n)) for n in ("cook", "twist", "heart")}),
+                           families={n: sum(1 for j in jobs if j[4].startswith(n)) for n in ("cook", "twist", "heart")},
+                           displacement_form_requests=eligible),
                p50_latency_s=round(float(np.percentile(lat, 50)), 4) if len(lat) else None,
                p99_latency_s=round(float(np.percentile(lat, 99)), 4) if len(lat) else None,
                failed=len(res) - len(done),
-               baseline_one_at_a_time=dict(value=round(cap, 4), unit="solves/s", failed=len(jobs) - solo_ok,
-                                                p50_solve_s=round(float(np.percentile(solo, 50)), 4),
-                                                p99_solve_s=round(float(np.percentile(solo, 99)), 4)))
+               accuracy=dict(note="relative difference of each served solution from the plain FP64 solution, "
+                                  "both at ||R||/||R0|| <= %g" % TOL,
+                             median=float(np.median(diffs)) if diffs else None,
+                             max=float(np.max(diffs)) if diffs else None),
+               autotuner=tune,
+               baseline_fp64_one_at_a_time=dict(value=round(cap, 4), unit="solves/s", failed=len(jobs) - solo_ok,
+                                                 p50_solve_s=round(float(np.percentile(solo, 50)), 4),
+                                                 p99_solve_s=round(float(np.percentile(solo, 99)), 4)))
     print(json.dumps(out), flush=True)
 
 
@@ -496,7 +529,42 @@ def method_matrix(m, dev, opts_base, ref, methods=("NK", "iNK", "B", "iB"), prec
     return out
 
 
-def dynamic_cardiac(dev, opts_base, nsteps=10, methods=("iB", "NK")):
+def other_configs(dev, opts_base):
+    """The metric's other configurations, each method timed on its last of
+    `reps` solves (the twist: its only solve, which includes building the
+    AMG structure), outside the timed region: config 1 (Cook P1 8x8x2,
+    FP64, all four methods), config 3 (twist P2-P1 32^3, step 1 of 10, iNK
+    and iB) and config 4 (cardiac shell 4x80x78, time step 1 of 100, all
+    four methods), the last two in the run's precision and preconditioner."""
+    import torch
+    import paper_2203_05610_gb300 as fe
+    import workloads as W
+    runs = [("cook_p1_8x8x2", W.cook(8, 8, 2, order=1), ("NK", "iNK", "B", "iB"), dict(opts_base, precision="fp64"), 2),
+            ("twist_p2p1_32", W.twist(32, order=2), ("iNK", "iB"), opts_base, 1),
+            ("heart_p1_4x80x78", W.heart(), ("NK", "iNK", "B", "iB"), opts_base, 2)]
+    out = {}
+    for name, w, methods, o, reps in runs:
+        m = fe.Mesh(w, device=dev.index or 0)
+        load, tm = w["steps"][0]
+        m.set_load(load, tm)
+        d = torch.zeros(m.ndof, dtype=torch.float64, device=dev)
+        res = dict(dofs=m.ndof, solves_per_method=reps)
+        for meth in methods:
+            for rep in range(reps):
+                d.zero_()
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                _, st = m.solve(meth, d, tol=TOL, opts=o)
+                torch.cuda.synchronize()
+                t = time.perf_counter() - t0
+            res[meth] = dict(status=st["status"], nit=st["nit"], lit=st["lit_total"], time_to_tol_s=round(t, 4),
+                             rrel=st["rfinal"] / st["r0"] if st["r0"] > 0 else 0.0)
+        out[name] = res
+        m.close()
+    return out
+
+
+def dynamic_cardiac(dev, opts_base, nsteps=10, methods=("NK", "iNK", "B", "iB")):
     """The cardiac configuration (4 x 80 x 78 hexes, 149,760 P1 tets) as an
     elastodynamic heartbeat: inertia, epicardial dashpots and the follower
     endocardial pressure, nsteps Newmark steps from rest, each step
@@ -629,10 +697,11 @@ def main():
                 matrix.update({k + "/block_jacobi": v for k, v in
                                method_matrix(m, dev, dict(base, pc_type="bj"), ref, methods=("iB",),
                                              precisions=("mixed_fp32",)).items()})
-        dyn = None
+        dyn = others = None
         if not args.no_matrix and args.workload == "cook":
-            dyn = dynamic_cardiac(dev, dict(ksp_restart=args.restart, orthog=args.orthog, pc_type=args.pc,
-                                            precision=args.precision))
+            ob = dict(ksp_restart=args.restart, orthog=args.orthog, pc_type=args.pc, precision=args.precision)
+            dyn = dynamic_cardiac(dev, ob)
+            others = other_configs(dev, ob)
         pk, src = peaks()
         timed = {k: v for k, v in prof.items() if v["timed"] > 0}
         dom = max(timed, key=lambda k: timed[k]["ms"])
@@ -685,7 +754,8 @@ def main():
                                load_step=f"step 1 of {len(w['steps'])} from rest", methods=methods,
                                precision=args.precision, tol=TOL, ksp_restart=args.restart,
                                orthog=["mgs", "mgs_lowsync", "mgs_blocked"][args.orthog],
-                               preconditioner={"bj": "nodal block-Jacobi", "amg": "AMG V-cycle"}[args.pc],
+                               preconditioner={"bj": "nodal block-Jacobi", "amg": "AMG V-cycle",
+                                               "amg_bf16": "AMG V-cycle, BF16 fine-level smoother"}[args.pc],
                                ib_h0_tolerance="adaptive (extension)" if args.ib_adaptive else "fixed",
                                l2="working set > L2 (tangent and Krylov basis), no flush",
                                parallelism=f"replicas x{world}"),
@@ -704,6 +774,8 @@ def main():
                                              "solution (tests/golden/cook_p2_64x64x8_step1.npz)", results=matrix)
         if dyn is not None:
             out["dynamic_cardiac"] = dyn
+        if others is not None:
+            out["other_configs"] = others
         if cpu_proc is not None:
             try:
                 line = cpu_proc.communicate(timeout=900)[0].strip().splitlines()[-1]

@@ -104,10 +104,14 @@ typedef enum {
                            has no potential (fe_energy leaves it out).  The
                            pressure on the moving endocardium of the paper's
                            heartbeat test. */
-  FE_FACE_DASHPOT = 4   /* dashpots of the epicardial Robin condition (Eq. "bc epi",
+  FE_FACE_DASHPOT = 4,  /* dashpots of the epicardial Robin condition (Eq. "bc epi",
                            the C terms): t = -(cperp N x N + cpar (I - N x N)) v,
                            v the velocity of the Newmark step, data = {cperp, cpar, 0};
                            inactive until fe_set_dynamics turns inertia on */
+  FE_FACE_TRACTION_DEFORMED = 5 /* traction load * data[0..2] per unit DEFORMED area (the
+                           Cook load "in the deformed configuration"): nodal forces
+                           load * t int N_a |x_xi x x_eta| dxi deta; not symmetric, no
+                           potential (fe_energy leaves it out) */
 } fe_face_kind;
 
 /* ---- mesh description (host data, copied by fe_mesh_create) ------------ */
@@ -315,7 +319,8 @@ typedef struct {
   int32_t pc_type;     /* preconditioner of the displacement block (GMRES and the B/iB H0):
                           0 (default) nodal block-Jacobi; 1 algebraic multigrid, one
                           smoothed-aggregation V-cycle on the nodal blocks (the class of
-                          the paper's BoomerAMG with block size 3, Appendix A); see
+                          the paper's BoomerAMG with block size 3, Appendix A); 2 that
+                          V-cycle with a BF16 fine-level smoother (mixed FP32); see
                           fe_set_pc */
 } nl_opts;
 
@@ -410,7 +415,12 @@ int fe_profile_read(fe_mesh m, fe_profile_info* out);
  * assembly (device, FP64 for an FP64 tangent, FP32 for the mixed forms; the
  * V-cycle runs in the tangent's precision).  For the u-p form it replaces
  * the block-Jacobi of the displacement block inside the lower Schur
- * preconditioner.  FE_ERR_ARG for pc_type outside {0, 1}. */
+ * preconditioner.  2: the same V-cycle whose fine-level smoother reads a
+ * BF16 copy of the FP32 tangent (made after each assembly; the V-cycle's
+ * dominant passes then move 22 instead of 40 bytes per block, the coarse
+ * levels, transfers and vectors stay FP32; the GMRES operator stays the
+ * FP32 tangent, so the solution's accuracy is unchanged); with an FP64 or
+ * BF16 tangent 2 acts as 1.  FE_ERR_ARG for pc_type outside {0, 1, 2}. */
 int fe_set_pc(fe_mesh m, int pc_type);
 
 /* The AMG hierarchy of the last assembly, for inspection and tests:

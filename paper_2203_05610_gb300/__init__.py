@@ -27,7 +27,7 @@ FE_OK = 0
 NL_DIVERGED, NL_MAX_IT, NL_NONFINITE, KSP_BREAKDOWN = 1, 2, 3, 4
 METHODS = {"NK": 0, "iNK": 1, "B": 2, "iB": 3}
 PRECISIONS = {"fp64": 0, "mixed_fp32": 1, "mixed_bf16": 2}
-PC_TYPES = {"bj": 0, "amg": 1}
+PC_TYPES = {"bj": 0, "amg": 1, "amg_bf16": 2}
 NL_HIST = 1024
 
 

@@ -707,9 +707,12 @@ __device__ __forceinline__ void cheb_rows(int64_t row, const T (&s)[B], const T*
 // consecutive block rows and walks their (contiguous) blocks in chunks of 32,
 // one block per lane, forming the row sums by a segmented scan across the
 // lanes and carrying a row's partial sum into the next chunk; values, column
-// indices and the gather of g run two chunks ahead.  The lane holding a
-// row's last block applies that row's Chebyshev update (cheb_rows), so the
-// updates of a chunk's rows run in parallel.  Every row of A holds its
+// indices and the gather of g run two chunks ahead.  A row's sum goes to
+// shared memory when its last block is reached; the group's 16 Chebyshev
+// row updates (cheb_rows' arithmetic) run together after its last chunk,
+// lane i on row i, with the rows' g, r, x and block-Jacobi inverse loaded
+// when the group starts: one memory latency per group for the updates
+// instead of one per chunk that ends a row.  Every row of A holds its
 // diagonal block, so no row is empty.
 constexpr int VC_RPW = 16;
 
@@ -740,7 +743,9 @@ __global__ void __launch_bounds__(256) k_vc_cheb0(int n, const int* __restrict__
                                                   const T* __restrict__ g, T* __restrict__ x, T* __restrict__ r,
                                                   T* __restrict__ dout, T cx, const T* __restrict__ coef,
                                                   int flags) {
-  const int lane = threadIdx.x & 31;
+  __shared__ T rsum[8][VC_RPW][3];  // row sums of each warp's current group
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const bool wx = !(flags & VC_KEEPX), rx = wx && !(flags & VC_SETX);
   const int ngroups = (n + VC_RPW - 1) / VC_RPW;
   const int nwarps = (int)(((int64_t)gridDim.x * blockDim.x) >> 5);
   for (int grp = (int)((((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5)); grp < ngroups; grp += nwarps) {
@@ -749,6 +754,22 @@ __global__ void __launch_bounds__(256) k_vc_cheb0(int n, const int* __restrict__
     const int rpl = lane < nr ? __ldg(row_ptr + r0 + lane) : INT_MAX;  // start of row r0 + lane
     const int kstart = __shfl_sync(0xffffffffu, rpl, 0);
     const int kend = __ldg(row_ptr + r0 + nr);
+    // this lane's row of the group (lane < nr): its update operands, loaded now
+    T gi[3] = {T(0), T(0), T(0)}, ri[3] = {T(0), T(0), T(0)}, xo[3] = {T(0), T(0), T(0)}, di[9];
+#pragma unroll
+    for (int q = 0; q < 9; q++) di[q] = T(0);
+    if (lane < nr) {
+      const int64_t o = 3 * (int64_t)(r0 + lane);
+#pragma unroll
+      for (int q = 0; q < 3; q++) {
+        gi[q] = g[o + q];
+        ri[q] = r[o + q];
+        if (rx) xo[q] = x[o + q];
+      }
+      if (dout)
+#pragma unroll
+        for (int q = 0; q < 9; q++) di[q] = dinv[9 * (int64_t)(r0 + lane) + q];
+    }
     int c0, c1;
     T v0[9], v1[9];
     vc_load_chunk<V, T>(col, val, (int64_t)kstart + lane, kend, c0, v0);
@@ -786,10 +807,8 @@ __global__ void __launch_bounds__(256) k_vc_cheb0(int n, const int* __restrict__
       if (tail) {
         const int row = rowbase + __popc(below);
         const bool add = sstart < 0;
-        T sum[3];
 #pragma unroll
-        for (int q = 0; q < 3; q++) sum[q] = p[q] + (add ? carry[q] : T(0));
-        cheb_rows<T, 3>(row, sum, dinv, g, x, r, dout, cx, coef, flags);
+        for (int q = 0; q < 3; q++) rsum[wid][row - r0][q] = p[q] + (add ? carry[q] : T(0));
       }
       T l[3];
 #pragma unroll
@@ -813,6 +832,34 @@ __global__ void __launch_bounds__(256) k_vc_cheb0(int n, const int* __restrict__
 #pragma unroll
       for (int j = 0; j < 3; j++) xa[j] = xb[j];
     }
+    __syncwarp();
+    if (lane < nr) {  // the group's row updates (cheb_rows' arithmetic, operands preloaded)
+      const int64_t row = r0 + lane, o = 3 * row;
+      T rn[3], xi[3];
+#pragma unroll
+      for (int q = 0; q < 3; q++) {
+        rn[q] = ri[q] - rsum[wid][lane][q];
+        r[o + q] = rn[q];
+        xi[q] = xo[q] + cx * gi[q];
+      }
+      if (dout) {
+        const T k1 = (flags & VC_START) ? T(0) : coef[1];
+        const T k2 = (flags & VC_START) ? coef[0] : coef[2];
+#pragma unroll
+        for (int q = 0; q < 3; q++) {
+          T t = T(0);
+#pragma unroll
+          for (int jj = 0; jj < 3; jj++) t += di[3 * q + jj] * rn[jj];
+          const T dn = k1 * gi[q] + k2 * t;
+          dout[o + q] = dn;
+          if (flags & VC_FINAL) xi[q] += dn;
+        }
+      }
+      if (wx)
+#pragma unroll
+        for (int q = 0; q < 3; q++) x[o + q] = xi[q];
+    }
+    __syncwarp();
   }
 }
 
@@ -1450,10 +1497,16 @@ int fe_amg_apply(fe_mesh m, const double* x, void* z, bool z_double) {
   const bool d64 = m->prec == FE_PREC_FP64;
   FE_TRY(ensure_vectors(m, d64 ? 8 : 4));
   if (!h->vin) FE_TRY(dev_alloc(m, &h->vin, (size_t)N));
-  if (!h->exec || h->exec_prec != m->prec) {
+  // pc_type 2 with the FP32 tangent: the smoother reads a BF16 copy of the
+  // fine level (half the bytes of the V-cycle's dominant passes); coarse
+  // levels, transfers and vectors stay FP32
+  const bool bf_smooth = m->pc_type == 2 && m->prec == FE_PREC_MIXED_FP32;
+  const int variant = bf_smooth ? 16 : m->prec;
+  if (!h->exec || h->exec_prec != variant) {
     if (d64) FE_TRY((capture<double, double>(m, m->K64)));
-    else if (m->prec == FE_PREC_MIXED_BF16) FE_TRY((capture<float, __nv_bfloat16>(m, m->K16)));
+    else if (m->prec == FE_PREC_MIXED_BF16 || bf_smooth) FE_TRY((capture<float, __nv_bfloat16>(m, m->K16)));
     else FE_TRY((capture<float, float>(m, m->K32)));
+    h->exec_prec = variant;
   }
   FE_CUDA(cudaMemcpyAsync(h->vin, x, N * sizeof(double), cudaMemcpyDeviceToDevice, m->stream));
   {

@@ -17,7 +17,8 @@
 
 // ---------------------------------------------------------------- residual
 static FollowerFaces follower_faces(fe_mesh m) {
-  return FollowerFaces{m->nff, m->ff_nodes, m->ff_p, m->fn_ptr, m->fn_list, m->fk_ptr, m->fk_list, m->X};
+  return FollowerFaces{m->nff, m->ff_nodes, m->ff_kind, m->ff_data, m->fn_ptr, m->fn_list, m->fk_ptr, m->fk_list,
+                       m->X};
 }
 
 // MASS adds the inertia of a Newmark step, mass_c M d with mass_c = 4 rho /
@@ -307,7 +308,14 @@ int fe_tangent_dev(fe_mesh m, const double* d, int precision) {
     FE_CUDA(cudaGetLastError());
   }
   m->prec = precision;
-  if (m->pc_type == 1) FE_TRY(fe_amg_setup(m));  // the AMG hierarchy of this tangent
+  if (m->pc_type == 2 && precision == FE_PREC_MIXED_FP32) {  // BF16 fine level for the V-cycle's smoother
+    const size_t nval = kv_count(m->nnzb);
+    if (!m->K16) FE_TRY(fe_alloc_t(m, &m->K16, nval));
+    FE_SCOPE(m, FE_PROF_TANGENT, 6.0 * nval);
+    k_to_bf16<<<(unsigned)((nval + 255) / 256), 256, 0, m->stream>>>((int64_t)nval, m->K32, m->K16);
+    FE_CUDA(cudaGetLastError());
+  }
+  if (m->pc_type >= 1) FE_TRY(fe_amg_setup(m));  // the AMG hierarchy of this tangent
   return FE_OK;
 }
 

@@ -97,7 +97,7 @@ __device__ double cta_residual(const BatchReq& q, const double* d, double* r, do
     elem_residual_item<ORDER, false>(base + (int)threadIdx.x, q.ne, q.conn, q.geo, d, q.nn, 0, q.mp, q.fib, 0.0,
                                      q.rel, nullptr);
   __syncthreads();
-  const FollowerFaces none{0, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+  const FollowerFaces none{0, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
   for (int a = threadIdx.x; a < q.nn; a += blockDim.x)
     gather_node<ORDER, false>(a, q.nn, NEN, q.node_ptr, q.node_list, q.rel, q.fext1, q.load, q.ks_ptr, q.ks_col,
                               q.ks_val, d, q.fixmask, 0, nullptr, nullptr, nullptr, none, nullptr, r,
@@ -123,7 +123,7 @@ __device__ void cta_tangent(const BatchReq& q, const double* d) {
       __syncthreads();
     }
   }
-  const FollowerFaces none{0, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+  const FollowerFaces none{0, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
   for (int a = threadIdx.x; a < q.nn; a += blockDim.x)
     face_blocks_row<ORDER, T>(a, q.nn, q.ks_ptr, q.ks_col, q.ks_val, q.ks_kpos, q.fixmask, none, d, q.load, K);
   __syncthreads();
@@ -177,9 +177,12 @@ __device__ void cta_spmv(const BatchReq& q, const double* x, double* y) {
 
 // Restarted GMRES, right-preconditioned by the block-Jacobi, modified
 // Gram-Schmidt (FP64), Givens rotations; solves K x = b from x = 0 to
-// ||b - K x|| <= max(rtol ||b||, atol) or kmaxit iterations.  H, the
-// rotations and the projected right-hand side live in shared memory.
-// Returns the iterations; *res the final residual estimate.
+// ||b - K x|| <= max(rtol ||b||, atol) or kmaxit iterations, as fe_gmres:
+// every cycle starts from the residual b - K x, and in the mixed form with a
+// target below 1e-4 ||b|| that residual takes FP64 products and an estimate
+// at the target sends the iterate back to it (mixed-precision iterative
+// refinement).  H, the rotations and the projected right-hand side live in
+// shared memory.  Returns the iterations; *res the final residual (estimate).
 template <class T>
 __device__ int cta_gmres(const BatchReq& q, const double* b, double* x, double rtol, double atol, double* sh,
                          double* sh8, double* slot, double* res) {
@@ -191,23 +194,33 @@ __device__ int cta_gmres(const BatchReq& q, const double* b, double* x, double r
   double* g = sn + m;            // [m+1]
   double* y = g + m + 1;         // [m]
   for (int64_t i = threadIdx.x; i < n; i += blockDim.x) x[i] = 0.0;
-  double beta = sqrt(cta_dot(b, b, n, sh8, slot));
-  const double target = fmax(rtol * beta, atol);
+  const double bnorm = sqrt(cta_dot(b, b, n, sh8, slot));
+  const double target = fmax(rtol * bnorm, atol);
+  const bool refine = sizeof(T) == 4 && target < 1e-4 * bnorm;
+  double* r = q.gr;  // residual of the current iterate
   int its = 0;
-  if (beta <= target || beta == 0.0) {
-    *res = beta;
-    return 0;
-  }
-  double* r = q.gr;  // current residual (b first)
-  cta_axpby(1.0, b, 0.0, r, n);
-  __syncthreads();
+  bool first = true;
   for (;;) {
+    // r = b - K x (x = 0 on the first cycle)
+    if (first) {
+      cta_axpby(1.0, b, 0.0, r, n);
+    } else {
+      if (refine) cta_spmv<T, double>(q, x, r);
+      else cta_spmv<T, T>(q, x, r);
+      __syncthreads();
+      for (int64_t k = threadIdx.x; k < n; k += blockDim.x) r[k] = b[k] - r[k];
+    }
+    __syncthreads();
+    const double beta = first ? bnorm : sqrt(cta_dot(r, r, n, sh8, slot));
+    first = false;
+    *res = beta;
+    if (beta <= target || beta == 0.0 || its >= q.kmaxit || !isfinite(beta)) break;
     double* v0 = q.V;
     cta_axpby(1.0 / beta, r, 0.0, v0, n);
     if (threadIdx.x == 0) g[0] = beta;
     __syncthreads();
     int j = 0;
-    bool done = false;
+    bool stop = false;
     for (; j < m && its < q.kmaxit; j++) {
       double* vj = q.V + (int64_t)j * n;
       double* w = q.V + (int64_t)(j + 1) * n;
@@ -245,12 +258,13 @@ __device__ int cta_gmres(const BatchReq& q, const double* b, double* x, double r
       __syncthreads();
       its++;
       if (fabs(g[j + 1]) <= target || hn == 0.0) {
-        done = true;
+        stop = hn == 0.0;
         j++;
         break;
       }
     }
     const int kdim = j;
+    const double est = fabs(g[kdim]);
     if (threadIdx.x == 0) {  // back substitution H y = g
       for (int i = kdim - 1; i >= 0; i--) {
         double s = g[i];
@@ -267,22 +281,15 @@ __device__ int cta_gmres(const BatchReq& q, const double* b, double* x, double r
       u[k] = s;
     }
     __syncthreads();
-    double* pu = q.V;  // basis no longer needed: preconditioned correction
+    double* pu = q.V;  // the basis is spent: preconditioned correction
     cta_pc<T>(q, u, pu);
     __syncthreads();
     for (int64_t k = threadIdx.x; k < n; k += blockDim.x) x[k] += pu[k];
     __syncthreads();
-    *res = fabs(g[kdim]);
-    if (done || its >= q.kmaxit) break;
-    // restart: r = b - K x
-    cta_spmv<T, T>(q, x, r);
-    __syncthreads();
-    for (int64_t k = threadIdx.x; k < n; k += blockDim.x) r[k] = b[k] - r[k];
-    beta = sqrt(cta_dot(r, r, n, sh8, slot));
-    if (beta <= target) {
-      *res = beta;
-      break;
-    }
+    *res = est;
+    // the estimate decides, except in the refined mixed form, where an
+    // estimate at the target goes back to the top for the FP64-product residual
+    if (its >= q.kmaxit || stop || !isfinite(est) || (est <= target && !refine)) break;
   }
   return its;
 }

@@ -424,10 +424,12 @@ __device__ __forceinline__ void face_tangents(const int* __restrict__ fnodes, co
   }
 }
 
-// nodal force of local node a of a follower face: p int N_a (x_xi x x_eta)
+// residual contribution of local node a of a follower face (load factor
+// applied): kind 3, p int N_a (x_xi x x_eta); kind 5, -int N_a t |x_xi x x_eta|
 template <int ORDER>
-__device__ void follower_force(const int* __restrict__ fnodes, double p, int a, const double* __restrict__ X,
-                               const double* __restrict__ d, double f[3]) {
+__device__ void follower_force(const int* __restrict__ fnodes, int kind, const double* fd, double load, int a,
+                               const double* __restrict__ X, const double* __restrict__ d, double f[3]) {
+  const double p = load * fd[0];
   f[0] = f[1] = f[2] = 0.0;
   for (int q = 0; q < (ORDER == 1 ? 1 : 6); q++) {
     double l[3], w, N[6], Nx[6], Ne[6], xs[3], xe[3];
@@ -439,18 +441,30 @@ __device__ void follower_force(const int* __restrict__ fnodes, double p, int a, 
     }
     tri_shapes<ORDER>(l, N, Nx, Ne);
     face_tangents<ORDER>(fnodes, X, d, Nx, Ne, xs, xe);
-    const double s = w * p * N[a];
-    f[0] += s * (xs[1] * xe[2] - xs[2] * xe[1]);
-    f[1] += s * (xs[2] * xe[0] - xs[0] * xe[2]);
-    f[2] += s * (xs[0] * xe[1] - xs[1] * xe[0]);
+    const double n0 = xs[1] * xe[2] - xs[2] * xe[1], n1 = xs[2] * xe[0] - xs[0] * xe[2],
+                 n2 = xs[0] * xe[1] - xs[1] * xe[0];
+    if (kind == 5) {
+      const double s = -w * load * N[a] * sqrt(n0 * n0 + n1 * n1 + n2 * n2);
+      f[0] += s * fd[0];
+      f[1] += s * fd[1];
+      f[2] += s * fd[2];
+    } else {
+      const double s = w * p * N[a];
+      f[0] += s * n0;
+      f[1] += s * n1;
+      f[2] += s * n2;
+    }
   }
 }
 
-// derivative of that force with respect to the displacement of local node b:
-// p int N_a skew(Ne_b x_xi - Nx_b x_eta), skew(w) v = w x v (not symmetric)
+// derivative of that contribution with respect to the displacement of
+// local node b (not symmetric): kind 3, p int N_a skew(Ne_b x_xi - Nx_b
+// x_eta) with skew(w) v = w x v; kind 5, -int N_a t (x) g_b with g_b =
+// d|n|/d x_b = Nx_b (x_eta x n^) + Ne_b (n^ x x_xi), n^ = n/|n|
 template <int ORDER>
-__device__ void follower_block(const int* __restrict__ fnodes, double p, int a, int b,
+__device__ void follower_block(const int* __restrict__ fnodes, int kind, const double* fd, double load, int a, int b,
                                const double* __restrict__ X, const double* __restrict__ d, double K[9]) {
+  const double p = load * fd[0];
   for (int k = 0; k < 9; k++) K[k] = 0.0;
   for (int q = 0; q < (ORDER == 1 ? 1 : 6); q++) {
     double l[3], w, N[6], Nx[6], Ne[6], xs[3], xe[3];
@@ -462,6 +476,19 @@ __device__ void follower_block(const int* __restrict__ fnodes, double p, int a, 
     }
     tri_shapes<ORDER>(l, N, Nx, Ne);
     face_tangents<ORDER>(fnodes, X, d, Nx, Ne, xs, xe);
+    if (kind == 5) {
+      const double n0 = xs[1] * xe[2] - xs[2] * xe[1], n1 = xs[2] * xe[0] - xs[0] * xe[2],
+                   n2 = xs[0] * xe[1] - xs[1] * xe[0];
+      const double inl = 1.0 / sqrt(n0 * n0 + n1 * n1 + n2 * n2);
+      const double h0 = n0 * inl, h1 = n1 * inl, h2 = n2 * inl;
+      const double gb[3] = {Nx[b] * (xe[1] * h2 - xe[2] * h1) + Ne[b] * (h1 * xs[2] - h2 * xs[1]),
+                            Nx[b] * (xe[2] * h0 - xe[0] * h2) + Ne[b] * (h2 * xs[0] - h0 * xs[2]),
+                            Nx[b] * (xe[0] * h1 - xe[1] * h0) + Ne[b] * (h0 * xs[1] - h1 * xs[0])};
+      const double s = -w * load * N[a];
+      for (int i = 0; i < 3; i++)
+        for (int k = 0; k < 3; k++) K[3 * i + k] += s * fd[i] * gb[k];
+      continue;
+    }
     const double s = w * p * N[a];
     double v[3];
     for (int i = 0; i < 3; i++) v[i] = s * (Ne[b] * xs[i] - Nx[b] * xe[i]);
@@ -515,7 +542,8 @@ __device__ __forceinline__ void grid_sum_finish(double v, double* red, unsigned*
 struct FollowerFaces {
   int n;                    // number of follower faces (0: none)
   const int* nodes;         // [n][6]
-  const double* p;          // [n] pressure at load factor 1
+  const int* kind;          // [n] 3 (pressure) or 5 (traction per unit deformed area)
+  const double* data;       // [n][3] p or t at load factor 1
   const int* node_ptr;      // [nn+1] node -> slots face * 8 + local node
   const int* node_list;
   const int* blk_ptr;       // [nnz_ks+1] face-pattern entry -> face * 64 + a * 8 + b
@@ -562,7 +590,8 @@ __device__ __forceinline__ double gather_node(int t,
       for (int k = ff.node_ptr[t]; k < ff.node_ptr[t + 1]; k++) {
         const int slot = ff.node_list[k], f = fe_idx(slot >> 3, ff.n);
         double fv[3];
-        follower_force<ORDER>(ff.nodes + 6 * (size_t)f, load * ff.p[f], slot & 7, ff.X, d, fv);
+        follower_force<ORDER>(ff.nodes + 6 * (size_t)f, ff.kind[f], ff.data + 3 * (size_t)f, load, slot & 7, ff.X,
+                              d, fv);
         s0 += fv[0];
         s1 += fv[1];
         s2 += fv[2];
@@ -789,7 +818,8 @@ __device__ __forceinline__ void face_blocks_row(int a, int nn, const int* __rest
       for (int j = ff.blk_ptr[k]; j < ff.blk_ptr[k + 1]; j++) {
         const int code = ff.blk_list[j], f = fe_idx(code >> 6, ff.n);
         double fk[9];
-        follower_block<ORDER>(ff.nodes + 6 * (size_t)f, load * ff.p[f], (code >> 3) & 7, code & 7, ff.X, d, fk);
+        follower_block<ORDER>(ff.nodes + 6 * (size_t)f, ff.kind[f], ff.data + 3 * (size_t)f, load, (code >> 3) & 7,
+                              code & 7, ff.X, d, fk);
         for (int c = 0; c < 9; c++) blk[c] += fk[c];
       }
     for (int i = 0; i < 3; i++)

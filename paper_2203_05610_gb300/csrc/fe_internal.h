@@ -133,10 +133,12 @@ struct fe_mesh_s {
   std::vector<double> h_ks_spring, h_ks_dashpot;  // [nnz_ks][9] each
   bool has_dashpots = false;
   double* kc_val = nullptr;  // [nnz_ks][9] the dashpots alone (device, while dynamics is on)
-  // follower pressure faces (kind 3), evaluated on the deformed surface
+  // follower faces, evaluated on the deformed surface: kind 3 (pressure)
+  // and kind 5 (traction per unit deformed area)
   int nff = 0;
   int* ff_nodes = nullptr;   // [nff][6] face nodes (vertices, then P2 edge nodes (0,1), (1,2), (2,0))
-  double* ff_p = nullptr;    // [nff] pressure at load factor 1
+  int* ff_kind = nullptr;    // [nff] 3 or 5
+  double* ff_data = nullptr; // [nff][3] p (kind 3) or t (kind 5) at load factor 1
   int* fn_ptr = nullptr;     // [nn+1] node -> its (follower face, local node) slots
   int* fn_list = nullptr;    // face * 8 + local node
   int* fk_ptr = nullptr;     // [nnz_ks+1] face-pattern entry -> its follower blocks
@@ -210,7 +212,8 @@ struct fe_mesh_s {
   std::vector<ProfRec> prof_pending;
   std::vector<cudaEvent_t> ev_free;
 
-  int pc_type = 0;           // displacement-block preconditioner: 0 nodal block-Jacobi, 1 AMG V-cycle
+  int pc_type = 0;           // displacement-block preconditioner: 0 nodal block-Jacobi, 1 AMG V-cycle,
+                             // 2 AMG V-cycle with a BF16 copy of the fine level in its smoother
   struct AmgHier* amg = nullptr;  // AMG hierarchy (fe_amg.cu), built at the first AMG tangent
   unsigned wait_limit = 1u << 26;  // polls before a bounded device wait gives up
   int coop_blocks = 0;       // co-resident blocks for the persistent kernels

@@ -835,6 +835,180 @@ __global__ void __launch_bounds__(NPT <= 12 ? 512 : 256)
   }
 }
 
+// The blocked MGS step for vectors too long for a register-resident grid:
+// the same passes, reductions and tail as k_arnoldi_bm, with the block's
+// slice of w in shared memory (NPT values per thread, up to 18,432 per
+// block) and each basis slice read straight from L2/HBM in 16-byte pairs
+// (the next block of basis vectors is prefetched into L2 as before).  One
+// block per SM holds 152 x 18,432 = 2.8 M unknowns.
+template <int NPT, int P, class DT, class ZT>
+__global__ void __launch_bounds__(256)
+    k_arnoldi_bm_ws(int64_t n, int j, double* __restrict__ V, int64_t ldv, const double* __restrict__ w,
+                    double* __restrict__ Hcol, double* part, BlockSync bs, double* __restrict__ T,
+                    double* __restrict__ cs, double* __restrict__ sn, double* __restrict__ g, double* __restrict__ out,
+                    const DT* __restrict__ Dinv, ZT* __restrict__ z, double target, int kmax, int it0, int max_it) {
+  static_assert(P == 2 || P == 4 || P == 8, "block of 2, 4 or 8 basis vectors");
+  extern __shared__ __align__(16) double ws[];
+  __shared__ double wpart[P][32];
+  __shared__ double s_h[P];
+  __shared__ double s_trow[P][P];
+  __shared__ int s_fail;
+  if (*(volatile double*)(out + 7) != 0.0) return;
+  unsigned seq = *(volatile unsigned*)bs.seq;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const int64_t S = (int64_t)NPT * blockDim.x;
+  const int64_t base = (int64_t)blockIdx.x * S;
+  const int64_t len = n - base < S ? n - base : S;
+  const int nb = j / P + 1;
+  const int nlast = j + 1 - (nb - 1) * P;
+  const int ng = (j + 1) % P ? nlast : 0;
+  if (threadIdx.x == 0) s_fail = 0;
+  if (threadIdx.x < P) s_h[threadIdx.x] = 0.0;
+  if (threadIdx.x < P && (int)threadIdx.x <= j) prefetch_l2(V + (int64_t)threadIdx.x * ldv + base, len);
+  // w's slice into shared memory (pairs at the register variant's offsets; 0 past the end)
+  for (int q = 0; q < NPT / 2; q++) {
+    const int64_t k = bm_off(q);
+    double2 p = make_double2(0.0, 0.0);
+    if (k + 1 < len) p = __ldcg(reinterpret_cast<const double2*>(w + base + k));
+    else if (k < len) p.x = __ldcg(w + base + k);
+    ws[k] = p.x;
+    ws[k + 1] = p.y;
+  }
+  auto pair = [&](const double* v, int64_t k) {
+    double2 p = make_double2(0.0, 0.0);
+    if (k + 1 < len) p = __ldcg(reinterpret_cast<const double2*>(v + k));
+    else if (k < len) p.x = __ldcg(v + k);
+    return p;
+  };
+  for (int kb = 0; kb <= nb; kb++) {
+    const int np = kb == 0 ? 0 : (kb == nb ? nlast : P);
+    const int nc = kb == nb ? ng : (kb == nb - 1 ? nlast : P);
+    const double* Vp = V + (int64_t)(kb > 0 ? kb - 1 : 0) * P * ldv + base;
+    const double* Vc = kb < nb ? V + (int64_t)kb * P * ldv + base : Vp;
+    // update passes w -= h_m v_m (previous block), each thread on its own pairs
+    for (int m = 0; m < np; m++) {
+      const double h = s_h[m];
+      const double* vm = Vp + (int64_t)m * ldv;
+      for (int q = 0; q < NPT / 2; q++) {
+        const int64_t k = bm_off(q);
+        const double2 p = pair(vm, k);
+        ws[k] -= h * p.x;
+        ws[k + 1] -= h * p.y;
+      }
+    }
+    double loc[P];
+#pragma unroll
+    for (int m = 0; m < P; m++) loc[m] = 0.0;
+#pragma unroll
+    for (int m = 0; m < P; m++) {
+      if (m < nc) {
+        const double* vm = Vc + (int64_t)m * ldv;
+        double a[2] = {0.0, 0.0};
+        for (int q = 0; q < NPT / 2; q++) {
+          const int64_t k = bm_off(q);
+          const double2 p = pair(vm, k);
+          a[0] += ws[k] * p.x;
+          a[1] += ws[k + 1] * p.y;
+        }
+        loc[m] = a[0] + a[1];
+      }
+    }
+    if (kb == nb) {  // final sweep: [||w||^2, Gram row]
+      double a[4] = {0.0, 0.0, 0.0, 0.0};
+      for (int q = 0; q < NPT / 2; q++) {
+        const int64_t k = bm_off(q);
+        a[(2 * q) & 3] += ws[k] * ws[k];
+        a[(2 * q + 1) & 3] += ws[k + 1] * ws[k + 1];
+      }
+#pragma unroll
+      for (int m = P - 1; m > 0; m--) loc[m] = loc[m - 1];
+      loc[0] = (a[0] + a[1]) + (a[2] + a[3]);
+    }
+    if (kb + 1 < nb && threadIdx.x < P && (kb + 1) * P + (int)threadIdx.x <= j)
+      prefetch_l2(V + (int64_t)((kb + 1) * P + threadIdx.x) * ldv + base, len);
+    const bool solve = kb < nb;
+    if (wid == 0 && solve && lane < nc) {
+      const double* tr = T + (int64_t)(kb * P + lane) * P;
+#pragma unroll
+      for (int l = 0; l < P - 1; l++)
+        if (l < lane) s_trow[lane][l] = tr[l];
+    }
+    const double r = warp_reduce_scatter<P>(loc, lane);
+    if ((lane & (32 / P - 1)) == 0) wpart[lane / (32 / P)][wid] = r;
+    __syncthreads();
+    if (wid == 0) {
+      double t = 0.0;
+      for (int q = lane / P; q < nw; q += 32 / P) t += wpart[lane % P][q];
+#pragma unroll
+      for (int x = P; x < 32; x <<= 1) t += __shfl_xor_sync(0xffffffffu, t, x);
+      __syncwarp();
+      if (!bm_reduce_w0<P>(bs, part, seq, t, s_trow, solve, nc, s_h) && lane == 0) s_fail = 1;
+    }
+    if (gridDim.x > 1) seq++;
+    __syncthreads();
+    if (s_fail) return;
+    if (solve && blockIdx.x == 0 && threadIdx.x < nc) Hcol[kb * P + threadIdx.x] = s_h[threadIdx.x];
+  }
+  const double hn = sqrt(s_h[0]);
+  if (hn > 0.0) {
+    const double inv = 1.0 / hn;
+    double* vnx = V + (int64_t)(j + 1) * ldv + base;
+    for (int q = 0; q < NPT / 2; q++) {
+      const int64_t k = bm_off(q);
+      const double v0 = ws[k] * inv, v1 = ws[k + 1] * inv;
+      ws[k] = v0;
+      ws[k + 1] = v1;
+      if (k + 1 < len) *reinterpret_cast<double2*>(vnx + k) = make_double2(v0, v1);
+      else if (k < len) vnx[k] = v0;
+    }
+    if (z) {
+      __syncthreads();
+      for (int64_t a = threadIdx.x; a < len / 3; a += blockDim.x) {
+        const DT* D = Dinv + ((base / 3) + a) * 9;
+        double x0 = ws[3 * a], x1 = ws[3 * a + 1], x2 = ws[3 * a + 2];
+        ZT* zo = z + base + 3 * a;
+        if constexpr (sizeof(DT) == 8) {
+          zo[0] = (ZT)(D[0] * x0 + D[1] * x1 + D[2] * x2);
+          zo[1] = (ZT)(D[3] * x0 + D[4] * x1 + D[5] * x2);
+          zo[2] = (ZT)(D[6] * x0 + D[7] * x1 + D[8] * x2);
+        } else {
+          float f0 = (float)x0, f1 = (float)x1, f2 = (float)x2;
+          zo[0] = (ZT)(D[0] * f0 + D[1] * f1 + D[2] * f2);
+          zo[1] = (ZT)(D[3] * f0 + D[4] * f1 + D[5] * f2);
+          zo[2] = (ZT)(D[6] * f0 + D[7] * f1 + D[8] * f2);
+        }
+      }
+    }
+    if (blockIdx.x == 0 && threadIdx.x < ng) {
+      const int c = threadIdx.x, b0 = (nb - 1) * P;
+      double acc = s_h[1 + c] * inv;
+      for (int l = c + 1; l < ng; l++) acc += s_h[1 + l] * inv * T[(int64_t)(b0 + l) * P + c];
+      T[(int64_t)(j + 1) * P + c] = -acc;
+    }
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    Hcol[j + 1] = hn;
+    for (int i = 0; i < j; i++) {
+      double a = Hcol[i], c = Hcol[i + 1];
+      Hcol[i] = cs[i] * a + sn[i] * c;
+      Hcol[i + 1] = -sn[i] * a + cs[i] * c;
+    }
+    double a = Hcol[j], c = Hcol[j + 1];
+    double r = hypot(a, c);
+    cs[j] = a / r;
+    sn[j] = c / r;
+    Hcol[j] = r;
+    Hcol[j + 1] = 0.0;
+    g[j + 1] = -sn[j] * g[j];
+    g[j] = cs[j] * g[j];
+    double res = fabs(g[j + 1]);
+    out[0] = res;
+    out[1] = hn;
+    out[8] = (double)(j + 1);
+    if (!(res > target) || hn == 0.0 || j + 1 >= kmax || it0 + j + 1 >= max_it) out[7] = 1.0;
+  }
+}
+
 // ---------------------------------------------------------------- SpMV
 // float -> double widening with integer operations only.  GB300's FP64 pipe
 // issues ~2 lane-operations per clock per SM, so the three hardware
@@ -1136,7 +1310,7 @@ __global__ void __launch_bounds__(256) k_pc_schur(int np, int nn, const int* __r
 
 template <class OT>
 static int pc_apply_t(fe_mesh m, const double* x, OT* z) {
-  if (m->pc_type == 1) {  // one AMG V-cycle on the displacement block
+  if (m->pc_type >= 1) {  // one AMG V-cycle on the displacement block
     FE_TRY(fe_amg_apply(m, x, z, sizeof(OT) == 8));
     if (!m->pres) return FE_OK;
     // u-p form: the lower Schur step z_p = S^-1 (x_p - B2 z_u) with the V-cycle's z_u
@@ -1606,6 +1780,8 @@ static int launch_arnoldi_ls_t(fe_mesh m, int j, int kmax, bool fuse_pc, const D
 
 template <int NPT, class DT, class ZT>
 static const void* arnoldi_bm_fn() { return (const void*)k_arnoldi_bm<NPT, BMGS_P, DT, ZT>; }
+template <int NPT, class DT, class ZT>
+static const void* arnoldi_bm_ws_fn() { return (const void*)k_arnoldi_bm_ws<NPT, BMGS_P, DT, ZT>; }
 
 static BlockSync block_sync(fe_mesh m) {
   BlockSync bs;
@@ -1617,20 +1793,23 @@ static BlockSync block_sync(fe_mesh m) {
   return bs;
 }
 
-// Slice selection as in launch_arnoldi_t (w, the current and the next basis
-// slice live in registers); returns 1 without launching when no co-resident
-// grid exists, and the caller takes the sequential sweep.
+// Slice selection as in launch_arnoldi_t: first the register-resident
+// kernels (w, the current and the next basis slice in registers), then, for
+// longer vectors, the shared-memory slices of k_arnoldi_bm_ws (48 or 72
+// values per thread); returns 1 without launching when no co-resident grid
+// exists, and the caller takes the sequential sweep.
 template <class DT, class ZT>
 static int launch_arnoldi_bm_t(fe_mesh m, int j, int kmax, bool fuse_pc, const DT* Dinv, double target, int it0,
                                int max_it) {
   const int64_t n = m->ndof;
   // 512 threads of 12 values first: four warps per SM sub-partition keep
   // the FP64 pipe busier than two
-  const void* fns[2] = {arnoldi_bm_fn<12, DT, ZT>(), arnoldi_bm_fn<24, DT, ZT>()};
-  const int npts[2] = {12, 24};
-  const int bds[2] = {512, 256};
+  const void* fns[4] = {arnoldi_bm_fn<12, DT, ZT>(), arnoldi_bm_fn<24, DT, ZT>(), arnoldi_bm_ws_fn<48, DT, ZT>(),
+                        arnoldi_bm_ws_fn<72, DT, ZT>()};
+  const int npts[4] = {12, 24, 48, 72};
+  const int bds[4] = {512, 256, 256, 256};
   int which = -1, grid = 0;
-  for (int q = 0; q < 2; q++) {
+  for (int q = 0; q < 4; q++) {
     size_t smem = (size_t)npts[q] * bds[q] * sizeof(double);
     FE_TRY(fe_kernel_smem(fns[q], (int)smem));
     int per_sm = 0;

@@ -415,7 +415,7 @@ static int validate(const fe_mesh_desc* d) {
   for (int64_t i = 0; i < 3LL * d->nf; i++)
     if (d->faces[i] < 0 || d->faces[i] >= d->nv) return fe_set_error("face vertex id out of range"), FE_ERR_ARG;
   for (int i = 0; i < d->nf; i++)
-    if (d->face_kind[i] < 0 || d->face_kind[i] > 4) return fe_set_error("bad face kind"), FE_ERR_ARG;
+    if (d->face_kind[i] < 0 || d->face_kind[i] > 5) return fe_set_error("bad face kind"), FE_ERR_ARG;
   for (int64_t i = 0; i < 3LL * d->nf; i++)
     if (!std::isfinite(d->face_data[i])) return fe_set_error("face data must be finite"), FE_ERR_ARG;
   if (d->dir_group)
@@ -572,8 +572,8 @@ static int create_impl(const fe_mesh_desc* desc, fe_mesh m) {
   };
   std::vector<double> fext((size_t)nn * 3, 0.0);
   std::map<std::pair<int, int>, FaceBlock> fpat;
-  std::vector<int> ff_nodes, fn_count(nn, 0);
-  std::vector<double> ff_p;
+  std::vector<int> ff_nodes, ff_kind, fn_count(nn, 0);
+  std::vector<double> ff_data;
   for (int f = 0; f < desc->nf; f++) {
     const int* v = desc->faces + 3 * f;
     const double* x0 = desc->coords + 3 * (size_t)v[0];
@@ -618,9 +618,10 @@ static int create_impl(const fe_mesh_desc* desc, fe_mesh m) {
       for (int i = 0; i < 3; i++) t[i] = kind == FE_FACE_TRACTION ? fd[i] : -fd[0] * N[i];
       for (int p = 0; p < nfn; p++)
         for (int i = 0; i < 3; i++) fext[3 * (size_t)nodes[p] + i] += t[i] * intphi[p];
-    } else if (kind == FE_FACE_FOLLOWER) {
-      int ff = (int)ff_p.size();
-      ff_p.push_back(fd[0]);
+    } else if (kind == FE_FACE_FOLLOWER || kind == FE_FACE_TRACTION_DEFORMED) {
+      int ff = (int)ff_kind.size();
+      ff_kind.push_back(kind);
+      for (int i = 0; i < 3; i++) ff_data.push_back(fd[i]);
       for (int p = 0; p < 6; p++) ff_nodes.push_back(p < nfn ? nodes[p] : nodes[0]);
       for (int p = 0; p < nfn; p++) {
         fn_count[nodes[p]]++;
@@ -652,7 +653,7 @@ static int create_impl(const fe_mesh_desc* desc, fe_mesh m) {
   }
   for (int a = 0; a < nn; a++) ks_ptr[a + 1] += ks_ptr[a];
   m->nnz_ks = (int64_t)ks_col.size();
-  m->nff = (int)ff_p.size();
+  m->nff = (int)ff_kind.size();
   std::vector<int> fn_ptr(nn + 1, 0), fn_list;
   if (m->nff) {  // node -> (follower face, local node), faces in order
     for (int a = 0; a < nn; a++) fn_ptr[a + 1] = fn_ptr[a] + fn_count[a];
@@ -685,7 +686,8 @@ static int create_impl(const fe_mesh_desc* desc, fe_mesh m) {
   FE_TRY(upload(m, &m->ks_kpos, ks_kpos));
   if (m->nff) {
     FE_TRY(upload(m, &m->ff_nodes, ff_nodes));
-    FE_TRY(upload(m, &m->ff_p, ff_p));
+    FE_TRY(upload(m, &m->ff_kind, ff_kind));
+    FE_TRY(upload(m, &m->ff_data, ff_data));
     FE_TRY(upload(m, &m->fn_ptr, fn_ptr));
     FE_TRY(upload(m, &m->fn_list, fn_list));
     FE_TRY(upload(m, &m->fk_ptr, fk_ptr));
@@ -831,9 +833,10 @@ extern "C" int fe_mesh_create(const fe_mesh_desc* desc, fe_mesh* out) {
 
 extern "C" int fe_set_pc(fe_mesh m, int pc_type) {
   if (!m) return fe_set_error("NULL mesh"), FE_ERR_ARG;
-  if (pc_type != 0 && pc_type != 1) return fe_set_error("pc_type must be 0 (block-Jacobi) or 1 (AMG)"), FE_ERR_ARG;
+  if (pc_type < 0 || pc_type > 2)
+    return fe_set_error("pc_type must be 0 (block-Jacobi), 1 (AMG) or 2 (AMG, BF16 fine-level smoother)"), FE_ERR_ARG;
   FE_CUDA(cudaSetDevice(m->device));
-  const bool rebuild = pc_type == 1 && m->pc_type != 1 && m->prec >= 0;
+  const bool rebuild = pc_type >= 1 && m->pc_type != pc_type && m->prec >= 0;
   m->pc_type = pc_type;
   if (rebuild) FE_TRY(fe_amg_setup(m));  // a tangent is assembled already
   return FE_OK;

@@ -83,7 +83,7 @@ int64_t estimate_footprint(const Request& r, int64_t* ndof_out) {
   b += 9 * sval * nnzb + 9 * sval * nn + (o.precision == FE_PREC_MIXED_BF16 ? 18 * nnzb : 0);  // tangent
   b += 8 * ndof * (restart + 1) + 8 * (restart + 1) * (restart + 1);                             // Krylov basis
   b += 8 * ndof * (2 * mpairs + 12);                                                              // BFGS pairs, vectors
-  if (o.pc_type == 1) b += (d.order == 1 ? 2500 : 6000) * nn;  // AMG: P, A P, P^T in FP64 and coarse levels
+  if (o.pc_type >= 1) b += (d.order == 1 ? 2500 : 6000) * nn;  // AMG: P, A P, P^T in FP64 and coarse levels
   *ndof_out = ndof;
   return b + b / 8 + (64 << 20);
 }

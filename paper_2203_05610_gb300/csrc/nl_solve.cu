@@ -255,7 +255,7 @@ extern "C" int nl_solve(fe_mesh m, int method, double tol, int max_it, double* d
     return fe_set_error("jac_lag must be >= 1 (0 = 1) and hess_reassemble >= 0"), FE_ERR_ARG;
   if (o.orthog < 0 || o.orthog > 2) return fe_set_error("orthog must be 0, 1 or 2"), FE_ERR_ARG;
   if (o.precision < 0 || o.precision > 2) return fe_set_error("bad precision"), FE_ERR_ARG;
-  if (o.pc_type < 0 || o.pc_type > 1) return fe_set_error("pc_type must be 0 or 1"), FE_ERR_ARG;
+  if (o.pc_type < 0 || o.pc_type > 2) return fe_set_error("pc_type must be 0, 1 or 2"), FE_ERR_ARG;
   FE_CUDA(cudaSetDevice(m->device));
   nl_stats local;
   nl_stats& st = stats ? *stats : local;

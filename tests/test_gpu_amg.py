@@ -233,3 +233,34 @@ def test_mixed_accuracy_against_the_oracle_on_a_larger_mesh(fe):
         rrel[prec] = sg["rfinal"] / sg["r0"]
     bound = MIXED_FACTOR * max(errs["fp64"] * max(1.0, rrel["mixed_fp32"] / rrel["fp64"]), 1e-12)
     assert errs["mixed_fp32"] <= bound, (errs, rrel)
+
+
+def test_bf16_smoother_variant(fe):
+    """pc_type 2 (the V-cycle's fine-level smoother reads a BF16 copy of the
+    FP32 tangent): the preconditioned vector stays within BF16 rounding of
+    the FP32 V-cycle's (relative 5e-2: the V-cycle is a contraction, so the
+    values' relative rounding 2^-8 enters once per smoothing pass), and
+    mixed iB and NK with it reach the oracle's solution within the mixed bar
+    of the FP32 V-cycle."""
+    w = W.cook(6, 6, 2, order=2, nu=0.3)
+    m, om, _, _ = _pair(fe, w, 0.4)
+    d = m.zeros()
+    m.set_pc("amg")
+    m.tangent(d, "mixed_fp32")
+    x = torch.randn(m.ndof, dtype=torch.float64, device="cuda")
+    z1 = m.pc(x)
+    m.set_pc("amg_bf16")
+    m.tangent(d, "mixed_fp32")
+    z2 = m.pc(x)
+    assert not torch.equal(z1, z2)
+    assert torch.linalg.norm(z2 - z1) <= 5e-2 * torch.linalg.norm(z1)
+    for method in ("iB", "NK"):
+        xref, so = om.solve(method, np.zeros(om.ndof), tol=1e-12, opts=dict(ksp_atol=0.0, pc_type=1))
+        errs, rrel = {}, {}
+        for pc in ("amg", "amg_bf16"):
+            xg, sg = m.solve(method, m.zeros(), tol=1e-8, opts=dict(precision="mixed_fp32", ksp_atol=0.0, pc_type=pc))
+            assert sg["status"] == 0 and sg["rfinal"] <= 1e-8 * sg["r0"], (method, pc, sg["status"])
+            errs[pc] = np.linalg.norm(xg.cpu().numpy() - xref) / np.linalg.norm(xref)
+            rrel[pc] = sg["rfinal"] / sg["r0"]
+        bound = MIXED_FACTOR * max(errs["amg"] * max(1.0, rrel["amg_bf16"] / rrel["amg"]), 1e-12)
+        assert errs["amg_bf16"] <= bound, (method, errs, rrel)

@@ -33,10 +33,16 @@ LOADS = {"cook_p1": (0.4, 0.0), "cook_p2": (0.4, 0.0), "heart_p1": (0.2, 0.01)}
 OPTS = dict(ksp_atol=0.0, ksp_restart=50)
 
 
+def _case(c):
+    """The small families; the P2 Cook case at nu = 0.3 (at 0.49, GMRES(50)
+    with block-Jacobi stagnates and iB from rest diverges in the oracle)."""
+    return W.cook(3, 3, 1, order=2, nu=0.3) if c == "cook_p2" else small_cases()[c]
+
+
 def _requests(fe, cases, prec="fp64"):
     ms, ds = [], []
     for c in cases:
-        m = fe.Mesh(small_cases()[c])
+        m = fe.Mesh(_case(c))
         m.set_load(*LOADS[c])
         ms.append(m)
         ds.append(m.zeros())
@@ -53,7 +59,7 @@ def test_batch_matches_the_oracle_fp64(fe, method):
         assert fe.batch_supported(m, method, opts)
     st = fe.batch_solve(ms, [method] * len(ms), ds, [tol] * len(ms), opts=opts)
     for c, m, d, s in zip(cases, ms, ds, st):
-        om = O.Mesh(small_cases()[c])
+        om = O.Mesh(_case(c))
         om.set_load(*LOADS[c])
         x, so = om.solve(method, np.zeros(om.ndof), tol=tol,
                          opts=dict(ksp_atol=0.0, ksp_restart=50))
@@ -75,7 +81,7 @@ def test_batch_mixed_precision_error(fe, method):
         st = fe.batch_solve(ms, [method] * 2, ds, [1e-11] * 2, opts=dict(OPTS, precision=prec))
         errs[prec], rrel[prec] = [], []
         for c, d, s_ in zip(cases, ds, st):
-            om = O.Mesh(small_cases()[c])
+            om = O.Mesh(_case(c))
             om.set_load(*LOADS[c])
             x, so = om.solve("NK", np.zeros(om.ndof), tol=1e-12, opts=dict(ksp_rtol=1e-12, ksp_atol=0.0))
             assert s_["status"] == 0, (c, prec, s_["res_hist"][-3:])
@@ -105,7 +111,7 @@ def test_batch_agrees_with_the_single_solve_path(fe):
     c = "cook_p2"
     ms, ds = _requests(fe, [c])
     st = fe.batch_solve(ms, ["NK"], ds, [1e-11], opts=dict(OPTS, precision="fp64"), threads=128)
-    m = fe.Mesh(small_cases()[c])
+    m = fe.Mesh(_case(c))
     m.set_load(*LOADS[c])
     d = m.zeros()
     _, s1 = m.solve("NK", d, tol=1e-11, opts=dict(OPTS, precision="fp64"))

@@ -56,6 +56,7 @@ CASES = {
     "heart_p2_dyn": lambda: W.heart(nr=2, nc=8, nl=4, order=2, dynamics=True, follower=True),
     "cook_p2_dyn": _cook_dyn,
     "box_follower": _box_follower,
+    "cook_p2_deformed_traction": lambda: W.cook(4, 4, 2, order=2, nu=0.3, follower=True),
 }
 
 
@@ -176,6 +177,27 @@ def test_dynamic_heart_methods(fe, method):
     assert so["status"] == 0 and sg["status"] == 0
     assert abs(sg["nit"] - so["nit"]) <= max(1, so["nit"] // 10)
     assert np.linalg.norm(xg.cpu().numpy() - x) <= xtol * np.linalg.norm(x)
+
+
+@pytest.mark.parametrize("method", ["NK", "iNK"])
+def test_deformed_area_traction_solve(fe, method):
+    """Cook with its traction per unit deformed area (face kind 5, the load
+    "in the deformed configuration"): the static solve matches the oracle."""
+    w = W.cook(4, 4, 2, order=1, nu=0.3, follower=True)
+    m, om = fe.Mesh(w), O.Mesh(w)
+    for mm in (m, om):
+        mm.set_load(0.5)
+    x, so = om.solve(method, np.zeros(om.ndof), tol=1e-11, opts=dict(ksp_atol=0.0))
+    xg, sg = m.solve(method, m.zeros(), tol=1e-11, opts=dict(ksp_atol=0.0))
+    assert so["status"] == 0 and sg["status"] == 0
+    assert abs(sg["nit"] - so["nit"]) <= 1
+    assert np.linalg.norm(xg.cpu().numpy() - x) <= 1e-10 * np.linalg.norm(x)
+    # not the dead-traction solution
+    wd = W.cook(4, 4, 2, order=1, nu=0.3)
+    od = O.Mesh(wd)
+    od.set_load(0.5)
+    xd, _ = od.solve(method, np.zeros(od.ndof), tol=1e-11, opts=dict(ksp_atol=0.0))
+    assert np.linalg.norm(xd - x) > 1e-4 * np.linalg.norm(x)
 
 
 def test_dynamics_switches_and_errors(fe):

@@ -390,6 +390,40 @@ def test_config2_residual_and_tangent_full_size(fe):
     assert itg == 100 and resg < bn and abs(true - resg) <= bound, (resg / bn, true / bn, bound / bn)
 
 
+def test_blocked_mgs_beyond_a_register_resident_grid(fe):
+    """Cook P2 72x72x8 (1,072,275 unknowns): longer than a grid of
+    register-resident slices (152 SMs x 6,144 values), so the blocked MGS
+    step keeps its slices in shared memory (k_arnoldi_bm_ws).  GMRES(50)
+    with it: the residual estimate is the true residual up to gap_bound, and
+    the iterate equals the sequential sweep's to rounding."""
+    w = W.cook(72, 72, 8, order=2, nu=0.3)
+    m, om = _pair(fe, w)
+    assert m.ndof == 1072275
+    m.set_load(0.2)
+    om.set_load(0.2)
+    d = np.zeros(om.ndof)
+    om.apply_dirichlet(d)
+    dg = torch.from_numpy(d).cuda()
+    om.tangent(d)
+    m.tangent(dg)
+    v, _, _ = om.tangent_copy()
+    vg, _, _ = m.tangent_copy()
+    assert _rel(vg, v) < 1e-12
+    topo = om.topology()
+    b = np.random.default_rng(17).standard_normal(om.ndof)
+    bn = np.linalg.norm(b)
+    xs = {}
+    for orthog in (2, 0):
+        xg, itg, resg = m.gmres(torch.from_numpy(b).cuda(), rtol=1e-14, atol=0.0, restart=50, max_it=50,
+                                orthog=orthog)
+        xh = xg.cpu().numpy()
+        true = np.linalg.norm(b - om.spmv(xh))
+        bound = gap_bound(topo, v, vg, xh, 2.0 ** -53)
+        assert itg == 50 and resg < bn and abs(true - resg) <= bound, (orthog, resg / bn, true / bn, bound / bn)
+        xs[orthog] = xh
+    assert np.linalg.norm(xs[2] - xs[0]) <= 1e-7 * np.linalg.norm(xs[0])  # as in test_gmres
+
+
 def gap_bound(topo, v_oracle, v_used, x, u_op):
     """Bound on | ||b - K x|| - (GMRES residual estimate) | with K the oracle's
     tangent and x the GPU iterate.  In exact arithmetic the Arnoldi relation

@@ -33,6 +33,7 @@ FACE_PRESSURE = 1
 FACE_ROBIN = 2
 FACE_FOLLOWER = 3
 FACE_DASHPOT = 4
+FACE_TRACTION_DEFORMED = 5
 
 _PERMS = list(itertools.permutations(range(3)))  # lexicographic order
 
@@ -125,13 +126,15 @@ def _workload(name, coords, tets, order, pressure_order, dir_group, groups,
 
 
 def cook(nx=8, ny=8, nz=2, order=1, E=1.0, nu=0.49, traction_scale=1.0,
-         nsteps=5, vol_literal=0):
+         nsteps=5, vol_literal=0, follower=False):
     """Cook's membrane (paper: Cook test; sizes from the workload table).
 
     Map of the unit cube: x = 48 xi, y = 44 xi + eta (44 - 28 xi), z = 10 zeta.
     Vertex id = (k*(ny+1) + j)*(nx+1) + i.  Clamp on x = 0 (group 1, all
     components).  Dead traction (0, traction_scale/16, 0) per unit reference
     area on x = 48.  Load step s of nsteps scales the traction by s/nsteps.
+    follower=True applies the traction per unit deformed area instead (face
+    kind 5: the load "in the deformed configuration").
     """
     xi = np.linspace(0.0, 1.0, nx + 1)
     eta = np.linspace(0.0, 1.0, ny + 1)
@@ -151,11 +154,12 @@ def cook(nx=8, ny=8, nz=2, order=1, E=1.0, nu=0.49, traction_scale=1.0,
     on_right = np.all(np.isclose(coords[bf][:, :, 0], 48.0), axis=1)
     faces = bf[on_right]
     t = traction_scale / 16.0
-    face_kind = np.full(faces.shape[0], FACE_TRACTION, dtype=np.int32)
+    face_kind = np.full(faces.shape[0], FACE_TRACTION_DEFORMED if follower else FACE_TRACTION, dtype=np.int32)
     face_data = np.tile(np.array([0.0, t, 0.0]), (faces.shape[0], 1))
     material = dict(kind=MAT_COOK_NH, E=E, nu=nu, vol_literal=vol_literal)
     steps = [((s + 1) / nsteps, 0.0) for s in range(nsteps)]
-    return _workload(f"cook_p{order}_{nx}x{ny}x{nz}", coords, tets, order, 0, dir_group,
+    return _workload(f"cook_p{order}_{nx}x{ny}x{nz}" + ("_follower" if follower else ""), coords, tets, order, 0,
+                     dir_group,
                      groups, faces, face_kind, face_data, material, None, steps,
                      nx=nx, ny=ny, nz=nz)
 
@@ -208,7 +212,7 @@ def heart(nr=4, nc=80, nl=78, order=1, a_endo=2.0, c_endo=5.0, a_epi=3.0, c_epi=
           z_base=1.0, apex_hole=0.15, C=0.88, bf=18.5, bt=3.58, bfs=1.63, kappa=1.0e3,
           Ta_peak=60.0, period=0.8, p_endo=2.0, k_perp=20.0, k_par=2.0, nsteps=100,
           helix_endo_deg=60.0, helix_epi_deg=-60.0, dynamics=False, follower=False,
-          rho=1.05e-4, c_perp=2.0, c_par=0.2):
+          rho=1.0, c_perp=2.0, c_par=0.2):
     """Truncated prolate-ellipsoid shell (cardiac-like test stand-in).
 
     Index space (i transmural 0..nr, j circumferential 0..nc periodic,
@@ -228,10 +232,11 @@ def heart(nr=4, nc=80, nl=78, order=1, a_endo=2.0, c_endo=5.0, a_epi=3.0, c_epi=
     3) instead of a dead one.  dynamics=True adds the inertia of the
     momentum equation and the dashpots of the epicardial Robin condition:
     duplicate epicardial faces of kind 4 with (c_perp, c_par), and the keys
-    rho (density) and dt = period / nsteps of the Newmark steps.  Units are
-    cm, s and kPa: rho = 1.05e-4 kPa s^2 / cm^2 is a tissue density of
-    1050 kg / m^3; (k_perp, k_par) = (20, 2) kPa / cm and (c_perp, c_par) =
-    (2, 0.2) kPa s / cm.
+    rho (density) and dt = period / nsteps of the Newmark steps.  The
+    default rho = 1 is the momentum equation as printed (no density
+    coefficient); in the units of this shell (cm, s, kPa) a tissue density of
+    1050 kg / m^3 is rho = 1.05e-4 kPa s^2 / cm^2.  (k_perp, k_par) = (20, 2)
+    kPa / cm, (c_perp, c_par) = (2, 0.2) kPa s / cm.
     """
     def geom(e, ph, tt):
         a = a_endo + e * (a_epi - a_endo)
