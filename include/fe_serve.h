@@ -35,8 +35,10 @@ typedef struct {
   int64_t hbm_budget;  /* bytes admitted requests may hold together; 0 = 80% of free memory */
   int32_t max_active;  /* requests solved concurrently (slots); <= 0 means 8 */
   int64_t batch_max_dofs; /* requests up to this many unknowns that fe_batch_supported
-                             accepts are solved in shared launches (fe_batch.h);
-                             0 = 60000, < 0 = never */
+                             accepts are solved in shared launches (fe_batch.h), one
+                             launch per size class (order, precision, floor(log2
+                             ndof)); 0 = 4000 (where one CTA still solves a request
+                             about as fast as the whole GPU does), < 0 = never */
 } fe_server_opts;
 
 /* One entry of the launch-shape autotuner of the batched path: per size

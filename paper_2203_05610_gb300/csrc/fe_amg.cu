@@ -1529,7 +1529,7 @@ void fe_amg_free(fe_mesh m) {
   if (!m->amg) return;
   if (m->amg->exec) cudaGraphExecDestroy(m->amg->exec);
   if (m->amg->cap) cudaStreamDestroy(m->amg->cap);
-  for (void* p : m->amg->allocs) cudaFree(p);
+  for (void* p : m->amg->allocs) cudaFreeAsync(p, m->stream);
   m->device_bytes -= m->amg->bytes;
   delete m->amg;
   m->amg = nullptr;

@@ -363,12 +363,13 @@ static int copy_out(fe_mesh m, double* host, const double* d64, const float* d32
     return FE_OK;
   }
   double* tmp = nullptr;
-  FE_CUDA(cudaMalloc(&tmp, n * sizeof(double)));
+  FE_CUDA(cudaMallocAsync((void**)&tmp, n * sizeof(double), m->stream));
   if (d16) k_widen_bf<<<(unsigned)((n + 255) / 256), 256, 0, m->stream>>>(n, d16, tmp);
   else k_widen<<<(unsigned)((n + 255) / 256), 256, 0, m->stream>>>(n, d32, tmp);
   cudaError_t e = cudaStreamSynchronize(m->stream);
   if (e == cudaSuccess) e = cudaMemcpy(host, tmp, n * sizeof(double), cudaMemcpyDeviceToHost);
-  cudaFree(tmp);
+  cudaFreeAsync(tmp, m->stream);
+  cudaStreamSynchronize(m->stream);
   if (e != cudaSuccess) return fe_set_error("%s", cudaGetErrorString(e)), FE_ERR_CUDA;
   return FE_OK;
 }

@@ -493,8 +493,18 @@ static int batch_group(int nreq, fe_mesh* meshes, const int* methods, const doub
   const int prec = opts[0].precision;
   std::vector<BatchReq> h(nreq);
   std::vector<void*> allocs;
+  cudaStream_t stream = m0->stream;
+  // stream-ordered allocations: no device-wide synchronisation, so batches
+  // on other streams keep running
   auto cleanup = [&]() {
-    for (void* p : allocs) cudaFree(p);
+    for (void* p : allocs) cudaFreeAsync(p, stream);
+  };
+  std::vector<size_t> off_base(nreq), off_K(nreq), off_D(nreq);
+  size_t total = 0;
+  auto take = [&](size_t bytes) {
+    const size_t o = total;
+    total += (bytes + 255) / 256 * 256;
+    return o;
   };
   int restart_max = 1;
   for (int i = 0; i < nreq; i++) {
@@ -560,19 +570,20 @@ static int batch_group(int nreq, fe_mesh* meshes, const int* methods, const doub
     const int64_t nvec = 7 + (q.restart + 1) + ((q.method >= NL_B) ? 2 * (int64_t)std::min(q.mcap, BATCH_HIST) : 0);
     const int64_t nrel = (int64_t)m->ne * m->nen * 3;
     const size_t sval = prec == FE_PREC_FP64 ? 8 : 4;
-    double* base = nullptr;
-    void *K = nullptr, *Dinv = nullptr;
-    if (cudaMalloc(&base, sizeof(double) * (size_t)(nvec * n + nrel)) != cudaSuccess ||
-        cudaMalloc(&K, sval * kv_count(m->nnzb)) != cudaSuccess ||
-        cudaMalloc(&Dinv, sval * 9 * (size_t)m->nn) != cudaSuccess) {
-      if (base) cudaFree(base);
-      if (K) cudaFree(K);
-      cleanup();
-      return fe_set_error("batch workspace allocation failed"), FE_ERR_OOM;
-    }
-    allocs.push_back(base);
-    allocs.push_back(K);
-    allocs.push_back(Dinv);
+    off_base[i] = take(sizeof(double) * (size_t)(nvec * n + nrel));
+    off_K[i] = take(sval * kv_count(m->nnzb));
+    off_D[i] = take(sval * 9 * (size_t)m->nn);
+  }
+  FE_CUDA(cudaSetDevice(m0->device));
+  char* pool = nullptr;
+  if (cudaMallocAsync((void**)&pool, total, stream) != cudaSuccess)
+    return fe_set_error("batch workspace allocation failed"), FE_ERR_OOM;
+  allocs.push_back(pool);
+  for (int i = 0; i < nreq; i++) {
+    BatchReq& q = h[i];
+    const int64_t n = 3 * (int64_t)meshes[i]->nn;
+    const int64_t nrel = (int64_t)meshes[i]->ne * meshes[i]->nen * 3;
+    double* base = (double*)(pool + off_base[i]);
     q.d = d[i];
     q.r = base;
     q.rn = base + n;
@@ -585,20 +596,20 @@ static int batch_group(int nreq, fe_mesh* meshes, const int* methods, const doub
     q.V = q.rel + nrel;
     q.S = q.V + (int64_t)(q.restart + 1) * n;
     q.Y = q.S + (int64_t)std::min(q.mcap, BATCH_HIST) * n;
-    q.K = K;
-    q.Dinv = Dinv;
+    q.K = pool + off_K[i];
+    q.Dinv = pool + off_D[i];
   }
-  cudaStream_t stream = m0->stream;
-  FE_CUDA(cudaSetDevice(m0->device));
   BatchReq* dq = nullptr;
   fe_batch_out* dout = nullptr;
-  if (cudaMalloc(&dq, sizeof(BatchReq) * nreq) != cudaSuccess ||
-      cudaMalloc(&dout, sizeof(fe_batch_out) * nreq) != cudaSuccess) {
-    if (dq) cudaFree(dq);
+  if (cudaMallocAsync((void**)&dq, sizeof(BatchReq) * nreq, stream) != cudaSuccess) {
     cleanup();
     return fe_set_error("batch table allocation failed"), FE_ERR_OOM;
   }
   allocs.push_back(dq);
+  if (cudaMallocAsync((void**)&dout, sizeof(fe_batch_out) * nreq, stream) != cudaSuccess) {
+    cleanup();
+    return fe_set_error("batch table allocation failed"), FE_ERR_OOM;
+  }
   allocs.push_back(dout);
   for (int i = 0; i < nreq; i++) h[i].out = dout + i;
   // Dirichlet values of each request's load first (on each mesh's stream),
@@ -632,8 +643,8 @@ static int batch_group(int nreq, fe_mesh* meshes, const int* methods, const doub
     e = cudaLaunchKernel(fn, dim3(nreq), dim3(threads), args, smem, stream);
   }
   if (e == cudaSuccess) e = cudaMemcpyAsync(out_host, dout, sizeof(fe_batch_out) * nreq, cudaMemcpyDeviceToHost, stream);
+  cleanup();  // stream-ordered: after the kernel and the copy-back
   if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
-  cleanup();
   if (e != cudaSuccess) return fe_set_error("batch solve: %s", cudaGetErrorString(e)), FE_ERR_CUDA;
   return FE_OK;
 }

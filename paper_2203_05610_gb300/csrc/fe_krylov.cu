@@ -1627,13 +1627,13 @@ int fe_workspace(fe_mesh m, int restart) {
     // the Arnoldi kernel's 16-byte pair loads stay inside a row
     const int64_t ldv = (m->ndof + 31) / 32 * 32;
     if (m->V) {
-      cudaFree(m->V);
-      cudaFree(m->H);
-      cudaFree(m->gv);
+      cudaFreeAsync(m->V, m->stream);
+      cudaFreeAsync(m->H, m->stream);
+      cudaFreeAsync(m->gv, m->stream);
       m->device_bytes -= (int64_t)(m->ws_restart + 1) * m->ldv * 8 + (int64_t)(m->ws_restart + 1) * (m->ws_restart + 1) * 8 +
                          (int64_t)4 * (m->ws_restart + 2) * 8;
       m->V = m->H = m->gv = nullptr;
-      cudaFree(m->Tbm);
+      cudaFreeAsync(m->Tbm, m->stream);
       m->device_bytes -= (int64_t)(m->ws_restart + 2) * BMGS_P * 8;
       m->Tbm = nullptr;
     }
@@ -1646,9 +1646,9 @@ int fe_workspace(fe_mesh m, int restart) {
     FE_TRY(fe_alloc_t(m, &m->Tbm, (size_t)(restart + 2) * BMGS_P));
     if (restart <= LOWSYNC_MAX_RESTART) {  // low-synchronisation MGS: L, h, per-block inner products
       if (m->Lmat) {
-        cudaFree(m->Lmat);
-        cudaFree(m->hpub);
-        cudaFree(m->partv);
+        cudaFreeAsync(m->Lmat, m->stream);
+        cudaFreeAsync(m->hpub, m->stream);
+        cudaFreeAsync(m->partv, m->stream);
       }
       m->partv_blocks = 2 * m->sm_count;
       FE_TRY(fe_alloc_t(m, &m->Lmat, (size_t)(restart + 1) * (restart + 1)));

@@ -29,12 +29,15 @@ void fe_set_error(const char* fmt, ...) {
 }
 extern "C" const char* fe_last_error(void) { return g_err; }
 
+// Stream-ordered allocations on the mesh's stream: freeing them does not
+// synchronise the device, so meshes created and destroyed by the serving
+// loop's workers do not stall the kernels of other requests.
 int fe_alloc(fe_mesh m, void** p, size_t bytes) {
   *p = nullptr;
   if (bytes == 0) bytes = 16;
-  cudaError_t e = cudaMalloc(p, bytes);
+  cudaError_t e = cudaMallocAsync(p, bytes, m->stream);
   if (e != cudaSuccess) {
-    fe_set_error("cudaMalloc(%zu bytes) failed: %s", bytes, cudaGetErrorString(e));
+    fe_set_error("cudaMallocAsync(%zu bytes) failed: %s", bytes, cudaGetErrorString(e));
     cudaGetLastError();
     return FE_ERR_OOM;
   }
@@ -755,9 +758,9 @@ static int create_impl(const fe_mesh_desc* desc, fe_mesh m) {
     if (rem == 0) break;
   }
   FE_TRY(fe_check_device_error(m));
-  cudaFree(d_vptr);
-  cudaFree(d_vel);
-  cudaFree(d_rem);
+  cudaFreeAsync(d_vptr, m->stream);
+  cudaFreeAsync(d_vel, m->stream);
+  cudaFreeAsync(d_rem, m->stream);
   m->device_bytes -= (int64_t)(vptr.size() + vel.size() + 1) * sizeof(int);
   std::vector<int> colors(ne);
   FE_CUDA(cudaMemcpy(colors.data(), m->colors, sizeof(int) * ne, cudaMemcpyDeviceToHost));
@@ -807,9 +810,12 @@ static void free_all(fe_mesh m) {
                   m->ks_kpos, m->K64, m->K32, m->K16, m->B64, m->B32, m->Dinv64, m->Dinv32,
                   m->Sd, m->rel, m->relp, m->red, m->red_ticket, m->scal, m->bar, m->V,
                   m->H, m->gv, m->w64, m->t64, m->u64, m->zx, m->S, m->Yv, m->nl_R, m->nl_Rn,
-                  m->nl_dl, m->nl_t, m->rho_d, m->lb_x, m->alpha_d, m->Lmat, m->hpub, m->partv, m->Tbm};
+                  m->nl_dl, m->nl_t, m->rho_d, m->lb_x, m->alpha_d, m->Lmat, m->hpub, m->partv, m->Tbm,
+                  m->ff_nodes, m->ff_kind, m->ff_data, m->fn_ptr, m->fn_list, m->fk_ptr, m->fk_list, m->kc_val,
+                  m->dyn_keep};
   for (void* p : ptrs)
-    if (p) cudaFree(p);
+    if (p) cudaFreeAsync(p, m->stream);
+  cudaStreamSynchronize(m->stream);
   if (m->h_scal) cudaFreeHost(m->h_scal);
 }
 

@@ -10,8 +10,9 @@
 //
 // Small requests that the batched solver supports (fe_batch.h) are handed
 // by their worker, once the mesh is built, to batcher threads: a batcher
-// takes every waiting request of one (order, precision) and solves them in
-// one launch, one CTA each; requests that arrive meanwhile wait for the next
+// takes every waiting request of one size class (order, precision,
+// floor(log2 ndof)) and solves them in one launch, one CTA each; requests
+// that arrive meanwhile wait for the next
 // launch (continuous batching at launch granularity).  Its launch shape
 // (threads per CTA) comes from a small autotuner per size class.
 #include <algorithm>
@@ -129,7 +130,7 @@ struct fe_server_s {
   std::map<int64_t, std::thread> workers;  // running requests' threads, by request id
   std::vector<int64_t> finished;           // workers that have returned, to be joined
   // batched path
-  int64_t batch_max_dofs = 60000;
+  int64_t batch_max_dofs = 4000;
   std::deque<BatchItem*> bq;               // requests waiting for a batched launch
   std::condition_variable bcv;             // batchers wait here; items are signalled on cv
   std::vector<std::thread> batchers;
@@ -168,7 +169,7 @@ static void run_request(fe_server s, Request* r) {
       fe_set_error("initial guess has %zu entries, mesh has %lld unknowns", r->d0.size(), (long long)ndof);
     }
   }
-  if (rc == FE_OK && cudaMalloc(&d, ndof * sizeof(double)) != cudaSuccess) {
+  if (rc == FE_OK && cudaMallocAsync((void**)&d, ndof * sizeof(double), stream) != cudaSuccess) {
     rc = FE_ERR_OOM;
     fe_set_error("cudaMalloc of the solution vector failed");
   }
@@ -231,7 +232,7 @@ static void run_request(fe_server s, Request* r) {
     }
   }
   std::string err = rc < 0 ? std::string(fe_last_error()) : std::string();
-  if (d) cudaFree(d);
+  if (d) cudaFreeAsync(d, stream);
   if (m) fe_mesh_destroy(m);
   if (stream) cudaStreamDestroy(stream);
   {
@@ -267,29 +268,28 @@ static void join_finished(fe_server s, std::unique_lock<std::mutex>& lk) {
 }
 
 // Batcher thread: takes every waiting request of the first waiting
-// request's (order, precision), solves them in one launch with the
-// autotuner's shape, and signals their workers.
+// request's size class, solves them in one launch with the autotuner's
+// shape, and signals their workers.
 static void batcher_loop(fe_server s) {
   cudaSetDevice(s->device);
   std::unique_lock<std::mutex> lk(s->mu);
   for (;;) {
     s->bcv.wait(lk, [s] { return s->stop_batch || !s->bq.empty(); });
     if (s->bq.empty()) break;  // stopping and nothing left
-    const int order = s->bq.front()->m->order;
-    const int prec = s->bq.front()->r->opts.precision;
+    // one size class per launch (order, precision, floor(log2 ndof)): a
+    // launch lasts as long as its slowest request, so small requests do not
+    // wait for large ones
+    const BatchItem* f = s->bq.front();
+    const int64_t key = tune_key(f->m->order, f->r->opts.precision, f->ndof);
     std::vector<BatchItem*> take;
     for (auto it = s->bq.begin(); it != s->bq.end();) {
-      if ((*it)->m->order == order && (*it)->r->opts.precision == prec) {
+      if (tune_key((*it)->m->order, (*it)->r->opts.precision, (*it)->ndof) == key) {
         take.push_back(*it);
         it = s->bq.erase(it);
       } else {
         ++it;
       }
     }
-    // launch shape: the class of the largest request decides
-    int64_t nmax = 0;
-    for (BatchItem* b : take) nmax = std::max(nmax, b->ndof);
-    const int64_t key = tune_key(order, prec, nmax);
     TuneEntry& te = s->tune[key];
     int slot = te.chosen ? (te.chosen == 128 ? 0 : 1) : (te.batches[0] <= te.batches[1] ? 0 : 1);
     const int threads = slot == 0 ? 128 : 256;
@@ -377,9 +377,9 @@ extern "C" int serve_create(const fe_server_opts* opts, fe_server* out) {
   s->device = opts->device;
   s->budget = opts->hbm_budget > 0 ? opts->hbm_budget : (int64_t)(0.8 * (double)free_b);
   s->max_active = opts->max_active > 0 ? opts->max_active : 8;
-  s->batch_max_dofs = opts->batch_max_dofs == 0 ? 60000 : opts->batch_max_dofs;
+  s->batch_max_dofs = opts->batch_max_dofs == 0 ? 4000 : opts->batch_max_dofs;
   s->scheduler = std::thread(scheduler_loop, s);
-  for (int i = 0; i < 2; i++) s->batchers.emplace_back(batcher_loop, s);
+  for (int i = 0; i < 4; i++) s->batchers.emplace_back(batcher_loop, s);
   *out = s;
   return FE_OK;
 }

@@ -145,8 +145,8 @@ static int solve_impl(fe_mesh m, int method, double tol, int max_it, double* d, 
     if (mcap < 1 || mcap > LBFGS_MAX) return fe_set_error("lbfgs_m must lie in [1, %d]", LBFGS_MAX), FE_ERR_ARG;
     if (m->lb_m < mcap) {
       if (m->S) {
-        cudaFree(m->S);
-        cudaFree(m->Yv);
+        cudaFreeAsync(m->S, m->stream);
+        cudaFreeAsync(m->Yv, m->stream);
         m->device_bytes -= 2LL * m->lb_m * n * 8;
         m->S = m->Yv = nullptr;
       }
