@@ -71,8 +71,8 @@ def parse():
     p.add_argument("--serve", type=int, default=0,
                    help="serving mix: number of requests of the seeded Poisson stream (0 = off)")
     p.add_argument("--serve-max-dofs", type=float, default=5e4)
-    p.add_argument("--serve-slots", type=int, default=16)
-    p.add_argument("--serve-batch-dofs", type=float, default=4e3,
+    p.add_argument("--serve-slots", type=int, default=64)
+    p.add_argument("--serve-batch-dofs", type=float, default=1e3,
                    help="serving: requests up to this size run in shared launches (0: never)")
     p.add_argument("--serve-rate", type=float, default=4.0,
                    help="offered load: arrival rate as a multiple of the measured one-at-a-time capacity "

@@ -9,7 +9,8 @@
  * requests overlaps on the device.  Small requests (fe_batch.h) are instead
  * handed to batcher threads that solve all such requests waiting at that
  * moment in one launch (one CTA per request), so requests that arrive while
- * a batch runs form the next one.  Results are the same as a solve of the
+ * a batch runs form the next one.  Meshes stay resident between requests
+ * with the same description (fe_server_opts.mesh_cache).  Results are the same as a solve of the
  * same request alone (same kernels, same launch shapes, deterministic
  * reductions; a batched request's result does not depend on its batch).
  * Each request is one call of nl_solve (include/fe.h) or its batched form,
@@ -37,8 +38,16 @@ typedef struct {
   int64_t batch_max_dofs; /* requests up to this many unknowns that fe_batch_supported
                              accepts are solved in shared launches (fe_batch.h), one
                              launch per size class (order, precision, floor(log2
-                             ndof)); 0 = 4000 (where one CTA still solves a request
-                             about as fast as the whole GPU does), < 0 = never */
+                             ndof)); 0 = 1000 (up to where one CTA solves a
+                             request about as fast as the whole GPU does; a launch
+                             lasts as long as its slowest request and holds its SMs
+                             meanwhile), < 0 = never */
+  int32_t mesh_cache;     /* 0 = a mesh whose solve ran stays resident on the device
+                             (pattern, colouring, AMG structure, workspace) and the
+                             next request with a byte-identical description reuses
+                             it; resident meshes keep their admission charge and
+                             are evicted least recently used when a request needs
+                             the room; < 0 = every request builds and frees its own */
 } fe_server_opts;
 
 /* One entry of the launch-shape autotuner of the batched path: per size
@@ -72,6 +81,7 @@ typedef struct {
   int64_t footprint;     /* admission estimate of its device bytes */
   double t_submit, t_start, t_end; /* seconds on the server's steady clock */
   nl_stats stats;        /* filled when DONE */
+  int32_t mesh_reused;   /* 1: ran on a resident mesh of an earlier request */
 } fe_request_status;
 
 /* Create a server and start its scheduler thread. */

@@ -98,7 +98,7 @@ class fe_profile_info(C.Structure):
 
 class fe_server_opts(C.Structure):
     _fields_ = [("device", C.c_int32), ("hbm_budget", C.c_int64), ("max_active", C.c_int32),
-                ("batch_max_dofs", C.c_int64)]
+                ("batch_max_dofs", C.c_int64), ("mesh_cache", C.c_int32)]
 
 
 class fe_tuning_entry(C.Structure):
@@ -114,7 +114,8 @@ class fe_request(C.Structure):
 
 class fe_request_status(C.Structure):
     _fields_ = [("state", C.c_int32), ("result", C.c_int32), ("ndof", C.c_int64), ("footprint", C.c_int64),
-                ("t_submit", C.c_double), ("t_start", C.c_double), ("t_end", C.c_double), ("stats", nl_stats)]
+                ("t_submit", C.c_double), ("t_start", C.c_double), ("t_end", C.c_double), ("stats", nl_stats),
+                ("mesh_reused", C.c_int32)]
 
 
 REQ_STATES = {0: "queued", 1: "running", 2: "done", 3: "failed"}
@@ -491,11 +492,11 @@ def _stats_dict(st):
 class Server:
     """Continuous-batching request loop on one GPU (include/fe_serve.h)."""
 
-    def __init__(self, device=0, hbm_budget=0, max_active=8, batch_max_dofs=0):
+    def __init__(self, device=0, hbm_budget=0, max_active=8, batch_max_dofs=0, mesh_cache=True):
         import torch
         torch.cuda.init()
         o = fe_server_opts(device=int(device), hbm_budget=int(hbm_budget), max_active=int(max_active),
-                           batch_max_dofs=int(batch_max_dofs))
+                           batch_max_dofs=int(batch_max_dofs), mesh_cache=0 if mesh_cache else -1)
         h = C.c_void_p()
         _check(lib().serve_create(C.byref(o), C.byref(h)))
         self.h = h
@@ -527,7 +528,7 @@ class Server:
         st = fe_request_status()
         _check(lib().serve_poll(self.h, int(rid), 1 if wait else 0, C.byref(st), None))
         out = dict(state=REQ_STATES[st.state], result=st.result, ndof=int(st.ndof), footprint=int(st.footprint),
-                   t_submit=st.t_submit, t_start=st.t_start, t_end=st.t_end)
+                   t_submit=st.t_submit, t_start=st.t_start, t_end=st.t_end, mesh_reused=bool(st.mesh_reused))
         if st.state == 2:
             x = np.zeros(int(st.ndof))
             _check(lib().serve_poll(self.h, int(rid), 0, C.byref(st), _np_ptr(x)))

@@ -874,6 +874,21 @@ __global__ void __launch_bounds__(256) k_vc_cheb(int n, const int* __restrict__ 
   const int row = (int)(((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
   const int lane = threadIdx.x & 31;
   if (row >= n) return;
+  // lane q < B updates component q of the row (cheb_rows' arithmetic); its
+  // operands are loaded before the row's products, so their latency overlaps
+  const bool wx = !(flags & VC_KEEPX), rx = wx && !(flags & VC_SETX);
+  const int64_t o = (int64_t)B * row;
+  T gq = T(0), rq = T(0), xq = T(0), dq[B];
+#pragma unroll
+  for (int j = 0; j < B; j++) dq[j] = T(0);
+  if (lane < B) {
+    gq = g[o + lane];
+    rq = r[o + lane];
+    if (rx) xq = x[o + lane];
+    if (dout)
+#pragma unroll
+      for (int j = 0; j < B; j++) dq[j] = dinv[(int64_t)row * B * B + B * lane + j];
+  }
   T s[B];
 #pragma unroll
   for (int q = 0; q < B; q++) s[q] = T(0);
@@ -890,7 +905,30 @@ __global__ void __launch_bounds__(256) k_vc_cheb(int n, const int* __restrict__ 
 #pragma unroll
   for (int q = 0; q < B; q++)
     for (int off = 16; off > 0; off >>= 1) s[q] += __shfl_xor_sync(0xffffffffu, s[q], off);
-  if (lane == 0) cheb_rows<T, B>(row, s, dinv, g, x, r, dout, cx, coef, flags);
+  // this lane's component of the new residual, then every lane gets all of them
+  T sq = T(0);
+#pragma unroll
+  for (int q = 0; q < B; q++)
+    if (q == lane) sq = s[q];
+  const T rn_q = rq - sq;
+  T rn[B];
+#pragma unroll
+  for (int j = 0; j < B; j++) rn[j] = __shfl_sync(0xffffffffu, rn_q, j);
+  if (lane < B) {
+    r[o + lane] = rn_q;
+    T xi = xq + cx * gq;
+    if (dout) {
+      const T c1 = (flags & VC_START) ? T(0) : coef[1];
+      const T c2 = (flags & VC_START) ? coef[0] : coef[2];
+      T t = T(0);
+#pragma unroll
+      for (int j = 0; j < B; j++) t += dq[j] * rn[j];
+      const T dn = c1 * gq + c2 * t;
+      dout[o + lane] = dn;
+      if (flags & VC_FINAL) xi += dn;
+    }
+    if (wx) x[o + lane] = xi;
+  }
 }
 
 // level-0 start of the pre-smoothing: r = b, d = D^-1 b / theta

@@ -13,8 +13,9 @@
 // takes every waiting request of one size class (order, precision,
 // floor(log2 ndof)) and solves them in one launch, one CTA each; requests
 // that arrive meanwhile wait for the next
-// launch (continuous batching at launch granularity).  Its launch shape
-// (threads per CTA) comes from a small autotuner per size class.
+// launch (continuous batching at launch granularity); there is one batcher
+// per slot, so a lone request is not held back.  The launch shape (threads
+// per CTA) comes from a small autotuner per size class.
 #include <algorithm>
 #include <chrono>
 #include <condition_variable>
@@ -49,7 +50,50 @@ struct Request {
   fe_request_status st{};
   std::vector<double> result;
   std::string error;
+  std::string mesh_key;            // the description's bytes (cache identity)
+  size_t key_hash = 0;
+  struct CachedMesh* cm = nullptr;  // the resident mesh it runs on, if any
+  std::vector<struct CachedMesh*> victims;  // idle meshes evicted to admit it
+  int64_t charge = 0;              // budget bytes it holds itself while running
 };
+
+// A mesh kept on the device between requests with the same description:
+// its pattern, colouring, AMG structure and workspace stay resident, and
+// the next request skips building them.  One request uses it at a time.
+struct CachedMesh {
+  std::string key;
+  size_t key_hash = 0;
+  fe_mesh m = nullptr;
+  cudaStream_t stream = nullptr;
+  int64_t bytes = 0;  // the admission charge it holds while resident
+  bool busy = false;
+  uint64_t last_used = 0;
+};
+
+// exact identity of a mesh description (geometry, topology, boundary data,
+// material, fibres); fe_material has no padding
+std::string mesh_key(const Request& r) {
+  const fe_mesh_desc& d = r.desc;
+  std::string k;
+  auto put = [&](const void* p, size_t n) { k.append(reinterpret_cast<const char*>(p), n); };
+  const int32_t hdr[6] = {d.order, d.pressure_order, d.nv, d.ne, d.ngroups, d.nf};
+  put(hdr, sizeof(hdr));
+  put(&d.material, sizeof(d.material));
+  put(r.coords.data(), r.coords.size() * sizeof(double));
+  put(r.tets.data(), r.tets.size() * sizeof(int32_t));
+  put(r.dir_group.data(), r.dir_group.size());
+  for (const fe_dirichlet_group& g : r.groups) {  // field by field: the struct has padding
+    put(&g.comp_mask, sizeof(g.comp_mask));
+    put(g.center, sizeof(g.center));
+    put(&g.angle, sizeof(g.angle));
+    put(g.translation, sizeof(g.translation));
+  }
+  put(r.faces.data(), r.faces.size() * sizeof(int32_t));
+  put(r.face_kind.data(), r.face_kind.size() * sizeof(int32_t));
+  put(r.face_data.data(), r.face_data.size() * sizeof(double));
+  put(r.fibers.data(), r.fibers.size() * sizeof(double));
+  return k;
+}
 
 // device bytes a request will hold, estimated from its description before
 // anything is allocated (exact node count; block count from the measured
@@ -130,34 +174,51 @@ struct fe_server_s {
   std::map<int64_t, std::thread> workers;  // running requests' threads, by request id
   std::vector<int64_t> finished;           // workers that have returned, to be joined
   // batched path
-  int64_t batch_max_dofs = 4000;
+  bool cache_on = true;
+  int64_t batch_max_dofs = 1000;
   std::deque<BatchItem*> bq;               // requests waiting for a batched launch
   std::condition_variable bcv;             // batchers wait here; items are signalled on cv
   std::vector<std::thread> batchers;
   std::map<int64_t, TuneEntry> tune;
   bool stop_batch = false;
+  std::vector<std::unique_ptr<CachedMesh>> cache;  // resident meshes
+  uint64_t tick = 0;
   std::chrono::steady_clock::time_point t0 = std::chrono::steady_clock::now();
   double now() const {
     return std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
   }
 };
 
+static void release_mesh(CachedMesh* c) {
+  if (c->m) fe_mesh_destroy(c->m);
+  if (c->stream) cudaStreamDestroy(c->stream);
+  delete c;
+}
+
 static void run_request(fe_server s, Request* r) {
   int rc = FE_OK;
-  cudaStream_t stream = nullptr;
-  fe_mesh m = nullptr;
   double* d = nullptr;
   nl_stats stats{};
   std::vector<double> out;
   cudaSetDevice(s->device);
-  if (cudaStreamCreateWithFlags(&stream, cudaStreamNonBlocking) != cudaSuccess) {
-    rc = FE_ERR_CUDA;
-    fe_set_error("cudaStreamCreate failed");
+  // idle resident meshes the scheduler evicted to make room for this one
+  for (CachedMesh* v : r->victims) release_mesh(v);
+  r->victims.clear();
+  // the resident mesh of the same description, or a new one
+  const bool reused = r->cm != nullptr;
+  CachedMesh* c = reused ? r->cm : new CachedMesh();
+  if (!reused) {
+    if (cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking) != cudaSuccess) {
+      rc = FE_ERR_CUDA;
+      fe_set_error("cudaStreamCreate failed");
+    }
+    fe_mesh_desc desc = r->desc;
+    desc.device = s->device;
+    desc.stream = c->stream;
+    if (rc == FE_OK) rc = fe_mesh_create(&desc, &c->m);
   }
-  fe_mesh_desc desc = r->desc;
-  desc.device = s->device;
-  desc.stream = stream;
-  if (rc == FE_OK) rc = fe_mesh_create(&desc, &m);
+  cudaStream_t stream = c->stream;
+  fe_mesh m = c->m;
   if (rc == FE_OK) rc = fe_set_load(m, r->load, r->time);
   int64_t ndof = 0;
   if (rc == FE_OK) {
@@ -233,8 +294,11 @@ static void run_request(fe_server s, Request* r) {
   }
   std::string err = rc < 0 ? std::string(fe_last_error()) : std::string();
   if (d) cudaFreeAsync(d, stream);
-  if (m) fe_mesh_destroy(m);
-  if (stream) cudaStreamDestroy(stream);
+  // a mesh whose solve ran (converged or not) stays resident for the next
+  // request of the same description; one that failed to build or met a
+  // CUDA error is freed
+  const bool keep = s->cache_on && rc >= 0;
+  CachedMesh* drop = nullptr;
   {
     std::lock_guard<std::mutex> lk(s->mu);
     r->st.t_end = s->now();
@@ -243,10 +307,35 @@ static void run_request(fe_server s, Request* r) {
     r->st.stats = stats;
     r->result.swap(out);
     r->error = err;
-    s->used -= r->st.footprint;
+    if (reused) {
+      c->busy = false;
+      c->last_used = ++s->tick;
+      if (!keep) {  // unlink it; its charge goes with it
+        for (auto it = s->cache.begin(); it != s->cache.end(); ++it)
+          if (it->get() == c) {
+            it->release();
+            s->cache.erase(it);
+            break;
+          }
+        s->used -= c->bytes;
+        drop = c;
+      }
+    } else if (keep) {  // the request's charge becomes the resident mesh's
+      c->key.swap(r->mesh_key);
+      c->key_hash = r->key_hash;
+      c->bytes = r->charge;
+      c->last_used = ++s->tick;
+      s->cache.emplace_back(c);
+    } else {
+      s->used -= r->charge;
+      drop = c;
+    }
+    r->charge = 0;
+    r->cm = nullptr;
     s->active--;
     s->finished.push_back(r->id);
   }
+  if (drop) release_mesh(drop);
   s->cv.notify_all();
 }
 
@@ -351,16 +440,62 @@ static void scheduler_loop(fe_server s) {
         s->cv.notify_all();
         continue;
       }
-      if (s->active < s->max_active && s->used + r->st.footprint <= s->budget) {
-        s->used += r->st.footprint;
-        s->active++;
-        r->st.state = FE_REQ_RUNNING;
-        it = s->queue.erase(it);
-        s->workers.emplace(r->id, std::thread(run_request, s, r));
-        admitted = true;
+      if (s->active >= s->max_active) {  // no slot (later oversized requests are still rejected)
+        ++it;
         continue;
       }
-      ++it;
+      // an idle resident mesh of the same description is reused; the
+      // request is then charged only what it needs beyond that mesh's charge
+      CachedMesh* hit = nullptr;
+      if (s->cache_on)
+        for (auto& c : s->cache)
+          if (!c->busy && c->key_hash == r->key_hash && c->key == r->mesh_key) {
+            hit = c.get();
+            break;
+          }
+      const int64_t need = hit ? std::max<int64_t>(0, r->st.footprint - hit->bytes) : r->st.footprint;
+      if (s->used + need > s->budget) {
+        // room from idle resident meshes, least recently used first
+        std::vector<CachedMesh*> idle;
+        int64_t idle_bytes = 0;
+        for (auto& c : s->cache)
+          if (!c->busy && c.get() != hit) {
+            idle.push_back(c.get());
+            idle_bytes += c->bytes;
+          }
+        if (s->used - idle_bytes + need > s->budget) {
+          ++it;
+          continue;
+        }
+        std::sort(idle.begin(), idle.end(),
+                  [](const CachedMesh* a, const CachedMesh* b) { return a->last_used < b->last_used; });
+        for (CachedMesh* v : idle) {
+          if (s->used + need <= s->budget) break;
+          for (auto ci = s->cache.begin(); ci != s->cache.end(); ++ci)
+            if (ci->get() == v) {
+              ci->release();
+              s->cache.erase(ci);
+              break;
+            }
+          s->used -= v->bytes;
+          r->victims.push_back(v);  // freed by the request's worker before it builds
+        }
+      }
+      s->used += need;
+      s->active++;
+      if (hit) {
+        hit->busy = true;
+        hit->bytes += need;
+        r->cm = hit;
+        r->charge = 0;
+        r->st.mesh_reused = 1;
+      } else {
+        r->charge = need;
+      }
+      r->st.state = FE_REQ_RUNNING;
+      it = s->queue.erase(it);
+      s->workers.emplace(r->id, std::thread(run_request, s, r));
+      admitted = true;
     }
     if (s->stop && s->queue.empty() && s->active == 0) break;
     if (!admitted) s->cv.wait(lk);
@@ -377,9 +512,12 @@ extern "C" int serve_create(const fe_server_opts* opts, fe_server* out) {
   s->device = opts->device;
   s->budget = opts->hbm_budget > 0 ? opts->hbm_budget : (int64_t)(0.8 * (double)free_b);
   s->max_active = opts->max_active > 0 ? opts->max_active : 8;
-  s->batch_max_dofs = opts->batch_max_dofs == 0 ? 4000 : opts->batch_max_dofs;
+  s->batch_max_dofs = opts->batch_max_dofs == 0 ? 1000 : opts->batch_max_dofs;
+  s->cache_on = opts->mesh_cache >= 0;
   s->scheduler = std::thread(scheduler_loop, s);
-  for (int i = 0; i < 4; i++) s->batchers.emplace_back(batcher_loop, s);
+  // one batcher per slot: a lone small request launches at once, and
+  // requests that wait together share a launch
+  for (int i = 0; i < s->max_active; i++) s->batchers.emplace_back(batcher_loop, s);
   *out = s;
   return FE_OK;
 }
@@ -426,6 +564,8 @@ extern "C" int serve_submit(fe_server s, const fe_request* q, int64_t* id_out) {
   r->time = q->time;
   int64_t ndof = 0;
   r->st.footprint = estimate_footprint(*r, &ndof);
+  r->mesh_key = mesh_key(*r);
+  r->key_hash = std::hash<std::string>{}(r->mesh_key);
   if (q->d0) r->d0.assign(q->d0, q->d0 + ndof);
   r->st.state = FE_REQ_QUEUED;
   {
@@ -492,6 +632,8 @@ extern "C" int serve_destroy(fe_server s) {
   }
   s->bcv.notify_all();
   for (auto& t : s->batchers) t.join();
+  for (auto& c : s->cache) release_mesh(c.release());
+  s->cache.clear();
   delete s;
   return FE_OK;
 }

@@ -106,7 +106,7 @@ def test_small_requests_are_batched_and_match_alone(fe):
         assert st["status"] == 0, (meth, st["res_hist"][-3:])
         alone.append(d.cpu().numpy())
         m.close()
-    srv = fe.Server(max_active=32)
+    srv = fe.Server(max_active=32, batch_max_dofs=4000)
     ids = [srv.submit(w, meth, tol=1e-8, opts=opts, load=load, time=tm) for w, meth, opts, (load, tm) in reqs]
     res = [srv.poll(i, wait=True) for i in ids]
     tune = srv.tuning()
@@ -118,3 +118,49 @@ def test_small_requests_are_batched_and_match_alone(fe):
         else:
             assert np.abs(r["d"] - a).max() <= 1e-12 * np.abs(a).max()
     assert tune and sum(sum(e["batches"]) for e in tune) >= 2
+
+
+def test_resident_mesh_is_reused_and_matches_a_fresh_one(fe):
+    """A request whose mesh description matches an earlier request's runs on
+    that request's resident mesh (pattern, colouring, AMG structure and
+    workspace kept); its result is bit-identical to a solve on a freshly
+    built mesh, whatever the earlier request's load, method and
+    preconditioner were."""
+    w = W.cook(6, 6, 2, order=2, nu=0.3)
+    amg = dict(precision="mixed_fp32", pc_type="amg", ksp_restart=30)
+    bj = dict(precision="fp64", ksp_atol=0.0, ksp_restart=30)
+    seq = [("NK", amg, 0.2), ("iB", bj, 0.3), ("NK", amg, 0.2), ("iNK", bj, 0.1)]
+    fresh = []
+    for meth, opts, load in seq:
+        m = fe.Mesh(w)
+        m.set_load(load, 0.0)
+        d, st = m.solve(meth, m.zeros(), tol=1e-8, opts=opts)
+        assert st["status"] == 0, (meth, st["res_hist"][-3:])
+        fresh.append(d.cpu().numpy())
+        m.close()
+    for cache in (True, False):
+        srv = fe.Server(max_active=1, batch_max_dofs=-1, mesh_cache=cache)
+        res = [srv.poll(srv.submit(w, meth, tol=1e-8, opts=opts, load=load), wait=True) for meth, opts, load in seq]
+        srv.close()
+        assert [r["mesh_reused"] for r in res] == [False] + [cache] * 3
+        for r, a, (meth, _, _) in zip(res, fresh, seq):
+            assert r["state"] == "done" and r["result"] == 0, (meth, r)
+            assert np.array_equal(r["d"], a), (cache, meth)
+
+
+def test_resident_meshes_are_evicted_least_recently_used(fe):
+    """Resident meshes keep their admission charge; a request that needs the
+    room evicts the least recently used idle one."""
+    a = W.cook(4, 4, 2, order=1, nu=0.3)
+    b = W.cook(5, 5, 2, order=1, nu=0.3)
+    srv = fe.Server(max_active=1, batch_max_dofs=-1)
+    fa = srv.poll(srv.submit(a, "NK", load=0.1), wait=True)["footprint"]
+    fb = srv.poll(srv.submit(b, "NK", load=0.1), wait=True)["footprint"]
+    r = srv.poll(srv.submit(a, "NK", load=0.2), wait=True)
+    srv.close()
+    assert r["state"] == "done" and r["mesh_reused"]  # room for both: a stays resident
+    srv = fe.Server(hbm_budget=fa + fb - 1, max_active=1, batch_max_dofs=-1)  # room for one
+    res = [srv.poll(srv.submit(x, "NK", load=0.1), wait=True) for x in (a, b, a, a)]
+    srv.close()
+    assert all(x["state"] == "done" for x in res)
+    assert [x["mesh_reused"] for x in res] == [False, False, False, True]
