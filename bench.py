@@ -13,6 +13,13 @@ workspace are resident in HBM before the timed region; the timed working set
 (tangent 280-560 MB, Krylov basis 3.4 GB) is far larger than L2, so no flush
 is needed between steps.
 
+After the timed region the line adds, measured outside it: each method in
+FP64 and mixed precision with its error against the FP64 oracle's solution,
+the other configurations (Cook P1, the twist, the cardiac shell quasi-static
+and as an elastodynamic heartbeat) and a bounded sample of the serving mix
+(--serve-sample requests up to --serve-sample-max-dofs unknowns); --serve N
+prints the serving mix alone as the line.
+
 Multi-GPU: replicas only -- every rank solves its own copy of the workload on
 its own GPU, no data-path collective; value = solves of all ranks / max time.
 
@@ -78,6 +85,10 @@ def parse():
                    help="offered load: arrival rate as a multiple of the measured one-at-a-time capacity "
                         "(above 1 the queue fills and the served rate is the server's capacity)")
     p.add_argument("--serve-precision", default="mixed_fp32", choices=["fp64", "mixed_fp32"])
+    p.add_argument("--serve-sample", type=int, default=32,
+                   help="requests of the serving mix measured after the timed region of the default line "
+                        "(sizes up to --serve-sample-max-dofs; 0 = off)")
+    p.add_argument("--serve-sample-max-dofs", type=float, default=4e3)
     return p.parse_args()
 
 
@@ -409,21 +420,28 @@ def serving_workload(req, max_dofs):
 
 
 def run_serving(args):
+    """--serve N: the serving mix as the JSON line (see serve_mix)."""
+    out = serve_mix(args.serve, args.serve_max_dofs, args.serve_slots, args.serve_batch_dofs, args.serve_rate,
+                    args.serve_precision, args.restart, args.orthog, per_request=True)
+    print(json.dumps(out), flush=True)
+
+
+def serve_mix(nreq, max_dofs, slots, batch_dofs, rate, precision, restart, orthog, per_request=False):
     """Serving mix: the seeded Poisson stream served with continuous batching
     in the mixed form (small requests in shared launches, the rest on their
     own streams), against the plain FP64 solve of each request one at a time;
-    arrivals at --serve-rate times the one-at-a-time capacity.  Both forms
-    solve to the same relative residual; each served result's difference
-    from the FP64 solution is reported."""
+    arrivals at `rate` times the one-at-a-time capacity.  Both forms solve to
+    the same relative residual; each served result's difference from the
+    FP64 solution is reported (per request on stderr with per_request)."""
     import numpy as np
     import torch
     import paper_2203_05610_gb300 as fe
     import workloads as W
-    reqs = W.serving_stream(nreq=args.serve)
-    jobs = [serving_workload(r, args.serve_max_dofs) for r in reqs]
-    base = dict(ksp_restart=args.restart, orthog=args.orthog)
+    reqs = W.serving_stream(nreq=nreq)
+    jobs = [serving_workload(r, max_dofs) for r in reqs]
+    base = dict(ksp_restart=restart, orthog=orthog)
     bopts = dict(base, precision="fp64")
-    sopts = dict(base, precision=args.serve_precision)
+    sopts = dict(base, precision=precision)
     # plain FP64 one at a time (also warms up the library)
     t_solo, solo_st, solo_x = [], [], []
     for w, meth, load, tm, _ in jobs:
@@ -441,9 +459,8 @@ def run_serving(args):
     cap = solo_ok / sum(t_solo)
     # arrivals: the stream's exponential gaps rescaled to rate x capacity
     arr = np.array([r["arrival"] for r in reqs])
-    arr = (arr - arr[0]) / (arr[-1] - arr[0] + 1e-12) * (len(jobs) / (args.serve_rate * cap))
-    srv = fe.Server(max_active=args.serve_slots, batch_max_dofs=int(args.serve_batch_dofs) if args.serve_batch_dofs
-                    else -1)
+    arr = (arr - arr[0]) / (arr[-1] - arr[0] + 1e-12) * (len(jobs) / (rate * cap))
+    srv = fe.Server(max_active=slots, batch_max_dofs=int(batch_dofs) if batch_dofs else -1)
     t0 = srv.clock()
     ids = []
     for (w, meth, load, tm, _), a in zip(jobs, arr):
@@ -463,22 +480,24 @@ def run_serving(args):
         if r["state"] == "done" and r["result"] == 0 and ss == 0:
             rd = float(np.linalg.norm(r["d"] - xs) / max(np.linalg.norm(xs), 1e-300))
             diffs.append(rd)
+        if not per_request:
+            continue
         print(json.dumps(dict(request=name, ndof=r["ndof"], solo_fp64_s=round(ts, 4), solo_status=int(ss),
                               served_state=r["state"], served_result=r["result"],
                               served_run_s=round(r["t_end"] - r["t_start"], 4),
                               latency_s=round(r["t_end"] - r["t_submit"], 4), rel_diff_vs_fp64=rd)),
               file=sys.stderr)
-    eligible = sum(1 for w, *_ in jobs if w["pressure_order"] == 0) if args.serve_batch_dofs else 0
+    eligible = sum(1 for w, *_ in jobs if w["pressure_order"] == 0) if batch_dofs else 0
     out = dict(metric=METRIC, value=round(len(done) / span, 4), unit="solves/s", n_gpus=1, steps=len(jobs),
                warmup=0, ms_per_step=round(1e3 * span / len(jobs), 3), higher_is_better=True, scaling="weak",
-               vs_baseline=None, dtype="f32+f64" if args.serve_precision == "mixed_fp32" else "f64",
+               vs_baseline=None, dtype="f32+f64" if precision == "mixed_fp32" else "f64",
                data="synthetic",
                config=dict(workload="serving_mix", requests=len(jobs), seed=20220311,
-                           dofs_range=[1e3, args.serve_max_dofs], slots=args.serve_slots,
-                           batch_max_dofs=args.serve_batch_dofs, ksp_restart=args.restart,
-                           orthog=["mgs", "mgs_lowsync", "mgs_blocked"][args.orthog], method="iNK",
+                           dofs_range=[1e3, max_dofs], slots=slots,
+                           batch_max_dofs=batch_dofs, ksp_restart=restart,
+                           orthog=["mgs", "mgs_lowsync", "mgs_blocked"][orthog], method="iNK",
                            preconditioner="nodal block-Jacobi", tol=TOL,
-                           arrival_rate_x_capacity=args.serve_rate, precision=args.serve_precision,
+                           arrival_rate_x_capacity=rate, precision=precision,
                            families={n: sum(1 for j in jobs if j[4].startswith(n)) for n in ("cook", "twist", "heart")},
                            displacement_form_requests=eligible),
                p50_latency_s=round(float(np.percentile(lat, 50)), 4) if len(lat) else None,
@@ -492,7 +511,7 @@ def run_serving(args):
                baseline_fp64_one_at_a_time=dict(value=round(cap, 4), unit="solves/s", failed=len(jobs) - solo_ok,
                                                  p50_solve_s=round(float(np.percentile(solo, 50)), 4),
                                                  p99_solve_s=round(float(np.percentile(solo, 99)), 4)))
-    print(json.dumps(out), flush=True)
+    return out
 
 
 def oracle_solution(name):
@@ -708,6 +727,12 @@ def main():
             ob = dict(ksp_restart=args.restart, orthog=args.orthog, pc_type=args.pc, precision=args.precision)
             dyn = dynamic_cardiac(dev, ob)
             others = other_configs(dev, ob)
+        serving = None
+        if not args.no_matrix and args.workload == "cook" and world == 1 and args.serve_sample > 0:
+            srv = serve_mix(args.serve_sample, args.serve_sample_max_dofs, args.serve_slots, args.serve_batch_dofs,
+                            args.serve_rate, args.serve_precision, args.restart, args.orthog)
+            serving = {k: v for k, v in srv.items() if k not in ("metric", "n_gpus", "steps", "warmup",
+                                                                  "higher_is_better", "scaling", "vs_baseline", "data")}
         pk, src = peaks()
         timed = {k: v for k, v in prof.items() if v["timed"] > 0}
         dom = max(timed, key=lambda k: timed[k]["ms"])
@@ -782,6 +807,12 @@ def main():
             out["dynamic_cardiac"] = dyn
         if others is not None:
             out["other_configs"] = others
+        if serving is not None:
+            out["serving_mix"] = dict(note="a bounded sample (see config) of the seeded Poisson stream of Cook, "
+                                           "twist and cardiac requests, "
+                                           "served in the mixed form with continuous batching against the plain "
+                                           "FP64 solve of each request one at a time; outside the timed region",
+                                      **serving)
         if cpu_proc is not None:
             try:
                 line = cpu_proc.communicate(timeout=900)[0].strip().splitlines()[-1]

@@ -863,17 +863,16 @@ __global__ void __launch_bounds__(256) k_vc_cheb0(int n, const int* __restrict__
   }
 }
 
-// Chebyshev step of a coarse level: one warp per block row (coarse rows
-// are few and long), one lane per block, values tiled
+// Chebyshev step of a coarse level, one block row per warp (coarse rows
+// are few and long), one lane per block, values tiled.  Device function of
+// warp-uniform `row` (< n): the kernel below runs it for its warp's row, the
+// fused bottom of the V-cycle (k_vc_bottom) for rows strided over its warps;
+// both sum in the same order, so their results are identical.  Vectors are
+// read with plain loads: in k_vc_bottom they were written by the same block.
 template <class T, int B>
-__global__ void __launch_bounds__(256) k_vc_cheb(int n, const int* __restrict__ ptr, const int* __restrict__ col,
-                                                 const T* __restrict__ val, const T* __restrict__ dinv,
-                                                 const T* __restrict__ g, T* __restrict__ x, T* __restrict__ r,
-                                                 T* __restrict__ dout, T cx, const T* __restrict__ coef,
-                                                 int flags) {
-  const int row = (int)(((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
-  const int lane = threadIdx.x & 31;
-  if (row >= n) return;
+__device__ __forceinline__ void vc_cheb_row(int row, int lane, int n, const int* ptr, const int* col, const T* val,
+                                            const T* dinv, const T* g, T* x, T* r, T* dout, T cx, const T* coef,
+                                            int flags) {
   // lane q < B updates component q of the row (cheb_rows' arithmetic); its
   // operands are loaded before the row's products, so their latency overlaps
   const bool wx = !(flags & VC_KEEPX), rx = wx && !(flags & VC_SETX);
@@ -931,6 +930,18 @@ __global__ void __launch_bounds__(256) k_vc_cheb(int n, const int* __restrict__ 
   }
 }
 
+template <class T, int B>
+__global__ void __launch_bounds__(256) k_vc_cheb(int n, const int* __restrict__ ptr, const int* __restrict__ col,
+                                                 const T* __restrict__ val, const T* __restrict__ dinv,
+                                                 const T* __restrict__ g, T* __restrict__ x, T* __restrict__ r,
+                                                 T* __restrict__ dout, T cx, const T* __restrict__ coef,
+                                                 int flags) {
+  const int row = (int)(((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+  const int lane = threadIdx.x & 31;
+  if (row >= n) return;
+  vc_cheb_row<T, B>(row, lane, n, ptr, col, val, dinv, g, x, r, dout, cx, coef, flags);
+}
+
 // level-0 start of the pre-smoothing: r = b, d = D^-1 b / theta
 template <class T>
 __global__ void k_vc_init0(int n, const T* __restrict__ dinv, const double* __restrict__ b, T* __restrict__ r,
@@ -956,18 +967,15 @@ __global__ void k_vc_init0(int n, const T* __restrict__ dinv, const double* __re
 // neighbours, hundreds of blocks at level 0), so a warp per row would leave
 // too few warps in flight; the block's partial sums are reduced in a fixed
 // order (deterministic).
+constexpr int VC_RESTRICT_THREADS = 128;
+
+// thread t's partial sums of coarse row a (entries t, t + 128, ...)
 template <class T, int BF>
-__global__ void __launch_bounds__(128) k_vc_restrict(int nc, const int* __restrict__ rptr, const int* __restrict__ rcol,
-                                                     const T* __restrict__ rv, const T* __restrict__ rf,
-                                                     const T* __restrict__ dinvc, T* __restrict__ rc,
-                                                     T* __restrict__ dc, const T* __restrict__ coefc, int nfine) {
-  __shared__ T sh[4][AMG_NS];
-  const int a = blockIdx.x;
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  T s[AMG_NS];
+__device__ __forceinline__ void vc_restrict_part(int a, int t, T (&s)[AMG_NS], const int* rptr, const int* rcol,
+                                                 const T* rv, const T* rf, int nfine) {
 #pragma unroll
   for (int q = 0; q < AMG_NS; q++) s[q] = T(0);
-  for (int k = rptr[a] + threadIdx.x; k < rptr[a + 1]; k += blockDim.x) {
+  for (int k = rptr[a] + t; k < rptr[a + 1]; k += VC_RESTRICT_THREADS) {
     const int i = fe_idx(__ldg(rcol + k), nfine);
     T f[BF];
 #pragma unroll
@@ -975,15 +983,18 @@ __global__ void __launch_bounds__(128) k_vc_restrict(int nc, const int* __restri
 #pragma unroll
     for (int q = 0; q < AMG_NS; q++)
 #pragma unroll
-      for (int j = 0; j < BF; j++) s[q] += rv[(int64_t)k * BF * AMG_NS + BF * q + j] * f[j];
+      for (int j = 0; j < BF; j++) s[q] += __ldg(rv + (int64_t)k * BF * AMG_NS + BF * q + j) * f[j];
   }
 #pragma unroll
-  for (int q = 0; q < AMG_NS; q++) {
+  for (int q = 0; q < AMG_NS; q++)
     for (int off = 16; off > 0; off >>= 1) s[q] += __shfl_xor_sync(0xffffffffu, s[q], off);
-    if (lane == 0) sh[w][q] = s[q];
-  }
-  __syncthreads();
-  if (threadIdx.x != 0) return;
+}
+
+// coarse row a from its four warps' sums sh[w][q] (one thread)
+template <class T>
+__device__ __forceinline__ void vc_restrict_finish(int a, const T (*sh)[AMG_NS], const T* dinvc, T* rc, T* dc,
+                                                   const T* coefc) {
+  T s[AMG_NS];
 #pragma unroll
   for (int q = 0; q < AMG_NS; q++) s[q] = (sh[0][q] + sh[1][q]) + (sh[2][q] + sh[3][q]);
   const int64_t o = (int64_t)AMG_NS * a;
@@ -999,6 +1010,25 @@ __global__ void __launch_bounds__(128) k_vc_restrict(int nc, const int* __restri
       dc[o + q] = t * inv_theta;
     }
   }
+}
+
+template <class T, int BF>
+__global__ void __launch_bounds__(VC_RESTRICT_THREADS) k_vc_restrict(int nc, const int* __restrict__ rptr,
+                                                                     const int* __restrict__ rcol,
+                                                                     const T* __restrict__ rv, const T* __restrict__ rf,
+                                                                     const T* __restrict__ dinvc, T* __restrict__ rc,
+                                                                     T* __restrict__ dc, const T* __restrict__ coefc,
+                                                                     int nfine) {
+  __shared__ T sh[4][AMG_NS];
+  const int a = blockIdx.x;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  T s[AMG_NS];
+  vc_restrict_part<T, BF>(a, threadIdx.x, s, rptr, rcol, rv, rf, nfine);
+  if (lane == 0)
+#pragma unroll
+    for (int q = 0; q < AMG_NS; q++) sh[w][q] = s[q];
+  __syncthreads();
+  if (threadIdx.x == 0) vc_restrict_finish<T>(a, sh, dinvc, rc, dc, coefc);
 }
 
 // coarsest solve: x = inv b (one block)
@@ -1017,17 +1047,20 @@ __global__ void k_vc_dense(int N, const T* __restrict__ inv, const T* __restrict
 // together); P is tiled, so the lanes of a warp
 // (consecutive rows, consecutive blocks) read each component in one run.
 // Rows of wholly absent nodes have no blocks: their e stays zero.
+// thread t of the prolongation (row t / LPR, lane t % LPR); every lane of
+// the warp calls it (the row sums are reduced across the row's lanes)
 template <class T, int BF, int LPR>
-__global__ void __launch_bounds__(256) k_vc_prolong(int n, const int* __restrict__ pptr, const int* __restrict__ pcol,
-                                                    const T* __restrict__ pv, const T* __restrict__ xc,
-                                                    T* __restrict__ x, T* __restrict__ e, int ncoarse) {
-  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+__device__ __forceinline__ void vc_prolong_thread(int64_t t, int n, const int* pptr, const int* pcol, const T* pv,
+                                                  const T* xc, T* x, T* e, int ncoarse) {
   const int i = (int)(t / LPR);
   const int l = (int)(t % LPR);
   const bool active = i < n;
-  T s[BF];
+  T s[BF], xo[BF];
 #pragma unroll
-  for (int q = 0; q < BF; q++) s[q] = T(0);
+  for (int q = 0; q < BF; q++) s[q] = xo[q] = T(0);
+  if (active && l == 0)  // the row's x, loaded ahead of its products
+#pragma unroll
+    for (int q = 0; q < BF; q++) xo[q] = x[(int64_t)BF * i + q];
   if (active)
     for (int k = pptr[i] + l; k < pptr[i + 1]; k += LPR) {
       const int a = fe_idx(__ldg(pcol + k), ncoarse);
@@ -1046,7 +1079,99 @@ __global__ void __launch_bounds__(256) k_vc_prolong(int n, const int* __restrict
 #pragma unroll
   for (int q = 0; q < BF; q++) {
     e[(int64_t)BF * i + q] = s[q];
-    x[(int64_t)BF * i + q] += s[q];
+    x[(int64_t)BF * i + q] = xo[q] + s[q];
+  }
+}
+
+template <class T, int BF, int LPR>
+__global__ void __launch_bounds__(256) k_vc_prolong(int n, const int* __restrict__ pptr, const int* __restrict__ pcol,
+                                                    const T* __restrict__ pv, const T* __restrict__ xc,
+                                                    T* __restrict__ x, T* __restrict__ e, int ncoarse) {
+  vc_prolong_thread<T, BF, LPR>((int64_t)blockIdx.x * blockDim.x + threadIdx.x, n, pptr, pcol, pv, xc, x, e, ncoarse);
+}
+
+// The bottom of the V-cycle in one block.  Below a few hundred nodes per
+// level the coarse kernels are a few blocks each, and their cost is launch
+// latency, not bytes: levels q0..L-1 (each at most VC_BOTTOM_MAXN nodes,
+// q0 >= 1) run as one launch of one block -- smoothing, restriction, the
+// coarsest solve, prolongation and smoothing again, separated by block
+// barriers.  Each stage runs the same device functions as the per-level
+// kernels, with the same assignment of rows and entries to warps, lanes and
+// 128-thread groups, so the result is identical to theirs.
+constexpr int VC_BOTTOM_THREADS = 1024;
+constexpr int VC_BOTTOM_MAXN = 256;
+
+template <class T>
+struct VcLevelArgs {  // one level of the bottom (device pointers)
+  int n, nc;
+  const int *ptr, *col;            // A_l pattern, tiled values, block-Jacobi inverse, Chebyshev coefficients
+  const T *val, *dinv, *coef;
+  const int *rptr, *rcol;          // P_l^T (l below the coarsest)
+  const T* rv;
+  const int *pptr, *pcol;          // P_l, tiled
+  const T* pv;
+  const T* inv;                    // coarsest: dense inverse
+  T *x, *r, *d0, *d1, *e;          // V-cycle vectors
+};
+template <class T>
+struct VcBottomArgs {
+  int nb;                          // levels q0 .. q0 + nb - 1, the last one the coarsest
+  VcLevelArgs<T> lev[AMG_MAXLEV];
+};
+
+template <class T>
+__global__ void __launch_bounds__(VC_BOTTOM_THREADS) k_vc_bottom(const VcBottomArgs<T> P) {
+  constexpr int NW = VC_BOTTOM_THREADS / 32;
+  constexpr int NG = VC_BOTTOM_THREADS / VC_RESTRICT_THREADS;
+  __shared__ T sh[NG][4][AMG_NS];
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  // one Chebyshev step of a level: rows strided over the warps
+  auto cheb = [&](const VcLevelArgs<T>& L, const T* g, T* dout, T cx, int flags) {
+    for (int row = wid; row < L.n; row += NW)
+      vc_cheb_row<T, AMG_NS>(row, lane, L.n, L.ptr, L.col, L.val, L.dinv, g, L.x, L.r, dout, cx, L.coef, flags);
+    __syncthreads();
+  };
+  const int nb = P.nb;
+  for (int l = 0; l < nb - 1; l++) {  // downward
+    const VcLevelArgs<T>& L = P.lev[l];
+    const VcLevelArgs<T>& C = P.lev[l + 1];
+    cheb(L, L.d0, L.d1, T(1), VC_SETX);
+    cheb(L, L.d1, nullptr, T(1), 0);
+    const bool coarsest = l + 1 == nb - 1;
+    const int grp = tid / VC_RESTRICT_THREADS, t = tid % VC_RESTRICT_THREADS, w = t >> 5;
+    for (int a0 = 0; a0 < C.n; a0 += NG) {  // coarse rows, one per 128-thread group
+      const int a = a0 + grp;
+      if (a < C.n) {
+        T s[AMG_NS];
+        vc_restrict_part<T, AMG_NS>(a, t, s, L.rptr, L.rcol, L.rv, L.r, L.n);
+        if (lane == 0)
+#pragma unroll
+          for (int q = 0; q < AMG_NS; q++) sh[grp][w][q] = s[q];
+      }
+      __syncthreads();
+      if (t == 0 && a < C.n) vc_restrict_finish<T>(a, sh[grp], C.dinv, C.r, coarsest ? nullptr : C.d0, C.coef);
+      __syncthreads();
+    }
+  }
+  {  // coarsest: x = inv r
+    const VcLevelArgs<T>& Lc = P.lev[nb - 1];
+    const int N = Lc.n * AMG_NS;
+    for (int i = tid; i < N; i += VC_BOTTOM_THREADS) {
+      T s = T(0);
+      for (int j = 0; j < N; j++) s += Lc.inv[(int64_t)i * N + j] * Lc.r[j];
+      Lc.x[i] = s;
+    }
+    __syncthreads();
+  }
+  for (int l = nb - 2; l >= 0; l--) {  // upward
+    const VcLevelArgs<T>& L = P.lev[l];
+    const VcLevelArgs<T>& C = P.lev[l + 1];
+    constexpr int LPR = 4;
+    for (int64_t t0 = 0; t0 < (int64_t)L.n * LPR; t0 += VC_BOTTOM_THREADS)
+      vc_prolong_thread<T, AMG_NS, LPR>(t0 + tid, L.n, L.pptr, L.pcol, L.pv, C.x, L.x, L.e, L.nc);
+    __syncthreads();
+    cheb(L, L.e, L.d0, T(0), VC_KEEPX | VC_START);
+    cheb(L, L.d0, L.d1, T(1), VC_FINAL);
   }
 }
 
@@ -1419,8 +1544,14 @@ int vcycle_launches(fe_mesh m, cudaStream_t st, const V* K0, const double* b, do
     *flops += 2.0 * N * N;
     return FE_OK;
   }
+  // the bottom levels q0..L-1 (at most VC_BOTTOM_MAXN nodes each, q0 >= 1)
+  // run in one block when at least one of them is smoothed
+  int q0 = L - 1;
+  while (q0 > 1 && h->lev[q0 - 1].n <= VC_BOTTOM_MAXN) q0--;
+  const bool fused = q0 <= L - 2;
+  const int qf = fused ? q0 : L - 1;  // the per-level kernels run on levels 0..qf-1
   // downward: pre-smoothing, restriction
-  for (int q = 0; q < L - 1; q++) {
+  for (int q = 0; q < qf; q++) {
     AmgLevel& Lq = h->lev[q];
     if (q == 0) {
       k_vc_init0<T><<<blocks_for(Lq.n, 256), 256, 0, st>>>(Lq.n, dinv(0), b, (T*)Lq.r, (T*)Lq.d0, coef(0));
@@ -1443,7 +1574,49 @@ int vcycle_launches(fe_mesh m, cudaStream_t st, const V* K0, const double* b, do
                                                      (T*)Cq.r, coarsest ? nullptr : (T*)Cq.d0, coef(q + 1), Lq.n);
     FE_CUDA(cudaGetLastError());
   }
-  {  // coarsest
+  if (fused) {  // levels q0..L-1 in one block (the bytes and flops of the kernels it replaces)
+    VcBottomArgs<T> a{};
+    a.nb = L - q0;
+    for (int l = 0; l < a.nb; l++) {
+      AmgLevel& Lq = h->lev[q0 + l];
+      VcLevelArgs<T>& A = a.lev[l];
+      A.n = Lq.n;
+      A.nc = Lq.nc;
+      A.ptr = Lq.ptr;
+      A.col = Lq.col;
+      A.val = vals(q0 + l);
+      A.dinv = dinv(q0 + l);
+      A.coef = coef(q0 + l);
+      A.rptr = Lq.rptr;
+      A.rcol = Lq.rcol;
+      A.rv = rv(q0 + l);
+      A.pptr = Lq.pptr;
+      A.pcol = Lq.pcol;
+      A.pv = pv(q0 + l);
+      A.inv = l == a.nb - 1 ? inv(q0 + l) : nullptr;
+      A.x = X(q0 + l);
+      A.r = (T*)Lq.r;
+      A.d0 = (T*)Lq.d0;
+      A.d1 = (T*)Lq.d1;
+      A.e = (T*)Lq.e;
+      if (l < a.nb - 1) {
+        const AmgLevel& Cq = h->lev[q0 + l + 1];
+        const int B = Lq.b;
+        *bytes += 4 * ((double)Lq.nnz * (B * B * sv + 4) + 4.0 * (Lq.n + 1) + (double)Lq.n * B * (sv * 5 + B * sv));
+        *flops += 4 * 2.0 * Lq.nnz * B * B;
+        *bytes += (double)Lq.nnzr * (B * AMG_NS * sv + 4) + (double)Lq.n * B * sv + (double)Cq.n * AMG_NS * sv * 2;
+        *flops += 2.0 * Lq.nnzr * B * AMG_NS;
+        *bytes += (double)Lq.nnzp * (B * AMG_NS * sv + 4) + (double)Lq.n * B * sv * 3;
+        *flops += 2.0 * Lq.nnzp * B * AMG_NS;
+      } else {
+        const int N = Lq.n * Lq.b;
+        *bytes += (double)N * N * sv;
+        *flops += 2.0 * N * N;
+      }
+    }
+    k_vc_bottom<T><<<1, VC_BOTTOM_THREADS, 0, st>>>(a);
+    FE_CUDA(cudaGetLastError());
+  } else {  // coarsest
     AmgLevel& Lc = h->lev[L - 1];
     const int N = Lc.n * Lc.b;
     k_vc_dense<T><<<1, 256, 0, st>>>(N, inv(L - 1), (const T*)Lc.r, X(L - 1));
@@ -1452,7 +1625,7 @@ int vcycle_launches(fe_mesh m, cudaStream_t st, const V* K0, const double* b, do
     *flops += 2.0 * N * N;
   }
   // upward: prolongation, post-smoothing
-  for (int q = L - 2; q >= 0; q--) {
+  for (int q = qf - 1; q >= 0; q--) {
     AmgLevel& Lq = h->lev[q];
     *bytes += (double)Lq.nnzp * (Lq.b * AMG_NS * sv + 4) + (double)Lq.n * Lq.b * sv * 3;
     *flops += 2.0 * Lq.nnzp * Lq.b * AMG_NS;
