@@ -99,8 +99,8 @@ struct AmgLevel {
   double* inv64 = nullptr;
   float* inv32 = nullptr;
   double rho = 0.0;
-  double *vt64 = nullptr, *pt64 = nullptr;  // tiled V-cycle copies of A_l (l >= 1) and P_l
-  float *vt32 = nullptr, *pt32 = nullptr;
+  double* pt64 = nullptr;    // tiled V-cycle copy of P_l
+  float* pt32 = nullptr;
   double* coef64 = nullptr;  // Chebyshev coefficients {1/theta, c1, c2} in device memory, so
   float* coef32 = nullptr;   // a captured V-cycle stays valid when a new tangent changes them
   // V-cycle vectors [n*b] in the V-cycle precision
@@ -864,7 +864,9 @@ __global__ void __launch_bounds__(256) k_vc_cheb0(int n, const int* __restrict__
 }
 
 // Chebyshev step of a coarse level, one block row per warp (coarse rows
-// are few and long), one lane per block, values tiled.  Device function of
+// are few and long), one lane per block; a lane reads its 6x6 block
+// (block-major, from a device allocation, so 16-byte aligned) with 16-byte
+// loads: nine load instructions in FP32 instead of 36.  Device function of
 // warp-uniform `row` (< n): the kernel below runs it for its warp's row, the
 // fused bottom of the V-cycle (k_vc_bottom) for rows strided over its warps;
 // both sum in the same order, so their results are identical.  Vectors are
@@ -893,13 +895,33 @@ __device__ __forceinline__ void vc_cheb_row(int row, int lane, int n, const int*
   for (int q = 0; q < B; q++) s[q] = T(0);
   for (int k = ptr[row] + lane; k < ptr[row + 1]; k += 32) {
     const int c = fe_idx(__ldg(col + k), n);
+    T v[B * B];  // the block, block-major: B * B * sizeof(T) bytes, a multiple of 16
+    if constexpr (sizeof(T) == 4) {
+      const float4* p4 = reinterpret_cast<const float4*>(val + (int64_t)k * B * B);
+#pragma unroll
+      for (int t = 0; t < B * B / 4; t++) {
+        const float4 u = __ldg(p4 + t);
+        v[4 * t] = u.x;
+        v[4 * t + 1] = u.y;
+        v[4 * t + 2] = u.z;
+        v[4 * t + 3] = u.w;
+      }
+    } else {
+      const double2* p2 = reinterpret_cast<const double2*>(val + (int64_t)k * B * B);
+#pragma unroll
+      for (int t = 0; t < B * B / 2; t++) {
+        const double2 u = __ldg(p2 + t);
+        v[2 * t] = u.x;
+        v[2 * t + 1] = u.y;
+      }
+    }
     T gv[B];
 #pragma unroll
     for (int j = 0; j < B; j++) gv[j] = g[(int64_t)B * c + j];
 #pragma unroll
     for (int q = 0; q < B; q++)
 #pragma unroll
-      for (int j = 0; j < B; j++) s[q] += __ldg(val + tix<B * B>(k, B * q + j)) * gv[j];
+      for (int j = 0; j < B; j++) s[q] += v[B * q + j] * gv[j];
   }
 #pragma unroll
   for (int q = 0; q < B; q++)
@@ -1098,7 +1120,8 @@ __global__ void __launch_bounds__(256) k_vc_prolong(int n, const int* __restrict
 // barriers.  Each stage runs the same device functions as the per-level
 // kernels, with the same assignment of rows and entries to warps, lanes and
 // 128-thread groups, so the result is identical to theirs.
-constexpr int VC_BOTTOM_THREADS = 1024;
+template <class T>
+__host__ __device__ constexpr int vc_bottom_threads() { return sizeof(T) == 8 ? 512 : 1024; }
 constexpr int VC_BOTTOM_MAXN = 256;
 
 template <class T>
@@ -1120,9 +1143,10 @@ struct VcBottomArgs {
 };
 
 template <class T>
-__global__ void __launch_bounds__(VC_BOTTOM_THREADS) k_vc_bottom(const VcBottomArgs<T> P) {
-  constexpr int NW = VC_BOTTOM_THREADS / 32;
-  constexpr int NG = VC_BOTTOM_THREADS / VC_RESTRICT_THREADS;
+__global__ void __launch_bounds__(vc_bottom_threads<T>()) k_vc_bottom(const VcBottomArgs<T> P) {
+  constexpr int NT = vc_bottom_threads<T>();
+  constexpr int NW = NT / 32;
+  constexpr int NG = NT / VC_RESTRICT_THREADS;
   __shared__ T sh[NG][4][AMG_NS];
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
   // one Chebyshev step of a level: rows strided over the warps
@@ -1156,7 +1180,7 @@ __global__ void __launch_bounds__(VC_BOTTOM_THREADS) k_vc_bottom(const VcBottomA
   {  // coarsest: x = inv r
     const VcLevelArgs<T>& Lc = P.lev[nb - 1];
     const int N = Lc.n * AMG_NS;
-    for (int i = tid; i < N; i += VC_BOTTOM_THREADS) {
+    for (int i = tid; i < N; i += NT) {
       T s = T(0);
       for (int j = 0; j < N; j++) s += Lc.inv[(int64_t)i * N + j] * Lc.r[j];
       Lc.x[i] = s;
@@ -1167,7 +1191,7 @@ __global__ void __launch_bounds__(VC_BOTTOM_THREADS) k_vc_bottom(const VcBottomA
     const VcLevelArgs<T>& L = P.lev[l];
     const VcLevelArgs<T>& C = P.lev[l + 1];
     constexpr int LPR = 4;
-    for (int64_t t0 = 0; t0 < (int64_t)L.n * LPR; t0 += VC_BOTTOM_THREADS)
+    for (int64_t t0 = 0; t0 < (int64_t)L.n * LPR; t0 += NT)
       vc_prolong_thread<T, AMG_NS, LPR>(t0 + tid, L.n, L.pptr, L.pcol, L.pv, C.x, L.x, L.e, L.nc);
     __syncthreads();
     cheb(L, L.e, L.d0, T(0), VC_KEEPX | VC_START);
@@ -1425,15 +1449,13 @@ int tile_one(fe_mesh m, const T* src, T** dst, int64_t nblocks) {
   return FE_OK;
 }
 
-// tiled V-cycle copies of the coarse operators and the prolongators
+// tiled V-cycle copies of the prolongators
 template <class C>
 int tile_copies(fe_mesh m) {
   AmgHier* h = m->amg;
   for (int q = 0; q < h->nlev; q++) {
     AmgLevel& L = h->lev[q];
-    C** vt = std::is_same<C, double>::value ? (C**)&L.vt64 : (C**)&L.vt32;
     C** pt = std::is_same<C, double>::value ? (C**)&L.pt64 : (C**)&L.pt32;
-    if (q > 0) FE_TRY((tile_one<AMG_NS * AMG_NS, C>(m, Arr<C>::val(L), vt, L.nnz)));
     if (q < h->nlev - 1) {
       if (L.b == 3) FE_TRY((tile_one<3 * AMG_NS, C>(m, Arr<C>::p(L), pt, L.nnzp)));
       else FE_TRY((tile_one<AMG_NS * AMG_NS, C>(m, Arr<C>::p(L), pt, L.nnzp)));
@@ -1511,7 +1533,7 @@ int vcycle_launches(fe_mesh m, cudaStream_t st, const V* K0, const double* b, do
   AmgHier* h = m->amg;
   const int L = h->nlev;
   constexpr bool D = sizeof(T) == 8;
-  auto vals = [&](int q) -> const T* { return D ? (const T*)h->lev[q].vt64 : (const T*)h->lev[q].vt32; };
+  auto vals = [&](int q) -> const T* { return D ? (const T*)h->lev[q].val64 : (const T*)h->lev[q].val32; };
   auto dinv = [&](int q) -> const T* { return D ? (const T*)h->lev[q].dinv64 : (const T*)h->lev[q].dinv32; };
   auto pv = [&](int q) -> const T* { return D ? (const T*)h->lev[q].pt64 : (const T*)h->lev[q].pt32; };
   auto rv = [&](int q) -> const T* { return D ? (const T*)h->lev[q].r64 : (const T*)h->lev[q].r32; };
@@ -1614,7 +1636,7 @@ int vcycle_launches(fe_mesh m, cudaStream_t st, const V* K0, const double* b, do
         *flops += 2.0 * N * N;
       }
     }
-    k_vc_bottom<T><<<1, VC_BOTTOM_THREADS, 0, st>>>(a);
+    k_vc_bottom<T><<<1, vc_bottom_threads<T>(), 0, st>>>(a);
     FE_CUDA(cudaGetLastError());
   } else {  // coarsest
     AmgLevel& Lc = h->lev[L - 1];
