@@ -1870,6 +1870,18 @@ static int launch_arnoldi(fe_mesh m, int j, int kmax, bool fuse_pc, double targe
 // end of every cycle with x += M^{-1} V_j y.
 constexpr int GMRES_BATCH = 8;
 
+// Steps of the next GMRES batch after j steps of a cycle that started at
+// residual beta and now estimates resid: the steps to the target at the
+// cycle's mean rate of decrease so far (at least 1, at most GMRES_BATCH;
+// GMRES_BATCH when there is no decrease yet to go by).
+static int gmres_next_batch(double beta, double resid, double target, int j) {
+  if (j < 1 || !(resid > target) || !(resid < beta) || !(target > 0.0)) return GMRES_BATCH;
+  const double per_step = std::log(resid / beta) / j;  // < 0
+  const double left = std::log(target / resid) / per_step;
+  if (!std::isfinite(left)) return GMRES_BATCH;
+  return (int)std::min<double>(GMRES_BATCH, std::max(1.0, std::ceil(left)));
+}
+
 int fe_gmres_dev(fe_mesh m, const double* b, double* x, double rtol, double atol, int restart, int max_it,
                  int* iters, double* res) {
   if (m->prec < 0) return fe_set_error("no tangent assembled"), FE_ERR_STATE;
@@ -1916,9 +1928,14 @@ int fe_gmres_dev(fe_mesh m, const double* b, double* x, double rtol, double atol
     // the block-Jacobi application is fused into the Arnoldi step (it writes
     // z = D^{-1} V_{j+1} for the next SpMV); the u-p Schur preconditioner
     // (it needs B2 z_u) and the AMG V-cycle run as their own kernels.  Steps are queued in batches
-    // of GMRES_BATCH; the step that meets the stopping test raises a device
-    // flag that turns the rest of its batch into no-ops, so the host reads
-    // the scalars once per batch.
+    // of up to GMRES_BATCH; the step that meets the stopping test raises a
+    // device flag that turns the rest of its batch's Arnoldi steps into
+    // no-ops, so the host reads the scalars once per batch.  The SpMV and the
+    // preconditioner of a step queued past the end still run, so after the
+    // first step a batch holds the steps that the estimate's decrease so far
+    // predicts are left to the target: a batch that falls short costs one
+    // more host synchronisation, one that overshoots a V-cycle and an SpMV
+    // per extra step.
     const bool fuse = !m->pres && m->pc_type == 0;
     FE_CUDA(cudaMemsetAsync(m->scal + 10, 0, 2 * sizeof(double), m->stream));  // out[7], out[8]
     int batch = 1;
@@ -1939,9 +1956,19 @@ int fe_gmres_dev(fe_mesh m, const double* b, double* x, double rtol, double atol
       done = m->h_scal[10] != 0.0;
       j = (int)m->h_scal[11];
       resid = m->h_scal[3];
+      // the batch's Arnoldi launches past the cycle's end did no work: their
+      // algorithmic bytes and flops leave the profile (their time stays)
+      if (m->prof_timing && !m->prof_suspend) {
+        int drop = jend - std::max(j, jprev);
+        for (auto r = m->prof_pending.rbegin(); r != m->prof_pending.rend() && drop > 0; ++r)
+          if (r->cls == FE_PROF_ARNOLDI) {
+            r->bytes = r->flops = 0.0;
+            drop--;
+          }
+      }
       if (!std::isfinite(resid)) done = true;
       if (!done && j <= jprev) return fe_set_error("GMRES made no progress in a batch"), FE_ERR_STATE;
-      batch = std::min(2 * batch, GMRES_BATCH);
+      batch = gmres_next_batch(beta, resid, target, j);
     }
     it += j;
     // FP64 (and loose mixed targets): the residual estimate decides, as in
