@@ -555,12 +555,12 @@ def method_matrix(m, dev, opts_base, ref, methods=("NK", "iNK", "B", "iB"), prec
 
 
 def other_configs(dev, opts_base):
-    """The metric's other configurations, each method timed on its last of
+    """The other workloads of the metric, each method timed on its last of
     `reps` solves (the twist: its only solve, which includes building the
-    AMG structure), outside the timed region: config 1 (Cook P1 8x8x2,
-    FP64, all four methods), config 3 (twist P2-P1 32^3, step 1 of 10, iNK
-    and iB) and config 4 (cardiac shell 4x80x78, time step 1 of 100, all
-    four methods), the last two in the run's precision and preconditioner."""
+    AMG structure), outside the timed region: Cook P1 8x8x2 (FP64, all four
+    methods), the Taylor-Hood twist P2-P1 32^3 (step 1 of 10, iNK and iB)
+    and the cardiac shell 4x80x78 (time step 1 of 100, all four methods),
+    the last two in the run's precision and preconditioner."""
     import torch
     import paper_2203_05610_gb300 as fe
     import workloads as W
@@ -718,7 +718,7 @@ def main():
         if not args.no_matrix and args.workload == "cook":
             base = dict(ksp_restart=args.restart, orthog=args.orthog, pc_type=args.pc)
             matrix = method_matrix(m, dev, base, ref)
-            if args.pc == "amg":  # the benchmark spec's nodal block-Jacobi, for comparison
+            if args.pc == "amg":  # nodal block-Jacobi (the simpler preconditioner), for comparison
                 matrix.update({k + "/block_jacobi": v for k, v in
                                method_matrix(m, dev, dict(base, pc_type="bj"), ref, methods=("iB",),
                                              precisions=("mixed_fp32",)).items()})
