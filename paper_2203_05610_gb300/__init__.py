@@ -374,6 +374,17 @@ class Mesh:
         """Displacement-block preconditioner: "bj" (nodal block-Jacobi) or "amg"."""
         _check(lib().fe_set_pc(self.h, PC_TYPES.get(pc_type, pc_type)))
 
+    def amg_sizes(self):
+        """Block rows (nodes) of each AMG level of the last assembly."""
+        out = []
+        for lv in range(lib().fe_amg_levels(self.h)):
+            info = np.zeros(5, dtype=np.int64)
+            rho = C.c_double()
+            _check(lib().fe_amg_get_level(self.h, lv, _np_ptr(info), C.byref(rho), None, None, None, None, None,
+                                          None, None, None))
+            out.append(int(info[0]))
+        return out
+
     def amg_levels(self):
         """The AMG hierarchy of the last assembly (fe_amg_get_level), one dict per level."""
         out = []

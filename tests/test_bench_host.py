@@ -51,3 +51,14 @@ def test_source_region_hash_ignores_edits_outside(tmp_path):
     assert bench.source_sha(str(f), ["// A", "// B"]) == h
     f.write_text("head\n// A\nkernel body changed\n// B\ntail\n")
     assert bench.source_sha(str(f), ["// A", "// B"]) != h
+
+
+def test_vcycle_kernel_count():
+    # one V-cycle graph: k_vc_init0, 2 steps + restriction per level above the
+    # bottom, the bottom block or the coarsest solve, prolongation + 2 steps
+    # per level above it again
+    assert bench.vcycle_kernels([282897, 3799, 41, 2]) == 14  # levels 2-3 in one block
+    assert bench.vcycle_kernels([9801, 147, 4]) == 8          # levels 1-2 in one block
+    assert bench.vcycle_kernels([243, 13]) == 8               # level 1 is the coarsest: no bottom block
+    assert bench.vcycle_kernels([21609, 323, 7]) == 14        # level 1 too large for the block
+    assert bench.vcycle_kernels([12]) == 2                    # one level: conversion and dense solve
