@@ -39,7 +39,11 @@
 // Chebyshev step is one fused kernel: the SpMV with A_l, the residual update,
 // the block-Jacobi product and the direction and iterate updates of its
 // rows (r stays b - A x throughout, so the residual for the restriction
-// comes for free); level 0 reads the tangent in its tiled layout.
+// comes for free); level 0 reads the tangent in its tiled layout, coarser
+// levels their 6x6 blocks block-major with 16-byte loads.  The levels of at
+// most a few hundred nodes below level 0 run in one block (one launch
+// instead of seven or more latency-bound ones), and the whole V-cycle is
+// captured as one CUDA graph.
 #include <algorithm>
 #include <climits>
 #include <cmath>
