@@ -62,3 +62,18 @@ def test_vcycle_kernel_count():
     assert bench.vcycle_kernels([243, 13]) == 8               # level 1 is the coarsest: no bottom block
     assert bench.vcycle_kernels([21609, 323, 7]) == 14        # level 1 too large for the block
     assert bench.vcycle_kernels([12]) == 2                    # one level: conversion and dense solve
+
+
+def test_serving_sample_requests_snap_to_their_sizes():
+    # the bench line's serving sample: each request of the seeded stream is
+    # built at the structured resolution nearest its (capped) size and solved
+    # by iNK from rest
+    import oracle as O
+    import workloads as W
+    for r in W.serving_stream(nreq=32):
+        w, meth, load, tm, name = bench.serving_workload(r, 4e3)
+        target = min(r["dofs"], 4e3)
+        ndof = O.Mesh(w).ndof
+        assert meth == "iNK" and name.split("_")[0] in ("cook", "twist", "heart")
+        assert 0.7 * target <= ndof <= 1.3 * target, (name, ndof, target)
+        assert (load, tm) == tuple(w["steps"][0])
