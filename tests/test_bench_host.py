@@ -4,6 +4,7 @@ source-region hash that keeps `roofline.traffic` tied to the captured
 kernels."""
 import json
 import os
+import sys
 
 import pytest
 
@@ -77,3 +78,24 @@ def test_serving_sample_requests_snap_to_their_sizes():
         assert meth == "iNK" and name.split("_")[0] in ("cook", "twist", "heart")
         assert 0.7 * target <= ndof <= 1.3 * target, (name, ndof, target)
         assert (load, tm) == tuple(w["steps"][0])
+
+
+def test_reference_arm_line(monkeypatch, capsys):
+    # the reference arm on a small Cook P2 mesh with a stand-in solve record:
+    # ms_per_step is the measured wall time of one sample, value the solve
+    # rate scaled with the record's iteration structure
+    rec = dict(workload="cook_p2_4x4x2", method="iB", ksp_restart=50, pc="amg", status=0, nit=6,
+               assemblies=1, lit_total=60, wall_s=1.0, host=dict(machine="test"))
+    monkeypatch.setattr(bench, "oracle_work", lambda *a: rec)
+    monkeypatch.setattr(sys, "argv", ["bench.py"])
+    args = bench.parse()
+    args.impl, args.mesh, args.steps, args.warmup = "reference", "4,4,2", 2, 0
+    bench.run_reference(args)
+    out = json.loads(capsys.readouterr().out.strip().splitlines()[-1])
+    assert out["impl"] == "reference" and out["unit"] == "solves/s" and out["steps"] == 2
+    assert out["value"] > 0 and out["cpu_baseline"]["value"] == out["value"]
+    assert out["e2e"] == dict(value=out["value"], unit="solves/s", h2d_bytes_per_step=0, d2h_bytes_per_step=0)
+    # a sample is one residual and REF_KRYLOV_ITS Krylov iterations; the scaled
+    # solve adds the setup, nit + 1 residuals and lit_total iterations
+    assert 1.0 / out["value"] > out["ms_per_step"] / 1e3 > 0
+    assert abs(1.0 / out["value"] - out["scaled_solve_s"]) <= 0.05 + 1e-6  # scaled_solve_s is rounded to 0.1 s
