@@ -1,7 +1,8 @@
 """Host logic of bench.py that its JSON line depends on, without a GPU: the
-oracle solve-time model behind `cpu_baseline` and the reference arm, and the
-source-region hash that keeps `roofline.traffic` tied to the captured
-kernels."""
+oracle solve-time model behind `cpu_baseline` and the reference arm (and the
+reference arm's line itself), the source-region hash that keeps
+`roofline.traffic` tied to the captured kernels, the kernel count of a
+V-cycle graph behind `gpu_launches`, and the serving sample's requests."""
 import json
 import os
 import sys
