@@ -107,6 +107,21 @@ def workload(args):
     return w, f"cook_p2_{nx}x{ny}x{nz}"
 
 
+PC_NAMES = {"bj": "nodal block-Jacobi", "amg": "AMG V-cycle", "amg_bf16": "AMG V-cycle, BF16 fine-level smoother"}
+ORTHOG_NAMES = ["mgs", "mgs_lowsync", "mgs_blocked"]
+
+
+def line_config(args, w, name, dofs, blocks, methods, world):
+    """`config` of both arms' lines: the workload and the solve it asks for
+    (how an arm computes it -- precision, orthogonalisation -- is its
+    `solver`)."""
+    return dict(workload=name, dofs=int(dofs), blocks=int(blocks), nu=args.nu, traction=args.traction,
+                load_step=f"step 1 of {len(w['steps'])} from rest", methods=list(methods), tol=TOL,
+                ksp_restart=args.restart, preconditioner=PC_NAMES[args.pc],
+                ib_h0_tolerance="adaptive (extension)" if args.ib_adaptive else "fixed",
+                l2="working set > L2 (tangent and Krylov basis), no flush", parallelism=f"replicas x{world}")
+
+
 def world_reduce(x, dist=None, device="cpu", op="max"):
     """x reduced over the ranks of the job (max or sum); x itself without a
     process group.  The timed region's duration is the max over ranks and
@@ -378,11 +393,9 @@ def run_reference(args):
                      f"(value scales it to a full solve)"),
                scaled_solve_s=round(t_model / args.steps, 1),
                higher_is_better=True, scaling="weak", vs_baseline=None, dtype="f64", data="synthetic",
-               config=dict(workload=name, nu=args.nu, traction=args.traction,
-                           load_step=f"step 1 of {len(w['steps'])} from rest", methods=[method],
-                           preconditioner={"bj": "nodal block-Jacobi", "amg": "AMG V-cycle",
-                                               "amg_bf16": "AMG V-cycle, BF16 fine-level smoother"}[args.pc],
-                           ksp_restart=args.restart, tol=TOL),
+               config=line_config(args, w, name, m.ndof, m.nnzb, [method], world),
+               solver=dict(precision="fp64", orthog="mgs",
+                           preconditioner=f"{oracle_pc(args.pc).upper()} (FP64 throughout)"),
                cpu_baseline=dict(kind="oracle", cores=1, value=round(value, 6), unit="solves/s", sample=sample,
                                  scaled_solve_s=round(t_model / args.steps, 1),
                                  measured_full_solve=dict(wall_s=rec["wall_s"], host=rec.get("host"))),
@@ -811,15 +824,8 @@ def main():
                    dtype="f64" if args.precision == "fp64" else ("f32+f64" if args.precision == "mixed_fp32"
                                                                  else "bf16+f32+f64"),
                    data="synthetic",
-                   config=dict(workload=name, dofs=m.ndof, blocks=m.nnzb, nu=args.nu, traction=args.traction,
-                               load_step=f"step 1 of {len(w['steps'])} from rest", methods=methods,
-                               precision=args.precision, tol=TOL, ksp_restart=args.restart,
-                               orthog=["mgs", "mgs_lowsync", "mgs_blocked"][args.orthog],
-                               preconditioner={"bj": "nodal block-Jacobi", "amg": "AMG V-cycle",
-                                               "amg_bf16": "AMG V-cycle, BF16 fine-level smoother"}[args.pc],
-                               ib_h0_tolerance="adaptive (extension)" if args.ib_adaptive else "fixed",
-                               l2="working set > L2 (tangent and Krylov basis), no flush",
-                               parallelism=f"replicas x{world}"),
+                   config=line_config(args, w, name, m.ndof, m.nnzb, methods, world),
+                   solver=dict(precision=args.precision, orthog=ORTHOG_NAMES[args.orthog]),
                    methods=per_method, roofline=roof,
                    roofline_spmv=hbm_line("spmv") if "spmv" in timed else None,
                    roofline_arnoldi=alu_line("arnoldi") if "arnoldi" in timed else None,

@@ -98,5 +98,10 @@ def test_reference_arm_line(monkeypatch, capsys):
     assert out["e2e"] == dict(value=out["value"], unit="solves/s", h2d_bytes_per_step=0, d2h_bytes_per_step=0)
     # a sample is one residual and REF_KRYLOV_ITS Krylov iterations; the scaled
     # solve adds the setup, nit + 1 residuals and lit_total iterations
+    # the same `config` as the GPU arm's line for these arguments
+    w, name = bench.workload(args)
+    assert out["config"] == bench.line_config(args, w, name, out["config"]["dofs"], out["config"]["blocks"],
+                                              ["iB"], 1)
+    assert name == "cook_p2_4x4x2" and out["config"]["dofs"] == 3 * 9 * 9 * 5 and out["solver"]["precision"] == "fp64"
     assert 1.0 / out["value"] > out["ms_per_step"] / 1e3 > 0
     assert abs(1.0 / out["value"] - out["scaled_solve_s"]) <= 0.05 + 1e-6  # scaled_solve_s is rounded to 0.1 s
